@@ -1,0 +1,362 @@
+"""CPU oracle for the vibronic-continuum linear systems (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl
+reference`` legs of ``bench.py`` may import this module.  The CUDA path never calls it
+and shares no code with it.
+
+Everything here is the plain definition, in complex128 with NumPy/SciPy:
+
+* per-mode truncated oscillator matrices (Sec. III, ladder action of q_g and q_u;
+  Eq. H0harm for E_nu),
+* the level-shift factor F[f](eps) (Eq. IntF with the widths of Sec. II.B), written in
+  closed form through Dawson's function and the scaled complementary error function,
+* the matrix A = E - H_ef = E - H_0 - U - F in the product basis (Eqs. H_ef, Amatrix),
+  assembled as Kronecker products (state index slowest, last mode fastest),
+* the right-hand side Phi (Sec. II.D), the solve (Eq. Ax=b) by direct LU,
+* T-matrix and cross section (Eqs. Td, crs, crs2), the 2D EELS sum (Eq. 2Dsp),
+* the gradient of a cross-section loss by a dense-LU adjoint.
+
+Readings of the paper taken here (the CUDA path takes the same ones):
+
+* powers q^k are products of the truncated matrices (PqP)^k, the "successive
+  multiplications" of Sec. III;
+* f_d^mu(eps) = sqrt(Gamma_d^mu(eps) / 2 pi) is real and non-negative, and zero for
+  eps <= 0 (closed channel);
+* energies in eV; sigma is reported raw as 2 pi^3 |T|^2 / eps_i with eps_i in eV;
+* the EELS resolution function is a unit-area Gaussian of FWHM 10 meV.
+
+Parity status: every function here is pinned by tests under ``tests/`` against
+closed forms, quadrature, invariants or brute force (see the test module docstrings).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+import scipy.special as sps
+
+EELS_FWHM = 0.010  # eV, resolution of the spectrometer (Eq. 2Dsp)
+
+
+# ----------------------------------------------------------------------------------------
+# One-mode pieces (Sec. III; Eq. H0harm)
+# ----------------------------------------------------------------------------------------
+def q_matrix(n: int) -> np.ndarray:
+    """Truncated coordinate operator: <k|q|k+1> = <k+1|q|k> = sqrt((k+1)/2) (Sec. III)."""
+    q = np.zeros((n, n))
+    k = np.arange(n - 1)
+    q[k, k + 1] = np.sqrt((k + 1) / 2.0)
+    q[k + 1, k] = q[k, k + 1]
+    return q
+
+
+def q_power(n: int, k: int) -> np.ndarray:
+    """(PqP)^k: the k-th power of the truncated q matrix."""
+    return np.linalg.matrix_power(q_matrix(n), k)
+
+
+def mode_energies(omega: float, n: int) -> np.ndarray:
+    """Harmonic levels omega (k + 1/2), k = 0..n-1 (Eq. H0harm)."""
+    return omega * (np.arange(n) + 0.5)
+
+
+def level_energies(model: dict) -> np.ndarray:
+    """E_nu = sum_m omega_m (n_m + 1/2) over the product basis, last mode fastest."""
+    e = np.zeros(1)
+    for m in model["modes"]:
+        e = (e[:, None] + mode_energies(m["omega"], m["n"])[None, :]).ravel()
+    return e
+
+
+def basis_shape(model: dict):
+    return tuple(m["n"] for m in model["modes"])
+
+
+def flat_index(model: dict, nu) -> int:
+    """Position of the multi-index nu in the product basis (last mode fastest)."""
+    return int(np.ravel_multi_index(tuple(nu), basis_shape(model)))
+
+
+# ----------------------------------------------------------------------------------------
+# Level shift (Eq. IntF, widths of Sec. II.B)
+# ----------------------------------------------------------------------------------------
+def width(eps, a: float, b: float, l: int):
+    """Gamma(eps) = a eps^(l+1/2) exp(-b eps) for eps > 0, zero otherwise (Sec. II.B)."""
+    eps = np.asarray(eps, dtype=np.float64)
+    out = np.zeros_like(eps)
+    pos = eps > 0
+    out[pos] = a * eps[pos] ** (l + 0.5) * np.exp(-b * eps[pos])
+    return out
+
+
+def coupling_amplitude(eps, a: float, b: float, l: int):
+    """f(eps) = sqrt(Gamma(eps)/(2 pi)), real, non-negative (Sec. II.C)."""
+    return np.sqrt(width(eps, a, b, l) / (2.0 * np.pi))
+
+
+def level_shift(eps, a: float, b: float, l: int):
+    """F[Gamma/2pi](eps) = PV int f(x)/(eps-x) dx - i pi f(eps), f = Gamma/(2 pi) (Eq. IntF).
+
+    With P_l(eps) = PV int_0^inf x^(l+1/2) e^(-bx) / (eps - x) dx the closed form is
+      P_l = -Gamma(l+1/2) b^-(l+1/2) + eps P_(l-1),
+      eps P_(-1) = 2 sqrt(pi eps) D(sqrt(b eps))          for eps > 0,
+                 = pi sqrt(|eps|) erfcx(sqrt(b |eps|))     for eps < 0,
+                 = 0                                       for eps = 0,
+    where D is Dawson's function.  (Substituting x = t^2 turns P_(-1) into the Hilbert
+    transform of a Gaussian for eps > 0 and into a Lorentzian-Gaussian integral for
+    eps < 0.)  The imaginary part is -pi f(eps), so Gamma = -2 Im F (Sec. II.B).
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    ae = np.abs(eps)
+    eps_pm1 = np.where(
+        eps > 0,
+        2.0 * np.sqrt(np.pi * ae) * sps.dawsn(np.sqrt(b * ae)),
+        np.pi * np.sqrt(ae) * sps.erfcx(np.sqrt(b * ae)),
+    )
+    eps_pm1 = np.where(eps == 0, 0.0, eps_pm1)
+    p = -math.gamma(0.5) / math.sqrt(b) + eps_pm1  # P_0
+    for k in range(1, l + 1):
+        p = -math.gamma(k + 0.5) / b ** (k + 0.5) + eps * p
+    re = a / (2.0 * np.pi) * p
+    im = -np.pi * width(eps, a, b, l) / (2.0 * np.pi)
+    return re + 1j * im
+
+
+# ----------------------------------------------------------------------------------------
+# The matrix A = E - H_ef (Eqs. H_ef, U, Amatrix)
+# ----------------------------------------------------------------------------------------
+def _kron_all(mats):
+    out = sp.csr_matrix(np.ones((1, 1)))
+    for m in mats:
+        out = sp.kron(out, sp.csr_matrix(m), format="csr")
+    return out
+
+
+def term_matrix(model: dict, pows) -> sp.csr_matrix:
+    """prod_m q_m^(pow_m) on the vibrational product basis (Kronecker product)."""
+    return _kron_all([q_power(m["n"], int(k)) for m, k in zip(model["modes"], pows)])
+
+
+def coupling_matrix(model: dict) -> sp.csr_matrix:
+    """U (Eq. H_d / Eq. U) as a real symmetric sparse matrix over (d, nu)."""
+    ns = model["n_states"]
+    nv = int(np.prod(basis_shape(model)))
+    blocks = [[sp.csr_matrix((nv, nv)) for _ in range(ns)] for _ in range(ns)]
+    for t in model["terms"]:
+        m = t["coef"] * term_matrix(model, t["pow"])
+        blocks[t["d"]][t["dp"]] = blocks[t["d"]][t["dp"]] + m
+        if t["d"] != t["dp"]:
+            blocks[t["dp"]][t["d"]] = blocks[t["dp"]][t["d"]] + m
+    return sp.bmat(blocks, format="csr")
+
+
+def check_channels(model: dict):
+    mus = [c["mu"] for c in model["channels"]]
+    if len(set(mus)) != len(mus):
+        raise ValueError("each partial wave must couple to a single discrete state")
+
+
+def continuum_diagonal(model: dict, E: float) -> np.ndarray:
+    """Diagonal of F(E - H_0): sum over the channels of state d of F[Gamma/2pi](E - E_nu)."""
+    check_channels(model)
+    ns = model["n_states"]
+    en = level_energies(model)
+    out = np.zeros((ns, en.size), dtype=np.complex128)
+    for c in model["channels"]:
+        out[c["d"]] += level_shift(E - en, c["a"], c["b"], c["l"])
+    return out.ravel()
+
+
+def a_matrix(model: dict, E: float) -> sp.csr_matrix:
+    """A = E - H_0 - U - F(E - H_0) over alpha = (d, nu) (Eq. Amatrix), complex128."""
+    ns = model["n_states"]
+    en = np.tile(level_energies(model), ns)
+    diag = E - en - continuum_diagonal(model, E)
+    return (sp.diags(diag) - coupling_matrix(model)).tocsr().astype(np.complex128)
+
+
+# ----------------------------------------------------------------------------------------
+# Right-hand sides, solve, observables (Eqs. Ax=b, Td, crs, crs2, 2Dsp)
+# ----------------------------------------------------------------------------------------
+def n_partial_waves(model: dict) -> int:
+    return max(c["mu"] for c in model["channels"]) + 1
+
+
+def phi(model: dict, E: float, v, mu: int) -> np.ndarray:
+    """Phi^{v mu}_{d,nu} = <nu| V^mu_{d eps} |v> with eps = E - E_v (Sec. II.D).
+
+    With q-independent couplings this is f_d^mu(E - E_v) on the single entry (d, v)."""
+    ns = model["n_states"]
+    nv = int(np.prod(basis_shape(model)))
+    out = np.zeros(ns * nv)
+    ev = float(level_energies(model)[flat_index(model, v)])
+    for c in model["channels"]:
+        if c["mu"] == mu:
+            out[c["d"] * nv + flat_index(model, v)] += coupling_amplitude(E - ev, c["a"], c["b"], c["l"])
+    return out
+
+
+def total_energy(model: dict, eps_i: float, vi) -> float:
+    """E = eps_i + E_vi (Eq. Econserv)."""
+    return float(eps_i + level_energies(model)[flat_index(model, vi)])
+
+
+def solve(model: dict, E: float, rhs: np.ndarray, dense_limit: int = 6000) -> np.ndarray:
+    """psi = A^-1 rhs by direct LU (dense up to ``dense_limit`` unknowns, else sparse)."""
+    A = a_matrix(model, E)
+    if A.shape[0] <= dense_limit:
+        return sla.lu_solve(sla.lu_factor(A.toarray()), rhs.astype(np.complex128))
+    return spla.splu(A.tocsc()).solve(rhs.astype(np.complex128))
+
+
+def solve_many(model: dict, E: float, rhss, dense_limit: int = 6000):
+    """One LU factorisation, several right-hand sides (columns of the result)."""
+    A = a_matrix(model, E)
+    R = np.stack([np.asarray(r, dtype=np.complex128) for r in rhss], axis=1)
+    if A.shape[0] <= dense_limit:
+        return sla.lu_solve(sla.lu_factor(A.toarray()), R)
+    return spla.splu(A.tocsc()).solve(R)
+
+
+def relative_residual(model: dict, E: float, psi: np.ndarray, rhs: np.ndarray) -> float:
+    """||rhs - A psi|| / ||rhs|| in complex128 (the stopping quantity of Sec. III)."""
+    A = a_matrix(model, E)
+    return float(np.linalg.norm(rhs - A @ psi) / np.linalg.norm(rhs))
+
+
+def t_amplitude(model: dict, E: float, vf, mu_f: int, psi: np.ndarray) -> complex:
+    """T_{mu_f v_f <- mu_i v_i} = <Phi^{v_f mu_f} | Psi> with real Phi (Eq. crs2)."""
+    return complex(phi(model, E, vf, mu_f) @ psi)
+
+
+def cross_section(eps_i: float, t_values) -> float:
+    """sigma = 2 pi^3 / eps_i * sum |T|^2 over the listed (mu_i, mu_f) amplitudes (Eq. crs)."""
+    t = np.asarray(t_values)
+    return float(2.0 * np.pi ** 3 / eps_i * np.sum(np.abs(t) ** 2))
+
+
+def cross_sections(model: dict, eps, vi_list, vf_list, dense_limit: int = 6000):
+    """sigma[e, i, f] for incident energies eps, initial states vi_list, final vf_list.
+
+    Sums over mu_i and mu_f (Eq. crs).  Also returns psi[e][i][mu_i] (flat vectors)."""
+    nmu = n_partial_waves(model)
+    sig = np.zeros((len(eps), len(vi_list), len(vf_list)))
+    psis = []
+    for e, ei in enumerate(eps):
+        row = []
+        for i, vi in enumerate(vi_list):
+            E = total_energy(model, ei, vi)
+            rhs = [phi(model, E, vi, mu) for mu in range(nmu)]
+            ps = solve_many(model, E, rhs, dense_limit)
+            row.append([ps[:, k] for k in range(nmu)])
+            for f, vf in enumerate(vf_list):
+                ts = [t_amplitude(model, E, vf, muf, ps[:, mi]) for mi in range(nmu) for muf in range(nmu)]
+                sig[e, i, f] = cross_section(ei, ts)
+        psis.append(row)
+    return sig, psis
+
+
+def open_levels(model: dict, E: float):
+    """Multi-indices nu with E_nu < E (open final channels, eps_f > 0)."""
+    en = level_energies(model)
+    idx = np.nonzero(en < E)[0]
+    return [list(np.unravel_index(int(k), basis_shape(model))) for k in idx]
+
+
+def eels(model: dict, eps, vi, vf_list, sigma_ef: np.ndarray, de_grid, fwhm: float = EELS_FWHM):
+    """S(eps_i, d_eps) = sum_f sigma_f(eps_i) rho(d_eps - (E_vf - E_vi)) (Eq. 2Dsp).
+
+    rho is a unit-area Gaussian with the given FWHM.  sigma_ef[e, f]."""
+    en = level_energies(model)
+    e_vi = en[flat_index(model, vi)]
+    shifts = np.array([en[flat_index(model, vf)] - e_vi for vf in vf_list])
+    s = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    de = np.asarray(de_grid, dtype=np.float64)
+    rho = np.exp(-0.5 * ((de[None, :] - shifts[:, None]) / s) ** 2) / (s * math.sqrt(2.0 * math.pi))
+    return np.asarray(sigma_ef) @ rho
+
+
+# ----------------------------------------------------------------------------------------
+# Gradient of L = sum (sigma - target)^2 by the dense-LU adjoint
+# ----------------------------------------------------------------------------------------
+def with_parameter(model: dict, theta: int, value: float) -> dict:
+    """Copy of the model with parameter theta replaced.
+
+    theta < n_terms: coefficient of term theta; else channel c = (theta - n_terms) // 2,
+    its ``a`` (even) or ``b`` (odd)."""
+    import copy
+
+    m = copy.deepcopy(model)
+    nt = len(m["terms"])
+    if theta < nt:
+        m["terms"][theta]["coef"] = value
+    else:
+        c, which = divmod(theta - nt, 2)
+        m["channels"][c]["ab"[which]] = value
+    return m
+
+
+def get_parameter(model: dict, theta: int) -> float:
+    nt = len(model["terms"])
+    if theta < nt:
+        return float(model["terms"][theta]["coef"])
+    c, which = divmod(theta - nt, 2)
+    return float(model["channels"][c]["ab"[which]])
+
+
+def loss(model: dict, eps, vi, vf_list, target) -> float:
+    sig, _ = cross_sections(model, eps, [vi], vf_list)
+    return float(np.sum((sig[:, 0, :] - target) ** 2))
+
+
+def loss_gradient_fd(model: dict, eps, vi, vf_list, target, thetas, h: float = 1e-6):
+    """Central finite differences of the loss with step h."""
+    g = np.zeros(len(thetas))
+    for k, th in enumerate(thetas):
+        p0 = get_parameter(model, th)
+        lp = loss(with_parameter(model, th, p0 + h), eps, vi, vf_list, target)
+        lm = loss(with_parameter(model, th, p0 - h), eps, vi, vf_list, target)
+        g[k] = (lp - lm) / (2.0 * h)
+    return g
+
+
+def loss_gradient_adjoint(model: dict, eps, vi, vf_list, target, thetas):
+    """dL/dtheta by the adjoint of A psi = Phi with dense LU.
+
+    T = Phi_f^T A^-1 Phi_i, so dT = dPhi_f^T psi + lambda_f^T dPhi_i - lambda_f^T dA psi
+    with lambda_f = A^-T Phi_f = A^-1 Phi_f (A is complex symmetric).  dA/dtheta is
+    obtained here by central differences of the assembled matrix in the parameter
+    (A is linear in the term coefficients and in a, so the difference is exact for
+    those up to rounding)."""
+    nmu = n_partial_waves(model)
+    grads = np.zeros(len(thetas))
+    sig, _ = cross_sections(model, eps, [vi], vf_list)
+    for e, ei in enumerate(eps):
+        E = total_energy(model, ei, vi)
+        A = a_matrix(model, E).toarray()
+        lu = sla.lu_factor(A)
+        phis_i = [phi(model, E, vi, mu) for mu in range(nmu)]
+        psis = [sla.lu_solve(lu, p.astype(complex)) for p in phis_i]
+        phis_f = [[phi(model, E, vf, mu) for mu in range(nmu)] for vf in vf_list]
+        lams = [[sla.lu_solve(lu, p.astype(complex)) for p in row] for row in phis_f]
+        for k, th in enumerate(thetas):
+            p0 = get_parameter(model, th)
+            hh = 1e-5 * max(1.0, abs(p0))
+            mp, mm = with_parameter(model, th, p0 + hh), with_parameter(model, th, p0 - hh)
+            dA = (a_matrix(mp, E).toarray() - a_matrix(mm, E).toarray()) / (2 * hh)
+            dphi_i = [(phi(mp, E, vi, mu) - phi(mm, E, vi, mu)) / (2 * hh) for mu in range(nmu)]
+            dphi_f = [[(phi(mp, E, vf, mu) - phi(mm, E, vf, mu)) / (2 * hh) for mu in range(nmu)] for vf in vf_list]
+            tot = 0.0
+            for f in range(len(vf_list)):
+                w = 2.0 * (sig[e, 0, f] - target[e, f]) * 2.0 * np.pi ** 3 / ei
+                for mi in range(nmu):
+                    for mf in range(nmu):
+                        T = phis_f[f][mf] @ psis[mi]
+                        dT = dphi_f[f][mf] @ psis[mi] + lams[f][mf] @ dphi_i[mi] - lams[f][mf] @ (dA @ psis[mi])
+                        tot += w * 2.0 * np.real(np.conj(T) * dT)
+            grads[k] += tot
+    return grads
