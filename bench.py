@@ -1,0 +1,352 @@
+"""Benchmark: batched solves of (E - H_ef) psi = Phi over many energies on one GB300.
+
+Workload (default): the 2-state, 2-mode conical-intersection model with 80 x 80 oscillator
+functions (N = 12,800 unknowns), 256 incident energies on (0, 3] eV, v_i = 0, both partial
+waves (512 systems), true relative residual 1e-8, complex-FP32 Krylov iterations inside FP64
+iterative refinement.  One step = one vbk_solve call over the whole batch (level-shift
+tables, preconditioner factorisation, Krylov iterations, refinement).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (sparse LU per
+energy, complex128) on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "energy points solved/s at rel. residual 1e-8, mixed vs FP64; matvec HBM GB/s"
+UNIT = "energy points/s"
+
+
+def load_json(name):
+    p = os.path.join(ROOT, name)
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh)
+    return None
+
+
+def workload():
+    import workloads as w
+
+    spec = w.WORKLOADS["ci2d_batched"]
+    return spec["model"](), spec["eps"], spec["vi"]
+
+
+WORKLOAD_NAME = ("ci2d_batched: 2 states x 80 x 80 oscillator functions (N=12800), 256 incident energies "
+                 "on (0,3] eV, v_i=(0,0), 2 partial waves = 512 systems, tol 1e-8")
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        idx = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", idx, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx = float(s[1])
+                for k, nm in enumerate(names):
+                    if s[4 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------- roofline model
+def kernel_bytes_per_unit(name, N, nmu, c, p_band):
+    """Algorithmic bytes one kernel moves per system-iteration (kernel table)."""
+    if name == "matvec":
+        return (2 * c + c / nmu) * N          # read x, write y, diagonal shared by the n_mu waves
+    if name == "cocg_update":
+        return 6 * c * N                      # x, r read+write; p, q read
+    if name == "cocg_update_jacobi":
+        return (7 * c + c / nmu) * N
+    if name == "cocg_p":
+        return 3 * c * N                      # z read, p read+write
+    if name == "block_apply":
+        return (2 * c + (p_band + 1) * c / nmu) * N  # r in, z out, L D L^T factor shared by the waves
+    if name == "point_precond":
+        return (2 * c + c / nmu) * N
+    return None
+
+
+def roofline(model_N, nmu, stats, timings, opts, peaks):
+    c = 8 if opts.precision == 1 else 16
+    units = sum(s["iterations"] for s in stats)
+    # dominant kernel by total time
+    name, (launches, ms) = max(timings.items(), key=lambda kv: kv[1][1])
+    p_band = 4 if opts.precond_span == 0x5 else 0
+    bname = name
+    if name == "cocg_update" and opts.precond_span == 0:
+        bname = "cocg_update_jacobi"
+    bpu = kernel_bytes_per_unit(bname, model_N, nmu, c, p_band)
+    peak = (peaks or {}).get("hbm_gbs")
+    peak_note = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    if bpu is None or launches == 0:
+        return {"kernel": name, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "traffic": None, "peak_source": peak_note}
+    total_bytes = bpu * units
+    achieved = total_bytes / (ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_note,
+            "bytes_per_launch": round(total_bytes / launches), "launches": launches,
+            "avg_launch_us": round(ms * 1e3 / launches, 2), "share_of_step": None}
+
+
+# ------------------------------------------------------------------------------ oracle
+def oracle_rate(desc, eps, vi, n_sample):
+    """Oracle energies/s on a bounded, evenly spaced sample of the energy grid."""
+    from oracle import vibronic as o
+
+    idx = np.linspace(0, eps.size - 1, n_sample).round().astype(int)
+    t0 = time.perf_counter()
+    for k in idx:
+        E = o.total_energy(desc, float(eps[k]), vi[0])
+        o.solve_many(desc, E, [o.phi(desc, E, vi[0], mu) for mu in range(o.n_partial_waves(desc))])
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    desc, eps, vi = workload()
+    per_step = 16
+    for _ in range(args.warmup):
+        oracle_rate(desc, eps, vi, per_step)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_rate(desc, eps, vi, per_step)
+        times.append(dt)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "complex128", "data": "synthetic (seeded model)",
+        "config": {"workload": WORKLOAD_NAME, "solver": "sparse LU (SuperLU) per energy, 2 right-hand sides"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} evenly spaced energies of the 256-point grid per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- ours
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method", default="cocg", choices=["cocg", "gmres"])
+    ap.add_argument("--precond", type=int, default=0x5, help="span mask (0x5 = M^g, 0 = Jacobi, -1 = none)")
+    ap.add_argument("--restart", type=int, default=64)
+    ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparisons and the CPU baseline")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2307_13483_gb300 as vbk
+    from oracle import vibronic as o
+
+    desc, eps, vi = workload()
+    model = vbk.Model(desc)
+    N, nmu = model.N, model.n_mu
+    opts = vbk.vbk_default_opts(method=args.method, precision="mixed", precond_span=args.precond, tol=1e-8,
+                                restart=args.restart, inner_tol=args.inner_tol, max_refine=100)
+    psi = torch.empty((eps.size, len(vi), nmu, N), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        psi, stats = vbk.vbk_solve(model, eps, vi, opts, psi=psi)
+    # timed steps (device time of each solve; L2 flushed between steps outside the events)
+    timing_opts = vbk.vbk_default_opts(method=args.method, precision="mixed", precond_span=args.precond, tol=1e-8,
+                                       restart=args.restart, inner_tol=args.inner_tol, max_refine=100, timing=1)
+    sampler = ClockSampler()
+    sampler.start()
+    barrier()
+    stream = torch.cuda.current_stream()
+    step_ms = []
+    launches = 0
+    timings = {}
+    all_stats = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        psi, stats = vbk.vbk_solve(model, eps, vi, timing_opts, psi=psi)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        launches += vbk.vbk_last_launch_count(model)
+        for nm, (nl, ms) in vbk.vbk_kernel_timings(model).items():
+            t = timings.setdefault(nm, [0, 0.0])
+            t[0] += nl
+            t[1] += ms
+        all_stats.extend(stats)
+    barrier()
+    clocks = sampler.stop()
+    t_step = max(step_ms) if False else sum(step_ms) / len(step_ms)
+    if dist is not None:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    n_energies = eps.size * len(vi)
+    value = world * n_energies / (t_step * 1e-3)
+    converged = all(s["status"] == "converged" for s in all_stats)
+    worst = max(s["rel_residual"] for s in all_stats)
+    iters = [s["iterations"] for s in stats]
+    peaks = load_json("MEASURED_PEAKS.json")
+    roof = roofline(N, nmu, all_stats, {k: tuple(v) for k, v in timings.items()}, opts, peaks)
+    total_kernel_ms = sum(v[1] for v in timings.values())
+    if roof.get("kernel") in timings and total_kernel_ms > 0:
+        roof["share_of_step"] = round(timings[roof["kernel"]][1] / (t_step * args.steps), 4)
+    # matvec HBM GB/s (part of the metric)
+    mv = timings.get("matvec")
+    matvec_gbs = None
+    if mv and mv[1] > 0:
+        units = sum(s["iterations"] for s in all_stats)
+        matvec_gbs = round(kernel_bytes_per_unit("matvec", N, nmu, 8, 0) * units / (mv[1] * 1e-3) / 1e9, 1)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # end to end through the public API: host energies in, cross sections back to the host
+        vf = o.open_levels(desc, o.total_energy(desc, float(eps[-1]), vi[0]))
+        vf_h = np.asarray(vf, dtype=np.int32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            psi, _ = vbk.vbk_solve(model, eps, vi, opts, psi=psi)
+            sig = vbk.vbk_cross_sections(model, eps, vi, psi, vf_h)
+            sig_h = sig.cpu()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        extras["e2e"] = {"value": n_energies / e2e_s, "unit": UNIT,
+                         "h2d_bytes_per_step": int(eps.nbytes + np.asarray(vi, np.int32).nbytes + vf_h.nbytes),
+                         "d2h_bytes_per_step": int(sig_h.numel() * 8)}
+        # FP64 batched (same workload, every Krylov iteration in FP64)
+        o64 = vbk.vbk_default_opts(method=args.method, precision="fp64", precond_span=args.precond, tol=1e-8,
+                                   restart=args.restart, max_refine=100)
+        psi, st64 = vbk.vbk_solve(model, eps, vi, o64, psi=psi, check=False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        psi, st64 = vbk.vbk_solve(model, eps, vi, o64, psi=psi, check=False)
+        b.record()
+        b.synchronize()
+        extras["fp64_batched"] = {"value": n_energies / (a.elapsed_time(b) * 1e-3), "unit": UNIT,
+                                  "converged": all(s["status"] == "converged" for s in st64)}
+        # plain FP64 single-energy solves (GMRES + Jacobi, one energy per call), 16 energies
+        o1 = vbk.vbk_default_opts(method="gmres", precision="fp64", precond_span=0, tol=1e-8, restart=64,
+                                  max_refine=200)
+        sel = np.linspace(0, eps.size - 1, 16).round().astype(int)
+        psi1 = torch.empty((1, 1, nmu, N), dtype=torch.complex128, device="cuda")
+        vbk.vbk_solve(model, eps[sel[:1]], vi, o1, psi=psi1, check=False)
+        torch.cuda.synchronize()
+        a.record()
+        for kk in sel:
+            vbk.vbk_solve(model, eps[kk:kk + 1], vi, o1, psi=psi1, check=False)
+        b.record()
+        b.synchronize()
+        extras["fp64_single_energy"] = {"value": sel.size / (a.elapsed_time(b) * 1e-3), "unit": UNIT,
+                                        "method": "GMRES(64) + Jacobi, FP64, one energy per call"}
+        # CPU oracle on a bounded sample
+        rate, dt = oracle_rate(desc, eps, vi, 48)
+        extras["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"48 of 256 energies (evenly spaced), sparse LU per energy, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 Krylov + c128 refinement", "data": "synthetic (seeded model, no dataset)",
+            "config": {"workload": WORKLOAD_NAME, "method": args.method, "precond_span": args.precond,
+                       "inner_tol": args.inner_tol, "restart": args.restart,
+                       "l2": "256 MB buffer written between timed steps (outside the step events)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "matvec_hbm_gbs": matvec_gbs,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "converged": converged, "worst_rel_residual": worst,
+            "iterations": {"min": min(iters), "median": float(np.median(iters)), "max": max(iters)},
+            "kernel_ms": {k: round(v[1] / args.steps, 3) for k, v in sorted(timings.items(), key=lambda kv: -kv[1][1])},
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -360,3 +360,36 @@ def loss_gradient_adjoint(model: dict, eps, vi, vf_list, target, thetas):
                         tot += w * 2.0 * np.real(np.conj(T) * dT)
             grads[k] += tot
     return grads
+
+
+# ----------------------------------------------------------------------------------------
+# Block-diagonal preconditioners (Sec. III.B)
+# ----------------------------------------------------------------------------------------
+def block_labels(model: dict, span: int) -> np.ndarray:
+    """Block label of every compound index alpha = (d, nu) for a preconditioner whose blocks
+    span the indices in ``span`` (bit 0: state d, bit 1+m: mode m).  Two entries of A belong
+    to the same block when all indices NOT spanned agree (Sec. III.B: the block-diagonal
+    section of A)."""
+    ns = model["n_states"]
+    shape = (ns,) + basis_shape(model)
+    grids = np.indices(shape).reshape(len(shape), -1)
+    fixed = [k for k in range(len(shape)) if not (span >> k) & 1]
+    if not fixed:
+        return np.zeros(grids.shape[1], dtype=np.int64)
+    sub = grids[fixed]
+    dims = [shape[k] for k in fixed]
+    return np.ravel_multi_index(tuple(sub), dims)
+
+
+def block_diagonal(model: dict, E: float, span: int) -> sp.csr_matrix:
+    """M = the entries of A whose row and column lie in the same block (Sec. III.B)."""
+    A = a_matrix(model, E).tocoo()
+    lab = block_labels(model, span)
+    keep = lab[A.row] == lab[A.col]
+    return sp.csr_matrix((A.data[keep], (A.row[keep], A.col[keep])), shape=A.shape)
+
+
+def precond_apply(model: dict, E: float, span: int, r: np.ndarray) -> np.ndarray:
+    """z = M^-1 r by a direct solve with the block-diagonal section M of A."""
+    M = block_diagonal(model, E, span)
+    return spla.splu(M.tocsc()).solve(np.asarray(r, dtype=np.complex128))

@@ -1,0 +1,978 @@
+// C ABI entry points, model builder, observables (T, sigma, EELS) and the adjoint gradient.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "vbk_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+void vbk_set_error(const std::string& msg) { g_last_error = msg; }
+
+int vbk_cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+        cudaGetLastError();
+        return VBK_ERR_OOM;
+    }
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return VBK_ERR_CUDA;
+}
+
+namespace {
+
+constexpr int TPB = 256;
+inline unsigned cdiv_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+int invalid(const std::string& msg) {
+    g_last_error = msg;
+    return VBK_ERR_INVALID_ARG;
+}
+
+// Banded representation of the truncated matrix power (PqP)^k: pw[off][n] = (q^k)_{n, n + off - k}.
+std::vector<std::vector<double>> q_power_band(int n, int k) {
+    std::vector<std::vector<double>> cur(1, std::vector<double>(n, 1.0));  // identity, k = 0
+    for (int kk = 1; kk <= k; ++kk) {
+        std::vector<std::vector<double>> nxt(2 * kk + 1, std::vector<double>(n, 0.0));
+        // (P q)[r][r+delta] = P[r][r+delta-1] q[r+delta-1][r+delta] + P[r][r+delta+1] q[r+delta+1][r+delta]
+        // with q[a][a+1] = q[a+1][a] = sqrt((a+1)/2)
+        for (int off = 0; off <= 2 * kk; ++off) {
+            const int delta = off - kk;
+            for (int r = 0; r < n; ++r) {
+                const int col = r + delta;
+                if (col < 0 || col >= n) continue;
+                double v = 0.0;
+                const int c1 = col - 1;  // P[r][col-1] * q[col-1][col]
+                if (c1 >= 0) {
+                    const int o1 = c1 - r + (kk - 1);
+                    if (o1 >= 0 && o1 <= 2 * (kk - 1)) v += cur[o1][r] * std::sqrt((c1 + 1) / 2.0);
+                }
+                const int c2 = col + 1;  // P[r][col+1] * q[col+1][col]
+                if (c2 < n) {
+                    const int o2 = c2 - r + (kk - 1);
+                    if (o2 >= 0 && o2 <= 2 * (kk - 1)) v += cur[o2][r] * std::sqrt((col + 1) / 2.0);
+                }
+                nxt[off][r] = v;
+            }
+        }
+        cur.swap(nxt);
+    }
+    return cur;
+}
+
+int build(const vbk_model_desc* d, vbk_model* m) {
+    if (!d) return invalid("model description is NULL");
+    if (d->n_states < 1 || d->n_states > VBK_MAX_STATES) return invalid("n_states out of range");
+    if (d->n_modes < 1 || d->n_modes > VBK_MAX_MODES) return invalid("n_modes out of range");
+    long long nnu = 1;
+    for (int k = 0; k < d->n_modes; ++k) {
+        if (d->n_basis[k] < 1 || d->n_basis[k] > 100000) return invalid("n_basis out of range");
+        if (!(d->omega[k] > 0.0) || !std::isfinite(d->omega[k])) return invalid("omega must be positive and finite");
+        nnu *= d->n_basis[k];
+    }
+    if (nnu * d->n_states > (1LL << 30)) return invalid("basis too large");
+    if (d->n_terms < 0 || (d->n_terms > 0 && !d->terms)) return invalid("terms missing");
+    if (d->n_channels < 1 || d->n_channels > VBK_MAX_CHANNELS || !d->channels) return invalid("n_channels out of range");
+    m->ns = d->n_states;
+    m->M = d->n_modes;
+    m->Nnu = (int)nnu;
+    m->N = (int)(nnu * d->n_states);
+    int str = 1;
+    for (int k = m->M - 1; k >= 0; --k) {
+        m->nb[k] = d->n_basis[k];
+        m->stride[k] = str;
+        str *= d->n_basis[k];
+    }
+    m->terms.assign(d->terms, d->terms + d->n_terms);
+    m->chans.assign(d->channels, d->channels + d->n_channels);
+    int mu_d[VBK_MAX_CHANNELS];
+    for (int k = 0; k < VBK_MAX_CHANNELS; ++k) mu_d[k] = -1;
+    int nmu = 0;
+    for (const auto& c : m->chans) {
+        if (c.d < 0 || c.d >= m->ns) return invalid("channel state index out of range");
+        if (c.mu < 0 || c.mu >= VBK_MAX_CHANNELS) return invalid("partial-wave index out of range");
+        if (!(c.a >= 0.0) || !std::isfinite(c.a) || !(c.b > 0.0) || !std::isfinite(c.b) || c.l < 0 || c.l > 20)
+            return invalid("channel parameters out of range (a >= 0, b > 0, 0 <= l <= 20)");
+        if (mu_d[c.mu] >= 0) return invalid("a partial wave may couple to a single state only");
+        mu_d[c.mu] = c.d;
+        nmu = std::max(nmu, c.mu + 1);
+    }
+    m->nmu = nmu;
+    int kmax[MAXM] = {0};
+    for (const auto& t : m->terms) {
+        if (t.d < 0 || t.dp < 0 || t.d >= m->ns || t.dp >= m->ns || t.d > t.dp) return invalid("term state indices must satisfy 0 <= d <= dp < n_states");
+        if (!std::isfinite(t.coef)) return invalid("term coefficient not finite");
+        for (int k = 0; k < m->M; ++k) {
+            if (t.pow[k] < 0 || t.pow[k] > 8) return invalid("term power out of range (0..8)");
+            kmax[k] = std::max(kmax[k], t.pow[k]);
+        }
+        for (int k = m->M; k < VBK_MAX_MODES; ++k)
+            if (t.pow[k] != 0) return invalid("power given for a mode beyond n_modes");
+    }
+    // tables: for every mode and power k = 1..kmax[m], columns o = 0..k of length n_m
+    m->tab.clear();
+    m->colbase.assign(m->M, std::vector<int>());
+    for (int mm = 0; mm < m->M; ++mm) {
+        m->colbase[mm].assign(kmax[mm] + 1, -1);
+        for (int k = 1; k <= kmax[mm]; ++k) {
+            auto band = q_power_band(m->nb[mm], k);
+            m->colbase[mm][k] = (int)m->tab.size();
+            for (int o = 0; o <= k; ++o) {
+                const int off = 2 * o;  // delta = -k + 2 o  ->  band index delta + k
+                for (int n = 0; n < m->nb[mm]; ++n) m->tab.push_back(band[off][n]);
+            }
+        }
+    }
+    if (m->tab.empty()) m->tab.push_back(0.0);
+    // stencil points
+    std::vector<HostEntry> offd, diagp;
+    for (int ti = 0; ti < (int)m->terms.size(); ++ti) {
+        const auto& t = m->terms[ti];
+        int cnt[MAXM], o[MAXM];
+        long long ncomb = 1;
+        for (int k = 0; k < m->M; ++k) {
+            cnt[k] = t.pow[k] + 1;
+            ncomb *= cnt[k];
+            o[k] = 0;
+        }
+        for (long long c = 0; c < ncomb; ++c) {
+            long long rem = c;
+            for (int k = m->M - 1; k >= 0; --k) {
+                o[k] = (int)(rem % cnt[k]);
+                rem /= cnt[k];
+            }
+            DevEntry e{};
+            e.coef = t.coef;
+            e.lin = 0;
+            bool zero = true;
+            for (int k = 0; k < MAXM; ++k) {
+                e.col[k] = -1;
+                e.delta[k] = 0;
+            }
+            for (int k = 0; k < m->M; ++k) {
+                if (t.pow[k] == 0) continue;
+                e.delta[k] = -t.pow[k] + 2 * o[k];
+                e.col[k] = m->colbase[k][t.pow[k]] + o[k] * m->nb[k];
+                e.lin += e.delta[k] * m->stride[k];
+                if (e.delta[k] != 0) zero = false;
+            }
+            if (t.d == t.dp) {
+                e.dp = t.d;
+                if (zero)
+                    diagp.push_back({t.d, ti, 0, e});
+                else
+                    offd.push_back({t.d, ti, 0, e});
+            } else {
+                e.dp = t.dp;
+                offd.push_back({t.d, ti, 0, e});
+                DevEntry em = e;
+                em.dp = t.d;
+                offd.push_back({t.dp, ti, 1, em});
+            }
+        }
+    }
+    auto by_d = [](const HostEntry& a, const HostEntry& b) { return a.d < b.d; };
+    std::stable_sort(offd.begin(), offd.end(), by_d);
+    std::stable_sort(diagp.begin(), diagp.end(), by_d);
+    m->offd = offd;
+    m->diagp = diagp;
+    // device model
+    DevModel& dm = m->dm;
+    dm = DevModel{};
+    dm.ns = m->ns;
+    dm.M = m->M;
+    dm.Nnu = m->Nnu;
+    dm.N = m->N;
+    dm.nmu = m->nmu;
+    dm.nchan = (int)m->chans.size();
+    for (int k = 0; k < MAXM; ++k) {
+        dm.nb[k] = k < m->M ? m->nb[k] : 1;
+        dm.stride[k] = k < m->M ? m->stride[k] : 0;
+        dm.omega[k] = k < m->M ? d->omega[k] : 0.0;
+    }
+    for (int s = 0; s <= MAXS; ++s) {
+        dm.ebeg[s] = 0;
+        dm.dbeg[s] = 0;
+    }
+    for (int s = 0; s <= m->ns; ++s) {
+        dm.ebeg[s] = (int)(std::lower_bound(offd.begin(), offd.end(), HostEntry{s, 0, 0, {}}, by_d) - offd.begin());
+        dm.dbeg[s] = (int)(std::lower_bound(diagp.begin(), diagp.end(), HostEntry{s, 0, 0, {}}, by_d) - diagp.begin());
+    }
+    for (int s = m->ns + 1; s <= MAXS; ++s) {
+        dm.ebeg[s] = dm.ebeg[m->ns];
+        dm.dbeg[s] = dm.dbeg[m->ns];
+    }
+    for (int c = 0; c < dm.nchan; ++c) {
+        dm.ch_d[c] = m->chans[c].d;
+        dm.ch_mu[c] = m->chans[c].mu;
+        dm.ch_l[c] = m->chans[c].l;
+        dm.ch_a[c] = m->chans[c].a;
+        dm.ch_b[c] = m->chans[c].b;
+    }
+    for (int k = 0; k < MAXCH; ++k) dm.mu_d[k] = mu_d[k];
+    // one device allocation: entries | diagonal entries | tab64 | tab32
+    const size_t ne = std::max<size_t>(1, offd.size()), nd = std::max<size_t>(1, diagp.size()), nt = m->tab.size();
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b1 = al(ne * sizeof(DevEntry)), b2 = al(nd * sizeof(DevEntry)), b3 = al(nt * sizeof(double)),
+                 b4 = al(nt * sizeof(float));
+    char* mem = nullptr;
+    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4);
+    if (err != cudaSuccess) return vbk_cuda_fail(err, "model tables");
+    m->dev_mem = mem;
+    std::vector<DevEntry> he(ne), hd(nd);
+    for (size_t k = 0; k < offd.size(); ++k) he[k] = offd[k].e;
+    for (size_t k = 0; k < diagp.size(); ++k) hd[k] = diagp[k].e;
+    std::vector<float> t32(nt);
+    for (size_t k = 0; k < nt; ++k) t32[k] = (float)m->tab[k];
+    if ((err = cudaMemcpy(mem, he.data(), ne * sizeof(DevEntry), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(mem + b1, hd.data(), nd * sizeof(DevEntry), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(mem + b1 + b2, m->tab.data(), nt * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaMemcpy(mem + b1 + b2 + b3, t32.data(), nt * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return vbk_cuda_fail(err, "model table upload");
+    dm.ent = (const DevEntry*)mem;
+    dm.dent = (const DevEntry*)(mem + b1);
+    dm.tab64 = (const double*)(mem + b1 + b2);
+    dm.tab32 = (const float*)(mem + b1 + b2 + b3);
+    m->desc = *d;
+    m->desc.terms = m->terms.data();
+    m->desc.channels = m->chans.data();
+    return VBK_OK;
+}
+
+int flat_index(const vbk_model* m, const int* v, int* out) {
+    int f = 0;
+    for (int k = 0; k < m->M; ++k) {
+        if (v[k] < 0 || v[k] >= m->nb[k]) return invalid("vibrational multi-index out of range");
+        f += v[k] * m->stride[k];
+    }
+    *out = f;
+    return VBK_OK;
+}
+
+double level_energy(const vbk_model* m, const int* v) {
+    double e = 0.0;
+    for (int k = 0; k < m->M; ++k) e += m->dm.omega[k] * (v[k] + 0.5);
+    return e;
+}
+
+int check_model(const vbk_model* m) {
+    if (!m) return invalid("model handle is NULL");
+    return VBK_OK;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+// --------------------------------------------------------------------------- kernels
+// Dense right-hand sides Phi^{v_i mu} (Sec. II.D): f_{d(mu)}(E - E_vi) on entry (d(mu), v_i).
+__global__ void k_build_rhs(DevModel md, int nsys, int n_vi, const double* __restrict__ eps, const int* __restrict__ vflat,
+                            double2* __restrict__ b) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    const int mu = s % md.nmu, i = (s / md.nmu) % n_vi, e = s / (md.nmu * n_vi);
+    const int d = md.mu_d[mu];
+    if (d < 0) return;
+    for (int c = 0; c < md.nchan; ++c)
+        if (md.ch_mu[c] == mu) {
+            const double f = vbk_amplitude(eps[e], md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+            b[(long long)s * md.N + (long long)d * md.Nnu + vflat[i]] = make_double2(f, 0.0);
+        }
+}
+
+__device__ __forceinline__ int chan_of_mu(const DevModel& md, int mu) {
+    for (int c = 0; c < md.nchan; ++c)
+        if (md.ch_mu[c] == mu) return c;
+    return -1;
+}
+
+// T_{mu_f vf <- mu_i vi} = f_{mu_f}(E - E_vf) psi_{d(mu_f), vf}  (Eq. crs2 with real Phi);
+// sigma = 2 pi^3 / eps_i sum |T|^2 (Eq. crs).  One thread per (e, i, f).
+__global__ void k_sigma(DevModel md, int n_eps, int n_vi, int n_vf, const double* __restrict__ eps,
+                        const double* __restrict__ Etot, const double2* __restrict__ psi, const int* __restrict__ vf_flat,
+                        const double* __restrict__ E_vf, double* __restrict__ sigma, double2* __restrict__ T) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_eps * n_vi * n_vf) return;
+    const int f = (int)(t % n_vf), i = (int)((t / n_vf) % n_vi), e = (int)(t / ((long long)n_vf * n_vi));
+    const double E = Etot[(long long)e * n_vi + i];
+    const int nmu = md.nmu;
+    double acc = 0.0;
+    for (int mi = 0; mi < nmu; ++mi) {
+        const double2* ps = psi + (((long long)e * n_vi + i) * nmu + mi) * (long long)md.N;
+        for (int mf = 0; mf < nmu; ++mf) {
+            const int d = md.mu_d[mf], c = chan_of_mu(md, mf);
+            double2 tv = make_double2(0.0, 0.0);
+            if (d >= 0 && c >= 0) {
+                const double amp = vbk_amplitude(E - E_vf[f], md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+                const double2 pv = ps[(long long)d * md.Nnu + vf_flat[f]];
+                tv = make_double2(amp * pv.x, amp * pv.y);
+            }
+            acc += tv.x * tv.x + tv.y * tv.y;
+            if (T) T[((((long long)e * n_vi + i) * nmu + mi) * n_vf + f) * nmu + mf] = tv;
+        }
+    }
+    const double PI = 3.14159265358979323846;
+    sigma[t] = 2.0 * PI * PI * PI / eps[e] * acc;
+}
+
+// S(eps, de_k) = sum_f sigma_f rho(de_k - (E_vf - E_vi)), rho a unit-area Gaussian (Eq. 2Dsp)
+__global__ void k_eels(int n_eps, int n_vi, int n_vf, int n_de, const double* __restrict__ sigma,
+                       const double* __restrict__ de, const double* __restrict__ E_vf, const double* __restrict__ E_vi,
+                       double sdev, double* __restrict__ S) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n_eps * n_vi * n_de) return;
+    const int k = (int)(t % n_de), i = (int)((t / n_de) % n_vi), e = (int)(t / ((long long)n_de * n_vi));
+    const double* sg = sigma + ((long long)e * n_vi + i) * n_vf;
+    const double norm = 1.0 / (sdev * 2.5066282746310002);  // 1 / (s sqrt(2 pi))
+    double acc = 0.0;
+    for (int f = 0; f < n_vf; ++f) {
+        const double x = (de[k] - (E_vf[f] - E_vi[i])) / sdev;
+        acc += sg[f] * exp(-0.5 * x * x);
+    }
+    S[t] = acc * norm;
+}
+
+// Adjoint right-hand side per forward system (e, i, mu_i):
+//   g = sum_{f, mu_f} w Phi_f^{mu_f},  w = dL/dsigma * 2 pi^3/eps * 2 conj(T)
+// and the weights w (stored for the parameter derivatives of Phi_f).
+__global__ void k_adjoint_rhs(DevModel md, int n_eps, int n_vi, int n_vf, const double* __restrict__ eps,
+                              const double* __restrict__ Etot, const double2* __restrict__ T,
+                              const double* __restrict__ dLds, const int* __restrict__ vf_flat, const double* __restrict__ E_vf,
+                              double2* __restrict__ g, double2* __restrict__ W) {
+    const int nmu = md.nmu;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (long long)n_eps * n_vi * nmu) return;
+    const int mi = (int)(s % nmu), i = (int)((s / nmu) % n_vi), e = (int)(s / ((long long)nmu * n_vi));
+    const double E = Etot[(long long)e * n_vi + i];
+    const double PI = 3.14159265358979323846;
+    const double pre = 2.0 * PI * PI * PI / eps[e] * 2.0;
+    for (int f = 0; f < n_vf; ++f) {
+        const double dl = dLds[((long long)e * n_vi + i) * n_vf + f];
+        for (int mf = 0; mf < nmu; ++mf) {
+            const double2 tv = T[((((long long)e * n_vi + i) * nmu + mi) * n_vf + f) * nmu + mf];
+            const double2 w = make_double2(dl * pre * tv.x, -dl * pre * tv.y);
+            W[(s * n_vf + f) * nmu + mf] = w;
+            const int d = md.mu_d[mf], c = chan_of_mu(md, mf);
+            if (d < 0 || c < 0) continue;
+            const double amp = vbk_amplitude(E - E_vf[f], md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+            double2& gv = g[s * md.N + (long long)d * md.Nnu + vf_flat[f]];
+            gv.x += w.x * amp;
+            gv.y += w.y * amp;
+        }
+    }
+}
+
+// Gradient parameter descriptor: kind 0 = term coefficient (points [pb, pe) of the point list),
+// kind 1 = channel a, kind 2 = channel b (channel index c).
+struct GradParam {
+    int kind, c, pb, pe;
+};
+
+template <int M> __device__ __forceinline__ void decode_nu(const DevModel& md, int nu, int (&n)[MAXM]) {
+    int rem = nu;
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) {
+        n[m] = rem % md.nb[m];
+        rem /= md.nb[m];
+    }
+#pragma unroll
+    for (int m = M; m < MAXM; ++m) n[m] = 0;
+}
+
+// Element-wise contractions  Re(lambda_i [dA-part psi]_i)  per parameter (see vbk_solve_adjoint);
+// part[s][blk][theta].
+template <int M>
+__global__ void __launch_bounds__(TPB) k_adjoint_contract(DevModel md, int nsys, int n_vi, const double* __restrict__ Etot,
+                                                         const double2* __restrict__ lam, const double2* __restrict__ psi,
+                                                         int ntheta, const GradParam* __restrict__ gp,
+                                                         const int* __restrict__ pt_d, const DevEntry* __restrict__ pts,
+                                                         double* __restrict__ part) {
+    __shared__ double red[TPB / 32];
+    const int s = blockIdx.y;
+    const int N = md.N;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nmu = md.nmu;
+    const double E = Etot[s / nmu];  // systems are (e, i, mu) with e*n_vi+i = s / nmu
+    (void)n_vi;
+    int d = 0, nu = 0;
+    int n[MAXM];
+    double en = 0.0;
+    double2 li = make_double2(0.0, 0.0), pi = make_double2(0.0, 0.0);
+    const double2* ps = psi + (long long)s * N;
+    if (i < N) {
+        d = i / md.Nnu;
+        nu = i - d * md.Nnu;
+        decode_nu<M>(md, nu, n);
+#pragma unroll
+        for (int m = 0; m < M; ++m) en += md.omega[m] * (n[m] + 0.5);
+        li = lam[(long long)s * N + i];
+        pi = ps[i];
+    }
+    for (int th = 0; th < ntheta; ++th) {
+        const GradParam g = gp[th];
+        double v = 0.0;
+        if (i < N) {
+            if (g.kind == 0) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int k = g.pb; k < g.pe; ++k) {
+                    if (pt_d[k] != d) continue;
+                    const DevEntry p = pts[k];
+                    double c = p.coef;
+                    bool ok = true;
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (p.col[m] >= 0) {
+                            const int nn = n[m] + p.delta[m];
+                            ok = ok && nn >= 0 && nn < md.nb[m];
+                            c *= md.tab64[p.col[m] + n[m]];
+                        }
+                    if (ok) {
+                        const double2 x = ps[p.dp * md.Nnu + nu + p.lin];
+                        acc.x += c * x.x;
+                        acc.y += c * x.y;
+                    }
+                }
+                // -lambda^T (dA) psi with dA = -(unit-coefficient term matrix)
+                const double2 t = cmul<double>(li, acc);
+                v = t.x;
+            } else if (md.ch_d[g.c] == d) {
+                const int c = g.c;
+                const double eps = E - en;
+                if (g.kind == 1) {  // dA/da = -F/a
+                    const double2 F = vbk_level_shift_eval(eps, 1.0, md.ch_b[c], md.ch_l[c]);
+                    v = cmul<double>(li, cmul<double>(F, pi)).x;
+                } else {  // dA/db = F^{(l+1)}  (the transform with l -> l+1)
+                    const double2 F = vbk_level_shift_eval(eps, md.ch_a[c], md.ch_b[c], md.ch_l[c] + 1);
+                    v = -cmul<double>(li, cmul<double>(F, pi)).x;
+                }
+            }
+        }
+        // block reduction of v
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < TPB / 32; ++w) t += red[w];
+            part[((long long)s * gridDim.x + blockIdx.x) * ntheta + th] = t;
+        }
+    }
+}
+
+// Parameter derivatives of the right-hand sides (channel a, b only), one thread per system:
+//   Re[ sum_f w_f dPhi_f^T psi + lambda^T dPhi_i ],  dPhi/da = Phi/(2a), dPhi/db = -(eps/2) Phi.
+__global__ void k_adjoint_rhs_terms(DevModel md, int n_eps, int n_vi, int n_vf, const double* __restrict__ eps,
+                                    const double* __restrict__ Etot, const int* __restrict__ vi_flat,
+                                    const double* __restrict__ E_vi, const int* __restrict__ vf_flat,
+                                    const double* __restrict__ E_vf, const double2* __restrict__ W,
+                                    const double2* __restrict__ lam, const double2* __restrict__ psi, int ntheta,
+                                    const GradParam* __restrict__ gp, double* __restrict__ out) {
+    const int nmu = md.nmu;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (long long)n_eps * n_vi * nmu) return;
+    const int mi = (int)(s % nmu), i = (int)((s / nmu) % n_vi), e = (int)(s / ((long long)nmu * n_vi));
+    const double E = Etot[(long long)e * n_vi + i];
+    const double2* ps = psi + s * md.N;
+    const double2* ls = lam + s * md.N;
+    for (int th = 0; th < ntheta; ++th) {
+        const GradParam g = gp[th];
+        double acc = 0.0;
+        if (g.kind != 0) {
+            const int c = g.c, mu = md.ch_mu[c], d = md.ch_d[c];
+            const double a = md.ch_a[c], b = md.ch_b[c];
+            const int l = md.ch_l[c];
+            if (mi == mu) {  // lambda^T dPhi_i
+                const double ei = E - E_vi[i];
+                const double f = vbk_amplitude(ei, a, b, l);
+                const double df = g.kind == 1 ? (a > 0 ? f / (2.0 * a) : 0.0) : -0.5 * ei * f;
+                acc += df * ls[(long long)d * md.Nnu + vi_flat[i]].x;
+            }
+            for (int f = 0; f < n_vf; ++f) {  // sum_f w_f dPhi_f^T psi
+                const double ef = E - E_vf[f];
+                const double fa = vbk_amplitude(ef, a, b, l);
+                const double df = g.kind == 1 ? (a > 0 ? fa / (2.0 * a) : 0.0) : -0.5 * ef * fa;
+                const double2 w = W[(s * n_vf + f) * nmu + mu];
+                const double2 pv = ps[(long long)d * md.Nnu + vf_flat[f]];
+                acc += df * cmul<double>(w, pv).x;
+            }
+        }
+        out[s * ntheta + th] = acc;
+    }
+}
+
+// grad[theta] = sum_s sum_blk part[s][blk][theta] + sum_s rhs_terms[s][theta] (fixed order)
+__global__ void k_grad_reduce(int nsys, int nblk, int ntheta, const double* __restrict__ part,
+                              const double* __restrict__ rhs_terms, double* __restrict__ grad) {
+    const int th = blockIdx.x * blockDim.x + threadIdx.x;
+    if (th >= ntheta) return;
+    double acc = 0.0;
+    for (int s = 0; s < nsys; ++s) {
+        for (int b = 0; b < nblk; ++b) acc += part[((long long)s * nblk + b) * ntheta + th];
+        acc += rhs_terms[(long long)s * ntheta + th];
+    }
+    grad[th] = acc;
+}
+
+}  // namespace
+
+// =============================================================================== C ABI
+extern "C" {
+
+void vbk_default_opts(vbk_opts* o) {
+    if (!o) return;
+    o->method = VBK_GMRES;
+    o->precision = VBK_MIXED;
+    o->precond_span = 0;
+    o->restart = 64;
+    o->max_iter = 20000;
+    o->max_refine = 40;
+    o->tol = 1e-8;
+    o->inner_tol = 1e-5;
+    o->check_every = 8;
+    o->timing = 0;
+}
+
+int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
+    g_last_error.clear();
+    if (!out) return invalid("output handle pointer is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        g_last_error = "no CUDA device visible";
+        return VBK_ERR_NO_DEVICE;
+    }
+    vbk_model* m = new (std::nothrow) vbk_model();
+    if (!m) return VBK_ERR_OOM;
+    cudaGetDevice(&m->device);
+    int rc = build(desc, m);
+    if (rc) {
+        vbk_free_model(m);
+        return rc;
+    }
+    *out = m;
+    return VBK_OK;
+}
+
+void vbk_free_model(vbk_model* m) {
+    if (!m) return;
+    if (m->dev_mem) cudaFree(m->dev_mem);
+    delete m;
+}
+
+int vbk_model_size(const vbk_model* m, int* n_unknowns, int* n_partial_waves) {
+    if (int rc = check_model(m)) return rc;
+    if (n_unknowns) *n_unknowns = m->N;
+    if (n_partial_waves) *n_partial_waves = m->nmu;
+    return VBK_OK;
+}
+
+static int check_opts(const vbk_opts* o) {
+    if (!o) return invalid("options are NULL");
+    if (o->method != VBK_GMRES && o->method != VBK_COCG) return invalid("unknown Krylov method");
+    if (o->precision != VBK_FP64 && o->precision != VBK_MIXED) return invalid("unknown precision");
+    if (o->restart < 1 || o->restart > 256) return invalid("restart must be in 1..256");
+    if (o->max_iter < 1 || o->max_refine < 1) return invalid("max_iter and max_refine must be >= 1");
+    if (!(o->tol > 0.0) || !(o->tol < 1.0)) return invalid("tol must be in (0, 1)");
+    if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)) return invalid("inner_tol must be in (0, 1)");
+    if (o->check_every < 1) return invalid("check_every must be >= 1");
+    if (o->precond_span < -1) return invalid("precond_span must be -1 or a span mask");
+    return VBK_OK;
+}
+
+// Shared set-up of solve / adjoint: energies, distinct-energy map, flat initial indices.
+static int make_systems(vbk_model* m, int n_eps, const double* eps, int n_vi, const int* vi, SolveJob* job,
+                        std::vector<double>* Etot, std::vector<int>* vflat, std::vector<double>* Evi) {
+    if (n_eps < 1 || n_vi < 1 || !eps || !vi) return invalid("n_eps, n_vi, eps_i and vi must be given");
+    if ((long long)n_eps * n_vi * m->nmu > 65535) return invalid("at most 65535 systems (energies x initial states x partial waves) per call");
+    for (int e = 0; e < n_eps; ++e)
+        if (!(eps[e] > 0.0) || !std::isfinite(eps[e])) return invalid("incident energies must be positive and finite");
+    vflat->resize(n_vi);
+    Evi->resize(n_vi);
+    for (int i = 0; i < n_vi; ++i) {
+        if (int rc = flat_index(m, vi + (long long)i * m->M, &(*vflat)[i])) return rc;
+        (*Evi)[i] = level_energy(m, vi + (long long)i * m->M);
+    }
+    Etot->resize((size_t)n_eps * n_vi);
+    std::map<double, int> idx;
+    job->E.clear();
+    job->sys_e.clear();
+    for (int e = 0; e < n_eps; ++e)
+        for (int i = 0; i < n_vi; ++i) {
+            const double E = eps[e] + (*Evi)[i];
+            (*Etot)[(size_t)e * n_vi + i] = E;
+            auto it = idx.find(E);
+            int k;
+            if (it == idx.end()) {
+                k = (int)job->E.size();
+                idx[E] = k;
+                job->E.push_back(E);
+            } else {
+                k = it->second;
+            }
+            for (int mu = 0; mu < m->nmu; ++mu) job->sys_e.push_back(k);
+        }
+    job->nE = (int)job->E.size();
+    job->nsys = (int)job->sys_e.size();
+    return VBK_OK;
+}
+
+int vbk_solve(vbk_model* m, int n_eps, const double* eps_i, int n_vi, const int* vi, const vbk_opts* opts, void* psi_dev,
+              vbk_stats* stats, void* stream) {
+    g_last_error.clear();
+    if (int rc = check_model(m)) return rc;
+    if (int rc = check_opts(opts)) return rc;
+    if (!psi_dev) return invalid("psi_dev is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveJob job;
+    std::vector<double> Etot, Evi;
+    std::vector<int> vflat;
+    if (int rc = make_systems(m, n_eps, eps_i, n_vi, vi, &job, &Etot, &vflat, &Evi)) return rc;
+    const size_t N = m->N;
+    DevBuf b;
+    b.st = st;
+    const size_t bbytes = (size_t)job.nsys * N * sizeof(double2);
+    const size_t extra = (size_t)n_eps * sizeof(double) + (size_t)n_vi * sizeof(int) + 512;
+    VBK_CUDA(cudaMallocAsync(&b.p, bbytes + extra, st));
+    double2* b64 = (double2*)b.p;
+    double* deps = (double*)((char*)b.p + bbytes);
+    int* dvf = (int*)((char*)deps + (((size_t)n_eps * sizeof(double) + 255) & ~size_t(255)));
+    VBK_CUDA(cudaMemsetAsync(b64, 0, bbytes, st));
+    VBK_CUDA(cudaMemcpyAsync(deps, eps_i, n_eps * sizeof(double), cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(dvf, vflat.data(), n_vi * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_build_rhs<<<cdiv_u(job.nsys, 128), 128, 0, st>>>(m->dm, job.nsys, n_vi, deps, dvf, b64);
+    VBK_CUDA(cudaGetLastError());
+    job.b64 = b64;
+    job.x64 = (double2*)psi_dev;
+    int rc = vbk_solve_job(m, job, *opts, stats, st);
+    m->launches += 1;  // k_build_rhs
+    return rc;
+}
+
+int vbk_cross_sections(vbk_model* m, int n_eps, const double* eps_i, int n_vi, const int* vi, const void* psi_dev, int n_vf,
+                       const int* vf, double* sigma_dev, void* t_dev, void* stream) {
+    g_last_error.clear();
+    if (int rc = check_model(m)) return rc;
+    if (!psi_dev || !sigma_dev) return invalid("psi_dev and sigma_dev must be given");
+    if (n_vf < 1 || !vf) return invalid("final states missing");
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveJob job;
+    std::vector<double> Etot, Evi;
+    std::vector<int> vflat;
+    if (int rc = make_systems(m, n_eps, eps_i, n_vi, vi, &job, &Etot, &vflat, &Evi)) return rc;
+    std::vector<int> ff(n_vf);
+    std::vector<double> Ef(n_vf);
+    for (int f = 0; f < n_vf; ++f) {
+        if (int rc = flat_index(m, vf + (long long)f * m->M, &ff[f])) return rc;
+        Ef[f] = level_energy(m, vf + (long long)f * m->M);
+    }
+    DevBuf b;
+    b.st = st;
+    const size_t s1 = ((size_t)n_eps * 8 + 255) & ~size_t(255), s2 = (Etot.size() * 8 + 255) & ~size_t(255),
+                 s3 = ((size_t)n_vf * 4 + 255) & ~size_t(255), s4 = ((size_t)n_vf * 8 + 255) & ~size_t(255);
+    VBK_CUDA(cudaMallocAsync(&b.p, s1 + s2 + s3 + s4, st));
+    char* p = (char*)b.p;
+    VBK_CUDA(cudaMemcpyAsync(p, eps_i, n_eps * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(p + s1, Etot.data(), Etot.size() * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(p + s1 + s2, ff.data(), n_vf * 4, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(p + s1 + s2 + s3, Ef.data(), n_vf * 8, cudaMemcpyHostToDevice, st));
+    const long long nt = (long long)n_eps * n_vi * n_vf;
+    k_sigma<<<cdiv_u(nt, 128), 128, 0, st>>>(m->dm, n_eps, n_vi, n_vf, (const double*)p, (const double*)(p + s1),
+                                             (const double2*)psi_dev, (const int*)(p + s1 + s2), (const double*)(p + s1 + s2 + s3),
+                                             sigma_dev, (double2*)t_dev);
+    VBK_CUDA(cudaGetLastError());
+    return VBK_OK;
+}
+
+int vbk_eels(vbk_model* m, int n_eps, int n_vi, const int* vi, int n_vf, const int* vf, const double* sigma_dev, int n_de,
+             const double* de, double fwhm, double* S_dev, void* stream) {
+    g_last_error.clear();
+    if (int rc = check_model(m)) return rc;
+    if (n_eps < 1 || n_vi < 1 || n_vf < 1 || n_de < 1 || !vi || !vf || !de || !sigma_dev || !S_dev)
+        return invalid("eels: sizes and buffers must be given");
+    if (!(fwhm > 0.0)) return invalid("fwhm must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> Ef(n_vf), Ei(n_vi);
+    for (int f = 0; f < n_vf; ++f) {
+        int tmp;
+        if (int rc = flat_index(m, vf + (long long)f * m->M, &tmp)) return rc;
+        Ef[f] = level_energy(m, vf + (long long)f * m->M);
+    }
+    for (int i = 0; i < n_vi; ++i) {
+        int tmp;
+        if (int rc = flat_index(m, vi + (long long)i * m->M, &tmp)) return rc;
+        Ei[i] = level_energy(m, vi + (long long)i * m->M);
+    }
+    DevBuf b;
+    b.st = st;
+    const size_t s1 = ((size_t)n_de * 8 + 255) & ~size_t(255), s2 = ((size_t)n_vf * 8 + 255) & ~size_t(255),
+                 s3 = ((size_t)n_vi * 8 + 255) & ~size_t(255);
+    VBK_CUDA(cudaMallocAsync(&b.p, s1 + s2 + s3, st));
+    char* p = (char*)b.p;
+    VBK_CUDA(cudaMemcpyAsync(p, de, n_de * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(p + s1, Ef.data(), n_vf * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(p + s1 + s2, Ei.data(), n_vi * 8, cudaMemcpyHostToDevice, st));
+    const double sdev = fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    const long long nt = (long long)n_eps * n_vi * n_de;
+    k_eels<<<cdiv_u(nt, 128), 128, 0, st>>>(n_eps, n_vi, n_vf, n_de, sigma_dev, (const double*)p, (const double*)(p + s1),
+                                            (const double*)(p + s1 + s2), sdev, S_dev);
+    VBK_CUDA(cudaGetLastError());
+    return VBK_OK;
+}
+
+int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, const int* vi, const vbk_opts* opts,
+                      const void* psi_dev, int n_vf, const int* vf, const double* dL_dsigma_dev, int n_theta,
+                      const int* theta_ids, double* grad, vbk_stats* stats, void* stream) {
+    g_last_error.clear();
+    if (int rc = check_model(m)) return rc;
+    if (int rc = check_opts(opts)) return rc;
+    if (!psi_dev || !dL_dsigma_dev || !grad || !theta_ids) return invalid("adjoint: buffers must be given");
+    if (n_vf < 1 || !vf || n_theta < 1 || n_theta > 4096) return invalid("adjoint: n_vf >= 1 and 1 <= n_theta <= 4096");
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveJob job;
+    std::vector<double> Etot, Evi;
+    std::vector<int> vflat;
+    if (int rc = make_systems(m, n_eps, eps_i, n_vi, vi, &job, &Etot, &vflat, &Evi)) return rc;
+    std::vector<int> ff(n_vf);
+    std::vector<double> Ef(n_vf);
+    for (int f = 0; f < n_vf; ++f) {
+        if (int rc = flat_index(m, vf + (long long)f * m->M, &ff[f])) return rc;
+        Ef[f] = level_energy(m, vf + (long long)f * m->M);
+    }
+    // parameter descriptors and the point lists of the term parameters
+    const int nterm = (int)m->terms.size();
+    std::vector<GradParam> gps(n_theta);
+    std::vector<DevEntry> pts;
+    std::vector<int> ptd;
+    for (int k = 0; k < n_theta; ++k) {
+        const int id = theta_ids[k];
+        if (id < 0 || id >= nterm + 2 * (int)m->chans.size()) return invalid("theta id out of range");
+        GradParam g{0, 0, 0, 0};
+        if (id < nterm) {
+            g.kind = 0;
+            g.pb = (int)pts.size();
+            for (const auto* lst : {&m->offd, &m->diagp})
+                for (const auto& he : *lst)
+                    if (he.term == id) {
+                        DevEntry e = he.e;
+                        e.coef = 1.0;  // derivative of coef * (term matrix)
+                        pts.push_back(e);
+                        ptd.push_back(he.d);
+                    }
+            g.pe = (int)pts.size();
+        } else {
+            g.kind = 1 + (id - nterm) % 2;
+            g.c = (id - nterm) / 2;
+            if (g.kind == 1 && !(m->chans[g.c].a > 0.0)) return invalid("gradient in a needs a > 0");
+        }
+        gps[k] = g;
+    }
+    if (pts.empty()) {
+        pts.push_back(DevEntry{});
+        ptd.push_back(-1);
+    }
+    const size_t N = m->N;
+    const long long nsys = job.nsys;
+    const int nblk = (int)cdiv_u(N, TPB);
+    const int nmu = m->nmu;
+    const size_t nT = (size_t)n_eps * n_vi * nmu * n_vf * nmu;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t off[16];
+    size_t tot = 0;
+    size_t sizes[] = {al(nsys * N * sizeof(double2)),                      // 0 g (adjoint rhs)
+                      al(nsys * N * sizeof(double2)),                      // 1 lambda
+                      al(nT * sizeof(double2)),                            // 2 T
+                      al(nT * sizeof(double2)),                            // 3 W
+                      al((size_t)n_eps * 8), al(Etot.size() * 8),          // 4 eps, 5 Etot
+                      al((size_t)n_vf * 4), al((size_t)n_vf * 8),          // 6 vf flat, 7 E_vf
+                      al((size_t)n_vi * 4), al((size_t)n_vi * 8),          // 8 vi flat, 9 E_vi
+                      al(gps.size() * sizeof(GradParam)),                  // 10
+                      al(pts.size() * sizeof(DevEntry)), al(ptd.size() * 4),  // 11, 12
+                      al(nsys * (size_t)nblk * n_theta * 8),               // 13 partials
+                      al(nsys * (size_t)n_theta * 8),                      // 14 rhs terms
+                      al((size_t)n_theta * 8)};                            // 15 grad (device)
+    for (int k = 0; k < 16; ++k) {
+        off[k] = tot;
+        tot += sizes[k];
+    }
+    DevBuf b;
+    b.st = st;
+    VBK_CUDA(cudaMallocAsync(&b.p, tot, st));
+    char* p = (char*)b.p;
+    auto P = [&](int k) { return p + off[k]; };
+    VBK_CUDA(cudaMemsetAsync(P(0), 0, sizes[0], st));
+    VBK_CUDA(cudaMemcpyAsync(P(4), eps_i, n_eps * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(5), Etot.data(), Etot.size() * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(6), ff.data(), n_vf * 4, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(7), Ef.data(), n_vf * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(8), vflat.data(), n_vi * 4, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(9), Evi.data(), n_vi * 8, cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(10), gps.data(), gps.size() * sizeof(GradParam), cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(11), pts.data(), pts.size() * sizeof(DevEntry), cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(P(12), ptd.data(), ptd.size() * 4, cudaMemcpyHostToDevice, st));
+    // T from the forward solutions, adjoint right-hand sides
+    const long long nt = (long long)n_eps * n_vi * n_vf;
+    std::vector<double> sig_dummy;  // sigma itself is not needed here
+    double* dsig = nullptr;
+    VBK_CUDA(cudaMallocAsync((void**)&dsig, std::max<long long>(1, nt) * sizeof(double), st));
+    k_sigma<<<cdiv_u(nt, 128), 128, 0, st>>>(m->dm, n_eps, n_vi, n_vf, (const double*)P(4), (const double*)P(5),
+                                             (const double2*)psi_dev, (const int*)P(6), (const double*)P(7), dsig,
+                                             (double2*)P(2));
+    k_adjoint_rhs<<<cdiv_u(nsys, 128), 128, 0, st>>>(m->dm, n_eps, n_vi, n_vf, (const double*)P(4), (const double*)P(5),
+                                                     (const double2*)P(2), dL_dsigma_dev, (const int*)P(6),
+                                                     (const double*)P(7), (double2*)P(0), (double2*)P(3));
+    cudaFreeAsync(dsig, st);
+    VBK_CUDA(cudaGetLastError());
+    // lambda = A^-1 g  (A = A^T: the forward operator serves as its own transpose)
+    job.b64 = (const double2*)P(0);
+    job.x64 = (double2*)P(1);
+    int rc = vbk_solve_job(m, job, *opts, stats, st);
+    if (rc != VBK_OK && rc != VBK_ERR_NOT_CONVERGED) return rc;
+    const long long extra_launches = 5;
+    // contractions
+    const dim3 gc(nblk, (unsigned)nsys);
+    switch (m->M) {
+        case 1: k_adjoint_contract<1><<<gc, TPB, 0, st>>>(m->dm, (int)nsys, n_vi, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const int*)P(12), (const DevEntry*)P(11), (double*)P(13)); break;
+        case 2: k_adjoint_contract<2><<<gc, TPB, 0, st>>>(m->dm, (int)nsys, n_vi, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const int*)P(12), (const DevEntry*)P(11), (double*)P(13)); break;
+        case 3: k_adjoint_contract<3><<<gc, TPB, 0, st>>>(m->dm, (int)nsys, n_vi, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const int*)P(12), (const DevEntry*)P(11), (double*)P(13)); break;
+        default: k_adjoint_contract<4><<<gc, TPB, 0, st>>>(m->dm, (int)nsys, n_vi, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const int*)P(12), (const DevEntry*)P(11), (double*)P(13)); break;
+    }
+    k_adjoint_rhs_terms<<<cdiv_u(nsys, 128), 128, 0, st>>>(m->dm, n_eps, n_vi, n_vf, (const double*)P(4), (const double*)P(5),
+                                                           (const int*)P(8), (const double*)P(9), (const int*)P(6),
+                                                           (const double*)P(7), (const double2*)P(3), (const double2*)P(1),
+                                                           (const double2*)psi_dev, n_theta, (const GradParam*)P(10),
+                                                           (double*)P(14));
+    k_grad_reduce<<<cdiv_u(n_theta, 64), 64, 0, st>>>((int)nsys, nblk, n_theta, (const double*)P(13), (const double*)P(14),
+                                                      (double*)P(15));
+    VBK_CUDA(cudaGetLastError());
+    VBK_CUDA(cudaMemcpyAsync(grad, P(15), n_theta * 8, cudaMemcpyDeviceToHost, st));
+    VBK_CUDA(cudaStreamSynchronize(st));
+    m->launches += extra_launches;
+    return rc;
+}
+
+int vbk_matvec(vbk_model* m, int n_E, const double* E, int n_vec, const void* x_dev, void* y_dev, int precision,
+               void* stream) {
+    g_last_error.clear();
+    if (int rc = check_model(m)) return rc;
+    if (n_E < 1 || n_vec < 1 || !E || !x_dev || !y_dev) return invalid("matvec: sizes and buffers must be given");
+    if (precision != VBK_FP64 && precision != VBK_MIXED) return invalid("unknown precision");
+    for (int k = 0; k < n_E; ++k)
+        if (!std::isfinite(E[k])) return invalid("energies must be finite");
+    return vbk_operator_run(m, 0, n_E, E, n_vec, 0, (const double2*)x_dev, (double2*)y_dev, precision,
+                            (cudaStream_t)stream);
+}
+
+int vbk_precond_apply(vbk_model* m, int n_E, const double* E, int n_vec, int precond_span, const void* r_dev, void* z_dev,
+                      int precision, void* stream) {
+    g_last_error.clear();
+    if (int rc = check_model(m)) return rc;
+    if (n_E < 1 || n_vec < 1 || !E || !r_dev || !z_dev) return invalid("precond: sizes and buffers must be given");
+    if (precision != VBK_FP64 && precision != VBK_MIXED) return invalid("unknown precision");
+    if (precond_span < -1 || precond_span >= (2 << m->M)) return invalid("precond_span out of range");
+    for (int k = 0; k < n_E; ++k)
+        if (!std::isfinite(E[k])) return invalid("energies must be finite");
+    return vbk_operator_run(m, 1, n_E, E, n_vec, precond_span, (const double2*)r_dev, (double2*)z_dev, precision,
+                            (cudaStream_t)stream);
+}
+
+int vbk_kernel_timings(const vbk_model* m, int cap, const char** names, int* launches, double* total_ms) {
+    if (!m) return 0;
+    const int n = (int)m->timers.size();
+    for (int k = 0; k < n && k < cap; ++k) {
+        if (names) names[k] = m->timers[k].name.c_str();
+        if (launches) launches[k] = (int)m->timers[k].launches;
+        if (total_ms) total_ms[k] = m->timers[k].ms;
+    }
+    return n;
+}
+
+long long vbk_last_launch_count(const vbk_model* m) { return m ? m->launches : 0; }
+
+const char* vbk_status_str(int code) {
+    switch (code) {
+        case VBK_OK: return "ok";
+        case VBK_ERR_INVALID_ARG: return "invalid argument";
+        case VBK_ERR_OOM: return "out of memory";
+        case VBK_ERR_CUDA: return "CUDA error";
+        case VBK_ERR_NOT_CONVERGED: return "not converged";
+        case VBK_ERR_UNSUPPORTED: return "unsupported";
+        case VBK_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+const char* vbk_sys_status_str(int status) {
+    switch (status) {
+        case VBK_SYS_CONVERGED: return "converged";
+        case VBK_SYS_MAX_ITER: return "iteration limit";
+        case VBK_SYS_BREAKDOWN: return "breakdown";
+        case VBK_SYS_NAN: return "non-finite value";
+        case VBK_SYS_PIVOT: return "zero pivot in preconditioner";
+        case VBK_SYS_ZERO_RHS: return "zero right-hand side";
+    }
+    return "unknown system status";
+}
+
+const char* vbk_last_error(void) { return g_last_error.c_str(); }
+
+int vbk_level_shift(double eps, double a, double b, int l, double* re, double* im) {
+    if (!re || !im) return invalid("output pointers are NULL");
+    if (!std::isfinite(eps) || !(a >= 0.0) || !(b > 0.0) || l < 0 || l > 20) return invalid("level shift parameters out of range");
+    const double2 F = vbk_level_shift_eval(eps, a, b, l);
+    *re = F.x;
+    *im = F.y;
+    return VBK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- block plans (host)
+int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* bp) {
+    if (span <= 0 || span >= (2 << m->M)) {
+        g_last_error = "block preconditioner span out of range";
+        return VBK_ERR_INVALID_ARG;
+    }
+    bp->span = span;
+    const bool sd = span & 1;
+    long long L = sd ? m->ns : 1;
+    long long cstr[MAXM] = {0};
+    long long acc = sd ? m->ns : 1;
+    for (int k = m->M - 1; k >= 0; --k)
+        if (span & (2 << k)) {
+            cstr[k] = acc;
+            acc *= m->nb[k];
+        }
+    L = acc;
+    bp->L = (int)L;
+    bp->nblk = (int)(m->N / L);
+    bp->ent_dc.assign(m->offd.size(), 0);
+    int p = 0;
+    for (size_t k = 0; k < m->offd.size(); ++k) {
+        const HostEntry& h = m->offd[k];
+        bool in = sd || h.e.dp == h.d;
+        long long dc = sd ? (h.e.dp - h.d) : 0;
+        for (int mm = 0; mm < m->M && in; ++mm) {
+            if (span & (2 << mm))
+                dc += (long long)h.e.delta[mm] * cstr[mm];
+            else if (h.e.delta[mm] != 0)
+                in = false;
+        }
+        if (!in || dc == 0) continue;
+        bp->ent_dc[k] = (int)dc;
+        p = std::max<int>(p, (int)std::llabs(dc));
+    }
+    if (p > PMAX) {
+        g_last_error = "block preconditioner bandwidth " + std::to_string(p) + " exceeds the supported " + std::to_string(PMAX);
+        return VBK_ERR_UNSUPPORTED;
+    }
+    bp->p = p;
+    return VBK_OK;
+}

@@ -1,0 +1,262 @@
+// Internal declarations of the vibronic-continuum Krylov library (sm_103a).
+//
+// Data layout in HBM (all per-system vectors contiguous, system-major):
+//   vector of one system : [d][n_1]...[n_M]  (d slowest, last mode fastest), N entries
+//   batch of vectors     : [system][N]        complex (float2 or double2)
+//   energy tables        : [energy][N]        the diagonal of A(E) for each distinct energy
+//   block factors        : [energy][row c][k = 0..p][block]  (block index fastest)
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/vbk.h"
+
+#define MAXM VBK_MAX_MODES
+#define MAXS VBK_MAX_STATES
+#define MAXCH VBK_MAX_CHANNELS
+#define PMAX 16  // widest band handled by the thread-per-block LDL^T kernels
+
+// ------------------------------------------------------------------------------- complex
+template <class R> struct cx_t;
+template <> struct cx_t<float> { typedef float2 T; };
+template <> struct cx_t<double> { typedef double2 T; };
+template <class R> using cx = typename cx_t<R>::T;
+
+template <class R> __host__ __device__ __forceinline__ cx<R> mkc(R a, R b) {
+    cx<R> z;
+    z.x = a;
+    z.y = b;
+    return z;
+}
+template <class R> __host__ __device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return mkc<R>(a.x + b.x, a.y + b.y); }
+template <class R> __host__ __device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return mkc<R>(a.x - b.x, a.y - b.y); }
+template <class R> __host__ __device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+    return mkc<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class R> __host__ __device__ __forceinline__ cx<R> cscale(cx<R> a, R s) { return mkc<R>(a.x * s, a.y * s); }
+// conj(a) * b
+template <class R> __host__ __device__ __forceinline__ cx<R> cconjmul(cx<R> a, cx<R> b) {
+    return mkc<R>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// acc + a*b
+template <class R> __host__ __device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc) {
+    return mkc<R>(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+template <class R> __host__ __device__ __forceinline__ cx<R> cdiv(cx<R> a, cx<R> b) {
+    R den = b.x * b.x + b.y * b.y;
+    return mkc<R>((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+template <class R> __host__ __device__ __forceinline__ R cabs2(cx<R> a) { return a.x * a.x + a.y * a.y; }
+
+__host__ __device__ __forceinline__ float2 to_f(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__host__ __device__ __forceinline__ double2 to_d(float2 a) { return make_double2(a.x, a.y); }
+template <class R> __host__ __device__ __forceinline__ cx<R> cvt_from_d(double2 a);
+template <> __host__ __device__ __forceinline__ float2 cvt_from_d<float>(double2 a) { return to_f(a); }
+template <> __host__ __device__ __forceinline__ double2 cvt_from_d<double>(double2 a) { return a; }
+template <class R> __host__ __device__ __forceinline__ double2 cvt_to_d(cx<R> a) { return make_double2((double)a.x, (double)a.y); }
+
+// --------------------------------------------------------------------------- model tables
+// One off-diagonal point of the q-polynomial stencil: a (term, offset) pair.  For output
+// element (d, nu) it contributes  -coef * prod_m tab[col[m] + n_m] * x[dp][nu + lin].
+// col[m] < 0 means the term does not involve mode m (factor 1, delta 0).
+struct DevEntry {
+    double coef;
+    int dp;
+    int lin;
+    int col[MAXM];
+    int delta[MAXM];
+};
+
+struct DevModel {
+    int ns, M, Nnu, N, nmu, nchan;
+    int nb[MAXM], stride[MAXM];
+    double omega[MAXM];
+    int ebeg[MAXS + 1];  // off-diagonal stencil points of output state d: [ebeg[d], ebeg[d+1])
+    int dbeg[MAXS + 1];  // diagonal parts (delta = 0, dp = d) of the terms of state d
+    const DevEntry* ent;
+    const DevEntry* dent;
+    const double* tab64;
+    const float* tab32;
+    int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
+    double ch_a[MAXCH], ch_b[MAXCH];
+    int mu_d[MAXCH];  // discrete state coupled to partial wave mu
+};
+
+// Host copy of a term, channel etc.
+struct HostEntry {
+    int d;       // output state
+    int term;    // index of the generating term (for gradients)
+    int mirror;  // 1 if this point comes from the transposed block of an off-diagonal term
+    DevEntry e;
+};
+
+struct KTimer {
+    std::string name;
+    long long launches = 0;
+    double ms = 0.0;
+};
+
+struct vbk_model {
+    vbk_model_desc desc;  // with pointers into the vectors below
+    std::vector<vbk_term> terms;
+    std::vector<vbk_channel> chans;
+    int M = 0, ns = 0, Nnu = 0, N = 0, nmu = 0;
+    int nb[MAXM] = {0}, stride[MAXM] = {0};
+    std::vector<double> tab;          // per-(mode, power, offset) columns of (q^k)_{n, n+delta}
+    std::vector<HostEntry> offd;      // off-diagonal stencil points, grouped by d
+    std::vector<HostEntry> diagp;     // diagonal parts, grouped by d
+    std::vector<std::vector<int>> colbase;  // colbase[m][k] = start of power k columns in tab
+    DevModel dm{};
+    void* dev_mem = nullptr;  // one allocation holding entries and tables
+    // bookkeeping of the last solve
+    std::vector<KTimer> timers;
+    long long launches = 0;
+    int device = 0;
+};
+
+// --------------------------------------------------------------------------- level shift
+// Dawson's integral D(x) = exp(-x^2) int_0^x exp(t^2) dt.  Taylor series for |x| < 0.5;
+// otherwise Rybicki's sampling-theorem method (G. B. Rybicki, Computers in Physics 3, 85
+// (1989)): D(x) = lim_{h->0} pi^-1/2 sum_{n odd} exp(-(x - n h)^2) / n, here with h = 1/4
+// (aliasing error ~exp(-(pi/2h)^2) ~ 1e-17), the sum centred on the even integer n0 nearest
+// x/h and the Gaussian factors generated by exact multiplicative recurrences.
+__host__ __device__ inline double vbk_dawson(double x) {
+    double ax = fabs(x);
+    double r;
+    if (ax < 0.5) {
+        double x2 = ax * ax, term = ax, sum = ax;
+        for (int k = 1; k < 22; ++k) {
+            term *= -2.0 * x2 / (2.0 * k + 1.0);
+            sum += term;
+        }
+        r = sum;
+    } else {
+        const double h = 0.25;
+        double n0 = 2.0 * rint(0.5 * ax / h);
+        double xp = ax - n0 * h;           // |xp| <= h
+        double e1 = exp(2.0 * xp * h);     // exp(2 xp h)
+        double e2 = e1 * e1, ie1 = 1.0 / e1, ie2 = ie1 * ie1;
+        double pk = e1, qk = ie1;          // exp(+-2 xp h (2k-1))
+        double ck = 0.93941306281347581;   // exp(-h^2)          = exp(-(2k-1)^2 h^2), k = 1
+        double rk = 0.60653065971263342;   // exp(-8 h^2 k), k=1 = exp(-1/2)
+        const double q = 0.60653065971263342;
+        double sum = 0.0;
+        for (int k = 1; k <= 14; ++k) {
+            double odd = 2.0 * k - 1.0;
+            sum += ck * (pk / (n0 + odd) + qk / (n0 - odd));
+            pk *= e2;
+            qk *= ie2;
+            ck *= rk;   // c_{k+1} = c_k exp(-8 k h^2)
+            rk *= q;
+        }
+        r = exp(-xp * xp) * sum * 0.56418958354775628;  // 1/sqrt(pi)
+    }
+    return x < 0 ? -r : r;
+}
+
+// exp(y^2) erfc(y), y >= 0
+__host__ __device__ inline double vbk_erfcx(double y) {
+#ifdef __CUDA_ARCH__
+    return erfcx(y);
+#else
+    if (y < 25.0) return std::exp(y * y) * std::erfc(y);
+    double y2 = y * y;  // asymptotic series, relative error < 1e-16 for y >= 25
+    return 0.56418958354775628 / y * (1.0 - 0.5 / y2 + 0.75 / (y2 * y2) - 1.875 / (y2 * y2 * y2));
+#endif
+}
+
+// F[f](eps) for f(x) = (a / 2 pi) x^(l+1/2) exp(-b x), x > 0 (Eq. IntF with the widths of
+// Sec. II.B):  (a/2pi) [ P_l(eps) - i pi eps^(l+1/2) exp(-b eps) theta(eps) ]  with
+//   P_l = -Gamma(l+1/2) b^-(l+1/2) + eps P_(l-1),
+//   eps P_(-1) = 2 sqrt(pi eps) D(sqrt(b eps))  (eps > 0),  pi sqrt(-eps) erfcx(sqrt(-b eps))
+//   (eps < 0), 0 (eps = 0).
+__host__ __device__ inline double2 vbk_level_shift_eval(double eps, double a, double b, int l) {
+    const double PI = 3.14159265358979323846;
+    double t;
+    if (eps > 0.0)
+        t = 2.0 * sqrt(PI * eps) * vbk_dawson(sqrt(b * eps));
+    else if (eps < 0.0)
+        t = PI * sqrt(-eps) * vbk_erfcx(sqrt(-b * eps));
+    else
+        t = 0.0;
+    double g = 1.7724538509055160;  // Gamma(1/2) = sqrt(pi)
+    double bp = sqrt(b);            // b^(k+1/2) for k = 0
+    double p = -g / bp + t;
+    for (int k = 1; k <= l; ++k) {
+        g *= (k - 0.5);  // Gamma(k + 1/2)
+        bp *= b;
+        p = -g / bp + eps * p;
+    }
+    double im = 0.0;
+    if (eps > 0.0) im = -0.5 * a * pow(eps, l + 0.5) * exp(-b * eps);
+    return make_double2(a / (2.0 * PI) * p, im);
+}
+
+// f(eps) = sqrt(Gamma(eps) / 2 pi), zero for eps <= 0 (reading: closed channels do not couple)
+__host__ __device__ inline double vbk_amplitude(double eps, double a, double b, int l) {
+    if (!(eps > 0.0)) return 0.0;
+    const double PI = 3.14159265358979323846;
+    return sqrt(a * pow(eps, l + 0.5) * exp(-b * eps) / (2.0 * PI));
+}
+
+// --------------------------------------------------------------------------- helpers
+void vbk_set_error(const std::string& msg);
+int vbk_cuda_fail(cudaError_t e, const char* what);
+#define VBK_CUDA(call)                                             \
+    do {                                                           \
+        cudaError_t e__ = (call);                                  \
+        if (e__ != cudaSuccess) return vbk_cuda_fail(e__, #call);  \
+    } while (0)
+
+// Per-system solver state (device).
+struct SysState {
+    double bnorm;    // ||b|| (FP64)
+    double rnorm;    // ||b - A x|| of the last FP64 residual
+    double scale;    // ||r|| used to scale the inner right-hand side
+    double target;   // inner stopping threshold relative to the (unit) inner rhs
+    double2 rho;     // COCG r^T z
+    double2 alpha;
+    double2 beta;
+    double inres;    // inner residual norm
+    int status;
+    int outer;       // 1 while the system still needs work
+    int inner;       // 1 while the inner solve runs
+    int iters;       // Krylov iterations
+    int refines;     // FP64 residuals after the first
+    int j;           // GMRES: steps in the current cycle
+    int cycle_iters; // iterations in the current inner solve
+    int pad;
+};
+
+// Internal solve over an explicit list of systems with dense FP64 right-hand sides.
+struct SolveJob {
+    int nsys = 0;
+    int nE = 0;
+    std::vector<double> E;      // distinct total energies
+    std::vector<int> sys_e;     // energy index of each system
+    const double2* b64 = nullptr;  // device [nsys][N]
+    double2* x64 = nullptr;        // device [nsys][N] (output)
+};
+int vbk_solve_job(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stats* st, cudaStream_t stream);
+
+// Block-preconditioner plan (Sec. III.B)
+struct BlockPlan {
+    int span = 0;
+    int L = 1;      // chain (block) length
+    int nblk = 0;   // blocks per energy
+    int p = 0;      // half bandwidth in chain order
+    std::vector<int> ent_dc;  // per off-diagonal stencil point: chain offset (0 = outside block)
+};
+int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* plan);
+
+// launch helpers implemented in vbk_kernels.cu
+struct Launch;
+
+// y = A x (op 0) or z = B^-1 r (op 1) outside a solve (implemented in vbk_solver.cu)
+int vbk_operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
+                     int precision, cudaStream_t st);

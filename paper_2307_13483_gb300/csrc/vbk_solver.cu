@@ -1,0 +1,1362 @@
+// Batched preconditioned Krylov solver for (E - H_ef) psi = Phi on sm_103a.
+//
+// Hot path of Sec. III: the matrix-free matvec (diagonal energy/level-shift factors plus the
+// q-polynomial ladder stencils), block-diagonal preconditioners factored as L D L^T
+// (Sec. III.B), restarted GMRES with CGS2 Arnoldi and an FP64 Givens least-squares problem,
+// and COCG with the bilinear form a^T b (Sec. III.A).  Every (energy, initial state, partial
+// wave) system of a batch is advanced by the same grid-wide kernels; a per-system mask
+// retires converged systems.  The Krylov iterations run in complex FP32 or FP64 inside an FP64
+// iterative-refinement loop whose residual b - A x is always evaluated in FP64.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "vbk_internal.cuh"
+
+namespace {
+
+constexpr int TPB = 256;       // threads per block, element-wise kernels
+constexpr int VEPT = 4;        // elements per thread in the basis-vector kernels
+constexpr int VCHUNK = TPB * VEPT;
+constexpr int BTPB = 64;       // threads per block, block-preconditioner kernels
+// narrowing / widening helpers used by the stand-alone entry points
+__global__ void k_inner_rhs_plain(long long n, const double2* __restrict__ a, float2* __restrict__ b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = to_f(a[i]);
+}
+__global__ void k_widen(long long n, const float2* __restrict__ a, double2* __restrict__ b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = to_d(a[i]);
+}
+
+// ----------------------------------------------------------------------------- reductions
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  `sh` holds >= 32 double2.
+__device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
+    v = warp_sum2(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? sh[lane] : make_double2(0.0, 0.0);
+        r = warp_sum2(r);
+    }
+    return r;
+}
+
+template <class R> __device__ __forceinline__ const R* tabp(const DevModel& md);
+template <> __device__ __forceinline__ const float* tabp<float>(const DevModel& md) { return md.tab32; }
+template <> __device__ __forceinline__ const double* tabp<double>(const DevModel& md) { return md.tab64; }
+
+template <int M> __device__ __forceinline__ void decode(const DevModel& md, int nu, int (&n)[MAXM]) {
+    int rem = nu;
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) {
+        n[m] = rem % md.nb[m];
+        rem /= md.nb[m];
+    }
+#pragma unroll
+    for (int m = M; m < MAXM; ++m) n[m] = 0;
+}
+
+// Coefficient of one stencil point at oscillator coordinates n; false if the neighbour lies
+// outside the truncated basis (the table holds zero there as well).
+template <class R, int M>
+__device__ __forceinline__ bool point_coef(const DevEntry& en, const int (&n)[MAXM], const DevModel& md, const R* tab,
+                                           R& c) {
+    R v = (R)en.coef;
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int col = en.col[m];
+        if (col >= 0) {
+            const int nn = n[m] + en.delta[m];
+            ok = ok && nn >= 0 && nn < md.nb[m];
+            v *= tab[col + n[m]];
+        }
+    }
+    c = v;
+    return ok;
+}
+
+// ------------------------------------------------------------------------ level-shift table
+// diag[e][i] = E_e - E_nu - (delta = 0 part of U_dd)(nu) - sum_{channels of d} F(E_e - E_nu)
+// (Eqs. H_ef, Amatrix; Sec. III "energy-dependent diagonal factors"), FP64, with an optional
+// FP32 copy for the inner iterations.
+template <int M>
+__global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, double2* __restrict__ d64,
+                             float2* __restrict__ d32) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nE * md.N) return;
+    const int e = (int)(t / md.N), i = (int)(t - (long long)e * md.N);
+    const int d = i / md.Nnu, nu = i - d * md.Nnu;
+    int n[MAXM];
+    decode<M>(md, nu, n);
+    double en = 0.0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) en += md.omega[m] * (n[m] + 0.5);
+    const double eps = E[e] - en;
+    double re = eps, im = 0.0;
+    for (int k = md.dbeg[d]; k < md.dbeg[d + 1]; ++k) {
+        const DevEntry p = md.dent[k];
+        double c;
+        point_coef<double, M>(p, n, md, md.tab64, c);
+        re -= c;
+    }
+    for (int c = 0; c < md.nchan; ++c) {
+        if (md.ch_d[c] != d) continue;
+        const double2 F = vbk_level_shift_eval(eps, md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+        re -= F.x;
+        im -= F.y;
+    }
+    d64[t] = make_double2(re, im);
+    if (d32) d32[t] = make_float2((float)re, (float)im);
+}
+
+// ------------------------------------------------------------------------------- matvec
+// y = A x  (or y = b - A x when b != nullptr) for every active system s with energy
+// sys_e[s]; optional fused reduction: red = 1 -> x^T y (bilinear), red = 2 -> ||y||^2.
+template <class R, int M>
+__global__ void __launch_bounds__(TPB) k_matvec(DevModel md, const int* __restrict__ sys_e, const int* __restrict__ act,
+                                               const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x, long long xs,
+                                               cx<R>* __restrict__ y, long long ys, const double2* __restrict__ b,
+                                               double2* __restrict__ part, int red) {
+    __shared__ double2 sh[32];
+    const int s = blockIdx.y;
+    if (act && !act[s]) return;
+    const int N = md.N;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const cx<R>* xv = x + (long long)s * xs;
+    double2 loc = make_double2(0.0, 0.0);
+    if (i < N) {
+        const int e = sys_e[s];
+        const int d = i / md.Nnu, nu = i - d * md.Nnu;
+        int n[MAXM];
+        decode<M>(md, nu, n);
+        const cx<R> xi = xv[i];
+        cx<R> acc = cmul<R>(diag[(long long)e * N + i], xi);
+        const R* tab = tabp<R>(md);
+        for (int k = md.ebeg[d]; k < md.ebeg[d + 1]; ++k) {
+            const DevEntry p = md.ent[k];
+            R c;
+            if (point_coef<R, M>(p, n, md, tab, c)) {
+                const cx<R> v = xv[p.dp * md.Nnu + nu + p.lin];
+                acc.x -= c * v.x;
+                acc.y -= c * v.y;
+            }
+        }
+        if (b) {
+            const double2 bb = b[(long long)s * N + i];
+            acc = mkc<R>((R)bb.x - acc.x, (R)bb.y - acc.y);
+        }
+        y[(long long)s * ys + i] = acc;
+        if (red == 1) {
+            const cx<R> t = cmul<R>(xi, acc);
+            loc = make_double2((double)t.x, (double)t.y);
+        } else if (red == 2) {
+            loc = make_double2((double)cabs2<R>(acc), 0.0);
+        }
+    }
+    if (red) {
+        const double2 tot = block_sum2(loc, sh);
+        if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// ---------------------------------------------------------------- block preconditioner
+struct PlanDev {
+    int L, nblk, p, span;
+    const int* chain_off;   // [L]   element offset of chain position c (relative)
+    const int* fixed_base;  // [nblk] element index of chain position 0 of each block
+    const int* ent_dc;      // [n off-diagonal points] chain offset of the point, 0 if outside
+};
+
+// B = L D L^T of every block of every energy (Sec. III.B: factors computed once and stored).
+// One thread per (energy, block); F[e][c][k][blk]: k = 0 holds 1/D_c, k >= 1 holds L_{c,c-k}.
+template <class R, int M>
+__global__ void k_block_factor(DevModel md, PlanDev pl, int nE, const cx<R>* __restrict__ diag, cx<R>* __restrict__ F,
+                               int* __restrict__ fail) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nE * pl.nblk) return;
+    const int e = (int)(t / pl.nblk), blk = (int)(t - (long long)e * pl.nblk);
+    const int L = pl.L, p = pl.p, nblk = pl.nblk;
+    const int base = pl.fixed_base[blk];
+    const R* tab = tabp<R>(md);
+    cx<R>* Fe = F + (long long)e * L * (p + 1) * nblk;
+    auto Fat = [&](int c, int k) -> cx<R>& { return Fe[((long long)c * (p + 1) + k) * nblk + blk]; };
+    cx<R> Dw[PMAX + 1];  // D of the last p rows (rolling)
+    cx<R> row[PMAX + 1];
+    bool bad = false;
+    for (int c = 0; c < L; ++c) {
+        const int i = base + pl.chain_off[c];
+        const int d = i / md.Nnu, nu = i - d * md.Nnu;
+        int n[MAXM];
+        decode<M>(md, nu, n);
+        for (int k = 0; k <= p; ++k) row[k] = mkc<R>(0, 0);
+        row[0] = diag[(long long)e * md.N + i];
+        for (int k = md.ebeg[d]; k < md.ebeg[d + 1]; ++k) {
+            const int dc = pl.ent_dc[k];
+            if (dc >= 0 || dc < -p || c + dc < 0) continue;
+            const DevEntry pt = md.ent[k];
+            R cf;
+            if (point_coef<R, M>(pt, n, md, tab, cf)) row[-dc].x -= cf;
+        }
+        // row[k] now holds B[c][c-k]; eliminate left to right
+        for (int jj = max(0, c - p); jj < c; ++jj) {
+            const int kj = c - jj;
+            cx<R> sacc = row[kj];
+            for (int tt = max(max(0, c - p), jj - p); tt < jj; ++tt) {
+                const cx<R> lct = row[c - tt];           // L[c][tt] (final)
+                const cx<R> ljt = Fat(jj, jj - tt);       // L[jj][tt]
+                sacc = csub<R>(sacc, cmul<R>(cmul<R>(lct, Dw[tt % (PMAX + 1)]), ljt));
+            }
+            row[kj] = cmul<R>(sacc, Fat(jj, 0));          // / D[jj]
+        }
+        cx<R> dc0 = row[0];
+        for (int tt = max(0, c - p); tt < c; ++tt) {
+            const cx<R> l = row[c - tt];
+            dc0 = csub<R>(dc0, cmul<R>(cmul<R>(l, l), Dw[tt % (PMAX + 1)]));
+        }
+        cx<R> inv;
+        const R a2 = cabs2<R>(dc0);
+        if (!(a2 > (R)0) || !isfinite(a2)) {
+            bad = true;
+            inv = mkc<R>(0, 0);
+        } else {
+            inv = mkc<R>(dc0.x / a2, -dc0.y / a2);
+        }
+        Dw[c % (PMAX + 1)] = dc0;
+        Fat(c, 0) = inv;
+        for (int k = 1; k <= p; ++k) Fat(c, k) = (k <= c) ? row[k] : mkc<R>(0, 0);
+    }
+    if (bad) atomicExch(fail + e, 1);
+}
+
+// z = B^-1 r for every block of every active system; optional fused rz = r^T z partials.
+// Grid: (ceil(nblk / BTPB), nsys).
+template <class R>
+__global__ void __launch_bounds__(BTPB) k_block_apply(PlanDev pl, const int* __restrict__ sys_e, const int* __restrict__ act,
+                                                     const cx<R>* __restrict__ F, const cx<R>* __restrict__ r, long long rs,
+                                                     cx<R>* __restrict__ z, long long zs, double2* __restrict__ part) {
+    __shared__ double2 sh[32];
+    const int s = blockIdx.y;
+    if (act && !act[s]) return;
+    const int blk = blockIdx.x * blockDim.x + threadIdx.x;
+    const int L = pl.L, p = pl.p, nblk = pl.nblk;
+    double2 loc = make_double2(0.0, 0.0);
+    if (blk < nblk) {
+        const int e = sys_e[s];
+        const cx<R>* Fe = F + (long long)e * L * (p + 1) * nblk + blk;
+        const cx<R>* rv = r + (long long)s * rs;
+        cx<R>* zv = z + (long long)s * zs;
+        const int base = pl.fixed_base[blk];
+        // forward: w_c = r_c - sum_k L[c][c-k] w_{c-k}
+        for (int c = 0; c < L; ++c) {
+            cx<R> w = rv[base + pl.chain_off[c]];
+            const int kmax = min(p, c);
+            for (int k = 1; k <= kmax; ++k)
+                w = csub<R>(w, cmul<R>(Fe[((long long)c * (p + 1) + k) * nblk], zv[base + pl.chain_off[c - k]]));
+            zv[base + pl.chain_off[c]] = w;
+        }
+        // backward: z_c = w_c / D_c - sum_k L[c+k][c] z_{c+k}
+        for (int c = L - 1; c >= 0; --c) {
+            const int ic = base + pl.chain_off[c];
+            cx<R> v = cmul<R>(zv[ic], Fe[((long long)c * (p + 1)) * nblk]);
+            const int kmax = min(p, L - 1 - c);
+            for (int k = 1; k <= kmax; ++k)
+                v = csub<R>(v, cmul<R>(Fe[((long long)(c + k) * (p + 1) + k) * nblk], zv[base + pl.chain_off[c + k]]));
+            zv[ic] = v;
+            if (part) {
+                const cx<R> t = cmul<R>(rv[ic], v);
+                loc.x += (double)t.x;
+                loc.y += (double)t.y;
+            }
+        }
+    }
+    if (part) {
+        const double2 tot = block_sum2(loc, sh);
+        if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// Point preconditioners: mode 0 -> z = r / diag (Jacobi), mode -1 -> z = r.  Optional r^T z.
+template <class R>
+__global__ void __launch_bounds__(TPB) k_point_precond(int N, const int* __restrict__ sys_e, const int* __restrict__ act,
+                                                      int mode, const cx<R>* __restrict__ diag, const cx<R>* __restrict__ r,
+                                                      long long rs, cx<R>* __restrict__ z, long long zs,
+                                                      double2* __restrict__ part) {
+    __shared__ double2 sh[32];
+    const int s = blockIdx.y;
+    if (act && !act[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double2 loc = make_double2(0.0, 0.0);
+    if (i < N) {
+        const cx<R> ri = r[(long long)s * rs + i];
+        cx<R> zi = ri;
+        if (mode == 0) zi = cdiv<R>(ri, diag[(long long)sys_e[s] * N + i]);
+        z[(long long)s * zs + i] = zi;
+        const cx<R> t = cmul<R>(ri, zi);
+        loc = make_double2((double)t.x, (double)t.y);
+    }
+    if (part) {
+        const double2 tot = block_sum2(loc, sh);
+        if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// ------------------------------------------------------------------- refinement (FP64)
+// First outer step: r = b (x = 0), partial ||r||^2.
+__global__ void __launch_bounds__(TPB) k_copy_b(int N, const int* __restrict__ act, const double2* __restrict__ b,
+                                               double2* __restrict__ r, double2* __restrict__ part) {
+    __shared__ double2 sh[32];
+    const int s = blockIdx.y;
+    if (act && !act[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double2 loc = make_double2(0.0, 0.0);
+    if (i < N) {
+        const double2 v = b[(long long)s * N + i];
+        r[(long long)s * N + i] = v;
+        loc.x = v.x * v.x + v.y * v.y;
+    }
+    const double2 tot = block_sum2(loc, sh);
+    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
+}
+
+// Outer convergence test on the FP64 residual (stopping rule of Sec. III, true residual).
+__global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restrict__ outer, int* __restrict__ inner,
+                              const double2* __restrict__ part, int nb, int first, double tol, double inner_tol,
+                              int max_refine, int max_iter, int* __restrict__ count) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    inner[s] = 0;
+    if (!outer[s]) return;
+    double rr = 0.0;
+    for (int k = 0; k < nb; ++k) rr += part[(long long)s * nb + k].x;
+    const double rn = sqrt(rr);
+    SysState& S = st[s];
+    if (first) {
+        S.bnorm = rn;
+        if (rn == 0.0) {
+            S.status = VBK_SYS_ZERO_RHS;
+            S.rnorm = 0.0;
+            outer[s] = 0;
+            return;
+        }
+    } else {
+        S.refines += 1;
+    }
+    S.rnorm = rn;
+    if (!isfinite(rn)) {
+        S.status = VBK_SYS_NAN;
+        outer[s] = 0;
+        return;
+    }
+    if (rn <= tol * S.bnorm) {
+        S.status = VBK_SYS_CONVERGED;
+        outer[s] = 0;
+        return;
+    }
+    if (S.refines >= max_refine || S.iters >= max_iter) {
+        S.status = VBK_SYS_MAX_ITER;
+        outer[s] = 0;
+        return;
+    }
+    S.scale = rn;
+    S.target = fmax(inner_tol, 0.3 * tol * S.bnorm / rn);
+    S.j = 0;
+    S.cycle_iters = 0;
+    S.inres = 1.0;
+    inner[s] = 1;
+    atomicAdd(count, 1);
+}
+
+// inner right-hand side r / ||r|| in the inner precision
+template <class R>
+__global__ void __launch_bounds__(TPB) k_inner_rhs(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+                                                  const double2* __restrict__ r, cx<R>* __restrict__ out, long long os) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double inv = 1.0 / st[s].scale;
+    const double2 v = r[(long long)s * N + i];
+    out[(long long)s * os + i] = cvt_from_d<R>(make_double2(v.x * inv, v.y * inv));
+}
+
+// x += ||r|| d (FP64 accumulation of the inner correction)
+template <class R>
+__global__ void __launch_bounds__(TPB) k_accumulate(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+                                                   const cx<R>* __restrict__ dv, long long ds, double2* __restrict__ x) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double sc = st[s].scale;
+    const double2 v = cvt_to_d<R>(dv[(long long)s * ds + i]);
+    double2 xv = x[(long long)s * N + i];
+    xv.x += sc * v.x;
+    xv.y += sc * v.y;
+    x[(long long)s * N + i] = xv;
+}
+
+// ----------------------------------------------------------------------------- COCG
+// Two-term preconditioned COCG (Sec. III.A; van der Vorst & Melissen):
+//   q = A p; alpha = rho / p^T q; x += alpha p; r -= alpha q; z = B^-1 r; rho' = r^T z;
+//   beta = rho'/rho; p = z + beta p.
+__global__ void k_cocg_start(int nsys, SysState* __restrict__ st, const int* __restrict__ act,
+                             const double2* __restrict__ part_rz, int nb) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys || !act[s]) return;
+    double2 rz = make_double2(0.0, 0.0);
+    for (int k = 0; k < nb; ++k) {
+        rz.x += part_rz[(long long)s * nb + k].x;
+        rz.y += part_rz[(long long)s * nb + k].y;
+    }
+    st[s].rho = rz;
+    st[s].beta = make_double2(0.0, 0.0);
+}
+
+__global__ void k_cocg_alpha(int nsys, SysState* __restrict__ st, int* __restrict__ act, int* __restrict__ outer,
+                             const double2* __restrict__ part, int nb) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys || !act[s]) return;
+    double2 pq = make_double2(0.0, 0.0);
+    for (int k = 0; k < nb; ++k) {
+        pq.x += part[(long long)s * nb + k].x;
+        pq.y += part[(long long)s * nb + k].y;
+    }
+    SysState& S = st[s];
+    const double den = pq.x * pq.x + pq.y * pq.y;
+    if (!(den > 0.0) || !isfinite(den)) {
+        S.status = isfinite(den) ? VBK_SYS_BREAKDOWN : VBK_SYS_NAN;
+        S.alpha = make_double2(0.0, 0.0);
+        act[s] = 0;
+        outer[s] = 0;
+        return;
+    }
+    S.alpha = cdiv<double>(S.rho, pq);
+}
+
+template <class R>
+__global__ void __launch_bounds__(TPB) k_cocg_update(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+                                                    const int* __restrict__ sys_e, int pmode, const cx<R>* __restrict__ diag,
+                                                    cx<R>* __restrict__ x, cx<R>* __restrict__ r, const cx<R>* __restrict__ p,
+                                                    const cx<R>* __restrict__ q, cx<R>* __restrict__ z,
+                                                    double2* __restrict__ part_rr, double2* __restrict__ part_rz) {
+    __shared__ double2 sh[32];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double2 lrr = make_double2(0.0, 0.0), lrz = make_double2(0.0, 0.0);
+    if (i < N) {
+        const long long o = (long long)s * N + i;
+        const cx<R> al = cvt_from_d<R>(st[s].alpha);
+        x[o] = cfma<R>(al, p[o], x[o]);
+        const cx<R> qa = cmul<R>(al, q[o]);
+        const cx<R> rn = csub<R>(r[o], qa);
+        r[o] = rn;
+        lrr.x = (double)cabs2<R>(rn);
+        if (pmode <= 0) {
+            const cx<R> zi = pmode == 0 ? cdiv<R>(rn, diag[(long long)sys_e[s] * N + i]) : rn;
+            z[o] = zi;
+            const cx<R> t = cmul<R>(rn, zi);
+            lrz = make_double2((double)t.x, (double)t.y);
+        }
+    }
+    double2 tot = block_sum2(lrr, sh);
+    if (threadIdx.x == 0) part_rr[(long long)s * gridDim.x + blockIdx.x] = tot;
+    if (pmode <= 0) {
+        tot = block_sum2(lrz, sh);
+        if (threadIdx.x == 0) part_rz[(long long)s * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+__global__ void k_cocg_beta(int nsys, SysState* __restrict__ st, int* __restrict__ act, int* __restrict__ outer,
+                            const double2* __restrict__ part_rr, int nb_rr, const double2* __restrict__ part_rz, int nb_rz,
+                            int max_iter, int* __restrict__ count) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys || !act[s]) return;
+    SysState& S = st[s];
+    double rr = 0.0;
+    for (int k = 0; k < nb_rr; ++k) rr += part_rr[(long long)s * nb_rr + k].x;
+    double2 rz = make_double2(0.0, 0.0);
+    for (int k = 0; k < nb_rz; ++k) {
+        rz.x += part_rz[(long long)s * nb_rz + k].x;
+        rz.y += part_rz[(long long)s * nb_rz + k].y;
+    }
+    S.iters += 1;
+    S.cycle_iters += 1;
+    const double rn = sqrt(rr);
+    S.inres = rn;
+    if (!isfinite(rn) || !isfinite(rz.x) || !isfinite(rz.y)) {
+        act[s] = 0;  // the outer FP64 residual decides (a NaN there ends the system)
+        return;
+    }
+    if (rn <= S.target || S.iters >= max_iter) {
+        act[s] = 0;
+        return;
+    }
+    const double den = S.rho.x * S.rho.x + S.rho.y * S.rho.y;
+    if (!(rz.x * rz.x + rz.y * rz.y > 0.0) || !(den > 0.0)) {
+        S.status = VBK_SYS_BREAKDOWN;
+        act[s] = 0;
+        outer[s] = 0;
+        return;
+    }
+    S.beta = cdiv<double>(rz, S.rho);
+    S.rho = rz;
+    atomicAdd(count, 1);
+}
+
+template <class R>
+__global__ void __launch_bounds__(TPB) k_cocg_p(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+                                               const cx<R>* __restrict__ z, cx<R>* __restrict__ p) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long o = (long long)s * N + i;
+    const cx<R> be = cvt_from_d<R>(st[s].beta);
+    p[o] = cfma<R>(be, p[o], z[o]);
+}
+
+// ---------------------------------------------------------------------------- GMRES
+// Restarted GMRES(m) with right preconditioning (Sec. III.A; Saad & Schultz): Arnoldi
+// A B^-1 V_n = V_{n+1} H_n with classical Gram-Schmidt applied twice (CGS2), the
+// (n+1) x n least-squares problem solved by complex Givens rotations in FP64.
+// V of system s: [s][k = 0..m][N] in the inner precision.
+
+// partial h_k = sum_i conj(V_k[i]) w[i], k = 0..j;  part[s][blk][k], (m+1) slots
+template <class R>
+__global__ void __launch_bounds__(TPB) k_vdots(int N, int m, const int* __restrict__ act, const cx<R>* __restrict__ V,
+                                              int j, const cx<R>* __restrict__ w, double2* __restrict__ part) {
+    __shared__ double2 sh[(TPB / 32) * 257];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const long long vs = (long long)(m + 1) * N;
+    const cx<R>* Vs = V + s * vs;
+    const cx<R>* ws = w + (long long)s * N;
+    const int i0 = blockIdx.x * VCHUNK + threadIdx.x;
+    cx<R> wl[VEPT];
+#pragma unroll
+    for (int u = 0; u < VEPT; ++u) {
+        const int i = i0 + u * TPB;
+        wl[u] = i < N ? ws[i] : mkc<R>(0, 0);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int k = 0; k <= j; ++k) {
+        const cx<R>* vk = Vs + (long long)k * N;
+        cx<R> a = mkc<R>(0, 0);
+#pragma unroll
+        for (int u = 0; u < VEPT; ++u) {
+            const int i = i0 + u * TPB;
+            if (i < N) {
+                const cx<R> t = cconjmul<R>(vk[i], wl[u]);
+                a.x += t.x;
+                a.y += t.y;
+            }
+        }
+        double2 dv = warp_sum2(make_double2((double)a.x, (double)a.y));
+        if (lane == 0) sh[wp * 257 + k] = dv;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int q = 0; q < TPB / 32; ++q) {
+            t.x += sh[q * 257 + k].x;
+            t.y += sh[q * 257 + k].y;
+        }
+        part[((long long)s * gridDim.x + blockIdx.x) * (m + 1) + k] = t;
+    }
+}
+
+// h[s][k] = sum over blocks of part[s][blk][k]
+__global__ void k_hreduce(int nsys, int m, const int* __restrict__ act, int j, const double2* __restrict__ part, int nb,
+                          double2* __restrict__ h) {
+    const int s = blockIdx.x;
+    if (s >= nsys || !act[s]) return;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int b = 0; b < nb; ++b) {
+            const double2 v = part[((long long)s * nb + b) * (m + 1) + k];
+            t.x += v.x;
+            t.y += v.y;
+        }
+        h[(long long)s * (m + 1) + k] = t;
+    }
+}
+
+// w -= sum_k V_k h_k; then (mode 0) partial dots conj(V_k) w, or (mode 1) partial ||w||^2
+template <class R>
+__global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, const int* __restrict__ act, const cx<R>* __restrict__ V,
+                                                int j, const double2* __restrict__ h, cx<R>* __restrict__ w, int mode,
+                                                double2* __restrict__ part) {
+    __shared__ double2 sh[(TPB / 32) * 257];
+    __shared__ double2 hs[257];
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) hs[k] = h[(long long)s * (m + 1) + k];
+    __syncthreads();
+    const long long vs = (long long)(m + 1) * N;
+    const cx<R>* Vs = V + s * vs;
+    cx<R>* ws = w + (long long)s * N;
+    const int i0 = blockIdx.x * VCHUNK + threadIdx.x;
+    cx<R> wl[VEPT];
+#pragma unroll
+    for (int u = 0; u < VEPT; ++u) {
+        const int i = i0 + u * TPB;
+        wl[u] = i < N ? ws[i] : mkc<R>(0, 0);
+    }
+    for (int k = 0; k <= j; ++k) {
+        const cx<R>* vk = Vs + (long long)k * N;
+        const cx<R> hk = cvt_from_d<R>(hs[k]);
+#pragma unroll
+        for (int u = 0; u < VEPT; ++u) {
+            const int i = i0 + u * TPB;
+            if (i < N) wl[u] = csub<R>(wl[u], cmul<R>(vk[i], hk));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < VEPT; ++u) {
+        const int i = i0 + u * TPB;
+        if (i < N) ws[i] = wl[u];
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (mode == 0) {
+        for (int k = 0; k <= j; ++k) {
+            const cx<R>* vk = Vs + (long long)k * N;
+            cx<R> a = mkc<R>(0, 0);
+#pragma unroll
+            for (int u = 0; u < VEPT; ++u) {
+                const int i = i0 + u * TPB;
+                if (i < N) {
+                    const cx<R> t = cconjmul<R>(vk[i], wl[u]);
+                    a.x += t.x;
+                    a.y += t.y;
+                }
+            }
+            double2 dv = warp_sum2(make_double2((double)a.x, (double)a.y));
+            if (lane == 0) sh[wp * 257 + k] = dv;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int q = 0; q < TPB / 32; ++q) {
+                t.x += sh[q * 257 + k].x;
+                t.y += sh[q * 257 + k].y;
+            }
+            part[((long long)s * gridDim.x + blockIdx.x) * (m + 1) + k] = t;
+        }
+    } else {
+        double a = 0.0;
+#pragma unroll
+        for (int u = 0; u < VEPT; ++u) a += (double)cabs2<R>(wl[u]);
+        const double2 tot = block_sum2(make_double2(a, 0.0), sh);
+        if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+// Column j of the Hessenberg matrix, Givens rotations and the residual estimate (FP64).
+__global__ void k_givens(int nsys, int m, SysState* __restrict__ st, int* __restrict__ act,
+                         const double2* __restrict__ h1, const double2* __restrict__ h2,
+                         const double2* __restrict__ part_n, int nb, double2* __restrict__ H, double* __restrict__ cs,
+                         double2* __restrict__ sn, double2* __restrict__ g, double* __restrict__ inv_h, int max_iter,
+                         int* __restrict__ count) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys || !act[s]) return;
+    SysState& S = st[s];
+    const int j = S.j;
+    double rr = 0.0;
+    for (int k = 0; k < nb; ++k) rr += part_n[(long long)s * nb + k].x;
+    const double hn = sqrt(rr);
+    double2* Hc = H + ((long long)s * m + j) * (m + 1);  // column j
+    for (int k = 0; k <= j; ++k) {
+        const double2 a = h1[(long long)s * (m + 1) + k], b = h2[(long long)s * (m + 1) + k];
+        Hc[k] = make_double2(a.x + b.x, a.y + b.y);
+    }
+    Hc[j + 1] = make_double2(hn, 0.0);
+    // apply previous rotations
+    double* csv = cs + (long long)s * m;
+    double2* snv = sn + (long long)s * m;
+    double2* gv = g + (long long)s * (m + 1);
+    for (int k = 0; k < j; ++k) {
+        const double c = csv[k];
+        const double2 sk = snv[k];
+        const double2 a = Hc[k], b = Hc[k + 1];
+        const double2 t1 = cmul<double>(sk, b);
+        const double2 t2 = cconjmul<double>(sk, a);  // conj(s) a
+        Hc[k] = make_double2(c * a.x + t1.x, c * a.y + t1.y);
+        Hc[k + 1] = make_double2(c * b.x - t2.x, c * b.y - t2.y);
+    }
+    // new rotation zeroing H[j+1][j]
+    const double2 a = Hc[j], b = Hc[j + 1];
+    const double aa = sqrt(cabs2<double>(a)), bb = sqrt(cabs2<double>(b));
+    double c;
+    double2 sg;
+    if (aa == 0.0) {
+        c = 0.0;
+        sg = make_double2(1.0, 0.0);
+        Hc[j] = b;
+    } else {
+        const double nu = hypot(aa, bb);
+        c = aa / nu;
+        const double2 ph = make_double2(a.x / aa, a.y / aa);
+        sg = cscale<double>(cmul<double>(ph, make_double2(b.x, -b.y)), 1.0 / nu);
+        Hc[j] = cscale<double>(ph, nu);
+    }
+    Hc[j + 1] = make_double2(0.0, 0.0);
+    csv[j] = c;
+    snv[j] = sg;
+    const double2 gj = gv[j];
+    const double2 t = cconjmul<double>(sg, gj);
+    gv[j + 1] = make_double2(-t.x, -t.y);
+    gv[j] = cscale<double>(gj, c);
+    S.j = j + 1;
+    S.iters += 1;
+    S.cycle_iters += 1;
+    const double res = sqrt(cabs2<double>(gv[j + 1]));
+    S.inres = res;
+    inv_h[s] = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (!isfinite(res) || res <= S.target || hn == 0.0 || j + 1 >= m || S.iters >= max_iter) {
+        act[s] = 0;
+        return;
+    }
+    atomicAdd(count, 1);
+}
+
+template <class R>
+__global__ void __launch_bounds__(TPB) k_vscale(int N, int m, const int* __restrict__ act, const double* __restrict__ inv_h,
+                                               const SysState* __restrict__ st, const cx<R>* __restrict__ w,
+                                               cx<R>* __restrict__ V) {
+    const int s = blockIdx.y;
+    if (!act[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const R inv = (R)inv_h[s];
+    const int j = st[s].j;  // new basis vector index
+    V[((long long)s * (m + 1) + j) * N + i] = cscale<R>(w[(long long)s * N + i], inv);
+}
+
+// y = H^-1 g (upper triangular, FP64) for the steps of the cycle; cyc[s] = 1 for systems
+// that ran a cycle.
+__global__ void k_tri_solve(int nsys, int m, const SysState* __restrict__ st, const int* __restrict__ cyc,
+                            const double2* __restrict__ H, const double2* __restrict__ g, double2* __restrict__ y) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys || !cyc[s]) return;
+    const int n = st[s].j;
+    double2* ys = y + (long long)s * (m + 1);
+    for (int k = n - 1; k >= 0; --k) {
+        double2 acc = g[(long long)s * (m + 1) + k];
+        for (int l = k + 1; l < n; ++l) acc = csub<double>(acc, cmul<double>(H[((long long)s * m + l) * (m + 1) + k], ys[l]));
+        const double2 dk = H[((long long)s * m + k) * (m + 1) + k];
+        ys[k] = (dk.x == 0.0 && dk.y == 0.0) ? make_double2(0.0, 0.0) : cdiv<double>(acc, dk);
+    }
+}
+
+// u = sum_{k < j} y_k V_k
+template <class R>
+__global__ void __launch_bounds__(TPB) k_vcombine(int N, int m, const int* __restrict__ cyc, const SysState* __restrict__ st,
+                                                 const cx<R>* __restrict__ V, const double2* __restrict__ y,
+                                                 cx<R>* __restrict__ u) {
+    const int s = blockIdx.y;
+    if (!cyc[s]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = st[s].j;
+    const cx<R>* Vs = V + (long long)s * (m + 1) * N;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < n; ++k) acc = cfma<double>(y[(long long)s * (m + 1) + k], cvt_to_d<R>(Vs[(long long)k * N + i]), acc);
+    u[(long long)s * N + i] = cvt_from_d<R>(acc);
+}
+
+__global__ void k_set_flags(int nsys, const int* __restrict__ src, int* __restrict__ dst) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsys) dst[s] = src[s];
+}
+
+__global__ void k_gmres_cycle_start(int nsys, int m, const int* __restrict__ act, double2* __restrict__ g) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys || !act[s]) return;
+    g[(long long)s * (m + 1)] = make_double2(1.0, 0.0);  // ||inner rhs|| = 1 after scaling
+}
+
+// ------------------------------------------------------------------------------ driver
+struct Runner {
+    vbk_model* m;
+    cudaStream_t st;
+    bool timing;
+    struct Pend {
+        int id;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pend> pend;
+    std::vector<cudaEvent_t> pool;
+    int id(const char* name) {
+        for (size_t k = 0; k < m->timers.size(); ++k)
+            if (m->timers[k].name == name) return (int)k;
+        KTimer t;
+        t.name = name;
+        m->timers.push_back(t);
+        return (int)m->timers.size() - 1;
+    }
+    cudaEvent_t ev() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    template <typename K, typename... A>
+    void go(const char* name, K kern, dim3 g, dim3 b, A... args) {
+        if (g.x == 0 || g.y == 0) return;
+        Pend pd{0, nullptr, nullptr};
+        if (timing) {
+            pd.id = id(name);
+            pd.a = ev();
+            pd.b = ev();
+            cudaEventRecord(pd.a, st);
+        }
+        kern<<<g, b, 0, st>>>(args...);
+        m->launches += 1;
+        if (timing) {
+            cudaEventRecord(pd.b, st);
+            m->timers[pd.id].launches += 1;
+            pend.push_back(pd);
+        }
+    }
+    void flush() {  // call after a stream synchronisation
+        for (auto& p : pend) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) m->timers[p.id].ms += ms;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pend.clear();
+    }
+    ~Runner() {
+        for (auto& p : pend) {
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+template <class T> T* carve(char*& p, size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* r = reinterpret_cast<T*>(p);
+    p += bytes;
+    return r;
+}
+template <class T> size_t carve_size(size_t count) { return (count * sizeof(T) + 255) & ~size_t(255); }
+
+inline unsigned cdiv_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+struct DevPlanBuf {
+    PlanDev pd{};
+    void* mem = nullptr;
+};
+
+int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPlanBuf* out, std::vector<int>& host_chain,
+                std::vector<int>& host_base) {
+    (void)m;
+    out->pd.L = bp.L;
+    out->pd.nblk = bp.nblk;
+    out->pd.p = bp.p;
+    out->pd.span = bp.span;
+    const size_t n1 = host_chain.size(), n2 = host_base.size(), n3 = std::max<size_t>(1, bp.ent_dc.size());
+    size_t bytes = (n1 + n2 + n3) * sizeof(int);
+    VBK_CUDA(cudaMallocAsync(&out->mem, bytes, st));
+    int* p = (int*)out->mem;
+    VBK_CUDA(cudaMemcpyAsync(p, host_chain.data(), n1 * sizeof(int), cudaMemcpyHostToDevice, st));
+    VBK_CUDA(cudaMemcpyAsync(p + n1, host_base.data(), n2 * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!bp.ent_dc.empty())
+        VBK_CUDA(cudaMemcpyAsync(p + n1 + n2, bp.ent_dc.data(), bp.ent_dc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    out->pd.chain_off = p;
+    out->pd.fixed_base = p + n1;
+    out->pd.ent_dc = p + n1 + n2;
+    // the host vectors must stay alive until the copies complete: synchronise here
+    VBK_CUDA(cudaStreamSynchronize(st));
+    return VBK_OK;
+}
+
+void plan_tables(const vbk_model* m, const BlockPlan& bp, std::vector<int>& chain, std::vector<int>& base) {
+    const int span = bp.span;
+    chain.assign(bp.L, 0);
+    base.assign(bp.nblk, 0);
+    for (int c = 0; c < bp.L; ++c) {
+        int rem = c, off = 0;
+        if (span & 1) {
+            off += (rem % m->ns) * m->Nnu;
+            rem /= m->ns;
+        }
+        for (int mm = m->M - 1; mm >= 0; --mm)
+            if (span & (2 << mm)) {
+                off += (rem % m->nb[mm]) * m->stride[mm];
+                rem /= m->nb[mm];
+            }
+        chain[c] = off;
+    }
+    for (int b = 0; b < bp.nblk; ++b) {
+        int rem = b, off = 0;
+        for (int mm = m->M - 1; mm >= 0; --mm)
+            if (!(span & (2 << mm))) {
+                off += (rem % m->nb[mm]) * m->stride[mm];
+                rem /= m->nb[mm];
+            }
+        if (!(span & 1)) off += rem * m->Nnu;
+        base[b] = off;
+    }
+}
+
+template <class R, int M> struct Solver {
+    static int run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vbk_stats* stats, cudaStream_t st);
+};
+
+template <class R, int M>
+int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vbk_stats* stats, cudaStream_t st) {
+    const DevModel& md = mdl->dm;
+    const int N = md.N, nsys = job.nsys, nE = job.nE;
+    const bool mixed = sizeof(R) == 4;
+    const int method = o.method;
+    const int mres = std::max(1, std::min(o.restart, 256));
+    const int pspan = o.precond_span;
+    const bool block = pspan > 0;
+    Runner rn{mdl, st, o.timing != 0, {}, {}};
+
+    BlockPlan bp;
+    std::vector<int> hchain, hbase;
+    DevPlanBuf pbuf;
+    if (block) {
+        int rc = vbk_make_block_plan(mdl, pspan, &bp);
+        if (rc) return rc;
+        plan_tables(mdl, bp, hchain, hbase);
+        rc = upload_plan(bp, mdl, st, &pbuf, hchain, hbase);
+        if (rc) return rc;
+    }
+
+    // ---- workspace
+    const size_t NN = (size_t)N;
+    const int nb_e = (int)cdiv_u(N, TPB);       // element-wise kernels
+    const int nb_v = (int)cdiv_u(N, VCHUNK);    // basis-vector kernels
+    const int nb_b = block ? (int)cdiv_u(bp.nblk, BTPB) : 0;
+    const int nslot = std::max(nb_e, std::max(nb_b, nb_v * (mres + 1)));
+    size_t bytes = 0;
+    bytes += carve_size<double2>((size_t)nE * NN);                    // diag64
+    bytes += carve_size<cx<R>>(mixed ? (size_t)nE * NN : 1);          // diagR
+    bytes += carve_size<double2>((size_t)nsys * NN);                  // r64
+    bytes += carve_size<SysState>(nsys);
+    bytes += 3 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
+    bytes += 3 * carve_size<double2>((size_t)nsys * nslot);           // partial buffers
+    if (block) bytes += carve_size<cx<R>>((size_t)nE * NN * (bp.p + 1));
+    if (method == VBK_COCG) {
+        bytes += 5 * carve_size<cx<R>>((size_t)nsys * NN);            // x r p q z
+    } else {
+        bytes += carve_size<cx<R>>((size_t)nsys * NN * (mres + 1));   // V
+        bytes += 2 * carve_size<cx<R>>((size_t)nsys * NN);            // z, w
+        bytes += carve_size<double2>((size_t)nsys * (mres + 1) * mres);  // H
+        bytes += 4 * carve_size<double2>((size_t)nsys * (mres + 1));     // g, h1, h2, y
+        bytes += carve_size<double2>((size_t)nsys * mres);               // sn
+        bytes += carve_size<double>((size_t)nsys * mres);                // cs
+        bytes += carve_size<double>((size_t)nsys);                       // inv_h
+    }
+    char* wsbase = nullptr;
+    {
+        cudaError_t e = cudaMallocAsync((void**)&wsbase, bytes, st);
+        if (e != cudaSuccess) {
+            if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+            vbk_set_error("workspace allocation of " + std::to_string(bytes) + " bytes failed");
+            cudaGetLastError();
+            return VBK_ERR_OOM;
+        }
+    }
+    char* p = wsbase;
+    double2* diag64 = carve<double2>(p, (size_t)nE * NN);
+    cx<R>* diagR = carve<cx<R>>(p, mixed ? (size_t)nE * NN : 1);
+    if (!mixed) diagR = reinterpret_cast<cx<R>*>(diag64);
+    double2* r64 = carve<double2>(p, (size_t)nsys * NN);
+    SysState* sst = carve<SysState>(p, nsys);
+    int* outer = carve<int>(p, nsys);
+    int* inner = carve<int>(p, nsys);
+    int* cyc = carve<int>(p, nsys);
+    int* pfail = carve<int>(p, nE);
+    int* sys_e = carve<int>(p, nsys);
+    int* cnt = carve<int>(p, 4);
+    double2* partA = carve<double2>(p, (size_t)nsys * nslot);
+    double2* partB = carve<double2>(p, (size_t)nsys * nslot);
+    double2* partC = carve<double2>(p, (size_t)nsys * nslot);
+    cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * NN * (bp.p + 1)) : nullptr;
+    cx<R>*x = nullptr, *r = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr, *V = nullptr, *w = nullptr;
+    double2 *H = nullptr, *g = nullptr, *h1 = nullptr, *h2 = nullptr, *yv = nullptr, *sn = nullptr;
+    double *cs = nullptr, *invh = nullptr;
+    if (method == VBK_COCG) {
+        x = carve<cx<R>>(p, (size_t)nsys * NN);
+        r = carve<cx<R>>(p, (size_t)nsys * NN);
+        pv = carve<cx<R>>(p, (size_t)nsys * NN);
+        q = carve<cx<R>>(p, (size_t)nsys * NN);
+        z = carve<cx<R>>(p, (size_t)nsys * NN);
+    } else {
+        V = carve<cx<R>>(p, (size_t)nsys * NN * (mres + 1));
+        z = carve<cx<R>>(p, (size_t)nsys * NN);
+        w = carve<cx<R>>(p, (size_t)nsys * NN);
+        H = carve<double2>(p, (size_t)nsys * (mres + 1) * mres);
+        g = carve<double2>(p, (size_t)nsys * (mres + 1));
+        h1 = carve<double2>(p, (size_t)nsys * (mres + 1));
+        h2 = carve<double2>(p, (size_t)nsys * (mres + 1));
+        yv = carve<double2>(p, (size_t)nsys * (mres + 1));
+        sn = carve<double2>(p, (size_t)nsys * mres);
+        cs = carve<double>(p, (size_t)nsys * mres);
+        invh = carve<double>(p, (size_t)nsys);
+    }
+
+    int rc = VBK_OK;
+    int* hcnt = nullptr;
+    double* dE = nullptr;
+    std::vector<int> ones(nsys, 1);
+    std::vector<SysState> hst(nsys);
+    auto fail = [&](int code) {
+        rc = code;
+        return code;
+    };
+    do {
+        if (cudaMallocHost((void**)&hcnt, 4 * sizeof(int)) != cudaSuccess) {
+            fail(VBK_ERR_OOM);
+            break;
+        }
+        if (cudaMallocAsync((void**)&dE, std::max(1, nE) * sizeof(double), st) != cudaSuccess) {
+            fail(VBK_ERR_OOM);
+            break;
+        }
+        if (cudaMemcpyAsync(dE, job.E.data(), nE * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(sys_e, job.sys_e.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(outer, ones.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(sst, 0, nsys * sizeof(SysState), st) != cudaSuccess ||
+            cudaMemsetAsync(job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) != cudaSuccess ||
+            cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess) {
+            fail(vbk_cuda_fail(cudaGetLastError(), "solver set-up copies"));
+            break;
+        }
+        // energy tables (FP64 + inner-precision copy)
+        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), md, nE, (const double*)dE,
+              diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr);
+        if (block) {
+            rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), md, pbuf.pd, nE,
+                  (const cx<R>*)diagR, F, pfail);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            fail(vbk_cuda_fail(cudaGetLastError(), "set-up kernels"));
+            break;
+        }
+        const dim3 ge(nb_e, nsys), gv(nb_v, nsys), gb(nb_b, nsys);
+        const unsigned gs = cdiv_u(nsys, 128);
+        const int pmode = pspan < 0 ? -1 : (block ? 1 : 0);
+        // apply the preconditioner to src -> dst (+ optional r^T z partials)
+        auto precond = [&](const int* act, const cx<R>* src, long long ss, cx<R>* dst, long long ds, double2* part) {
+            if (block)
+                rn.go("block_apply", k_block_apply<R>, gb, dim3(BTPB), pbuf.pd, (const int*)sys_e, act, (const cx<R>*)F, src, ss,
+                      dst, ds, part);
+            else
+                rn.go("point_precond", k_point_precond<R>, ge, dim3(TPB), N, (const int*)sys_e, act, pmode, (const cx<R>*)diagR,
+                      src, ss, dst, ds, part);
+        };
+        const int nb_rz = block ? nb_b : nb_e;
+
+        for (int it = 0; it <= o.max_refine + 1; ++it) {
+            // FP64 residual r = b - A x
+            if (it == 0)
+                rn.go("copy_b", k_copy_b, ge, dim3(TPB), N, (const int*)outer, job.b64, r64, partA);
+            else
+                rn.go("matvec_fp64", k_matvec<double, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)outer,
+                      (const double2*)diag64, (const double2*)job.x64, (long long)N, r64, (long long)N, job.b64, partA, 2);
+            cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
+            rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA, nb_e,
+                  it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt);
+            cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                fail(vbk_cuda_fail(cudaGetLastError(), "outer check"));
+                break;
+            }
+            rn.flush();
+            if (hcnt[0] == 0) break;
+
+            if (method == VBK_COCG) {
+                // r = rhs, x = 0, z = B^-1 r, p = z, rho = r^T z
+                rn.go("inner_rhs", k_inner_rhs<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst,
+                      (const double2*)r64, r, (long long)N);
+                cudaMemsetAsync(x, 0, (size_t)nsys * NN * sizeof(cx<R>), st);
+                precond(inner, r, N, z, N, partB);
+                rn.go("cocg_start", k_cocg_start, dim3(gs), dim3(128), nsys, sst, (const int*)inner, (const double2*)partB,
+                      nb_rz);
+                cudaMemcpyAsync(pv, z, (size_t)nsys * NN * sizeof(cx<R>), cudaMemcpyDeviceToDevice, st);
+                int k = 0;
+                for (;;) {
+                    rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)inner,
+                          (const cx<R>*)diagR, (const cx<R>*)pv, (long long)N, q, (long long)N, (const double2*)nullptr,
+                          partA, 1);
+                    rn.go("cocg_alpha", k_cocg_alpha, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partA,
+                          nb_e);
+                    rn.go("cocg_update", k_cocg_update<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst,
+                          (const int*)sys_e, pmode, (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z, partC,
+                          partB);
+                    if (block) precond(inner, r, N, z, N, partB);
+                    cudaMemsetAsync(cnt, 0, sizeof(int), st);
+                    rn.go("cocg_beta", k_cocg_beta, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partC, nb_e,
+                          (const double2*)partB, nb_rz, o.max_iter, cnt);
+                    rn.go("cocg_p", k_cocg_p<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst, (const cx<R>*)z,
+                          pv);
+                    ++k;
+                    if (k % std::max(1, o.check_every) == 0) {
+                        cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+                        if (cudaStreamSynchronize(st) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "COCG iterations"));
+                            break;
+                        }
+                        rn.flush();
+                        if (hcnt[0] == 0) break;
+                    }
+                    if (k > o.max_iter + 8) break;
+                }
+                if (rc) break;
+                rn.go("accumulate", k_accumulate<R>, ge, dim3(TPB), N, (const int*)outer, (const SysState*)sst,
+                      (const cx<R>*)x, (long long)N, job.x64);
+            } else {
+                // one GMRES(m) cycle on the scaled residual
+                const long long ldV = (long long)(mres + 1) * N;
+                rn.go("inner_rhs", k_inner_rhs<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst,
+                      (const double2*)r64, V, ldV);
+                rn.go("set_flags", k_set_flags, dim3(gs), dim3(128), nsys, (const int*)inner, cyc);
+                rn.go("gmres_start", k_gmres_cycle_start, dim3(gs), dim3(128), nsys, mres, (const int*)inner, g);
+                for (int j = 0; j < mres; ++j) {
+                    const cx<R>* vj = V + (long long)j * N;
+                    if (pspan < 0) {
+                        rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)inner,
+                              (const cx<R>*)diagR, vj, ldV, w, (long long)N, (const double2*)nullptr, partA, 0);
+                    } else {
+                        precond(inner, vj, ldV, z, N, nullptr);
+                        rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)inner,
+                              (const cx<R>*)diagR, (const cx<R>*)z, (long long)N, w, (long long)N, (const double2*)nullptr,
+                              partA, 0);
+                    }
+                    rn.go("gmres_dots", k_vdots<R>, gv, dim3(TPB), N, mres, (const int*)inner, (const cx<R>*)V, j,
+                          (const cx<R>*)w, partA);
+                    rn.go("gmres_hreduce", k_hreduce, dim3(nsys), dim3(64), nsys, mres, (const int*)inner, j,
+                          (const double2*)partA, nb_v, h1);
+                    rn.go("gmres_update_dots", k_vupdate<R>, gv, dim3(TPB), N, mres, (const int*)inner, (const cx<R>*)V, j,
+                          (const double2*)h1, w, 0, partA);
+                    rn.go("gmres_hreduce", k_hreduce, dim3(nsys), dim3(64), nsys, mres, (const int*)inner, j,
+                          (const double2*)partA, nb_v, h2);
+                    rn.go("gmres_update_norm", k_vupdate<R>, gv, dim3(TPB), N, mres, (const int*)inner, (const cx<R>*)V, j,
+                          (const double2*)h2, w, 1, partB);
+                    cudaMemsetAsync(cnt, 0, sizeof(int), st);
+                    rn.go("gmres_givens", k_givens, dim3(gs), dim3(128), nsys, mres, sst, inner, (const double2*)h1,
+                          (const double2*)h2, (const double2*)partB, nb_v, H, cs, sn, g, invh, o.max_iter, cnt);
+                    if (j + 1 < mres)
+                        rn.go("gmres_scale", k_vscale<R>, ge, dim3(TPB), N, mres, (const int*)inner, (const double*)invh,
+                              (const SysState*)sst, (const cx<R>*)w, V);
+                    if ((j + 1) % std::max(1, o.check_every) == 0 || j + 1 == mres) {
+                        cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+                        if (cudaStreamSynchronize(st) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "GMRES iterations"));
+                            break;
+                        }
+                        rn.flush();
+                        if (hcnt[0] == 0) break;
+                    }
+                }
+                if (rc) break;
+                rn.go("gmres_trisolve", k_tri_solve, dim3(gs), dim3(128), nsys, mres, (const SysState*)sst, (const int*)cyc,
+                      (const double2*)H, (const double2*)g, yv);
+                rn.go("gmres_combine", k_vcombine<R>, ge, dim3(TPB), N, mres, (const int*)cyc, (const SysState*)sst,
+                      (const cx<R>*)V, (const double2*)yv, w);
+                if (pspan < 0) {
+                    rn.go("accumulate", k_accumulate<R>, ge, dim3(TPB), N, (const int*)cyc, (const SysState*)sst,
+                          (const cx<R>*)w, (long long)N, job.x64);
+                } else {
+                    precond(cyc, w, N, z, N, nullptr);
+                    rn.go("accumulate", k_accumulate<R>, ge, dim3(TPB), N, (const int*)cyc, (const SysState*)sst,
+                          (const cx<R>*)z, (long long)N, job.x64);
+                }
+            }
+            if (cudaGetLastError() != cudaSuccess) {
+                fail(vbk_cuda_fail(cudaGetLastError(), "iteration kernels"));
+                break;
+            }
+        }
+        if (rc) break;
+        // results
+        if (cudaMemcpyAsync(hst.data(), sst, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            fail(vbk_cuda_fail(cudaGetLastError(), "result copy"));
+            break;
+        }
+        rn.flush();
+        std::vector<int> hfail(nE, 0);
+        if (block) {
+            cudaMemcpy(hfail.data(), pfail, nE * sizeof(int), cudaMemcpyDeviceToHost);
+        }
+        bool all_ok = true;
+        for (int s = 0; s < nsys; ++s) {
+            SysState& S = hst[s];
+            int status = S.status;
+            if (hfail[job.sys_e[s]] && status != VBK_SYS_CONVERGED) status = VBK_SYS_PIVOT;
+            if (status != VBK_SYS_CONVERGED && status != VBK_SYS_ZERO_RHS) all_ok = false;
+            if (stats) {
+                stats[s].status = status;
+                stats[s].iterations = S.iters;
+                stats[s].refinements = S.refines;
+                stats[s].rel_residual = S.bnorm > 0 ? S.rnorm / S.bnorm : 0.0;
+            }
+        }
+        if (!all_ok) rc = VBK_ERR_NOT_CONVERGED;
+    } while (0);
+    if (dE) cudaFreeAsync(dE, st);
+    cudaFreeAsync(wsbase, st);
+    if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+    cudaStreamSynchronize(st);
+    if (hcnt) cudaFreeHost(hcnt);
+    return rc;
+}
+
+template <class R>
+int dispatch(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stats* st, cudaStream_t s) {
+    switch (m->M) {
+        case 1: return Solver<R, 1>::run(m, job, o, st, s);
+        case 2: return Solver<R, 2>::run(m, job, o, st, s);
+        case 3: return Solver<R, 3>::run(m, job, o, st, s);
+        case 4: return Solver<R, 4>::run(m, job, o, st, s);
+    }
+    vbk_set_error("unsupported number of modes");
+    return VBK_ERR_UNSUPPORTED;
+}
+
+// ---------------------------------------------------------------- stand-alone operators
+// y = A x (op = 0) or z = B^-1 r (op = 1) for n_E energies x nvec vectors, FP64 in and out.
+template <class R, int M>
+int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
+                 cudaStream_t st) {
+    const int N = m->N;
+    const bool mixed = sizeof(R) == 4;
+    const long long nsys = (long long)nE * nvec;
+    BlockPlan bp;
+    std::vector<int> hchain, hbase;
+    DevPlanBuf pbuf;
+    const bool block = op == 1 && span > 0;
+    if (block) {
+        int rc = vbk_make_block_plan(m, span, &bp);
+        if (rc) return rc;
+        plan_tables(m, bp, hchain, hbase);
+        rc = upload_plan(bp, m, st, &pbuf, hchain, hbase);
+        if (rc) return rc;
+    }
+    size_t bytes = carve_size<double2>((size_t)nE * N) + carve_size<float2>(mixed ? (size_t)nE * N : 1) +
+                   2 * carve_size<cx<R>>(mixed ? (size_t)nsys * N : 1) + carve_size<int>(nsys) + carve_size<double>(nE) +
+                   carve_size<int>(nE) + (block ? carve_size<cx<R>>((size_t)nE * N * (bp.p + 1)) : 0);
+    char* base = nullptr;
+    if (cudaMallocAsync((void**)&base, bytes, st) != cudaSuccess) {
+        if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+        cudaGetLastError();
+        vbk_set_error("operator workspace allocation failed");
+        return VBK_ERR_OOM;
+    }
+    char* p = base;
+    double2* d64 = carve<double2>(p, (size_t)nE * N);
+    float2* d32 = carve<float2>(p, mixed ? (size_t)nE * N : 1);
+    cx<R>* xr = carve<cx<R>>(p, mixed ? (size_t)nsys * N : 1);
+    cx<R>* yr = carve<cx<R>>(p, mixed ? (size_t)nsys * N : 1);
+    int* se = carve<int>(p, nsys);
+    double* dE = carve<double>(p, nE);
+    int* pfail = carve<int>(p, nE);
+    cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * N * (bp.p + 1)) : nullptr;
+    if (!mixed) {
+        xr = reinterpret_cast<cx<R>*>(const_cast<double2*>(x));
+        yr = reinterpret_cast<cx<R>*>(y);
+    }
+    const cx<R>* diagR = mixed ? reinterpret_cast<const cx<R>*>(d32) : reinterpret_cast<const cx<R>*>(d64);
+    std::vector<int> hse(nsys);
+    for (long long s = 0; s < nsys; ++s) hse[s] = (int)(s / nvec);
+    int rc = VBK_OK;
+    Runner rn{m, st, false, {}, {}};
+    if (cudaMemcpyAsync(se, hse.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dE, E, nE * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess) {
+        rc = vbk_cuda_fail(cudaGetLastError(), "operator set-up");
+    } else {
+        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
+              mixed ? d32 : (float2*)nullptr);
+        const dim3 ge(cdiv_u(N, TPB), (unsigned)nsys);
+        if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
+        if (op == 0) {
+            rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), m->dm, (const int*)se, (const int*)nullptr, diagR, (const cx<R>*)xr,
+                  (long long)N, yr, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
+        } else if (block) {
+            rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), m->dm, pbuf.pd, nE,
+                  diagR, F, pfail);
+            rn.go("block_apply", k_block_apply<R>, dim3(cdiv_u(bp.nblk, BTPB), (unsigned)nsys), dim3(BTPB), pbuf.pd,
+                  (const int*)se, (const int*)nullptr, (const cx<R>*)F, (const cx<R>*)xr, (long long)N, yr, (long long)N,
+                  (double2*)nullptr);
+        } else {
+            rn.go("point_precond", k_point_precond<R>, ge, dim3(TPB), N, (const int*)se, (const int*)nullptr, span < 0 ? -1 : 0,
+                  diagR, (const cx<R>*)xr, (long long)N, yr, (long long)N, (double2*)nullptr);
+        }
+        if (mixed) rn.go("widen", k_widen, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, (const float2*)reinterpret_cast<float2*>(yr), y);
+        if (cudaGetLastError() != cudaSuccess) rc = vbk_cuda_fail(cudaGetLastError(), "operator kernels");
+        if (!rc && block) {
+            std::vector<int> hf(nE);
+            if (cudaMemcpyAsync(hf.data(), pfail, nE * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = vbk_cuda_fail(cudaGetLastError(), "operator pivot check");
+            } else {
+                for (int e = 0; e < nE; ++e)
+                    if (hf[e]) {
+                        vbk_set_error("zero pivot in the L D L^T factor of a preconditioner block");
+                        rc = VBK_ERR_NOT_CONVERGED;
+                    }
+            }
+        }
+    }
+    cudaFreeAsync(base, st);
+    if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+    return rc;
+}
+
+template <class R>
+int operator_dispatch(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
+                      cudaStream_t st) {
+    switch (m->M) {
+        case 1: return operator_run<R, 1>(m, op, nE, E, nvec, span, x, y, st);
+        case 2: return operator_run<R, 2>(m, op, nE, E, nvec, span, x, y, st);
+        case 3: return operator_run<R, 3>(m, op, nE, E, nvec, span, x, y, st);
+        case 4: return operator_run<R, 4>(m, op, nE, E, nvec, span, x, y, st);
+    }
+    vbk_set_error("unsupported number of modes");
+    return VBK_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+int vbk_solve_job(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stats* st, cudaStream_t s) {
+    m->timers.clear();
+    m->launches = 0;
+    if (o.precision == VBK_MIXED) return dispatch<float>(m, job, o, st, s);
+    return dispatch<double>(m, job, o, st, s);
+}
+
+int vbk_operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
+                     int precision, cudaStream_t st) {
+    if (precision == VBK_MIXED) return operator_dispatch<float>(m, op, nE, E, nvec, span, x, y, st);
+    return operator_dispatch<double>(m, op, nE, E, nvec, span, x, y, st);
+}

@@ -1,0 +1,96 @@
+"""The C-ABI library builds, loads and exports every function include/vbk.h declares; host-only
+entry points behave as documented (no GPU needed).
+
+The host level shift is pinned against the oracle's closed form (which is itself pinned
+against quadrature), so the library's own Dawson (Rybicki's method) and erfcx code paths
+are checked on both sides of threshold.
+"""
+
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vbk.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_13483_gb300 import build
+
+    build.build()
+    import paper_2307_13483_gb300 as vbk
+
+    return vbk
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vbk_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for required in ["vbk_build_model", "vbk_solve", "vbk_cross_sections", "vbk_solve_adjoint", "vbk_free_model"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (vbk_[a-z_0-9]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    # the Python binding marshals exactly these names
+    assert sorted(lib.EXPORTED) == declared_functions()
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3])
+def test_host_level_shift_matches_oracle(lib, l):
+    from oracle import vibronic as o
+
+    for b in (0.25, 0.4, 0.833, 1.7):
+        for eps in np.concatenate([np.linspace(-40, -0.01, 23), [-1e-6, 0.0, 1e-6], np.linspace(0.003, 12, 41)]):
+            got = lib.vbk_level_shift(eps, 0.13, b, l)
+            ref = complex(o.level_shift(np.array([eps]), 0.13, b, l)[0])
+            # the upward recursion P_l = -Gamma(l+1/2) b^-(l+1/2) + eps P_(l-1) cancels for eps < 0:
+            # both sides lose about (1 + |eps|)^l of relative accuracy there
+            cond = (1.0 + abs(eps)) ** (l + 0.5) if eps < 0 else 1.0
+            assert abs(got - ref) <= 2e-13 * cond * max(1.0, abs(ref)), (eps, b, l, got, ref)
+
+
+def test_host_level_shift_rejects_bad_arguments(lib):
+    with pytest.raises(lib.VbkError):
+        lib.vbk_level_shift(1.0, 0.1, -1.0, 0)
+    with pytest.raises(lib.VbkError):
+        lib.vbk_level_shift(float("nan"), 0.1, 1.0, 0)
+
+
+def test_default_options(lib):
+    o = lib.vbk_default_opts()
+    assert (o.method, o.precision, o.precond_span, o.restart) == (lib.VBK_GMRES, lib.VBK_MIXED, 0, 64)
+    assert o.tol == 1e-8 and o.inner_tol == 1e-5 and o.check_every == 8
+    o2 = lib.vbk_default_opts(method="cocg", precision="fp64", tol=1e-10)
+    assert (o2.method, o2.precision, o2.tol) == (lib.VBK_COCG, lib.VBK_FP64, 1e-10)
+
+
+def test_status_strings(lib):
+    assert lib.vbk_status_str(0) == "ok"
+    assert lib.vbk_status_str(4) == "not converged"
+    assert lib.vbk_sys_status_str(2) == "breakdown"
+    assert lib.vbk_status_str(99) == "unknown status"
+
+
+def test_build_without_device_reports_no_device(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    import workloads
+
+    with pytest.raises(lib.VbkError) as ei:
+        lib.Model(workloads.ci2d_model(4))
+    assert ei.value.code == 6

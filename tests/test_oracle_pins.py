@@ -262,3 +262,33 @@ def test_ecd86_parameters_match_table1():
     ch = {c["d"]: c for c in m["channels"]}
     assert (ch[0]["a"], ch[0]["b"], ch[0]["l"]) == (g["a1"], g["b1"], g["l1"])
     assert (ch[1]["a"], ch[1]["b"], ch[1]["l"]) == (g["a2"], g["b2"], g["l2"])
+
+
+# ------------------------------------------------------ preconditioner identities
+def test_ecd86_preconditioner_identities():
+    """Sec. III.B numerical testing, ECD86 paragraph: M^{dg} and M^{gu} hold only the diagonal of
+    A, and M^{du}, M^{d}, M^{u} coincide (no q_u terms on the diagonal of U, and the
+    inter-state coupling lambda q_u has no part diagonal in n_u)."""
+    m = w.ecd86_model(6, 7)
+    E = 3.3
+    A = o.a_matrix(m, E)
+    diag = sp_diag(A)
+    span = {"dg": 0x4, "gu": 0x1, "du": 0x2, "d": 0x6, "g": 0x5, "u": 0x3}
+    B = {k: o.block_diagonal(m, E, v).toarray() for k, v in span.items()}
+    np.testing.assert_array_equal(B["dg"], diag)
+    np.testing.assert_array_equal(B["gu"], diag)
+    np.testing.assert_array_equal(B["du"], B["d"])
+    np.testing.assert_array_equal(B["du"], B["u"])
+    assert np.abs(B["g"] - B["du"]).max() > 0.1  # M^g holds the lambda coupling
+
+
+def sp_diag(A):
+    return np.diag(A.diagonal())
+
+
+def test_block_labels_sizes():
+    m = w.ci2d_model(5)
+    for span, size in [(0x1, 2), (0x5, 10), (0x3, 10), (0x6, 25), (0x7, 50), (0x0, 1)]:
+        lab = o.block_labels(m, span)
+        _, counts = np.unique(lab, return_counts=True)
+        assert set(counts) == {size}
