@@ -19,9 +19,9 @@ HEADER = os.path.join(ROOT, "include", "vbk.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2307_13483_gb300 import build
+    import __graft_entry__
 
-    build.build()
+    __graft_entry__.build()
     import paper_2307_13483_gb300 as vbk
 
     return vbk

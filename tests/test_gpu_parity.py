@@ -28,9 +28,9 @@ pytestmark = pytest.mark.gpu
 def vbk():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2307_13483_gb300 import build
+    import __graft_entry__
 
-    build.build()
+    __graft_entry__.build()
     import paper_2307_13483_gb300 as lib
 
     return lib
