@@ -178,6 +178,11 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     std::stable_sort(diagp.begin(), diagp.end(), by_d);
     m->offd = offd;
     m->diagp = diagp;
+    for (int st = 0; st < m->ns; ++st) {
+        long long np = 0;
+        for (const auto& h : offd) np += h.d == st;
+        if (np > 256) return (g_last_error = "more than 256 stencil points for one state", VBK_ERR_UNSUPPORTED);
+    }
     // device model
     DevModel& dm = m->dm;
     dm = DevModel{};

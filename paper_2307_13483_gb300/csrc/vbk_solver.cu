@@ -55,6 +55,14 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
     return r;
 }
 
+// Systems a launch covers: blockIdx.y indexes `list` (compacted active systems) when given,
+// else the system itself; `act` masks systems that retired after the list was built.
+struct Sel {
+    const int* list;
+    const int* act;
+};
+__device__ __forceinline__ int sel_sys(const Sel& q) { return q.list ? q.list[blockIdx.y] : (int)blockIdx.y; }
+
 template <class R> __device__ __forceinline__ const R* tabp(const DevModel& md);
 template <> __device__ __forceinline__ const float* tabp<float>(const DevModel& md) { return md.tab32; }
 template <> __device__ __forceinline__ const double* tabp<double>(const DevModel& md) { return md.tab64; }
@@ -124,53 +132,120 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
     if (d32) d32[t] = make_float2((float)re, (float)im);
 }
 
-// ------------------------------------------------------------------------------- matvec
-// y = A x  (or y = b - A x when b != nullptr) for every active system s with energy
-// sys_e[s]; optional fused reduction: red = 1 -> x^T y (bilinear), red = 2 -> ||y||^2.
-template <class R, int M>
-__global__ void __launch_bounds__(TPB) k_matvec(DevModel md, const int* __restrict__ sys_e, const int* __restrict__ act,
-                                               const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x, long long xs,
-                                               cx<R>* __restrict__ y, long long ys, const double2* __restrict__ b,
-                                               double2* __restrict__ part, int red) {
+// Batched matvec, coefficient reuse across systems: one thread computes the stencil
+// coefficients of one element once and applies them to S systems (the off-diagonal part of A
+// does not depend on the energy; only the diagonal table does).  Grid: x = (state d, chunk of
+// TPB elements of that state), y = groups of S systems of the list.  The stencil points of
+// state d are staged in shared memory.  Partials (red = 1: x^T y, red = 2: ||y||^2) per
+// (system, blockIdx.x).
+constexpr int MV_MAXPTS = 256;
+
+template <class R> struct SPt {
+    R coef;
+    int off;              // (dp - d) * Nnu + lin: neighbour offset relative to the element
+    short col[MAXM];      // table column of each mode (-1: not involved)
+    short delta[MAXM];
+};
+
+template <class R, int M, int S>
+__global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
+                                                const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x, long long xs,
+                                                cx<R>* __restrict__ y, long long ys, const double2* __restrict__ b,
+                                                double2* __restrict__ part, int red) {
+    __shared__ SPt<R> pts[MV_MAXPTS];
     __shared__ double2 sh[32];
-    const int s = blockIdx.y;
-    if (act && !act[s]) return;
+    const int nchunk = (md.Nnu + TPB - 1) / TPB;
+    const int d = blockIdx.x / nchunk;
+    const int nu = (blockIdx.x - d * nchunk) * TPB + threadIdx.x;
     const int N = md.N;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const cx<R>* xv = x + (long long)s * xs;
-    double2 loc = make_double2(0.0, 0.0);
-    if (i < N) {
-        const int e = sys_e[s];
-        const int d = i / md.Nnu, nu = i - d * md.Nnu;
-        int n[MAXM];
-        decode<M>(md, nu, n);
-        const cx<R> xi = xv[i];
-        cx<R> acc = cmul<R>(diag[(long long)e * N + i], xi);
-        const R* tab = tabp<R>(md);
-        for (int k = md.ebeg[d]; k < md.ebeg[d + 1]; ++k) {
-            const DevEntry p = md.ent[k];
-            R c;
-            if (point_coef<R, M>(p, n, md, tab, c)) {
-                const cx<R> v = xv[p.dp * md.Nnu + nu + p.lin];
-                acc.x -= c * v.x;
-                acc.y -= c * v.y;
-            }
+    const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const DevEntry e = md.ent[pb + k];
+        SPt<R> q;
+        q.coef = (R)e.coef;
+        q.off = (e.dp - d) * md.Nnu + e.lin;
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) {
+            q.col[m] = (short)e.col[m];
+            q.delta[m] = (short)e.delta[m];
         }
-        if (b) {
-            const double2 bb = b[(long long)s * N + i];
-            acc = mkc<R>((R)bb.x - acc.x, (R)bb.y - acc.y);
+        pts[k] = q;
+    }
+    // systems of this CTA
+    int sy[S];
+    bool on[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const int li = blockIdx.y * S + k;
+        int s = -1;
+        if (li < nlist) {
+            s = sel.list ? sel.list[li] : li;
+            if (sel.act && !sel.act[s]) s = -1;
         }
-        y[(long long)s * ys + i] = acc;
-        if (red == 1) {
-            const cx<R> t = cmul<R>(xi, acc);
-            loc = make_double2((double)t.x, (double)t.y);
-        } else if (red == 2) {
-            loc = make_double2((double)cabs2<R>(acc), 0.0);
+        sy[k] = s;
+        on[k] = s >= 0;
+    }
+    __syncthreads();
+    const bool inr = nu < md.Nnu;
+    const int i = d * md.Nnu + nu;
+    cx<R> acc[S], xi[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        acc[k] = mkc<R>(0, 0);
+        xi[k] = mkc<R>(0, 0);
+        if (on[k] && inr) {
+            xi[k] = x[(long long)sy[k] * xs + i];
+            acc[k] = cmul<R>(diag[(long long)sys_e[sy[k]] * N + i], xi[k]);
         }
     }
-    if (red) {
-        const double2 tot = block_sum2(loc, sh);
-        if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
+    if (inr) {
+        int n[MAXM];
+        decode<M>(md, nu, n);
+        const R* tab = tabp<R>(md);
+        for (int k = 0; k < np; ++k) {
+            const SPt<R>& q = pts[k];
+            R c = q.coef;
+            bool ok = true;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                if (q.col[m] >= 0) {
+                    ok = ok && (unsigned)(n[m] + q.delta[m]) < (unsigned)md.nb[m];
+                    c *= __ldg(tab + q.col[m] + n[m]);
+                }
+            }
+            if (ok) {
+                const int j = i + q.off;
+#pragma unroll
+                for (int t = 0; t < S; ++t)
+                    if (on[t]) {
+                        const cx<R> v = x[(long long)sy[t] * xs + j];
+                        acc[t].x -= c * v.x;
+                        acc[t].y -= c * v.y;
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        double2 loc = make_double2(0.0, 0.0);
+        if (on[t] && inr) {
+            cx<R> out = acc[t];
+            if (b) {
+                const double2 bb = b[(long long)sy[t] * N + i];
+                out = mkc<R>((R)bb.x - out.x, (R)bb.y - out.y);
+            }
+            y[(long long)sy[t] * ys + i] = out;
+            if (red == 1) {
+                const cx<R> tt = cmul<R>(xi[t], out);
+                loc = make_double2((double)tt.x, (double)tt.y);
+            } else if (red == 2) {
+                loc = make_double2((double)cabs2<R>(out), 0.0);
+            }
+        }
+        if (red) {
+            const double2 tot = block_sum2(loc, sh);
+            if (threadIdx.x == 0 && on[t]) part[(long long)sy[t] * gridDim.x + blockIdx.x] = tot;
+        }
     }
 }
 
@@ -180,6 +255,12 @@ struct PlanDev {
     const int* chain_off;   // [L]   element offset of chain position c (relative)
     const int* fixed_base;  // [nblk] element index of chain position 0 of each block
     const int* ent_dc;      // [n off-diagonal points] chain offset of the point, 0 if outside
+    // staging through shared memory (blocks whose chain contains the fastest mode): the chain
+    // of a block is `nrun` contiguous runs of `runlen` elements; element k of run r sits at
+    // base + run_off[r] + k and has chain position run_c0[r] + k * cs_run.
+    int nrun, runlen, cs_run;
+    const int* run_off;
+    const int* run_c0;
 };
 
 // B = L D L^T of every block of every energy (Sec. III.B: factors computed once and stored).
@@ -246,12 +327,12 @@ __global__ void k_block_factor(DevModel md, PlanDev pl, int nE, const cx<R>* __r
 // z = B^-1 r for every block of every active system; optional fused rz = r^T z partials.
 // Grid: (ceil(nblk / BTPB), nsys).
 template <class R>
-__global__ void __launch_bounds__(BTPB) k_block_apply(PlanDev pl, const int* __restrict__ sys_e, const int* __restrict__ act,
+__global__ void __launch_bounds__(BTPB) k_block_apply(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
                                                      const cx<R>* __restrict__ F, const cx<R>* __restrict__ r, long long rs,
                                                      cx<R>* __restrict__ z, long long zs, double2* __restrict__ part) {
     __shared__ double2 sh[32];
-    const int s = blockIdx.y;
-    if (act && !act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int blk = blockIdx.x * blockDim.x + threadIdx.x;
     const int L = pl.L, p = pl.p, nblk = pl.nblk;
     double2 loc = make_double2(0.0, 0.0);
@@ -290,15 +371,138 @@ __global__ void __launch_bounds__(BTPB) k_block_apply(PlanDev pl, const int* __r
     }
 }
 
+
+// ------------------------------------------------------------- staged block preconditioner
+// z = B^-1 r for G consecutive blocks of one system per CTA.  The chains are gathered into
+// shared memory with coalesced loads over their contiguous runs (tile[c][b], b fastest,
+// padded), walked by one thread per block with a register window of P (>= p) previous
+// values, and scattered back.  With `upd`, the COCG update x += alpha p, r -= alpha q is
+// applied to the gathered elements first (partials ||r||^2).  r^T z = sum_c w_c^2 / D_c
+// with w = L^-1 r is accumulated in the forward sweep (partials part_rz).
+constexpr int SG = 32;       // blocks (chains) per CTA
+constexpr int STPB = 128;    // threads per CTA
+
+template <class R, int P>
+__global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __restrict__ alist, const int* __restrict__ act,
+                                                      const int* __restrict__ sys_e, const cx<R>* __restrict__ F,
+                                                      const SysState* __restrict__ st, int upd, cx<R>* __restrict__ x,
+                                                      cx<R>* __restrict__ r, long long rs, const cx<R>* __restrict__ pv,
+                                                      const cx<R>* __restrict__ q, cx<R>* __restrict__ z, long long zs,
+                                                      double2* __restrict__ part_rr, double2* __restrict__ part_rz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
+    __shared__ double2 sh[32];
+    const int s = alist ? alist[blockIdx.y] : blockIdx.y;
+    if (act && !act[s]) return;
+    const int L = pl.L, p = pl.p, nblk = pl.nblk;
+    const int b0 = blockIdx.x * SG;
+    const int G = min(SG, nblk - b0);
+    const int e = sys_e[s];
+    const int runlen = pl.runlen, nrun = pl.nrun, csr = pl.cs_run;
+    cx<R>* rv = r + (long long)s * rs;
+    cx<R>* zv = z + (long long)s * zs;
+    const long long so = (long long)s * (long long)(upd ? rs : 0);
+    cx<R> al = mkc<R>(0, 0);
+    if (upd) al = cvt_from_d<R>(st[s].alpha);
+    // ---- gather (and update)
+    double lrr = 0.0;
+    const int tot = G * nrun * runlen;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int k = idx % runlen;
+        const int t2 = idx / runlen;
+        const int rr_ = t2 % nrun, b = t2 / nrun;
+        const long long el = (long long)pl.fixed_base[b0 + b] + pl.run_off[rr_] + k;
+        cx<R> rvv = rv[el];
+        if (upd) {
+            const cx<R> xv = x[so + el], pp = pv[so + el], qq = q[so + el];
+            x[so + el] = cfma<R>(al, pp, xv);
+            rvv = csub<R>(rvv, cmul<R>(al, qq));
+            rv[el] = rvv;
+            lrr += (double)cabs2<R>(rvv);
+        }
+        tile[(pl.run_c0[rr_] + k * csr) * (SG + 1) + b] = rvv;
+    }
+    __syncthreads();
+    // ---- chain walk: thread b < G owns block b0 + b
+    double2 lrz = make_double2(0.0, 0.0);
+    if (threadIdx.x < G) {
+        const int b = threadIdx.x;
+        const cx<R>* Fe = F + (long long)e * L * (p + 1) * nblk + b0 + b;
+        cx<R> win[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) win[k] = mkc<R>(0, 0);
+        cx<R> Lr[P + 1], Ln[P + 1];
+#pragma unroll
+        for (int k = 0; k <= P; ++k) Lr[k] = (k <= p) ? Fe[(long long)k * nblk] : mkc<R>(0, 0);
+        for (int c = 0; c < L; ++c) {
+            // prefetch the next factor row
+#pragma unroll
+            for (int k = 0; k <= P; ++k)
+                Ln[k] = (k <= p && c + 1 < L) ? Fe[((long long)(c + 1) * (p + 1) + k) * nblk] : mkc<R>(0, 0);
+            cx<R> w = tile[c * (SG + 1) + b];
+#pragma unroll
+            for (int k = P; k >= 1; --k) w = csub<R>(w, cmul<R>(Lr[k], win[k - 1]));
+            const cx<R> v = cmul<R>(w, Lr[0]);
+            const cx<R> t = cmul<R>(w, v);
+            lrz.x += (double)t.x;
+            lrz.y += (double)t.y;
+            tile[c * (SG + 1) + b] = v;
+#pragma unroll
+            for (int k = P - 1; k >= 1; --k) win[k] = win[k - 1];
+            win[0] = w;
+#pragma unroll
+            for (int k = 0; k <= P; ++k) Lr[k] = Ln[k];
+        }
+        // backward: z_c = v_c - sum_k L[c+k][c] z_{c+k}
+#pragma unroll
+        for (int k = 0; k < P; ++k) win[k] = mkc<R>(0, 0);
+        cx<R> Lc[P + 1], Lcn[P + 1];
+#pragma unroll
+        for (int k = 1; k <= P; ++k)
+            Lc[k] = (k <= p && L - 1 + k < L) ? Fe[((long long)(L - 1 + k) * (p + 1) + k) * nblk] : mkc<R>(0, 0);
+        for (int c = L - 1; c >= 0; --c) {
+#pragma unroll
+            for (int k = 1; k <= P; ++k)
+                Lcn[k] = (k <= p && c >= 1 && c - 1 + k < L) ? Fe[((long long)(c - 1 + k) * (p + 1) + k) * nblk] : mkc<R>(0, 0);
+            cx<R> zz = tile[c * (SG + 1) + b];
+#pragma unroll
+            for (int k = P; k >= 1; --k) zz = csub<R>(zz, cmul<R>(Lc[k], win[k - 1]));
+            tile[c * (SG + 1) + b] = zz;
+#pragma unroll
+            for (int k = P - 1; k >= 1; --k) win[k] = win[k - 1];
+            win[0] = zz;
+#pragma unroll
+            for (int k = 1; k <= P; ++k) Lc[k] = Lcn[k];
+        }
+    }
+    __syncthreads();
+    // ---- scatter
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int k = idx % runlen;
+        const int t2 = idx / runlen;
+        const int rr_ = t2 % nrun, b = t2 / nrun;
+        const long long el = (long long)pl.fixed_base[b0 + b] + pl.run_off[rr_] + k;
+        zv[el] = tile[(pl.run_c0[rr_] + k * csr) * (SG + 1) + b];
+    }
+    if (part_rr) {
+        const double2 t = block_sum2(make_double2(lrr, 0.0), sh);
+        if (threadIdx.x == 0) part_rr[(long long)s * gridDim.x + blockIdx.x] = t;
+    }
+    if (part_rz) {
+        const double2 t = block_sum2(lrz, sh);
+        if (threadIdx.x == 0) part_rz[(long long)s * gridDim.x + blockIdx.x] = t;
+    }
+}
+
 // Point preconditioners: mode 0 -> z = r / diag (Jacobi), mode -1 -> z = r.  Optional r^T z.
 template <class R>
-__global__ void __launch_bounds__(TPB) k_point_precond(int N, const int* __restrict__ sys_e, const int* __restrict__ act,
+__global__ void __launch_bounds__(TPB) k_point_precond(int N, const int* __restrict__ sys_e, Sel sel,
                                                       int mode, const cx<R>* __restrict__ diag, const cx<R>* __restrict__ r,
                                                       long long rs, cx<R>* __restrict__ z, long long zs,
                                                       double2* __restrict__ part) {
     __shared__ double2 sh[32];
-    const int s = blockIdx.y;
-    if (act && !act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double2 loc = make_double2(0.0, 0.0);
     if (i < N) {
@@ -317,11 +521,11 @@ __global__ void __launch_bounds__(TPB) k_point_precond(int N, const int* __restr
 
 // ------------------------------------------------------------------- refinement (FP64)
 // First outer step: r = b (x = 0), partial ||r||^2.
-__global__ void __launch_bounds__(TPB) k_copy_b(int N, const int* __restrict__ act, const double2* __restrict__ b,
+__global__ void __launch_bounds__(TPB) k_copy_b(int N, Sel sel, const double2* __restrict__ b,
                                                double2* __restrict__ r, double2* __restrict__ part) {
     __shared__ double2 sh[32];
-    const int s = blockIdx.y;
-    if (act && !act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double2 loc = make_double2(0.0, 0.0);
     if (i < N) {
@@ -336,7 +540,8 @@ __global__ void __launch_bounds__(TPB) k_copy_b(int N, const int* __restrict__ a
 // Outer convergence test on the FP64 residual (stopping rule of Sec. III, true residual).
 __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restrict__ outer, int* __restrict__ inner,
                               const double2* __restrict__ part, int nb, int first, double tol, double inner_tol,
-                              int max_refine, int max_iter, int* __restrict__ count) {
+                              int max_refine, int max_iter, int* __restrict__ count, int* __restrict__ olist,
+                              int* __restrict__ ilist) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     inner[s] = 0;
@@ -378,15 +583,17 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
     S.cycle_iters = 0;
     S.inres = 1.0;
     inner[s] = 1;
-    atomicAdd(count, 1);
+    const int pos = atomicAdd(count, 1);
+    olist[pos] = s;
+    ilist[pos] = s;
 }
 
 // inner right-hand side r / ||r|| in the inner precision
 template <class R>
-__global__ void __launch_bounds__(TPB) k_inner_rhs(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+__global__ void __launch_bounds__(TPB) k_inner_rhs(int N, Sel sel, const SysState* __restrict__ st,
                                                   const double2* __restrict__ r, cx<R>* __restrict__ out, long long os) {
-    const int s = blockIdx.y;
-    if (!act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double inv = 1.0 / st[s].scale;
@@ -396,10 +603,10 @@ __global__ void __launch_bounds__(TPB) k_inner_rhs(int N, const int* __restrict_
 
 // x += ||r|| d (FP64 accumulation of the inner correction)
 template <class R>
-__global__ void __launch_bounds__(TPB) k_accumulate(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+__global__ void __launch_bounds__(TPB) k_accumulate(int N, Sel sel, const SysState* __restrict__ st,
                                                    const cx<R>* __restrict__ dv, long long ds, double2* __restrict__ x) {
-    const int s = blockIdx.y;
-    if (!act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double sc = st[s].scale;
@@ -449,14 +656,14 @@ __global__ void k_cocg_alpha(int nsys, SysState* __restrict__ st, int* __restric
 }
 
 template <class R>
-__global__ void __launch_bounds__(TPB) k_cocg_update(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+__global__ void __launch_bounds__(TPB) k_cocg_update(int N, Sel sel, const SysState* __restrict__ st,
                                                     const int* __restrict__ sys_e, int pmode, const cx<R>* __restrict__ diag,
                                                     cx<R>* __restrict__ x, cx<R>* __restrict__ r, const cx<R>* __restrict__ p,
                                                     const cx<R>* __restrict__ q, cx<R>* __restrict__ z,
                                                     double2* __restrict__ part_rr, double2* __restrict__ part_rz) {
     __shared__ double2 sh[32];
-    const int s = blockIdx.y;
-    if (!act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double2 lrr = make_double2(0.0, 0.0), lrz = make_double2(0.0, 0.0);
     if (i < N) {
@@ -484,7 +691,7 @@ __global__ void __launch_bounds__(TPB) k_cocg_update(int N, const int* __restric
 
 __global__ void k_cocg_beta(int nsys, SysState* __restrict__ st, int* __restrict__ act, int* __restrict__ outer,
                             const double2* __restrict__ part_rr, int nb_rr, const double2* __restrict__ part_rz, int nb_rz,
-                            int max_iter, int* __restrict__ count) {
+                            int max_iter, int* __restrict__ count, int* __restrict__ ilist) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys || !act[s]) return;
     SysState& S = st[s];
@@ -516,14 +723,14 @@ __global__ void k_cocg_beta(int nsys, SysState* __restrict__ st, int* __restrict
     }
     S.beta = cdiv<double>(rz, S.rho);
     S.rho = rz;
-    atomicAdd(count, 1);
+    ilist[atomicAdd(count, 1)] = s;
 }
 
 template <class R>
-__global__ void __launch_bounds__(TPB) k_cocg_p(int N, const int* __restrict__ act, const SysState* __restrict__ st,
+__global__ void __launch_bounds__(TPB) k_cocg_p(int N, Sel sel, const SysState* __restrict__ st,
                                                const cx<R>* __restrict__ z, cx<R>* __restrict__ p) {
-    const int s = blockIdx.y;
-    if (!act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const long long o = (long long)s * N + i;
@@ -539,11 +746,11 @@ __global__ void __launch_bounds__(TPB) k_cocg_p(int N, const int* __restrict__ a
 
 // partial h_k = sum_i conj(V_k[i]) w[i], k = 0..j;  part[s][blk][k], (m+1) slots
 template <class R>
-__global__ void __launch_bounds__(TPB) k_vdots(int N, int m, const int* __restrict__ act, const cx<R>* __restrict__ V,
+__global__ void __launch_bounds__(TPB) k_vdots(int N, int m, Sel sel, const cx<R>* __restrict__ V,
                                               int j, const cx<R>* __restrict__ w, double2* __restrict__ part) {
     __shared__ double2 sh[(TPB / 32) * 257];
-    const int s = blockIdx.y;
-    if (!act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const long long vs = (long long)(m + 1) * N;
     const cx<R>* Vs = V + s * vs;
     const cx<R>* ws = w + (long long)s * N;
@@ -599,13 +806,13 @@ __global__ void k_hreduce(int nsys, int m, const int* __restrict__ act, int j, c
 
 // w -= sum_k V_k h_k; then (mode 0) partial dots conj(V_k) w, or (mode 1) partial ||w||^2
 template <class R>
-__global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, const int* __restrict__ act, const cx<R>* __restrict__ V,
+__global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, Sel sel, const cx<R>* __restrict__ V,
                                                 int j, const double2* __restrict__ h, cx<R>* __restrict__ w, int mode,
                                                 double2* __restrict__ part) {
     __shared__ double2 sh[(TPB / 32) * 257];
     __shared__ double2 hs[257];
-    const int s = blockIdx.y;
-    if (!act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     for (int k = threadIdx.x; k <= j; k += blockDim.x) hs[k] = h[(long long)s * (m + 1) + k];
     __syncthreads();
     const long long vs = (long long)(m + 1) * N;
@@ -672,7 +879,7 @@ __global__ void k_givens(int nsys, int m, SysState* __restrict__ st, int* __rest
                          const double2* __restrict__ h1, const double2* __restrict__ h2,
                          const double2* __restrict__ part_n, int nb, double2* __restrict__ H, double* __restrict__ cs,
                          double2* __restrict__ sn, double2* __restrict__ g, double* __restrict__ inv_h, int max_iter,
-                         int* __restrict__ count) {
+                         int* __restrict__ count, int* __restrict__ ilist) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys || !act[s]) return;
     SysState& S = st[s];
@@ -732,15 +939,15 @@ __global__ void k_givens(int nsys, int m, SysState* __restrict__ st, int* __rest
         act[s] = 0;
         return;
     }
-    atomicAdd(count, 1);
+    ilist[atomicAdd(count, 1)] = s;
 }
 
 template <class R>
-__global__ void __launch_bounds__(TPB) k_vscale(int N, int m, const int* __restrict__ act, const double* __restrict__ inv_h,
+__global__ void __launch_bounds__(TPB) k_vscale(int N, int m, Sel sel, const double* __restrict__ inv_h,
                                                const SysState* __restrict__ st, const cx<R>* __restrict__ w,
                                                cx<R>* __restrict__ V) {
-    const int s = blockIdx.y;
-    if (!act[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const R inv = (R)inv_h[s];
@@ -766,11 +973,11 @@ __global__ void k_tri_solve(int nsys, int m, const SysState* __restrict__ st, co
 
 // u = sum_{k < j} y_k V_k
 template <class R>
-__global__ void __launch_bounds__(TPB) k_vcombine(int N, int m, const int* __restrict__ cyc, const SysState* __restrict__ st,
+__global__ void __launch_bounds__(TPB) k_vcombine(int N, int m, Sel sel, const SysState* __restrict__ st,
                                                  const cx<R>* __restrict__ V, const double2* __restrict__ y,
                                                  cx<R>* __restrict__ u) {
-    const int s = blockIdx.y;
-    if (!cyc[s]) return;
+    const int s = sel_sys(sel);
+    if (sel.act && !sel.act[s]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int n = st[s].j;
@@ -780,10 +987,6 @@ __global__ void __launch_bounds__(TPB) k_vcombine(int N, int m, const int* __res
     u[(long long)s * N + i] = cvt_from_d<R>(acc);
 }
 
-__global__ void k_set_flags(int nsys, const int* __restrict__ src, int* __restrict__ dst) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < nsys) dst[s] = src[s];
-}
 
 __global__ void k_gmres_cycle_start(int nsys, int m, const int* __restrict__ act, double2* __restrict__ g) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -822,6 +1025,10 @@ struct Runner {
     }
     template <typename K, typename... A>
     void go(const char* name, K kern, dim3 g, dim3 b, A... args) {
+        go_smem(name, kern, g, b, 0, args...);
+    }
+    template <typename K, typename... A>
+    void go_smem(const char* name, K kern, dim3 g, dim3 b, size_t smem, A... args) {
         if (g.x == 0 || g.y == 0) return;
         Pend pd{0, nullptr, nullptr};
         if (timing) {
@@ -830,7 +1037,7 @@ struct Runner {
             pd.b = ev();
             cudaEventRecord(pd.a, st);
         }
-        kern<<<g, b, 0, st>>>(args...);
+        kern<<<g, b, smem, st>>>(args...);
         m->launches += 1;
         if (timing) {
             cudaEventRecord(pd.b, st);
@@ -869,35 +1076,16 @@ inline unsigned cdiv_u(long long a, long long b) { return (unsigned)((a + b - 1)
 struct DevPlanBuf {
     PlanDev pd{};
     void* mem = nullptr;
+    bool staged = false;  // chains gathered through shared memory (k_block_staged)
+    int P = 0;            // register window of the staged kernel (>= p)
 };
 
-int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPlanBuf* out, std::vector<int>& host_chain,
-                std::vector<int>& host_base) {
-    (void)m;
-    out->pd.L = bp.L;
-    out->pd.nblk = bp.nblk;
-    out->pd.p = bp.p;
-    out->pd.span = bp.span;
-    const size_t n1 = host_chain.size(), n2 = host_base.size(), n3 = std::max<size_t>(1, bp.ent_dc.size());
-    size_t bytes = (n1 + n2 + n3) * sizeof(int);
-    VBK_CUDA(cudaMallocAsync(&out->mem, bytes, st));
-    int* p = (int*)out->mem;
-    VBK_CUDA(cudaMemcpyAsync(p, host_chain.data(), n1 * sizeof(int), cudaMemcpyHostToDevice, st));
-    VBK_CUDA(cudaMemcpyAsync(p + n1, host_base.data(), n2 * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (!bp.ent_dc.empty())
-        VBK_CUDA(cudaMemcpyAsync(p + n1 + n2, bp.ent_dc.data(), bp.ent_dc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    out->pd.chain_off = p;
-    out->pd.fixed_base = p + n1;
-    out->pd.ent_dc = p + n1 + n2;
-    // the host vectors must stay alive until the copies complete: synchronise here
-    VBK_CUDA(cudaStreamSynchronize(st));
-    return VBK_OK;
-}
-
-void plan_tables(const vbk_model* m, const BlockPlan& bp, std::vector<int>& chain, std::vector<int>& base) {
+// Host tables of a block plan: element offset of every chain position, base element of
+// every block, and (when the chain contains the fastest mode) its contiguous runs.
+int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPlanBuf* out) {
     const int span = bp.span;
-    chain.assign(bp.L, 0);
-    base.assign(bp.nblk, 0);
+    std::vector<int> chain(bp.L), base(bp.nblk), run_off, run_c0;
+    std::vector<int> nlast(bp.L, 0);
     for (int c = 0; c < bp.L; ++c) {
         int rem = c, off = 0;
         if (span & 1) {
@@ -906,7 +1094,9 @@ void plan_tables(const vbk_model* m, const BlockPlan& bp, std::vector<int>& chai
         }
         for (int mm = m->M - 1; mm >= 0; --mm)
             if (span & (2 << mm)) {
-                off += (rem % m->nb[mm]) * m->stride[mm];
+                const int nm = rem % m->nb[mm];
+                if (mm == m->M - 1) nlast[c] = nm;
+                off += nm * m->stride[mm];
                 rem /= m->nb[mm];
             }
         chain[c] = off;
@@ -921,7 +1111,76 @@ void plan_tables(const vbk_model* m, const BlockPlan& bp, std::vector<int>& chai
         if (!(span & 1)) off += rem * m->Nnu;
         base[b] = off;
     }
+    out->pd.L = bp.L;
+    out->pd.nblk = bp.nblk;
+    out->pd.p = bp.p;
+    out->pd.span = span;
+    const bool last_in_chain = (span >> m->M) & 1;
+    out->staged = false;
+    if (last_in_chain) {
+        for (int c = 0; c < bp.L; ++c)
+            if (nlast[c] == 0) {
+                run_c0.push_back(c);
+                run_off.push_back(chain[c]);
+            }
+        out->pd.runlen = m->nb[m->M - 1];
+        out->pd.nrun = (int)run_c0.size();
+        out->pd.cs_run = (span & 1) ? m->ns : 1;
+        const size_t tile = (size_t)bp.L * (32 + 1) * 16;  // worst case (FP64)
+        out->staged = tile <= 160 * 1024 && bp.p <= 16;
+        out->P = bp.p <= 2 ? 2 : bp.p <= 4 ? 4 : bp.p <= 8 ? 8 : 16;
+    }
+    if (run_c0.empty()) {
+        run_c0.push_back(0);
+        run_off.push_back(0);
+    }
+    const size_t n1 = chain.size(), n2 = base.size(), n3 = std::max<size_t>(1, bp.ent_dc.size()), n4 = run_off.size(),
+                 n5 = run_c0.size();
+    std::vector<int> all;
+    all.reserve(n1 + n2 + n3 + n4 + n5);
+    all.insert(all.end(), chain.begin(), chain.end());
+    all.insert(all.end(), base.begin(), base.end());
+    if (bp.ent_dc.empty())
+        all.push_back(0);
+    else
+        all.insert(all.end(), bp.ent_dc.begin(), bp.ent_dc.end());
+    all.insert(all.end(), run_off.begin(), run_off.end());
+    all.insert(all.end(), run_c0.begin(), run_c0.end());
+    VBK_CUDA(cudaMallocAsync(&out->mem, all.size() * sizeof(int), st));
+    int* p = (int*)out->mem;
+    VBK_CUDA(cudaMemcpyAsync(p, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    out->pd.chain_off = p;
+    out->pd.fixed_base = p + n1;
+    out->pd.ent_dc = p + n1 + n2;
+    out->pd.run_off = p + n1 + n2 + n3;
+    out->pd.run_c0 = p + n1 + n2 + n3 + n4;
+    // `all` must stay alive until the copy completes
+    VBK_CUDA(cudaStreamSynchronize(st));
+    return VBK_OK;
 }
+
+// Launches the block preconditioner z = B^-1 r (optionally fused with the COCG update).
+template <class R>
+void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny, const int* sys_e, const cx<R>* F,
+                   const SysState* sst, int upd, cx<R>* x, cx<R>* r, long long rs, const cx<R>* p, const cx<R>* q, cx<R>* z,
+                   long long zs, double2* part_rr, double2* part_rz);
+
+inline unsigned cdiv_u(long long a, long long b);
+inline int block_partials(const DevPlanBuf& pb) {
+    return pb.staged ? (int)((pb.pd.nblk + 31) / 32) : (int)((pb.pd.nblk + BTPB - 1) / BTPB);
+}
+
+
+template <class T, int M>
+void launch_matvec(Runner& rn, const char* name, const DevModel& md, const int* sys_e, Sel sel, unsigned nlist,
+                   const cx<T>* diag, const cx<T>* x, long long xs, cx<T>* y, long long ys, const double2* b, double2* part,
+                   int red) {
+    constexpr int S = sizeof(T) == 4 ? 8 : 4;
+    const int nchunk = (md.Nnu + TPB - 1) / TPB;
+    const dim3 g((unsigned)(md.ns * nchunk), (nlist + S - 1) / S);
+    rn.go(name, k_matvec2<T, M, S>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red);
+}
+inline int matvec_partials(const DevModel& md) { return md.ns * ((md.Nnu + TPB - 1) / TPB); }
 
 template <class R, int M> struct Solver {
     static int run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vbk_stats* stats, cudaStream_t st);
@@ -939,28 +1198,27 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     Runner rn{mdl, st, o.timing != 0, {}, {}};
 
     BlockPlan bp;
-    std::vector<int> hchain, hbase;
     DevPlanBuf pbuf;
     if (block) {
         int rc = vbk_make_block_plan(mdl, pspan, &bp);
         if (rc) return rc;
-        plan_tables(mdl, bp, hchain, hbase);
-        rc = upload_plan(bp, mdl, st, &pbuf, hchain, hbase);
+        rc = upload_plan(bp, mdl, st, &pbuf);
         if (rc) return rc;
     }
 
     // ---- workspace
     const size_t NN = (size_t)N;
     const int nb_e = (int)cdiv_u(N, TPB);       // element-wise kernels
+    const int nb_mv = matvec_partials(md);      // matvec partials per system
     const int nb_v = (int)cdiv_u(N, VCHUNK);    // basis-vector kernels
-    const int nb_b = block ? (int)cdiv_u(bp.nblk, BTPB) : 0;
-    const int nslot = std::max(nb_e, std::max(nb_b, nb_v * (mres + 1)));
+    const int nb_b = block ? block_partials(pbuf) : 0;
+    const int nslot = std::max(std::max(nb_e, nb_mv), std::max(nb_b, nb_v * (mres + 1)));
     size_t bytes = 0;
     bytes += carve_size<double2>((size_t)nE * NN);                    // diag64
     bytes += carve_size<cx<R>>(mixed ? (size_t)nE * NN : 1);          // diagR
     bytes += carve_size<double2>((size_t)nsys * NN);                  // r64
     bytes += carve_size<SysState>(nsys);
-    bytes += 3 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
+    bytes += 5 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
     bytes += 3 * carve_size<double2>((size_t)nsys * nslot);           // partial buffers
     if (block) bytes += carve_size<cx<R>>((size_t)nE * NN * (bp.p + 1));
     if (method == VBK_COCG) {
@@ -992,7 +1250,9 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     SysState* sst = carve<SysState>(p, nsys);
     int* outer = carve<int>(p, nsys);
     int* inner = carve<int>(p, nsys);
-    int* cyc = carve<int>(p, nsys);
+    int* olist = carve<int>(p, nsys);
+    int* ilist = carve<int>(p, nsys);
+    int* alll = carve<int>(p, nsys);
     int* pfail = carve<int>(p, nE);
     int* sys_e = carve<int>(p, nsys);
     int* cnt = carve<int>(p, 4);
@@ -1026,7 +1286,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     int rc = VBK_OK;
     int* hcnt = nullptr;
     double* dE = nullptr;
-    std::vector<int> ones(nsys, 1);
+    std::vector<int> ones(nsys, 1), iota(nsys);
+    for (int k = 0; k < nsys; ++k) iota[k] = k;
     std::vector<SysState> hst(nsys);
     auto fail = [&](int code) {
         rc = code;
@@ -1044,6 +1305,9 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         if (cudaMemcpyAsync(dE, job.E.data(), nE * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(sys_e, job.sys_e.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(outer, ones.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(alll, iota.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(olist, iota.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(ilist, iota.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemsetAsync(sst, 0, nsys * sizeof(SysState), st) != cudaSuccess ||
             cudaMemsetAsync(job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) != cudaSuccess ||
             cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess) {
@@ -1061,30 +1325,34 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             fail(vbk_cuda_fail(cudaGetLastError(), "set-up kernels"));
             break;
         }
-        const dim3 ge(nb_e, nsys), gv(nb_v, nsys), gb(nb_b, nsys);
         const unsigned gs = cdiv_u(nsys, 128);
         const int pmode = pspan < 0 ? -1 : (block ? 1 : 0);
-        // apply the preconditioner to src -> dst (+ optional r^T z partials)
-        auto precond = [&](const int* act, const cx<R>* src, long long ss, cx<R>* dst, long long ds, double2* part) {
+        const Sel sel_all{alll, outer};
+        unsigned n_out = (unsigned)nsys;  // systems in olist (host copy)
+        unsigned n_in = (unsigned)nsys;   // upper bound of systems in ilist
+        // z = B^-1 src for the systems of `sel` (+ optional r^T z partials)
+        auto precond = [&](Sel sel, unsigned ny, const cx<R>* src, long long ss, cx<R>* dst, long long ds, double2* part) {
             if (block)
-                rn.go("block_apply", k_block_apply<R>, gb, dim3(BTPB), pbuf.pd, (const int*)sys_e, act, (const cx<R>*)F, src, ss,
-                      dst, ds, part);
+                block_precond<R>(rn, pbuf, N, sel, ny, (const int*)sys_e, (const cx<R>*)F, (const SysState*)sst, 0, nullptr,
+                                 const_cast<cx<R>*>(src), ss, nullptr, nullptr, dst, ds, nullptr, part);
             else
-                rn.go("point_precond", k_point_precond<R>, ge, dim3(TPB), N, (const int*)sys_e, act, pmode, (const cx<R>*)diagR,
-                      src, ss, dst, ds, part);
+                rn.go("point_precond", k_point_precond<R>, dim3(nb_e, ny), dim3(TPB), N, (const int*)sys_e, sel, pmode,
+                      (const cx<R>*)diagR, src, ss, dst, ds, part);
         };
         const int nb_rz = block ? nb_b : nb_e;
 
         for (int it = 0; it <= o.max_refine + 1; ++it) {
             // FP64 residual r = b - A x
+            const Sel so{olist, outer};
             if (it == 0)
-                rn.go("copy_b", k_copy_b, ge, dim3(TPB), N, (const int*)outer, job.b64, r64, partA);
+                rn.go("copy_b", k_copy_b, dim3(nb_e, nsys), dim3(TPB), N, sel_all, job.b64, r64, partA);
             else
-                rn.go("matvec_fp64", k_matvec<double, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)outer,
-                      (const double2*)diag64, (const double2*)job.x64, (long long)N, r64, (long long)N, job.b64, partA, 2);
+                launch_matvec<double, M>(rn, "matvec_fp64", md, (const int*)sys_e, so, n_out, (const double2*)diag64,
+                                         (const double2*)job.x64, (long long)N, r64, (long long)N, job.b64, partA, 2);
             cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
-            rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA, nb_e,
-                  it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt);
+            rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
+                  it == 0 ? nb_e : nb_mv,
+                  it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
             cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) {
                 fail(vbk_cuda_fail(cudaGetLastError(), "outer check"));
@@ -1092,32 +1360,39 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             }
             rn.flush();
             if (hcnt[0] == 0) break;
+            n_out = n_in = (unsigned)hcnt[0];
+            const Sel si{ilist, inner};
+            const Sel so2{olist, outer};
 
             if (method == VBK_COCG) {
                 // r = rhs, x = 0, z = B^-1 r, p = z, rho = r^T z
-                rn.go("inner_rhs", k_inner_rhs<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst,
+                rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst,
                       (const double2*)r64, r, (long long)N);
                 cudaMemsetAsync(x, 0, (size_t)nsys * NN * sizeof(cx<R>), st);
-                precond(inner, r, N, z, N, partB);
+                precond(si, n_in, r, N, z, N, partB);
                 rn.go("cocg_start", k_cocg_start, dim3(gs), dim3(128), nsys, sst, (const int*)inner, (const double2*)partB,
                       nb_rz);
                 cudaMemcpyAsync(pv, z, (size_t)nsys * NN * sizeof(cx<R>), cudaMemcpyDeviceToDevice, st);
                 int k = 0;
                 for (;;) {
-                    rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)inner,
-                          (const cx<R>*)diagR, (const cx<R>*)pv, (long long)N, q, (long long)N, (const double2*)nullptr,
-                          partA, 1);
+                    const Sel sc{ilist, inner};
+                    launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, n_in, (const cx<R>*)diagR, (const cx<R>*)pv,
+                                        (long long)N, q, (long long)N, (const double2*)nullptr, partA, 1);
                     rn.go("cocg_alpha", k_cocg_alpha, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partA,
-                          nb_e);
-                    rn.go("cocg_update", k_cocg_update<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst,
-                          (const int*)sys_e, pmode, (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z, partC,
-                          partB);
-                    if (block) precond(inner, r, N, z, N, partB);
+                          nb_mv);
+                    if (block) {
+                        // fused x += alpha p, r -= alpha q and z = B^-1 r
+                        block_precond<R>(rn, pbuf, N, sc, n_in, (const int*)sys_e, (const cx<R>*)F, (const SysState*)sst, 1, x,
+                                         r, (long long)N, (const cx<R>*)pv, (const cx<R>*)q, z, (long long)N, partC, partB);
+                    } else {
+                        rn.go("cocg_update", k_cocg_update<R>, dim3(nb_e, n_in), dim3(TPB), N, sc, (const SysState*)sst,
+                              (const int*)sys_e, pmode, (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z,
+                              partC, partB);
+                    }
                     cudaMemsetAsync(cnt, 0, sizeof(int), st);
-                    rn.go("cocg_beta", k_cocg_beta, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partC, nb_e,
-                          (const double2*)partB, nb_rz, o.max_iter, cnt);
-                    rn.go("cocg_p", k_cocg_p<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst, (const cx<R>*)z,
-                          pv);
+                    rn.go("cocg_beta", k_cocg_beta, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partC,
+                          (block && pbuf.staged) ? nb_rz : nb_e, (const double2*)partB, nb_rz, o.max_iter, cnt, ilist);
+                    rn.go("cocg_p", k_cocg_p<R>, dim3(nb_e, n_in), dim3(TPB), N, sc, (const SysState*)sst, (const cx<R>*)z, pv);
                     ++k;
                     if (k % std::max(1, o.check_every) == 0) {
                         cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1127,45 +1402,46 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                         }
                         rn.flush();
                         if (hcnt[0] == 0) break;
+                        n_in = (unsigned)hcnt[0];
                     }
                     if (k > o.max_iter + 8) break;
                 }
                 if (rc) break;
-                rn.go("accumulate", k_accumulate<R>, ge, dim3(TPB), N, (const int*)outer, (const SysState*)sst,
+                rn.go("accumulate", k_accumulate<R>, dim3(nb_e, n_out), dim3(TPB), N, so2, (const SysState*)sst,
                       (const cx<R>*)x, (long long)N, job.x64);
             } else {
                 // one GMRES(m) cycle on the scaled residual
                 const long long ldV = (long long)(mres + 1) * N;
-                rn.go("inner_rhs", k_inner_rhs<R>, ge, dim3(TPB), N, (const int*)inner, (const SysState*)sst,
+                rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst,
                       (const double2*)r64, V, ldV);
-                rn.go("set_flags", k_set_flags, dim3(gs), dim3(128), nsys, (const int*)inner, cyc);
                 rn.go("gmres_start", k_gmres_cycle_start, dim3(gs), dim3(128), nsys, mres, (const int*)inner, g);
+                const Sel sc_out{olist, nullptr};  // systems that run this cycle (for the final combination)
                 for (int j = 0; j < mres; ++j) {
+                    const Sel sc{ilist, inner};
                     const cx<R>* vj = V + (long long)j * N;
                     if (pspan < 0) {
-                        rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)inner,
-                              (const cx<R>*)diagR, vj, ldV, w, (long long)N, (const double2*)nullptr, partA, 0);
+                        launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, n_in, (const cx<R>*)diagR, vj, ldV, w,
+                                            (long long)N, (const double2*)nullptr, partA, 0);
                     } else {
-                        precond(inner, vj, ldV, z, N, nullptr);
-                        rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), md, (const int*)sys_e, (const int*)inner,
-                              (const cx<R>*)diagR, (const cx<R>*)z, (long long)N, w, (long long)N, (const double2*)nullptr,
-                              partA, 0);
+                        precond(sc, n_in, vj, ldV, z, N, nullptr);
+                        launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, n_in, (const cx<R>*)diagR,
+                                            (const cx<R>*)z, (long long)N, w, (long long)N, (const double2*)nullptr, partA, 0);
                     }
-                    rn.go("gmres_dots", k_vdots<R>, gv, dim3(TPB), N, mres, (const int*)inner, (const cx<R>*)V, j,
+                    rn.go("gmres_dots", k_vdots<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const cx<R>*)w, partA);
                     rn.go("gmres_hreduce", k_hreduce, dim3(nsys), dim3(64), nsys, mres, (const int*)inner, j,
                           (const double2*)partA, nb_v, h1);
-                    rn.go("gmres_update_dots", k_vupdate<R>, gv, dim3(TPB), N, mres, (const int*)inner, (const cx<R>*)V, j,
+                    rn.go("gmres_update_dots", k_vupdate<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const double2*)h1, w, 0, partA);
                     rn.go("gmres_hreduce", k_hreduce, dim3(nsys), dim3(64), nsys, mres, (const int*)inner, j,
                           (const double2*)partA, nb_v, h2);
-                    rn.go("gmres_update_norm", k_vupdate<R>, gv, dim3(TPB), N, mres, (const int*)inner, (const cx<R>*)V, j,
+                    rn.go("gmres_update_norm", k_vupdate<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const double2*)h2, w, 1, partB);
                     cudaMemsetAsync(cnt, 0, sizeof(int), st);
                     rn.go("gmres_givens", k_givens, dim3(gs), dim3(128), nsys, mres, sst, inner, (const double2*)h1,
-                          (const double2*)h2, (const double2*)partB, nb_v, H, cs, sn, g, invh, o.max_iter, cnt);
+                          (const double2*)h2, (const double2*)partB, nb_v, H, cs, sn, g, invh, o.max_iter, cnt, ilist);
                     if (j + 1 < mres)
-                        rn.go("gmres_scale", k_vscale<R>, ge, dim3(TPB), N, mres, (const int*)inner, (const double*)invh,
+                        rn.go("gmres_scale", k_vscale<R>, dim3(nb_e, n_in), dim3(TPB), N, mres, sc, (const double*)invh,
                               (const SysState*)sst, (const cx<R>*)w, V);
                     if ((j + 1) % std::max(1, o.check_every) == 0 || j + 1 == mres) {
                         cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1175,19 +1451,20 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                         }
                         rn.flush();
                         if (hcnt[0] == 0) break;
+                        n_in = (unsigned)hcnt[0];
                     }
                 }
                 if (rc) break;
-                rn.go("gmres_trisolve", k_tri_solve, dim3(gs), dim3(128), nsys, mres, (const SysState*)sst, (const int*)cyc,
+                rn.go("gmres_trisolve", k_tri_solve, dim3(gs), dim3(128), nsys, mres, (const SysState*)sst, (const int*)outer,
                       (const double2*)H, (const double2*)g, yv);
-                rn.go("gmres_combine", k_vcombine<R>, ge, dim3(TPB), N, mres, (const int*)cyc, (const SysState*)sst,
+                rn.go("gmres_combine", k_vcombine<R>, dim3(nb_e, n_out), dim3(TPB), N, mres, sc_out, (const SysState*)sst,
                       (const cx<R>*)V, (const double2*)yv, w);
                 if (pspan < 0) {
-                    rn.go("accumulate", k_accumulate<R>, ge, dim3(TPB), N, (const int*)cyc, (const SysState*)sst,
+                    rn.go("accumulate", k_accumulate<R>, dim3(nb_e, n_out), dim3(TPB), N, sc_out, (const SysState*)sst,
                           (const cx<R>*)w, (long long)N, job.x64);
                 } else {
-                    precond(cyc, w, N, z, N, nullptr);
-                    rn.go("accumulate", k_accumulate<R>, ge, dim3(TPB), N, (const int*)cyc, (const SysState*)sst,
+                    precond(sc_out, n_out, w, N, z, N, nullptr);
+                    rn.go("accumulate", k_accumulate<R>, dim3(nb_e, n_out), dim3(TPB), N, sc_out, (const SysState*)sst,
                           (const cx<R>*)z, (long long)N, job.x64);
                 }
             }
@@ -1232,6 +1509,40 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
 }
 
 template <class R>
+void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny, const int* sys_e, const cx<R>* F,
+                   const SysState* sst, int upd, cx<R>* x, cx<R>* r, long long rs, const cx<R>* p, const cx<R>* q, cx<R>* z,
+                   long long zs, double2* part_rr, double2* part_rz) {
+    if (pb.staged) {
+        const size_t smem = (size_t)pb.pd.L * (SG + 1) * sizeof(cx<R>);
+        const dim3 g((pb.pd.nblk + SG - 1) / SG, ny);
+        auto launch = [&](auto kern) {
+            static bool attr_set = false;  // per instantiation
+            if (!attr_set) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+                attr_set = true;
+            }
+            if (g.x == 0 || g.y == 0) return;
+            rn.go_smem(upd ? "cocg_update_precond" : "block_apply", kern, g, dim3(STPB), smem, pb.pd, sel.list, sel.act, sys_e,
+                       F, sst, upd, x, r, rs, p, q, z, zs, part_rr, part_rz);
+        };
+        switch (pb.P) {
+            case 2: launch(k_block_staged<R, 2>); break;
+            case 4: launch(k_block_staged<R, 4>); break;
+            case 8: launch(k_block_staged<R, 8>); break;
+            default: launch(k_block_staged<R, 16>); break;
+        }
+        return;
+    }
+    if (upd) {
+        // generic path: the COCG update as its own kernel, then the block solve
+        rn.go("cocg_update", k_cocg_update<R>, dim3(cdiv_u(N, TPB), ny), dim3(TPB), N, sel, sst, sys_e, 1,
+              (const cx<R>*)nullptr, x, r, p, q, z, part_rr, (double2*)nullptr);
+    }
+    rn.go("block_apply", k_block_apply<R>, dim3((pb.pd.nblk + BTPB - 1) / BTPB, ny), dim3(BTPB), pb.pd, sys_e, sel, F,
+          (const cx<R>*)r, rs, z, zs, part_rz);
+}
+
+template <class R>
 int dispatch(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stats* st, cudaStream_t s) {
     switch (m->M) {
         case 1: return Solver<R, 1>::run(m, job, o, st, s);
@@ -1252,14 +1563,12 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     const bool mixed = sizeof(R) == 4;
     const long long nsys = (long long)nE * nvec;
     BlockPlan bp;
-    std::vector<int> hchain, hbase;
     DevPlanBuf pbuf;
     const bool block = op == 1 && span > 0;
     if (block) {
         int rc = vbk_make_block_plan(m, span, &bp);
         if (rc) return rc;
-        plan_tables(m, bp, hchain, hbase);
-        rc = upload_plan(bp, m, st, &pbuf, hchain, hbase);
+        rc = upload_plan(bp, m, st, &pbuf);
         if (rc) return rc;
     }
     size_t bytes = carve_size<double2>((size_t)nE * N) + carve_size<float2>(mixed ? (size_t)nE * N : 1) +
@@ -1290,6 +1599,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     for (long long s = 0; s < nsys; ++s) hse[s] = (int)(s / nvec);
     int rc = VBK_OK;
     Runner rn{m, st, false, {}, {}};
+    const Sel none{nullptr, nullptr};
     if (cudaMemcpyAsync(se, hse.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(dE, E, nE * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess) {
@@ -1300,16 +1610,15 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
         const dim3 ge(cdiv_u(N, TPB), (unsigned)nsys);
         if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
         if (op == 0) {
-            rn.go("matvec", k_matvec<R, M>, ge, dim3(TPB), m->dm, (const int*)se, (const int*)nullptr, diagR, (const cx<R>*)xr,
-                  (long long)N, yr, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
+            launch_matvec<R, M>(rn, "matvec", m->dm, (const int*)se, none, (unsigned)nsys, diagR, (const cx<R>*)xr, (long long)N,
+                                yr, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
         } else if (block) {
             rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), m->dm, pbuf.pd, nE,
                   diagR, F, pfail);
-            rn.go("block_apply", k_block_apply<R>, dim3(cdiv_u(bp.nblk, BTPB), (unsigned)nsys), dim3(BTPB), pbuf.pd,
-                  (const int*)se, (const int*)nullptr, (const cx<R>*)F, (const cx<R>*)xr, (long long)N, yr, (long long)N,
-                  (double2*)nullptr);
+            block_precond<R>(rn, pbuf, N, none, (unsigned)nsys, (const int*)se, (const cx<R>*)F, (const SysState*)nullptr, 0,
+                             nullptr, xr, (long long)N, nullptr, nullptr, yr, (long long)N, nullptr, nullptr);
         } else {
-            rn.go("point_precond", k_point_precond<R>, ge, dim3(TPB), N, (const int*)se, (const int*)nullptr, span < 0 ? -1 : 0,
+            rn.go("point_precond", k_point_precond<R>, ge, dim3(TPB), N, (const int*)se, none, span < 0 ? -1 : 0,
                   diagR, (const cx<R>*)xr, (long long)N, yr, (long long)N, (double2*)nullptr);
         }
         if (mixed) rn.go("widen", k_widen, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, (const float2*)reinterpret_cast<float2*>(yr), y);
