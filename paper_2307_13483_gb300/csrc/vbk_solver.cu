@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
         int s = -1;
         if (li < nlist) {
             s = sel.list ? sel.list[li] : li;
-            if (sel.act && !sel.act[s]) s = -1;
+            if (s >= 0 && sel.act && !sel.act[s]) s = -1;
         }
         sy[k] = s;
         on[k] = s >= 0;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(BTPB) k_block_apply(PlanDev pl, const int* __r
                                                      cx<R>* __restrict__ z, long long zs, double2* __restrict__ part) {
     __shared__ double2 sh[32];
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int blk = blockIdx.x * blockDim.x + threadIdx.x;
     const int L = pl.L, p = pl.p, nblk = pl.nblk;
     double2 loc = make_double2(0.0, 0.0);
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
     cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
     __shared__ double2 sh[32];
     const int s = alist ? alist[blockIdx.y] : blockIdx.y;
-    if (act && !act[s]) return;
+    if (s < 0 || (act && !act[s])) return;
     const int L = pl.L, p = pl.p, nblk = pl.nblk;
     const int b0 = blockIdx.x * SG;
     const int G = min(SG, nblk - b0);
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(TPB) k_point_precond(int N, const int* __restr
                                                       double2* __restrict__ part) {
     __shared__ double2 sh[32];
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double2 loc = make_double2(0.0, 0.0);
     if (i < N) {
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(TPB) k_copy_b(int N, Sel sel, const double2* _
                                                double2* __restrict__ r, double2* __restrict__ part) {
     __shared__ double2 sh[32];
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double2 loc = make_double2(0.0, 0.0);
     if (i < N) {
@@ -593,7 +593,7 @@ template <class R>
 __global__ void __launch_bounds__(TPB) k_inner_rhs(int N, Sel sel, const SysState* __restrict__ st,
                                                   const double2* __restrict__ r, cx<R>* __restrict__ out, long long os) {
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double inv = 1.0 / st[s].scale;
@@ -606,7 +606,7 @@ template <class R>
 __global__ void __launch_bounds__(TPB) k_accumulate(int N, Sel sel, const SysState* __restrict__ st,
                                                    const cx<R>* __restrict__ dv, long long ds, double2* __restrict__ x) {
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double sc = st[s].scale;
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(TPB) k_cocg_update(int N, Sel sel, const SysSt
                                                     double2* __restrict__ part_rr, double2* __restrict__ part_rz) {
     __shared__ double2 sh[32];
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double2 lrr = make_double2(0.0, 0.0), lrz = make_double2(0.0, 0.0);
     if (i < N) {
@@ -730,7 +730,7 @@ template <class R>
 __global__ void __launch_bounds__(TPB) k_cocg_p(int N, Sel sel, const SysState* __restrict__ st,
                                                const cx<R>* __restrict__ z, cx<R>* __restrict__ p) {
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const long long o = (long long)s * N + i;
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(TPB) k_vdots(int N, int m, Sel sel, const cx<R
                                               int j, const cx<R>* __restrict__ w, double2* __restrict__ part) {
     __shared__ double2 sh[(TPB / 32) * 257];
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const long long vs = (long long)(m + 1) * N;
     const cx<R>* Vs = V + s * vs;
     const cx<R>* ws = w + (long long)s * N;
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, Sel sel, const cx
     __shared__ double2 sh[(TPB / 32) * 257];
     __shared__ double2 hs[257];
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     for (int k = threadIdx.x; k <= j; k += blockDim.x) hs[k] = h[(long long)s * (m + 1) + k];
     __syncthreads();
     const long long vs = (long long)(m + 1) * N;
@@ -947,7 +947,7 @@ __global__ void __launch_bounds__(TPB) k_vscale(int N, int m, Sel sel, const dou
                                                const SysState* __restrict__ st, const cx<R>* __restrict__ w,
                                                cx<R>* __restrict__ V) {
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const R inv = (R)inv_h[s];
@@ -977,7 +977,7 @@ __global__ void __launch_bounds__(TPB) k_vcombine(int N, int m, Sel sel, const S
                                                  const cx<R>* __restrict__ V, const double2* __restrict__ y,
                                                  cx<R>* __restrict__ u) {
     const int s = sel_sys(sel);
-    if (sel.act && !sel.act[s]) return;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int n = st[s].j;
@@ -1039,10 +1039,18 @@ struct Runner {
         }
         kern<<<g, b, smem, st>>>(args...);
         m->launches += 1;
+        if (const cudaError_t ce = cudaPeekAtLastError(); ce != cudaSuccess) note_error(ce, name);
         if (timing) {
             cudaEventRecord(pd.b, st);
             m->timers[pd.id].launches += 1;
             pend.push_back(pd);
+        }
+    }
+    cudaError_t first_error = cudaSuccess;
+    void note_error(cudaError_t e, const char* where) {
+        if (first_error == cudaSuccess) {
+            first_error = e;
+            vbk_set_error(std::string("launch of ") + where + ": " + cudaGetErrorString(e));
         }
     }
     void flush() {  // call after a stream synchronisation
@@ -1321,8 +1329,12 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), md, pbuf.pd, nE,
                   (const cx<R>*)diagR, F, pfail);
         }
-        if (cudaGetLastError() != cudaSuccess) {
-            fail(vbk_cuda_fail(cudaGetLastError(), "set-up kernels"));
+        if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) {
+            fail(vbk_cuda_fail(ce, "set-up kernels"));
+            break;
+        }
+        if (rn.first_error != cudaSuccess) {
+            fail(VBK_ERR_CUDA);
             break;
         }
         const unsigned gs = cdiv_u(nsys, 128);
@@ -1350,6 +1362,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 launch_matvec<double, M>(rn, "matvec_fp64", md, (const int*)sys_e, so, n_out, (const double2*)diag64,
                                          (const double2*)job.x64, (long long)N, r64, (long long)N, job.b64, partA, 2);
             cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
+            cudaMemsetAsync(olist, 0xff, nsys * sizeof(int), st);  // -1: no system
+            cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
                   it == 0 ? nb_e : nb_mv,
                   it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
@@ -1390,6 +1404,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                               partC, partB);
                     }
                     cudaMemsetAsync(cnt, 0, sizeof(int), st);
+                    cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
                     rn.go("cocg_beta", k_cocg_beta, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partC,
                           (block && pbuf.staged) ? nb_rz : nb_e, (const double2*)partB, nb_rz, o.max_iter, cnt, ilist);
                     rn.go("cocg_p", k_cocg_p<R>, dim3(nb_e, n_in), dim3(TPB), N, sc, (const SysState*)sst, (const cx<R>*)z, pv);
@@ -1438,6 +1453,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     rn.go("gmres_update_norm", k_vupdate<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const double2*)h2, w, 1, partB);
                     cudaMemsetAsync(cnt, 0, sizeof(int), st);
+                    cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
                     rn.go("gmres_givens", k_givens, dim3(gs), dim3(128), nsys, mres, sst, inner, (const double2*)h1,
                           (const double2*)h2, (const double2*)partB, nb_v, H, cs, sn, g, invh, o.max_iter, cnt, ilist);
                     if (j + 1 < mres)
@@ -1468,8 +1484,12 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                           (const cx<R>*)z, (long long)N, job.x64);
                 }
             }
-            if (cudaGetLastError() != cudaSuccess) {
-                fail(vbk_cuda_fail(cudaGetLastError(), "iteration kernels"));
+            if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) {
+                fail(vbk_cuda_fail(ce, "iteration kernels"));
+                break;
+            }
+            if (rn.first_error != cudaSuccess) {
+                fail(VBK_ERR_CUDA);
                 break;
             }
         }
@@ -1516,12 +1536,14 @@ void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny
         const size_t smem = (size_t)pb.pd.L * (SG + 1) * sizeof(cx<R>);
         const dim3 g((pb.pd.nblk + SG - 1) / SG, ny);
         auto launch = [&](auto kern) {
-            static bool attr_set = false;  // per instantiation
-            if (!attr_set) {
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-                attr_set = true;
-            }
             if (g.x == 0 || g.y == 0) return;
+            if (smem > 48 * 1024) {
+                const cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (ce != cudaSuccess) {
+                    rn.note_error(ce, "block preconditioner shared-memory opt-in");
+                    return;
+                }
+            }
             rn.go_smem(upd ? "cocg_update_precond" : "block_apply", kern, g, dim3(STPB), smem, pb.pd, sel.list, sel.act, sys_e,
                        F, sst, upd, x, r, rs, p, q, z, zs, part_rr, part_rz);
         };
@@ -1622,7 +1644,8 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
                   diagR, (const cx<R>*)xr, (long long)N, yr, (long long)N, (double2*)nullptr);
         }
         if (mixed) rn.go("widen", k_widen, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, (const float2*)reinterpret_cast<float2*>(yr), y);
-        if (cudaGetLastError() != cudaSuccess) rc = vbk_cuda_fail(cudaGetLastError(), "operator kernels");
+        if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) rc = vbk_cuda_fail(ce, "operator kernels");
+        if (!rc && rn.first_error != cudaSuccess) rc = VBK_ERR_CUDA;
         if (!rc && block) {
             std::vector<int> hf(nE);
             if (cudaMemcpyAsync(hf.data(), pfail, nE * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
