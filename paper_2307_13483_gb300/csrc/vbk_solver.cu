@@ -63,6 +63,31 @@ struct Sel {
 };
 __device__ __forceinline__ int sel_sys(const Sel& q) { return q.list ? q.list[blockIdx.y] : (int)blockIdx.y; }
 
+// Sum over the block in the kernel's own precision (GB300 executes FP64 at a small fraction of
+// the FP32 rate, so FP32 kernels reduce in FP32); widened to double in thread 0 only.
+template <class R> __device__ __forceinline__ cx<R> warp_sum_c(cx<R> v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+template <class R> __device__ __forceinline__ double2 block_sum_c(cx<R> v, cx<R>* sh) {
+    v = warp_sum_c<R>(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    cx<R> r = mkc<R>(0, 0);
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? sh[lane] : mkc<R>(0, 0);
+        r = warp_sum_c<R>(r);
+    }
+    return cvt_to_d<R>(r);
+}
+
 template <class R> __device__ __forceinline__ const R* tabp(const DevModel& md);
 template <> __device__ __forceinline__ const float* tabp<float>(const DevModel& md) { return md.tab32; }
 template <> __device__ __forceinline__ const double* tabp<double>(const DevModel& md) { return md.tab64; }
@@ -153,7 +178,7 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
                                                 cx<R>* __restrict__ y, long long ys, const double2* __restrict__ b,
                                                 double2* __restrict__ part, int red) {
     __shared__ SPt<R> pts[MV_MAXPTS];
-    __shared__ double2 sh[32];
+    __shared__ cx<R> sh[32];
     const int nchunk = (md.Nnu + TPB - 1) / TPB;
     const int d = blockIdx.x / nchunk;
     const int nu = (blockIdx.x - d * nchunk) * TPB + threadIdx.x;
@@ -227,7 +252,7 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
     }
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-        double2 loc = make_double2(0.0, 0.0);
+        cx<R> loc = mkc<R>(0, 0);
         if (on[t] && inr) {
             cx<R> out = acc[t];
             if (b) {
@@ -236,14 +261,13 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
             }
             y[(long long)sy[t] * ys + i] = out;
             if (red == 1) {
-                const cx<R> tt = cmul<R>(xi[t], out);
-                loc = make_double2((double)tt.x, (double)tt.y);
+                loc = cmul<R>(xi[t], out);
             } else if (red == 2) {
-                loc = make_double2((double)cabs2<R>(out), 0.0);
+                loc = mkc<R>(cabs2<R>(out), 0);
             }
         }
         if (red) {
-            const double2 tot = block_sum2(loc, sh);
+            const double2 tot = block_sum_c<R>(loc, sh);
             if (threadIdx.x == 0 && on[t]) part[(long long)sy[t] * gridDim.x + blockIdx.x] = tot;
         }
     }
@@ -330,12 +354,12 @@ template <class R>
 __global__ void __launch_bounds__(BTPB) k_block_apply(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
                                                      const cx<R>* __restrict__ F, const cx<R>* __restrict__ r, long long rs,
                                                      cx<R>* __restrict__ z, long long zs, double2* __restrict__ part) {
-    __shared__ double2 sh[32];
+    __shared__ cx<R> sh[32];
     const int s = sel_sys(sel);
     if (s < 0 || (sel.act && !sel.act[s])) return;
     const int blk = blockIdx.x * blockDim.x + threadIdx.x;
     const int L = pl.L, p = pl.p, nblk = pl.nblk;
-    double2 loc = make_double2(0.0, 0.0);
+    cx<R> loc = mkc<R>(0, 0);
     if (blk < nblk) {
         const int e = sys_e[s];
         const cx<R>* Fe = F + (long long)e * L * (p + 1) * nblk + blk;
@@ -359,14 +383,12 @@ __global__ void __launch_bounds__(BTPB) k_block_apply(PlanDev pl, const int* __r
                 v = csub<R>(v, cmul<R>(Fe[((long long)(c + k) * (p + 1) + k) * nblk], zv[base + pl.chain_off[c + k]]));
             zv[ic] = v;
             if (part) {
-                const cx<R> t = cmul<R>(rv[ic], v);
-                loc.x += (double)t.x;
-                loc.y += (double)t.y;
+                loc = cfma<R>(rv[ic], v, loc);
             }
         }
     }
     if (part) {
-        const double2 tot = block_sum2(loc, sh);
+        const double2 tot = block_sum_c<R>(loc, sh);
         if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
     }
 }
@@ -391,7 +413,7 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
                                                       double2* __restrict__ part_rr, double2* __restrict__ part_rz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-    __shared__ double2 sh[32];
+    __shared__ cx<R> sh[32];
     const int s = alist ? alist[blockIdx.y] : blockIdx.y;
     if (s < 0 || (act && !act[s])) return;
     const int L = pl.L, p = pl.p, nblk = pl.nblk;
@@ -405,7 +427,7 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
     cx<R> al = mkc<R>(0, 0);
     if (upd) al = cvt_from_d<R>(st[s].alpha);
     // ---- gather (and update)
-    double lrr = 0.0;
+    R lrr = 0;
     const int tot = G * nrun * runlen;
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
         const int k = idx % runlen;
@@ -418,13 +440,13 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
             x[so + el] = cfma<R>(al, pp, xv);
             rvv = csub<R>(rvv, cmul<R>(al, qq));
             rv[el] = rvv;
-            lrr += (double)cabs2<R>(rvv);
+            lrr += cabs2<R>(rvv);
         }
         tile[(pl.run_c0[rr_] + k * csr) * (SG + 1) + b] = rvv;
     }
     __syncthreads();
     // ---- chain walk: thread b < G owns block b0 + b
-    double2 lrz = make_double2(0.0, 0.0);
+    cx<R> lrz = mkc<R>(0, 0);
     if (threadIdx.x < G) {
         const int b = threadIdx.x;
         const cx<R>* Fe = F + (long long)e * L * (p + 1) * nblk + b0 + b;
@@ -443,9 +465,7 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
 #pragma unroll
             for (int k = P; k >= 1; --k) w = csub<R>(w, cmul<R>(Lr[k], win[k - 1]));
             const cx<R> v = cmul<R>(w, Lr[0]);
-            const cx<R> t = cmul<R>(w, v);
-            lrz.x += (double)t.x;
-            lrz.y += (double)t.y;
+            lrz = cfma<R>(w, v, lrz);
             tile[c * (SG + 1) + b] = v;
 #pragma unroll
             for (int k = P - 1; k >= 1; --k) win[k] = win[k - 1];
@@ -485,11 +505,11 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
         zv[el] = tile[(pl.run_c0[rr_] + k * csr) * (SG + 1) + b];
     }
     if (part_rr) {
-        const double2 t = block_sum2(make_double2(lrr, 0.0), sh);
+        const double2 t = block_sum_c<R>(mkc<R>(lrr, 0), sh);
         if (threadIdx.x == 0) part_rr[(long long)s * gridDim.x + blockIdx.x] = t;
     }
     if (part_rz) {
-        const double2 t = block_sum2(lrz, sh);
+        const double2 t = block_sum_c<R>(lrz, sh);
         if (threadIdx.x == 0) part_rz[(long long)s * gridDim.x + blockIdx.x] = t;
     }
 }
@@ -500,21 +520,20 @@ __global__ void __launch_bounds__(TPB) k_point_precond(int N, const int* __restr
                                                       int mode, const cx<R>* __restrict__ diag, const cx<R>* __restrict__ r,
                                                       long long rs, cx<R>* __restrict__ z, long long zs,
                                                       double2* __restrict__ part) {
-    __shared__ double2 sh[32];
+    __shared__ cx<R> sh[32];
     const int s = sel_sys(sel);
     if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double2 loc = make_double2(0.0, 0.0);
+    cx<R> loc = mkc<R>(0, 0);
     if (i < N) {
         const cx<R> ri = r[(long long)s * rs + i];
         cx<R> zi = ri;
         if (mode == 0) zi = cdiv<R>(ri, diag[(long long)sys_e[s] * N + i]);
         z[(long long)s * zs + i] = zi;
-        const cx<R> t = cmul<R>(ri, zi);
-        loc = make_double2((double)t.x, (double)t.y);
+        loc = cmul<R>(ri, zi);
     }
     if (part) {
-        const double2 tot = block_sum2(loc, sh);
+        const double2 tot = block_sum_c<R>(loc, sh);
         if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
     }
 }
@@ -661,11 +680,11 @@ __global__ void __launch_bounds__(TPB) k_cocg_update(int N, Sel sel, const SysSt
                                                     cx<R>* __restrict__ x, cx<R>* __restrict__ r, const cx<R>* __restrict__ p,
                                                     const cx<R>* __restrict__ q, cx<R>* __restrict__ z,
                                                     double2* __restrict__ part_rr, double2* __restrict__ part_rz) {
-    __shared__ double2 sh[32];
+    __shared__ cx<R> sh[32];
     const int s = sel_sys(sel);
     if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double2 lrr = make_double2(0.0, 0.0), lrz = make_double2(0.0, 0.0);
+    cx<R> lrr = mkc<R>(0, 0), lrz = mkc<R>(0, 0);
     if (i < N) {
         const long long o = (long long)s * N + i;
         const cx<R> al = cvt_from_d<R>(st[s].alpha);
@@ -673,18 +692,17 @@ __global__ void __launch_bounds__(TPB) k_cocg_update(int N, Sel sel, const SysSt
         const cx<R> qa = cmul<R>(al, q[o]);
         const cx<R> rn = csub<R>(r[o], qa);
         r[o] = rn;
-        lrr.x = (double)cabs2<R>(rn);
+        lrr.x = cabs2<R>(rn);
         if (pmode <= 0) {
             const cx<R> zi = pmode == 0 ? cdiv<R>(rn, diag[(long long)sys_e[s] * N + i]) : rn;
             z[o] = zi;
-            const cx<R> t = cmul<R>(rn, zi);
-            lrz = make_double2((double)t.x, (double)t.y);
+            lrz = cmul<R>(rn, zi);
         }
     }
-    double2 tot = block_sum2(lrr, sh);
+    double2 tot = block_sum_c<R>(lrr, sh);
     if (threadIdx.x == 0) part_rr[(long long)s * gridDim.x + blockIdx.x] = tot;
     if (pmode <= 0) {
-        tot = block_sum2(lrz, sh);
+        tot = block_sum_c<R>(lrz, sh);
         if (threadIdx.x == 0) part_rz[(long long)s * gridDim.x + blockIdx.x] = tot;
     }
 }
@@ -774,8 +792,8 @@ __global__ void __launch_bounds__(TPB) k_vdots(int N, int m, Sel sel, const cx<R
                 a.y += t.y;
             }
         }
-        double2 dv = warp_sum2(make_double2((double)a.x, (double)a.y));
-        if (lane == 0) sh[wp * 257 + k] = dv;
+        const cx<R> dv = warp_sum_c<R>(a);
+        if (lane == 0) sh[wp * 257 + k] = cvt_to_d<R>(dv);
     }
     __syncthreads();
     for (int k = threadIdx.x; k <= j; k += blockDim.x) {
@@ -810,10 +828,10 @@ __global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, Sel sel, const cx
                                                 int j, const double2* __restrict__ h, cx<R>* __restrict__ w, int mode,
                                                 double2* __restrict__ part) {
     __shared__ double2 sh[(TPB / 32) * 257];
-    __shared__ double2 hs[257];
+    __shared__ cx<R> hs[257];
     const int s = sel_sys(sel);
     if (s < 0 || (sel.act && !sel.act[s])) return;
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) hs[k] = h[(long long)s * (m + 1) + k];
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) hs[k] = cvt_from_d<R>(h[(long long)s * (m + 1) + k]);
     __syncthreads();
     const long long vs = (long long)(m + 1) * N;
     const cx<R>* Vs = V + s * vs;
@@ -827,7 +845,7 @@ __global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, Sel sel, const cx
     }
     for (int k = 0; k <= j; ++k) {
         const cx<R>* vk = Vs + (long long)k * N;
-        const cx<R> hk = cvt_from_d<R>(hs[k]);
+        const cx<R> hk = hs[k];
 #pragma unroll
         for (int u = 0; u < VEPT; ++u) {
             const int i = i0 + u * TPB;
@@ -853,8 +871,8 @@ __global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, Sel sel, const cx
                     a.y += t.y;
                 }
             }
-            double2 dv = warp_sum2(make_double2((double)a.x, (double)a.y));
-            if (lane == 0) sh[wp * 257 + k] = dv;
+            const cx<R> dv = warp_sum_c<R>(a);
+            if (lane == 0) sh[wp * 257 + k] = cvt_to_d<R>(dv);
         }
         __syncthreads();
         for (int k = threadIdx.x; k <= j; k += blockDim.x) {
@@ -866,10 +884,10 @@ __global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, Sel sel, const cx
             part[((long long)s * gridDim.x + blockIdx.x) * (m + 1) + k] = t;
         }
     } else {
-        double a = 0.0;
+        R a = 0;
 #pragma unroll
-        for (int u = 0; u < VEPT; ++u) a += (double)cabs2<R>(wl[u]);
-        const double2 tot = block_sum2(make_double2(a, 0.0), sh);
+        for (int u = 0; u < VEPT; ++u) a += cabs2<R>(wl[u]);
+        const double2 tot = block_sum_c<R>(mkc<R>(a, 0), reinterpret_cast<cx<R>*>(sh));
         if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
     }
 }
@@ -971,22 +989,24 @@ __global__ void k_tri_solve(int nsys, int m, const SysState* __restrict__ st, co
     }
 }
 
-// u = sum_{k < j} y_k V_k
+// u = sum_{k < j} y_k V_k (accumulated in the inner precision)
 template <class R>
 __global__ void __launch_bounds__(TPB) k_vcombine(int N, int m, Sel sel, const SysState* __restrict__ st,
                                                  const cx<R>* __restrict__ V, const double2* __restrict__ y,
                                                  cx<R>* __restrict__ u) {
+    __shared__ cx<R> ys[257];
     const int s = sel_sys(sel);
     if (s < 0 || (sel.act && !sel.act[s])) return;
+    const int n = st[s].j;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) ys[k] = cvt_from_d<R>(y[(long long)s * (m + 1) + k]);
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int n = st[s].j;
     const cx<R>* Vs = V + (long long)s * (m + 1) * N;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int k = 0; k < n; ++k) acc = cfma<double>(y[(long long)s * (m + 1) + k], cvt_to_d<R>(Vs[(long long)k * N + i]), acc);
-    u[(long long)s * N + i] = cvt_from_d<R>(acc);
+    cx<R> acc = mkc<R>(0, 0);
+    for (int k = 0; k < n; ++k) acc = cfma<R>(ys[k], Vs[(long long)k * N + i], acc);
+    u[(long long)s * N + i] = acc;
 }
-
 
 __global__ void k_gmres_cycle_start(int nsys, int m, const int* __restrict__ act, double2* __restrict__ g) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
