@@ -217,13 +217,30 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         dm.ch_b[c] = m->chans[c].b;
     }
     for (int k = 0; k < MAXCH; ++k) dm.mu_d[k] = mu_d[k];
-    // one device allocation: entries | diagonal entries | tab64 | tab32
+    // coefficient columns of the stencil points (Sec. III: "all energy factors and square roots can
+    // be precalculated")
+    const size_t npc = std::max<size_t>(1, offd.size()) * (size_t)m->Nnu;
+    std::vector<double> pc(npc, 0.0);
+    for (size_t k = 0; k < offd.size(); ++k) {
+        const DevEntry& e = offd[k].e;
+        for (int nu = 0; nu < m->Nnu; ++nu) {
+            double c = e.coef;
+            for (int mm = 0; mm < m->M && c != 0.0; ++mm) {
+                if (e.col[mm] < 0) continue;
+                const int n = (nu / m->stride[mm]) % m->nb[mm];
+                const int nn = n + e.delta[mm];
+                c = (nn >= 0 && nn < m->nb[mm]) ? c * m->tab[e.col[mm] + n] : 0.0;
+            }
+            pc[k * m->Nnu + nu] = c;
+        }
+    }
+    // one device allocation: entries | diagonal entries | tab64 | tab32 | pc64 | pc32
     const size_t ne = std::max<size_t>(1, offd.size()), nd = std::max<size_t>(1, diagp.size()), nt = m->tab.size();
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b1 = al(ne * sizeof(DevEntry)), b2 = al(nd * sizeof(DevEntry)), b3 = al(nt * sizeof(double)),
-                 b4 = al(nt * sizeof(float));
+                 b4 = al(nt * sizeof(float)), b5 = al(npc * sizeof(double)), b6 = al(npc * sizeof(float));
     char* mem = nullptr;
-    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4);
+    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6);
     if (err != cudaSuccess) return vbk_cuda_fail(err, "model tables");
     m->dev_mem = mem;
     std::vector<DevEntry> he(ne), hd(nd);
@@ -236,6 +253,16 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         (err = cudaMemcpy(mem + b1 + b2, m->tab.data(), nt * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (err = cudaMemcpy(mem + b1 + b2 + b3, t32.data(), nt * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
         return vbk_cuda_fail(err, "model table upload");
+    {
+        std::vector<float> pc32(npc);
+        for (size_t k = 0; k < npc; ++k) pc32[k] = (float)pc[k];
+        if ((err = cudaMemcpy(mem + b1 + b2 + b3 + b4, pc.data(), npc * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(mem + b1 + b2 + b3 + b4 + b5, pc32.data(), npc * sizeof(float), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+            return vbk_cuda_fail(err, "model coefficient upload");
+        dm.pc64 = (const double*)(mem + b1 + b2 + b3 + b4);
+        dm.pc32 = (const float*)(mem + b1 + b2 + b3 + b4 + b5);
+    }
     dm.ent = (const DevEntry*)mem;
     dm.dent = (const DevEntry*)(mem + b1);
     dm.tab64 = (const double*)(mem + b1 + b2);

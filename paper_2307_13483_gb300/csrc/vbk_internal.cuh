@@ -82,6 +82,10 @@ struct DevModel {
     const DevEntry* dent;
     const double* tab64;
     const float* tab32;
+    // coefficient columns of the off-diagonal stencil points: pc[k][nu] = coef_k * prod_m
+    // (q_m^pow)_{n_m, n_m + delta_m}, zero where the neighbour leaves the basis (energy-independent)
+    const double* pc64;
+    const float* pc32;
     int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
     double ch_a[MAXCH], ch_b[MAXCH];
     int mu_d[MAXCH];  // discrete state coupled to partial wave mu

@@ -157,48 +157,37 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
     if (d32) d32[t] = make_float2((float)re, (float)im);
 }
 
-// Batched matvec, coefficient reuse across systems: one thread computes the stencil
-// coefficients of one element once and applies them to S systems (the off-diagonal part of A
-// does not depend on the energy; only the diagonal table does).  Grid: x = (state d, chunk of
-// TPB elements of that state), y = groups of S systems of the list.  The stencil points of
-// state d are staged in shared memory.  Partials (red = 1: x^T y, red = 2: ||y||^2) per
-// (system, blockIdx.x).
+// Batched matvec y = A x (or y = b - A x): one thread owns one element of one state and applies
+// its stencil to S systems.  The off-diagonal part of A is energy-independent, so the coefficient
+// of every stencil point is read once per element (precomputed column, L2-resident) and reused
+// for the S systems; only the diagonal table depends on the energy.  Neighbour indices are
+// clamped into the vector (their coefficient is zero there).  Grid: x = (state d, chunk of TPB
+// elements), y = groups of S systems of the list.  Optional partials (red = 1: x^T y,
+// red = 2: ||y||^2) per (system, blockIdx.x), reduced in the kernel's precision.
 constexpr int MV_MAXPTS = 256;
 
-template <class R> struct SPt {
-    R coef;
-    int off;              // (dp - d) * Nnu + lin: neighbour offset relative to the element
-    short col[MAXM];      // table column of each mode (-1: not involved)
-    short delta[MAXM];
-};
+template <class R> __device__ __forceinline__ const R* pcp(const DevModel& md);
+template <> __device__ __forceinline__ const float* pcp<float>(const DevModel& md) { return md.pc32; }
+template <> __device__ __forceinline__ const double* pcp<double>(const DevModel& md) { return md.pc64; }
 
-template <class R, int M, int S>
+template <class R, int S>
 __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
                                                 const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x, long long xs,
                                                 cx<R>* __restrict__ y, long long ys, const double2* __restrict__ b,
                                                 double2* __restrict__ part, int red) {
-    __shared__ SPt<R> pts[MV_MAXPTS];
-    __shared__ cx<R> sh[32];
+    __shared__ int offs[MV_MAXPTS];
+    __shared__ cx<R> redsh[TPB / 32][S];
     const int nchunk = (md.Nnu + TPB - 1) / TPB;
     const int d = blockIdx.x / nchunk;
     const int nu = (blockIdx.x - d * nchunk) * TPB + threadIdx.x;
-    const int N = md.N;
+    const int N = md.N, Nnu = md.Nnu;
     const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        const DevEntry e = md.ent[pb + k];
-        SPt<R> q;
-        q.coef = (R)e.coef;
-        q.off = (e.dp - d) * md.Nnu + e.lin;
-#pragma unroll
-        for (int m = 0; m < MAXM; ++m) {
-            q.col[m] = (short)e.col[m];
-            q.delta[m] = (short)e.delta[m];
-        }
-        pts[k] = q;
+        const DevEntry& e = md.ent[pb + k];
+        offs[k] = (e.dp - d) * Nnu + e.lin;
     }
-    // systems of this CTA
+    const cx<R>* xp[S];
     int sy[S];
-    bool on[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         const int li = blockIdx.y * S + k;
@@ -208,67 +197,64 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
             if (s >= 0 && sel.act && !sel.act[s]) s = -1;
         }
         sy[k] = s;
-        on[k] = s >= 0;
+        xp[k] = x + (long long)(s < 0 ? 0 : s) * xs;
     }
     __syncthreads();
-    const bool inr = nu < md.Nnu;
-    const int i = d * md.Nnu + nu;
+    const bool inr = nu < Nnu;
+    const int i = d * Nnu + nu;
     cx<R> acc[S], xi[S];
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         acc[k] = mkc<R>(0, 0);
         xi[k] = mkc<R>(0, 0);
-        if (on[k] && inr) {
-            xi[k] = x[(long long)sy[k] * xs + i];
+        if (sy[k] >= 0 && inr) {
+            xi[k] = xp[k][i];
             acc[k] = cmul<R>(diag[(long long)sys_e[sy[k]] * N + i], xi[k]);
         }
     }
     if (inr) {
-        int n[MAXM];
-        decode<M>(md, nu, n);
-        const R* tab = tabp<R>(md);
+        const R* pc = pcp<R>(md) + (long long)pb * Nnu + nu;
         for (int k = 0; k < np; ++k) {
-            const SPt<R>& q = pts[k];
-            R c = q.coef;
-            bool ok = true;
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                if (q.col[m] >= 0) {
-                    ok = ok && (unsigned)(n[m] + q.delta[m]) < (unsigned)md.nb[m];
-                    c *= __ldg(tab + q.col[m] + n[m]);
-                }
-            }
-            if (ok) {
-                const int j = i + q.off;
+            const R c = __ldg(pc + (long long)k * Nnu);
+            if (c != (R)0) {
+                const int j = min(max(i + offs[k], 0), N - 1);
 #pragma unroll
                 for (int t = 0; t < S; ++t)
-                    if (on[t]) {
-                        const cx<R> v = x[(long long)sy[t] * xs + j];
-                        acc[t].x -= c * v.x;
-                        acc[t].y -= c * v.y;
+                    if (sy[t] >= 0) {
+                        const cx<R> v = xp[t][j];
+                        acc[t].x = fma(-c, v.x, acc[t].x);
+                        acc[t].y = fma(-c, v.y, acc[t].y);
                     }
             }
         }
     }
+    cx<R> loc[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-        cx<R> loc = mkc<R>(0, 0);
-        if (on[t] && inr) {
+        loc[t] = mkc<R>(0, 0);
+        if (sy[t] >= 0 && inr) {
             cx<R> out = acc[t];
             if (b) {
                 const double2 bb = b[(long long)sy[t] * N + i];
                 out = mkc<R>((R)bb.x - out.x, (R)bb.y - out.y);
             }
             y[(long long)sy[t] * ys + i] = out;
-            if (red == 1) {
-                loc = cmul<R>(xi[t], out);
-            } else if (red == 2) {
-                loc = mkc<R>(cabs2<R>(out), 0);
-            }
+            if (red == 1) loc[t] = cmul<R>(xi[t], out);
+            else if (red == 2) loc[t] = mkc<R>(cabs2<R>(out), 0);
         }
-        if (red) {
-            const double2 tot = block_sum_c<R>(loc, sh);
-            if (threadIdx.x == 0 && on[t]) part[(long long)sy[t] * gridDim.x + blockIdx.x] = tot;
+    }
+    if (red) {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const cx<R> v = warp_sum_c<R>(loc[t]);
+            if (lane == 0) redsh[w][t] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < S && sy[threadIdx.x] >= 0) {
+            cx<R> tot = mkc<R>(0, 0);
+            for (int q = 0; q < TPB / 32; ++q) tot = cadd<R>(tot, redsh[q][threadIdx.x]);
+            part[(long long)sy[threadIdx.x] * gridDim.x + blockIdx.x] = cvt_to_d<R>(tot);
         }
     }
 }
@@ -1188,12 +1174,29 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
 }
 
 // Launches the block preconditioner z = B^-1 r (optionally fused with the COCG update).
+template <class R> int prepare_staged(const DevPlanBuf& pb) {
+    if (!pb.staged) return VBK_OK;
+    const size_t smem = (size_t)pb.pd.L * (SG + 1) * sizeof(cx<R>);
+    if (smem <= 48 * 1024) return VBK_OK;
+    cudaError_t ce = cudaSuccess;
+    switch (pb.P) {
+        case 2: ce = cudaFuncSetAttribute(k_block_staged<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+        case 4: ce = cudaFuncSetAttribute(k_block_staged<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+        case 8: ce = cudaFuncSetAttribute(k_block_staged<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+        default: ce = cudaFuncSetAttribute(k_block_staged<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+    }
+    return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "block preconditioner shared-memory opt-in");
+}
+
 template <class R>
 void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny, const int* sys_e, const cx<R>* F,
                    const SysState* sst, int upd, cx<R>* x, cx<R>* r, long long rs, const cx<R>* p, const cx<R>* q, cx<R>* z,
                    long long zs, double2* part_rr, double2* part_rz);
 
 inline unsigned cdiv_u(long long a, long long b);
+// Opt the staged kernel of this plan in to the shared memory it needs (outside any capture).
+template <class R> int prepare_staged(const DevPlanBuf& pb);
+
 inline int block_partials(const DevPlanBuf& pb) {
     return pb.staged ? (int)((pb.pd.nblk + 31) / 32) : (int)((pb.pd.nblk + BTPB - 1) / BTPB);
 }
@@ -1206,7 +1209,7 @@ void launch_matvec(Runner& rn, const char* name, const DevModel& md, const int* 
     constexpr int S = sizeof(T) == 4 ? 8 : 4;
     const int nchunk = (md.Nnu + TPB - 1) / TPB;
     const dim3 g((unsigned)(md.ns * nchunk), (nlist + S - 1) / S);
-    rn.go(name, k_matvec2<T, M, S>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red);
+    rn.go(name, k_matvec2<T, S>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red);
 }
 inline int matvec_partials(const DevModel& md) { return md.ns * ((md.Nnu + TPB - 1) / TPB); }
 
@@ -1231,7 +1234,11 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         int rc = vbk_make_block_plan(mdl, pspan, &bp);
         if (rc) return rc;
         rc = upload_plan(bp, mdl, st, &pbuf);
-        if (rc) return rc;
+        if (!rc) rc = prepare_staged<R>(pbuf);
+        if (rc) {
+            if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+            return rc;
+        }
     }
 
     // ---- workspace
@@ -1314,6 +1321,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     int rc = VBK_OK;
     int* hcnt = nullptr;
     double* dE = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     std::vector<int> ones(nsys, 1), iota(nsys);
     for (int k = 0; k < nsys; ++k) iota[k] = k;
     std::vector<SysState> hst(nsys);
@@ -1407,19 +1415,19 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 rn.go("cocg_start", k_cocg_start, dim3(gs), dim3(128), nsys, sst, (const int*)inner, (const double2*)partB,
                       nb_rz);
                 cudaMemcpyAsync(pv, z, (size_t)nsys * NN * sizeof(cx<R>), cudaMemcpyDeviceToDevice, st);
-                int k = 0;
-                for (;;) {
+                // one COCG iteration for the systems of the inner list
+                auto cocg_iter = [&](unsigned ny) {
                     const Sel sc{ilist, inner};
-                    launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, n_in, (const cx<R>*)diagR, (const cx<R>*)pv,
+                    launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, ny, (const cx<R>*)diagR, (const cx<R>*)pv,
                                         (long long)N, q, (long long)N, (const double2*)nullptr, partA, 1);
                     rn.go("cocg_alpha", k_cocg_alpha, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partA,
                           nb_mv);
                     if (block) {
                         // fused x += alpha p, r -= alpha q and z = B^-1 r
-                        block_precond<R>(rn, pbuf, N, sc, n_in, (const int*)sys_e, (const cx<R>*)F, (const SysState*)sst, 1, x,
+                        block_precond<R>(rn, pbuf, N, sc, ny, (const int*)sys_e, (const cx<R>*)F, (const SysState*)sst, 1, x,
                                          r, (long long)N, (const cx<R>*)pv, (const cx<R>*)q, z, (long long)N, partC, partB);
                     } else {
-                        rn.go("cocg_update", k_cocg_update<R>, dim3(nb_e, n_in), dim3(TPB), N, sc, (const SysState*)sst,
+                        rn.go("cocg_update", k_cocg_update<R>, dim3(nb_e, ny), dim3(TPB), N, sc, (const SysState*)sst,
                               (const int*)sys_e, pmode, (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z,
                               partC, partB);
                     }
@@ -1427,19 +1435,86 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
                     rn.go("cocg_beta", k_cocg_beta, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partC,
                           (block && pbuf.staged) ? nb_rz : nb_e, (const double2*)partB, nb_rz, o.max_iter, cnt, ilist);
-                    rn.go("cocg_p", k_cocg_p<R>, dim3(nb_e, n_in), dim3(TPB), N, sc, (const SysState*)sst, (const cx<R>*)z, pv);
-                    ++k;
-                    if (k % std::max(1, o.check_every) == 0) {
+                    rn.go("cocg_p", k_cocg_p<R>, dim3(nb_e, ny), dim3(TPB), N, sc, (const SysState*)sst, (const cx<R>*)z, pv);
+                };
+                const int K = std::max(1, o.check_every);
+                int k = 0;
+                if (!rn.timing) {
+                    // K iterations as one CUDA graph (grids sized for the active systems; systems that
+                    // retire inside a chunk leave their CTAs at once), relaunched until none is active and
+                    // re-captured when the active count has halved
+                    long long per_launch = 0;
+                    auto capture = [&](unsigned ny) -> bool {
+                        const long long l0 = mdl->launches;
+                        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "graph capture"));
+                            return false;
+                        }
+                        for (int t = 0; t < K; ++t) cocg_iter(ny);
+                        cudaGraph_t graph = nullptr;
+                        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+                        per_launch = mdl->launches - l0;
+                        mdl->launches = l0;
+                        if (ce != cudaSuccess || rn.first_error != cudaSuccess) {
+                            if (graph) cudaGraphDestroy(graph);
+                            fail(ce != cudaSuccess ? vbk_cuda_fail(ce, "graph capture") : VBK_ERR_CUDA);
+                            return false;
+                        }
+                        bool ok = false;
+                        if (gexec) {
+                            cudaGraphExecUpdateResultInfo info;
+                            ok = cudaGraphExecUpdate(gexec, graph, &info) == cudaSuccess;
+                            if (!ok) {
+                                cudaGetLastError();
+                                cudaGraphExecDestroy(gexec);
+                                gexec = nullptr;
+                            }
+                        }
+                        if (!ok && cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) {
+                            cudaGraphDestroy(graph);
+                            gexec = nullptr;
+                            fail(vbk_cuda_fail(cudaGetLastError(), "graph instantiation"));
+                            return false;
+                        }
+                        cudaGraphDestroy(graph);
+                        return true;
+                    };
+                    unsigned ny = n_in;
+                    if (!capture(ny)) break;
+                    for (;;) {
+                        if (cudaGraphLaunch(gexec, st) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "graph launch"));
+                            break;
+                        }
+                        mdl->launches += per_launch;
+                        k += K;
                         cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
                         if (cudaStreamSynchronize(st) != cudaSuccess) {
                             fail(vbk_cuda_fail(cudaGetLastError(), "COCG iterations"));
                             break;
                         }
-                        rn.flush();
-                        if (hcnt[0] == 0) break;
-                        n_in = (unsigned)hcnt[0];
+                        if (hcnt[0] == 0 || k > o.max_iter + K) break;
+                        if ((unsigned)hcnt[0] * 2 <= ny) {
+                            ny = (unsigned)hcnt[0];
+                            if (!capture(ny)) break;
+                        }
                     }
-                    if (k > o.max_iter + 8) break;
+                } else {
+                    for (;;) {
+                        cocg_iter(n_in);
+                        ++k;
+                        if (k % K == 0) {
+                            cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+                            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                                fail(vbk_cuda_fail(cudaGetLastError(), "COCG iterations"));
+                                break;
+                            }
+                            rn.flush();
+                            if (hcnt[0] == 0) break;
+                            n_in = (unsigned)hcnt[0];
+                        }
+                        if (k > o.max_iter + 8) break;
+                    }
                 }
                 if (rc) break;
                 rn.go("accumulate", k_accumulate<R>, dim3(nb_e, n_out), dim3(TPB), N, so2, (const SysState*)sst,
@@ -1544,6 +1619,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     cudaFreeAsync(wsbase, st);
     if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
     cudaStreamSynchronize(st);
+    if (gexec) cudaGraphExecDestroy(gexec);
     if (hcnt) cudaFreeHost(hcnt);
     return rc;
 }
@@ -1557,13 +1633,6 @@ void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny
         const dim3 g((pb.pd.nblk + SG - 1) / SG, ny);
         auto launch = [&](auto kern) {
             if (g.x == 0 || g.y == 0) return;
-            if (smem > 48 * 1024) {
-                const cudaError_t ce = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (ce != cudaSuccess) {
-                    rn.note_error(ce, "block preconditioner shared-memory opt-in");
-                    return;
-                }
-            }
             rn.go_smem(upd ? "cocg_update_precond" : "block_apply", kern, g, dim3(STPB), smem, pb.pd, sel.list, sel.act, sys_e,
                        F, sst, upd, x, r, rs, p, q, z, zs, part_rr, part_rz);
         };
@@ -1611,7 +1680,11 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
         int rc = vbk_make_block_plan(m, span, &bp);
         if (rc) return rc;
         rc = upload_plan(bp, m, st, &pbuf);
-        if (rc) return rc;
+        if (!rc) rc = prepare_staged<R>(pbuf);
+        if (rc) {
+            if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+            return rc;
+        }
     }
     size_t bytes = carve_size<double2>((size_t)nE * N) + carve_size<float2>(mixed ? (size_t)nE * N : 1) +
                    2 * carve_size<cx<R>>(mixed ? (size_t)nsys * N : 1) + carve_size<int>(nsys) + carve_size<double>(nE) +
