@@ -596,6 +596,7 @@ int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
 void vbk_free_model(vbk_model* m) {
     if (!m) return;
     if (m->dev_mem) cudaFree(m->dev_mem);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     delete m;
 }
 

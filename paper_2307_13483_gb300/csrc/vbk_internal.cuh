@@ -121,6 +121,7 @@ struct vbk_model {
     std::vector<KTimer> timers;
     long long launches = 0;
     int device = 0;
+    cudaStream_t cap_stream = nullptr;  // library-owned stream used only to capture CUDA graphs
 };
 
 // --------------------------------------------------------------------------- level shift

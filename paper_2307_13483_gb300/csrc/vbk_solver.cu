@@ -1431,8 +1431,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                               (const int*)sys_e, pmode, (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z,
                               partC, partB);
                     }
-                    cudaMemsetAsync(cnt, 0, sizeof(int), st);
-                    cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
+                    cudaMemsetAsync(cnt, 0, sizeof(int), rn.st);
+                    cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), rn.st);
                     rn.go("cocg_beta", k_cocg_beta, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partC,
                           (block && pbuf.staged) ? nb_rz : nb_e, (const double2*)partB, nb_rz, o.max_iter, cnt, ilist);
                     rn.go("cocg_p", k_cocg_p<R>, dim3(nb_e, ny), dim3(TPB), N, sc, (const SysState*)sst, (const cx<R>*)z, pv);
@@ -1445,14 +1445,23 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     // re-captured when the active count has halved
                     long long per_launch = 0;
                     auto capture = [&](unsigned ny) -> bool {
+                        // captured on a library-owned stream (the caller's may be the legacy default stream,
+                        // which cannot be captured); the graph is launched on the caller's stream
+                        if (!mdl->cap_stream &&
+                            cudaStreamCreateWithFlags(&mdl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "capture stream"));
+                            return false;
+                        }
                         const long long l0 = mdl->launches;
-                        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                        if (cudaStreamBeginCapture(mdl->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
                             fail(vbk_cuda_fail(cudaGetLastError(), "graph capture"));
                             return false;
                         }
+                        rn.st = mdl->cap_stream;
                         for (int t = 0; t < K; ++t) cocg_iter(ny);
+                        rn.st = st;
                         cudaGraph_t graph = nullptr;
-                        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+                        const cudaError_t ce = cudaStreamEndCapture(mdl->cap_stream, &graph);
                         per_launch = mdl->launches - l0;
                         mdl->launches = l0;
                         if (ce != cudaSuccess || rn.first_error != cudaSuccess) {
