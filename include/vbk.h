@@ -121,11 +121,14 @@ typedef struct {
     double inner_tol;  /* relative tolerance of each inner solve (COCG; GMRES stops a cycle
                           early when its residual estimate reaches it)                      */
     int check_every;   /* iterations between host convergence checks (>= 1)                */
-    int timing;        /* 1: record per-kernel CUDA-event timings (see vbk_kernel_timings)  */
+    int timing;        /* 1: record per-kernel CUDA-event timings (see vbk_kernel_timings);
+                          the Krylov loop then launches kernels directly instead of as graphs */
+    int autotune;      /* 1: on the first solve of a model, time the matvec kernel variants on
+                          the batch and keep the fastest (per precision) for later calls       */
 } vbk_opts;
 
 /* Fills `o` with defaults: GMRES, VBK_MIXED, Jacobi, restart 64, max_iter 20000,
- * max_refine 40, tol 1e-8, inner_tol 1e-5, check_every 8, timing 0. */
+ * max_refine 40, tol 1e-8, inner_tol 1e-5, check_every 8, timing 0, autotune 1. */
 void vbk_default_opts(vbk_opts* o);
 
 typedef struct {
@@ -201,9 +204,13 @@ int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi
  *   E       : host [n_E] total energies.   n_vec : vectors per energy.
  *   x_dev, y_dev : device complex128 [n_E][n_vec][N].
  *   precision: VBK_FP64 computes in FP64; VBK_MIXED rounds x and the operator to FP32,
- *   computes in FP32 and widens y.  Asynchronous on `stream`. */
+ *   computes in FP32 and widens y.
+ *   variant : kernel variant, -1 = the model's autotuned choice; 0..3 = direct kernel with
+ *   1, 2, 4, 8 systems per thread; 4..7 = shared-memory-windowed kernel with (systems,
+ *   elements) per thread (1,4), (2,4), (4,2), (8,1).  VBK_ERR_INVALID_ARG if the variant
+ *   does not fit this model and precision.  Asynchronous on `stream`. */
 int vbk_matvec(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,
-               void* y_dev, int precision, void* stream);
+               void* y_dev, int precision, int variant, void* stream);
 
 /* z = B^-1 r with B the block-diagonal preconditioner `precond_span` of A(E_k) (Sec. III.B),
  * factored as L D L^T.  Shapes as in vbk_matvec.  Asynchronous on `stream`.  A zero pivot

@@ -60,6 +60,7 @@ class vbk_opts(C.Structure):
         ("inner_tol", C.c_double),
         ("check_every", C.c_int),
         ("timing", C.c_int),
+        ("autotune", C.c_int),
     ]
 
 
@@ -90,7 +91,7 @@ def _load():
         "vbk_eels": (C.c_int, [vp, C.c_int, C.c_int, ip, C.c_int, ip, vp, C.c_int, dp, C.c_double, vp, vp]),
         "vbk_solve_adjoint": (C.c_int, [vp, C.c_int, dp, C.c_int, ip, C.POINTER(vbk_opts), vp, C.c_int, ip, vp,
                                         C.c_int, ip, dp, C.POINTER(vbk_stats), vp]),
-        "vbk_matvec": (C.c_int, [vp, C.c_int, dp, C.c_int, vp, vp, C.c_int, vp]),
+        "vbk_matvec": (C.c_int, [vp, C.c_int, dp, C.c_int, vp, vp, C.c_int, C.c_int, vp]),
         "vbk_precond_apply": (C.c_int, [vp, C.c_int, dp, C.c_int, C.c_int, vp, vp, C.c_int, vp]),
         "vbk_kernel_timings": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), ip, dp]),
         "vbk_last_launch_count": (C.c_longlong, [vp]),
@@ -277,15 +278,15 @@ def vbk_solve_adjoint(model: Model, eps_i, vi, psi, vf, dL_dsigma, theta_ids, op
     return grad, stats
 
 
-def vbk_matvec(model: Model, E, x, precision=VBK_FP64, stream=None):
-    """y = A(E_k) x for x of shape [n_E, n_vec, N] (complex128, CUDA)."""
+def vbk_matvec(model: Model, E, x, precision=VBK_FP64, variant=-1, stream=None):
+    """y = A(E_k) x for x of shape [n_E, n_vec, N] (complex128, CUDA); variant -1 = tuned choice."""
     import torch
 
     Ev = np.ascontiguousarray(np.asarray(E, dtype=np.float64).ravel())
     x = x.contiguous()
     y = torch.empty_like(x)
     _check(_lib.vbk_matvec(model.handle, Ev.size, _dptr(Ev), x.shape[1], _tensor_ptr(x), _tensor_ptr(y), precision,
-                           _stream(stream)), "vbk_matvec")
+                           int(variant), _stream(stream)), "vbk_matvec")
     return y
 
 

@@ -209,6 +209,14 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         dm.ebeg[s] = dm.ebeg[m->ns];
         dm.dbeg[s] = dm.dbeg[m->ns];
     }
+    for (int st = 0; st < MAXS; ++st) {
+        dm.lmin[st] = 0;
+        dm.lmax[st] = 0;
+    }
+    for (const auto& h : offd) {
+        dm.lmin[h.d] = std::min(dm.lmin[h.d], h.e.lin);
+        dm.lmax[h.d] = std::max(dm.lmax[h.d], h.e.lin);
+    }
     for (int c = 0; c < dm.nchan; ++c) {
         dm.ch_d[c] = m->chans[c].d;
         dm.ch_mu[c] = m->chans[c].mu;
@@ -569,6 +577,7 @@ void vbk_default_opts(vbk_opts* o) {
     o->inner_tol = 1e-5;
     o->check_every = 8;
     o->timing = 0;
+    o->autotune = 1;
 }
 
 int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
@@ -892,15 +901,16 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
 }
 
 int vbk_matvec(vbk_model* m, int n_E, const double* E, int n_vec, const void* x_dev, void* y_dev, int precision,
-               void* stream) {
+               int variant, void* stream) {
     g_last_error.clear();
     if (int rc = check_model(m)) return rc;
     if (n_E < 1 || n_vec < 1 || !E || !x_dev || !y_dev) return invalid("matvec: sizes and buffers must be given");
     if (precision != VBK_FP64 && precision != VBK_MIXED) return invalid("unknown precision");
     for (int k = 0; k < n_E; ++k)
         if (!std::isfinite(E[k])) return invalid("energies must be finite");
+    if (variant < -1) return invalid("matvec variant must be -1 or a variant index");
     return vbk_operator_run(m, 0, n_E, E, n_vec, 0, (const double2*)x_dev, (double2*)y_dev, precision,
-                            (cudaStream_t)stream);
+                            (cudaStream_t)stream, variant);
 }
 
 int vbk_precond_apply(vbk_model* m, int n_E, const double* E, int n_vec, int precond_span, const void* r_dev, void* z_dev,

@@ -77,6 +77,7 @@ struct DevModel {
     int nb[MAXM], stride[MAXM];
     double omega[MAXM];
     int ebeg[MAXS + 1];  // off-diagonal stencil points of output state d: [ebeg[d], ebeg[d+1])
+    int lmin[MAXS], lmax[MAXS];  // range of the in-plane offsets `lin` of the points of state d (with 0)
     int dbeg[MAXS + 1];  // diagonal parts (delta = 0, dp = d) of the terms of state d
     const DevEntry* ent;
     const DevEntry* dent;
@@ -122,6 +123,7 @@ struct vbk_model {
     long long launches = 0;
     int device = 0;
     cudaStream_t cap_stream = nullptr;  // library-owned stream used only to capture CUDA graphs
+    int mv_variant[2] = {-1, -1};       // autotuned matvec variant per precision (FP32, FP64); -1: untuned
 };
 
 // --------------------------------------------------------------------------- level shift
@@ -264,4 +266,4 @@ struct Launch;
 
 // y = A x (op 0) or z = B^-1 r (op 1) outside a solve (implemented in vbk_solver.cu)
 int vbk_operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
-                     int precision, cudaStream_t st);
+                     int precision, cudaStream_t st, int variant = -1);

@@ -259,6 +259,120 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
     }
 }
 
+
+// Windowed variant: the CTA stages, for each of its S systems and each state plane, the window
+// of x its TPB*EPT elements reach (contiguous, [nu0 + lmin, nu0 + T + lmax)) in shared memory,
+// so every neighbour is read from shared memory and x crosses L2 about (1 + (lmax-lmin)/T)
+// times.  Same contract as k_matvec2.
+template <class R, int S, int EPT>
+__global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
+                                                     const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x,
+                                                     long long xs, cx<R>* __restrict__ y, long long ys,
+                                                     const double2* __restrict__ b, double2* __restrict__ part, int red) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<R>* win = reinterpret_cast<cx<R>*>(smraw);
+    __shared__ int plin[MV_MAXPTS];
+    __shared__ int pdp[MV_MAXPTS];
+    __shared__ cx<R> redsh[TPB / 32][S];
+    constexpr int T = TPB * EPT;
+    const int Nnu = md.Nnu, N = md.N, ns = md.ns;
+    const int nchunk = (Nnu + T - 1) / T;
+    const int d = blockIdx.x / nchunk;
+    const int nu0 = (blockIdx.x - d * nchunk) * T;
+    const int lmin = md.lmin[d], W = T + md.lmax[d] - lmin, base = nu0 + lmin;
+    const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const DevEntry& e = md.ent[pb + k];
+        plin[k] = e.lin - lmin;
+        pdp[k] = e.dp;
+    }
+    int sy[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const int li = blockIdx.y * S + t;
+        int s = -1;
+        if (li < nlist) {
+            s = sel.list ? sel.list[li] : li;
+            if (s >= 0 && sel.act && !sel.act[s]) s = -1;
+        }
+        sy[t] = s;
+    }
+    // stage the windows
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        if (sy[t] < 0) continue;
+        for (int dp = 0; dp < ns; ++dp) {
+            cx<R>* w = win + (long long)(t * ns + dp) * W;
+            const cx<R>* src = x + (long long)sy[t] * xs + (long long)dp * Nnu;
+            for (int q = threadIdx.x; q < W; q += TPB) {
+                const int g = base + q;
+                w[q] = (g >= 0 && g < Nnu) ? src[g] : mkc<R>(0, 0);
+            }
+        }
+    }
+    __syncthreads();
+    cx<R> loc[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) loc[t] = mkc<R>(0, 0);
+    const R* pc = pcp<R>(md) + (long long)pb * Nnu;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        const int nu = nu0 + threadIdx.x + e * TPB;
+        if (nu >= Nnu) break;
+        const int i = d * Nnu + nu;
+        const int rel = nu - base;
+        cx<R> acc[S], xi[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            xi[t] = mkc<R>(0, 0);
+            acc[t] = mkc<R>(0, 0);
+            if (sy[t] >= 0) {
+                xi[t] = win[(long long)(t * ns + d) * W + rel];
+                acc[t] = cmul<R>(diag[(long long)sys_e[sy[t]] * N + i], xi[t]);
+            }
+        }
+        for (int k = 0; k < np; ++k) {
+            const R c = __ldg(pc + (long long)k * Nnu + nu);
+            if (c != (R)0) {
+                const int widx = pdp[k] * W + rel + plin[k];
+#pragma unroll
+                for (int t = 0; t < S; ++t)
+                    if (sy[t] >= 0) {
+                        const cx<R> v = win[(long long)t * ns * W + widx];
+                        acc[t].x = fma(-c, v.x, acc[t].x);
+                        acc[t].y = fma(-c, v.y, acc[t].y);
+                    }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            if (sy[t] < 0) continue;
+            cx<R> out = acc[t];
+            if (b) {
+                const double2 bb = b[(long long)sy[t] * N + i];
+                out = mkc<R>((R)bb.x - out.x, (R)bb.y - out.y);
+            }
+            y[(long long)sy[t] * ys + i] = out;
+            if (red == 1) loc[t] = cfma<R>(xi[t], out, loc[t]);
+            else if (red == 2) loc[t].x += cabs2<R>(out);
+        }
+    }
+    if (red) {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const cx<R> v = warp_sum_c<R>(loc[t]);
+            if (lane == 0) redsh[w][t] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < S && sy[threadIdx.x] >= 0) {
+            cx<R> tot = mkc<R>(0, 0);
+            for (int q = 0; q < TPB / 32; ++q) tot = cadd<R>(tot, redsh[q][threadIdx.x]);
+            part[(long long)sy[threadIdx.x] * gridDim.x + blockIdx.x] = cvt_to_d<R>(tot);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- block preconditioner
 struct PlanDev {
     int L, nblk, p, span;
@@ -639,15 +753,23 @@ __global__ void k_cocg_start(int nsys, SysState* __restrict__ st, const int* __r
     st[s].beta = make_double2(0.0, 0.0);
 }
 
+// per-system scalars: one warp per system sums its partials (lanes strided, then shuffles)
+__device__ __forceinline__ double2 warp_psum(const double2* __restrict__ p, int n) {
+    const int lane = threadIdx.x & 31;
+    double2 a = make_double2(0.0, 0.0);
+    for (int k = lane; k < n; k += 32) {
+        a.x += p[k].x;
+        a.y += p[k].y;
+    }
+    return warp_sum2(a);  // valid in lane 0
+}
+
 __global__ void k_cocg_alpha(int nsys, SysState* __restrict__ st, int* __restrict__ act, int* __restrict__ outer,
                              const double2* __restrict__ part, int nb) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= nsys || !act[s]) return;
-    double2 pq = make_double2(0.0, 0.0);
-    for (int k = 0; k < nb; ++k) {
-        pq.x += part[(long long)s * nb + k].x;
-        pq.y += part[(long long)s * nb + k].y;
-    }
+    const double2 pq = warp_psum(part + (long long)s * nb, nb);
+    if ((threadIdx.x & 31) != 0) return;
     SysState& S = st[s];
     const double den = pq.x * pq.x + pq.y * pq.y;
     if (!(den > 0.0) || !isfinite(den)) {
@@ -696,16 +818,12 @@ __global__ void __launch_bounds__(TPB) k_cocg_update(int N, Sel sel, const SysSt
 __global__ void k_cocg_beta(int nsys, SysState* __restrict__ st, int* __restrict__ act, int* __restrict__ outer,
                             const double2* __restrict__ part_rr, int nb_rr, const double2* __restrict__ part_rz, int nb_rz,
                             int max_iter, int* __restrict__ count, int* __restrict__ ilist) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (s >= nsys || !act[s]) return;
+    const double rr = warp_psum(part_rr + (long long)s * nb_rr, nb_rr).x;
+    const double2 rz = warp_psum(part_rz + (long long)s * nb_rz, nb_rz);
+    if ((threadIdx.x & 31) != 0) return;
     SysState& S = st[s];
-    double rr = 0.0;
-    for (int k = 0; k < nb_rr; ++k) rr += part_rr[(long long)s * nb_rr + k].x;
-    double2 rz = make_double2(0.0, 0.0);
-    for (int k = 0; k < nb_rz; ++k) {
-        rz.x += part_rz[(long long)s * nb_rz + k].x;
-        rz.y += part_rz[(long long)s * nb_rz + k].y;
-    }
     S.iters += 1;
     S.cycle_iters += 1;
     const double rn = sqrt(rr);
@@ -1202,16 +1320,125 @@ inline int block_partials(const DevPlanBuf& pb) {
 }
 
 
+// Matvec variants (chosen per model and precision by the autotuner below):
+//   0..3  direct k_matvec2 with S = 1, 2, 4, 8 systems per thread
+//   4..7  windowed k_matvec_tiled with (S, EPT) = (1, 4), (2, 4), (4, 2), (8, 1)
+constexpr int MV_NVAR = 8;
+inline int mv_ept(int v) { return v < 4 ? 1 : (v == 4 || v == 5) ? 4 : v == 6 ? 2 : 1; }
+inline int mv_sys(int v) { return v < 4 ? (1 << v) : (v == 4 ? 1 : v == 5 ? 2 : v == 6 ? 4 : 8); }
+inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
+    if (v < 4) return 0;
+    int lr = 0;
+    for (int d = 0; d < md.ns; ++d) lr = std::max(lr, md.lmax[d] - md.lmin[d]);
+    const long long W = (long long)TPB * mv_ept(v) + lr;
+    const long long bytes = (long long)mv_sys(v) * md.ns * W * (long long)c;
+    return bytes > 96 * 1024 ? -1 : (int)bytes;
+}
+inline bool mv_valid(const DevModel& md, int v, size_t c) {
+    if (c == 16 && mv_sys(v) > 4) return false;  // FP64: at most 4 systems per thread
+    return mv_tiled_smem(md, v, c) >= 0;
+}
+inline int matvec_partials_v(const DevModel& md, int v) {
+    const int T = TPB * mv_ept(v);
+    return md.ns * ((md.Nnu + T - 1) / T);
+}
+
+template <class T, int S, int EPT>
+void go_tiled(Runner& rn, const char* name, const DevModel& md, dim3 g, size_t smem, const int* sys_e, Sel sel,
+              unsigned nlist, const cx<T>* diag, const cx<T>* x, long long xs, cx<T>* y, long long ys, const double2* b,
+              double2* part, int red) {
+    rn.go_smem(name, k_matvec_tiled<T, S, EPT>, g, dim3(TPB), smem, md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part,
+               red);
+}
+
+template <class T>
+void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, const int* sys_e, Sel sel, unsigned nlist,
+                     const cx<T>* diag, const cx<T>* x, long long xs, cx<T>* y, long long ys, const double2* b,
+                     double2* part, int red) {
+    const int S = mv_sys(v);
+    const dim3 g((unsigned)matvec_partials_v(md, v), (nlist + S - 1) / S);
+    const size_t smem = v >= 4 ? (size_t)mv_tiled_smem(md, v, sizeof(cx<T>)) : 0;
+    switch (v) {
+        case 0: rn.go(name, k_matvec2<T, 1>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 1: rn.go(name, k_matvec2<T, 2>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 2: rn.go(name, k_matvec2<T, 4>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 3:
+            if constexpr (sizeof(T) == 4)
+                rn.go(name, k_matvec2<T, 8>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red);
+            break;
+        case 4: go_tiled<T, 1, 4>(rn, name, md, g, smem, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 5: go_tiled<T, 2, 4>(rn, name, md, g, smem, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 6: go_tiled<T, 4, 2>(rn, name, md, g, smem, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red); break;
+        default:
+            if constexpr (sizeof(T) == 4) go_tiled<T, 8, 1>(rn, name, md, g, smem, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red);
+            break;
+    }
+}
+
+// Opt the windowed variants in to the shared memory they need (outside any capture).
+template <class T> int prepare_matvec(const DevModel& md) {
+    const int need[4] = {mv_tiled_smem(md, 4, sizeof(cx<T>)), mv_tiled_smem(md, 5, sizeof(cx<T>)),
+                         mv_tiled_smem(md, 6, sizeof(cx<T>)), mv_tiled_smem(md, 7, sizeof(cx<T>))};
+    cudaError_t ce = cudaSuccess;
+    if (need[0] > 48 * 1024) ce = cudaFuncSetAttribute(k_matvec_tiled<T, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[0]);
+    if (need[1] > 48 * 1024 && ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(k_matvec_tiled<T, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[1]);
+    if (need[2] > 48 * 1024 && ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(k_matvec_tiled<T, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[2]);
+    if constexpr (sizeof(T) == 4)
+        if (need[3] > 48 * 1024 && ce == cudaSuccess)
+            ce = cudaFuncSetAttribute(k_matvec_tiled<T, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[3]);
+    return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "matvec shared-memory opt-in");
+}
+
+// Autotuner: times every valid variant on the batch at hand (CUDA events, best of 3) and keeps
+// the fastest for this model and precision.  Every variant writes the same y; the chosen one
+// runs last so that the partials match its grid.
+template <class T>
+int tune_matvec(Runner& rn, vbk_model* mdl, const int* sys_e, Sel sel, unsigned nlist, const cx<T>* diag, const cx<T>* x,
+                long long xs, cx<T>* y, long long ys, const double2* b, double2* part, int red) {
+    const DevModel& md = mdl->dm;
+    int& slot = mdl->mv_variant[sizeof(T) == 4 ? 0 : 1];
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return vbk_cuda_fail(cudaGetLastError(), "tuner");
+    float best = 1e30f;
+    int bestv = 0;
+    const bool timing = rn.timing;
+    rn.timing = false;
+    for (int v = 0; v < MV_NVAR; ++v) {
+        if (!mv_valid(md, v, sizeof(cx<T>))) continue;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, rn.st);
+            launch_matvec_v<T>(rn, v, "matvec_tune", md, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red);
+            cudaEventRecord(e1, rn.st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            tmin = std::min(tmin, ms);
+        }
+        if (tmin < best) {
+            best = tmin;
+            bestv = v;
+        }
+    }
+    rn.timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    slot = bestv;
+    launch_matvec_v<T>(rn, bestv, "matvec_tune", md, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red);
+    if (const cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) return vbk_cuda_fail(ce, "matvec tuner");
+    return VBK_OK;
+}
+
 template <class T, int M>
 void launch_matvec(Runner& rn, const char* name, const DevModel& md, const int* sys_e, Sel sel, unsigned nlist,
                    const cx<T>* diag, const cx<T>* x, long long xs, cx<T>* y, long long ys, const double2* b, double2* part,
-                   int red) {
-    constexpr int S = sizeof(T) == 4 ? 8 : 4;
-    const int nchunk = (md.Nnu + TPB - 1) / TPB;
-    const dim3 g((unsigned)(md.ns * nchunk), (nlist + S - 1) / S);
-    rn.go(name, k_matvec2<T, S>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red);
+                   int red, int variant) {
+    launch_matvec_v<T>(rn, variant < 0 ? (sizeof(T) == 4 ? 3 : 2) : variant, name, md, sys_e, sel, nlist, diag, x, xs, y, ys, b,
+                       part, red);
 }
-inline int matvec_partials(const DevModel& md) { return md.ns * ((md.Nnu + TPB - 1) / TPB); }
+inline int matvec_partials(const DevModel& md, int variant) { return matvec_partials_v(md, variant); }
 
 template <class R, int M> struct Solver {
     static int run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vbk_stats* stats, cudaStream_t st);
@@ -1241,13 +1468,24 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
     }
 
+    {
+        int rc = prepare_matvec<R>(md);
+        if (!rc && sizeof(R) == 4) rc = prepare_matvec<double>(md);
+        if (rc) {
+            if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+            return rc;
+        }
+    }
+    const bool tune = o.autotune != 0;
+
     // ---- workspace
     const size_t NN = (size_t)N;
     const int nb_e = (int)cdiv_u(N, TPB);       // element-wise kernels
-    const int nb_mv = matvec_partials(md);      // matvec partials per system
+    int nb_mv = matvec_partials(md, mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0 ? 0 : mdl->mv_variant[sizeof(R) == 4 ? 0 : 1]);
+    const int nb_mv_max = matvec_partials(md, 0);  // the largest partial count of any variant
     const int nb_v = (int)cdiv_u(N, VCHUNK);    // basis-vector kernels
     const int nb_b = block ? block_partials(pbuf) : 0;
-    const int nslot = std::max(std::max(nb_e, nb_mv), std::max(nb_b, nb_v * (mres + 1)));
+    const int nslot = std::max(std::max(nb_e, nb_mv_max), std::max(nb_b, nb_v * (mres + 1)));
     size_t bytes = 0;
     bytes += carve_size<double2>((size_t)nE * NN);                    // diag64
     bytes += carve_size<cx<R>>(mixed ? (size_t)nE * NN : 1);          // diagR
@@ -1366,6 +1604,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             break;
         }
         const unsigned gs = cdiv_u(nsys, 128);
+        const unsigned gw = cdiv_u(nsys, 4);  // warp-per-system kernels, 4 warps per block
         const int pmode = pspan < 0 ? -1 : (block ? 1 : 0);
         const Sel sel_all{alll, outer};
         unsigned n_out = (unsigned)nsys;  // systems in olist (host copy)
@@ -1387,13 +1626,25 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             if (it == 0)
                 rn.go("copy_b", k_copy_b, dim3(nb_e, nsys), dim3(TPB), N, sel_all, job.b64, r64, partA);
             else
-                launch_matvec<double, M>(rn, "matvec_fp64", md, (const int*)sys_e, so, n_out, (const double2*)diag64,
-                                         (const double2*)job.x64, (long long)N, r64, (long long)N, job.b64, partA, 2);
+            {
+                if (tune && mdl->mv_variant[1] < 0) {
+                    if (int trc = tune_matvec<double>(rn, mdl, (const int*)sys_e, so, n_out, (const double2*)diag64,
+                                                      (const double2*)job.x64, (long long)N, r64, (long long)N, job.b64,
+                                                      partA, 2)) {
+                        fail(trc);
+                        break;
+                    }
+                } else {
+                    launch_matvec<double, M>(rn, "matvec_fp64", md, (const int*)sys_e, so, n_out, (const double2*)diag64,
+                                             (const double2*)job.x64, (long long)N, r64, (long long)N, job.b64, partA, 2,
+                                             mdl->mv_variant[1]);
+                }
+            }
             cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
             cudaMemsetAsync(olist, 0xff, nsys * sizeof(int), st);  // -1: no system
             cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
-                  it == 0 ? nb_e : nb_mv,
+                  it == 0 ? nb_e : matvec_partials(md, std::max(0, mdl->mv_variant[1] < 0 ? 2 : mdl->mv_variant[1])),
                   it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
             cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -1415,12 +1666,21 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 rn.go("cocg_start", k_cocg_start, dim3(gs), dim3(128), nsys, sst, (const int*)inner, (const double2*)partB,
                       nb_rz);
                 cudaMemcpyAsync(pv, z, (size_t)nsys * NN * sizeof(cx<R>), cudaMemcpyDeviceToDevice, st);
+                if (tune && mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0) {
+                    if (int trc = tune_matvec<R>(rn, mdl, (const int*)sys_e, si, n_in, (const cx<R>*)diagR, (const cx<R>*)pv,
+                                                 (long long)N, q, (long long)N, (const double2*)nullptr, partA, 1)) {
+                        fail(trc);
+                        break;
+                    }
+                }
+                const int mvv = mdl->mv_variant[sizeof(R) == 4 ? 0 : 1];
+                nb_mv = matvec_partials(md, mvv < 0 ? (sizeof(R) == 4 ? 3 : 2) : mvv);
                 // one COCG iteration for the systems of the inner list
                 auto cocg_iter = [&](unsigned ny) {
                     const Sel sc{ilist, inner};
                     launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, ny, (const cx<R>*)diagR, (const cx<R>*)pv,
-                                        (long long)N, q, (long long)N, (const double2*)nullptr, partA, 1);
-                    rn.go("cocg_alpha", k_cocg_alpha, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partA,
+                                        (long long)N, q, (long long)N, (const double2*)nullptr, partA, 1, mvv);
+                    rn.go("cocg_alpha", k_cocg_alpha, dim3(gw), dim3(128), nsys, sst, inner, outer, (const double2*)partA,
                           nb_mv);
                     if (block) {
                         // fused x += alpha p, r -= alpha q and z = B^-1 r
@@ -1433,7 +1693,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     }
                     cudaMemsetAsync(cnt, 0, sizeof(int), rn.st);
                     cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), rn.st);
-                    rn.go("cocg_beta", k_cocg_beta, dim3(gs), dim3(128), nsys, sst, inner, outer, (const double2*)partC,
+                    rn.go("cocg_beta", k_cocg_beta, dim3(gw), dim3(128), nsys, sst, inner, outer, (const double2*)partC,
                           (block && pbuf.staged) ? nb_rz : nb_e, (const double2*)partB, nb_rz, o.max_iter, cnt, ilist);
                     rn.go("cocg_p", k_cocg_p<R>, dim3(nb_e, ny), dim3(TPB), N, sc, (const SysState*)sst, (const cx<R>*)z, pv);
                 };
@@ -1534,17 +1794,26 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst,
                       (const double2*)r64, V, ldV);
                 rn.go("gmres_start", k_gmres_cycle_start, dim3(gs), dim3(128), nsys, mres, (const int*)inner, g);
+                if (tune && mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0) {
+                    if (int trc = tune_matvec<R>(rn, mdl, (const int*)sys_e, si, n_in, (const cx<R>*)diagR, (const cx<R>*)V, ldV,
+                                                 w, (long long)N, (const double2*)nullptr, partA, 0)) {
+                        fail(trc);
+                        break;
+                    }
+                }
+                const int mvv = mdl->mv_variant[sizeof(R) == 4 ? 0 : 1];
                 const Sel sc_out{olist, nullptr};  // systems that run this cycle (for the final combination)
                 for (int j = 0; j < mres; ++j) {
                     const Sel sc{ilist, inner};
                     const cx<R>* vj = V + (long long)j * N;
                     if (pspan < 0) {
                         launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, n_in, (const cx<R>*)diagR, vj, ldV, w,
-                                            (long long)N, (const double2*)nullptr, partA, 0);
+                                            (long long)N, (const double2*)nullptr, partA, 0, mvv);
                     } else {
                         precond(sc, n_in, vj, ldV, z, N, nullptr);
                         launch_matvec<R, M>(rn, "matvec", md, (const int*)sys_e, sc, n_in, (const cx<R>*)diagR,
-                                            (const cx<R>*)z, (long long)N, w, (long long)N, (const double2*)nullptr, partA, 0);
+                                            (const cx<R>*)z, (long long)N, w, (long long)N, (const double2*)nullptr, partA, 0,
+                                            mvv);
                     }
                     rn.go("gmres_dots", k_vdots<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const cx<R>*)w, partA);
@@ -1678,7 +1947,7 @@ int dispatch(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stats* st
 // y = A x (op = 0) or z = B^-1 r (op = 1) for n_E energies x nvec vectors, FP64 in and out.
 template <class R, int M>
 int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
-                 cudaStream_t st) {
+                 cudaStream_t st, int variant) {
     const int N = m->N;
     const bool mixed = sizeof(R) == 4;
     const long long nsys = (long long)nE * nvec;
@@ -1694,6 +1963,13 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
             if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
             return rc;
         }
+    }
+    if (op == 0) {
+        if (variant >= MV_NVAR || (variant >= 0 && !mv_valid(m->dm, variant, sizeof(cx<R>)))) {
+            vbk_set_error("matvec variant not available for this model and precision");
+            return VBK_ERR_INVALID_ARG;
+        }
+        if (int rc = prepare_matvec<R>(m->dm)) return rc;
     }
     size_t bytes = carve_size<double2>((size_t)nE * N) + carve_size<float2>(mixed ? (size_t)nE * N : 1) +
                    2 * carve_size<cx<R>>(mixed ? (size_t)nsys * N : 1) + carve_size<int>(nsys) + carve_size<double>(nE) +
@@ -1735,7 +2011,8 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
         if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
         if (op == 0) {
             launch_matvec<R, M>(rn, "matvec", m->dm, (const int*)se, none, (unsigned)nsys, diagR, (const cx<R>*)xr, (long long)N,
-                                yr, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
+                                yr, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0,
+                                variant >= 0 ? variant : m->mv_variant[sizeof(R) == 4 ? 0 : 1]);
         } else if (block) {
             rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), m->dm, pbuf.pd, nE,
                   diagR, F, pfail);
@@ -1769,12 +2046,12 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
 
 template <class R>
 int operator_dispatch(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
-                      cudaStream_t st) {
+                      cudaStream_t st, int variant) {
     switch (m->M) {
-        case 1: return operator_run<R, 1>(m, op, nE, E, nvec, span, x, y, st);
-        case 2: return operator_run<R, 2>(m, op, nE, E, nvec, span, x, y, st);
-        case 3: return operator_run<R, 3>(m, op, nE, E, nvec, span, x, y, st);
-        case 4: return operator_run<R, 4>(m, op, nE, E, nvec, span, x, y, st);
+        case 1: return operator_run<R, 1>(m, op, nE, E, nvec, span, x, y, st, variant);
+        case 2: return operator_run<R, 2>(m, op, nE, E, nvec, span, x, y, st, variant);
+        case 3: return operator_run<R, 3>(m, op, nE, E, nvec, span, x, y, st, variant);
+        case 4: return operator_run<R, 4>(m, op, nE, E, nvec, span, x, y, st, variant);
     }
     vbk_set_error("unsupported number of modes");
     return VBK_ERR_UNSUPPORTED;
@@ -1790,7 +2067,7 @@ int vbk_solve_job(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stat
 }
 
 int vbk_operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
-                     int precision, cudaStream_t st) {
-    if (precision == VBK_MIXED) return operator_dispatch<float>(m, op, nE, E, nvec, span, x, y, st);
-    return operator_dispatch<double>(m, op, nE, E, nvec, span, x, y, st);
+                     int precision, cudaStream_t st, int variant) {
+    if (precision == VBK_MIXED) return operator_dispatch<float>(m, op, nE, E, nvec, span, x, y, st, variant);
+    return operator_dispatch<double>(m, op, nE, E, nvec, span, x, y, st, variant);
 }

@@ -56,14 +56,22 @@ MODELS = {
 
 @pytest.mark.parametrize("name", list(MODELS))
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_matvec_parity(vbk, name, precision):
+@pytest.mark.parametrize("variant", list(range(8)))
+def test_matvec_parity(vbk, name, precision, variant):
+    """Every matvec kernel variant (direct / shared-memory-windowed, 1..8 systems per thread)."""
     desc = MODELS[name]()
     model = vbk.Model(desc)
     rng = np.random.default_rng(7)
     E = np.array([0.35, 2.6, 4.1])
-    nvec = 2
+    nvec = 3  # 9 systems: a ragged last group for every systems-per-thread count
     x = rand_vectors(rng, (E.size, nvec, model.N))
-    y = vbk.vbk_matvec(model, E, torch.tensor(x, device="cuda"), precision=0 if precision == "fp64" else 1).cpu().numpy()
+    try:
+        y = vbk.vbk_matvec(model, E, torch.tensor(x, device="cuda"), precision=0 if precision == "fp64" else 1,
+                           variant=variant).cpu().numpy()
+    except vbk.VbkError as err:
+        if err.code == 1 and "variant not available" in str(err):
+            pytest.skip("variant does not fit this model / precision")
+        raise
     tol = 1e-13 if precision == "fp64" else 2e-6
     for e in range(E.size):
         A = o.a_matrix(desc, E[e])
