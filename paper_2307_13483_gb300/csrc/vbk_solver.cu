@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, const int* __
     const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
         const DevEntry& e = md.ent[pb + k];
-        plin[k] = e.lin - lmin;
+        plin[k] = e.lin;  // window position of the neighbour: (nu + lin) - base = rel + lin
         pdp[k] = e.dp;
     }
     int sy[S];
