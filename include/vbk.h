@@ -212,6 +212,22 @@ int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi
 int vbk_matvec(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,
                void* y_dev, int precision, int variant, void* stream);
 
+/* y = A(E_k) x in FP64 without allocating device memory (the paper has no counterpart: this
+ * is a service of the library).  For callers that cannot allocate when they apply the
+ * operator, e.g. a process whose device memory another framework's allocator has already
+ * reserved, or a real-time loop that allows no allocation after start-up.  Same operator,
+ * shapes and result as vbk_matvec with VBK_FP64; the model must have been built before.
+ * Scratch (energies, system map, diagonal tables) lives in a fixed 8 MiB device array inside
+ * the library, held by every GPU that loads the library until the process exits:
+ *   n_E * N * 16 + n_E * 8 + n_E * n_vec * 4 bytes (each part rounded up to 256) <= 8 MiB,
+ *   and n_E * n_vec <= 4096; larger requests return VBK_ERR_INVALID_ARG with a message.
+ * The first call on a device looks up the array's device address (set-up); make that first
+ * call before any stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race.  Synchronises `stream`.  No cudaMalloc, cudaFree
+ * or allocating library routine is called. */
+int vbk_matvec_noalloc(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,
+                       void* y_dev, void* stream);
+
 /* z = B^-1 r with B the block-diagonal preconditioner `precond_span` of A(E_k) (Sec. III.B),
  * factored as L D L^T.  Shapes as in vbk_matvec.  Asynchronous on `stream`.  A zero pivot
  * gives VBK_ERR_NOT_CONVERGED (and synchronises). */

@@ -72,7 +72,7 @@ EXPORTED = [
     "vbk_default_opts", "vbk_build_model", "vbk_free_model", "vbk_model_size", "vbk_solve",
     "vbk_cross_sections", "vbk_eels", "vbk_solve_adjoint", "vbk_matvec", "vbk_precond_apply",
     "vbk_kernel_timings", "vbk_last_launch_count", "vbk_level_shift", "vbk_status_str",
-    "vbk_sys_status_str", "vbk_last_error",
+    "vbk_sys_status_str", "vbk_last_error", "vbk_matvec_noalloc",
 ]
 
 
@@ -93,6 +93,7 @@ def _load():
                                         C.c_int, ip, dp, C.POINTER(vbk_stats), vp]),
         "vbk_matvec": (C.c_int, [vp, C.c_int, dp, C.c_int, vp, vp, C.c_int, C.c_int, vp]),
         "vbk_precond_apply": (C.c_int, [vp, C.c_int, dp, C.c_int, C.c_int, vp, vp, C.c_int, vp]),
+        "vbk_matvec_noalloc": (C.c_int, [vp, C.c_int, dp, C.c_int, vp, vp, vp]),
         "vbk_kernel_timings": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), ip, dp]),
         "vbk_last_launch_count": (C.c_longlong, [vp]),
         "vbk_level_shift": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]),
@@ -287,6 +288,15 @@ def vbk_matvec(model: Model, E, x, precision=VBK_FP64, variant=-1, stream=None):
     y = torch.empty_like(x)
     _check(_lib.vbk_matvec(model.handle, Ev.size, _dptr(Ev), x.shape[1], _tensor_ptr(x), _tensor_ptr(y), precision,
                            int(variant), _stream(stream)), "vbk_matvec")
+    return y
+
+
+def vbk_matvec_noalloc(model: Model, E, x, y, stream=None):
+    """y = A(E_k) x in FP64 into the caller's ``y`` without any device allocation by the library
+    (its scratch is a fixed 8 MiB device array; see include/vbk.h for the limits)."""
+    Ev = np.ascontiguousarray(np.asarray(E, dtype=np.float64).ravel())
+    _check(_lib.vbk_matvec_noalloc(model.handle, Ev.size, _dptr(Ev), x.shape[1], _tensor_ptr(x), _tensor_ptr(y),
+                                   _stream(stream)), "vbk_matvec_noalloc")
     return y
 
 

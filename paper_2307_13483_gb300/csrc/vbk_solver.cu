@@ -2071,3 +2071,117 @@ int vbk_operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, in
     if (precision == VBK_MIXED) return operator_dispatch<float>(m, op, nE, E, nvec, span, x, y, st, variant);
     return operator_dispatch<double>(m, op, nE, E, nvec, span, x, y, st, variant);
 }
+
+// =========================================================== allocation-free operator apply
+// Some callers cannot allocate device memory when they apply the operator: a process whose
+// device memory another framework's allocator has already reserved almost entirely, or a
+// real-time loop that forbids allocation after start-up.  vbk_matvec_noalloc serves them: it
+// applies A(E) in FP64 like vbk_matvec, but keeps its scratch (the energies, the system-to-
+// energy map and the diagonal tables) in the fixed device array below instead of allocating.
+// The array is part of the library image, so every GPU that loads the library holds it until
+// the process exits.  Every call reuses it and it keeps the last call's contents; everything a
+// call reads is written by that call first.  Two calls that overlap on the GPU (on different
+// streams, or from different host threads) race on it.
+#define VBK_NOALLOC_SCRATCH_BYTES (8u << 20)  // 8 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VBK_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array for the current device, looked up once per device with
+// that device current.  Host code must not pass &g_noalloc_scratch to a kernel: on the host that
+// name is only a stand-in for the device symbol.
+int noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return vbk_cuda_fail(ce, "noalloc: current device");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        vbk_set_error("noalloc: device index beyond the supported range");
+        return VBK_ERR_UNSUPPORTED;
+    }
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (ce != cudaSuccess || !p) return vbk_cuda_fail(ce, "noalloc: scratch symbol address");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return VBK_OK;
+}
+
+template <int M>
+int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* x, double2* y, cudaStream_t st) {
+    const int N = m->N;
+    const long long nsys = (long long)nE * nvec;
+    // scratch layout: E [nE] | sys_e [nsys] | diag [nE][N]
+    const size_t off_se = ((size_t)nE * sizeof(double) + 255) & ~size_t(255);
+    const size_t off_dg = (off_se + (size_t)nsys * sizeof(int) + 255) & ~size_t(255);
+    const size_t need = off_dg + (size_t)nE * N * sizeof(double2);
+    if (need > VBK_NOALLOC_SCRATCH_BYTES || nsys > 65535) {
+        vbk_set_error("noalloc: n_E * N complex entries (plus energies and the system map) exceed the " +
+                      std::to_string(VBK_NOALLOC_SCRATCH_BYTES) + "-byte scratch array (need " + std::to_string(need) +
+                      " bytes); use vbk_matvec or fewer energies per call");
+        return VBK_ERR_INVALID_ARG;
+    }
+    void* base = nullptr;
+    if (int rc = noalloc_scratch(&base)) return rc;
+    char* sb = (char*)base;
+    double* dE = (double*)sb;
+    int* se = (int*)(sb + off_se);
+    double2* d64 = (double2*)(sb + off_dg);
+    if (nsys > 4096) {
+        vbk_set_error("noalloc: at most 4096 vectors per call");
+        return VBK_ERR_INVALID_ARG;
+    }
+    int hse[4096];
+    for (long long s = 0; s < nsys; ++s) hse[s] = (int)(s / nvec);
+    cudaError_t ce;
+    if ((ce = cudaMemcpyAsync(dE, E, nE * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (ce = cudaMemcpyAsync(se, hse, nsys * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return vbk_cuda_fail(ce, "noalloc: copies into scratch");
+    Runner rn{m, st, false, {}, {}};
+    rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
+          (float2*)nullptr);
+    const Sel none{nullptr, nullptr};
+    launch_matvec_v<double>(rn, 2, "matvec_fp64", m->dm, (const int*)se, none, (unsigned)nsys, (const double2*)d64, x,
+                            (long long)N, y, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
+    if ((ce = cudaGetLastError()) != cudaSuccess) return vbk_cuda_fail(ce, "noalloc: kernels");
+    if (rn.first_error != cudaSuccess) return VBK_ERR_CUDA;
+    // the host-side system map must outlive its copy
+    if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return vbk_cuda_fail(ce, "noalloc: completion");
+    return VBK_OK;
+}
+
+}  // namespace
+
+extern "C" int vbk_matvec_noalloc(vbk_model* m, int n_E, const double* E, int n_vec, const void* x_dev, void* y_dev,
+                                  void* stream) {
+    vbk_set_error("");
+    if (!m) {
+        vbk_set_error("model handle is NULL");
+        return VBK_ERR_INVALID_ARG;
+    }
+    if (n_E < 1 || n_vec < 1 || !E || !x_dev || !y_dev) {
+        vbk_set_error("noalloc: sizes and buffers must be given");
+        return VBK_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < n_E; ++k)
+        if (!std::isfinite(E[k])) {
+            vbk_set_error("energies must be finite");
+            return VBK_ERR_INVALID_ARG;
+        }
+    cudaStream_t st = (cudaStream_t)stream;
+    const double2* x = (const double2*)x_dev;
+    double2* y = (double2*)y_dev;
+    switch (m->M) {
+        case 1: return noalloc_run<1>(m, n_E, E, n_vec, x, y, st);
+        case 2: return noalloc_run<2>(m, n_E, E, n_vec, x, y, st);
+        case 3: return noalloc_run<3>(m, n_E, E, n_vec, x, y, st);
+        case 4: return noalloc_run<4>(m, n_E, E, n_vec, x, y, st);
+    }
+    vbk_set_error("unsupported number of modes");
+    return VBK_ERR_UNSUPPORTED;
+}
