@@ -351,6 +351,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "matvec_hbm_gbs": matvec_gbs,
+            "matvec_variant": {"fp32": vbk.vbk_matvec_variant(model, 1), "fp64": vbk.vbk_matvec_variant(model, 0)},
             "gpu_launches": launches,
             "clocks": clocks,
             "converged": converged, "worst_rel_residual": worst,

@@ -240,6 +240,10 @@ int vbk_precond_apply(vbk_model* model, int n_E, const double* E, int n_vec, int
 int vbk_kernel_timings(const vbk_model* model, int cap, const char** names, int* launches,
                        double* total_ms);
 
+/* Matvec kernel variant the autotuner chose for this model in `precision` (VBK_MIXED: the FP32
+ * Krylov operator, VBK_FP64: the FP64 residual), or -1 if it has not run yet. */
+int vbk_matvec_variant(const vbk_model* model, int precision);
+
 /* Number of kernel launches issued by the last vbk_solve / vbk_solve_adjoint call. */
 long long vbk_last_launch_count(const vbk_model* model);
 

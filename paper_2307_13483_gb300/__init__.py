@@ -72,7 +72,7 @@ EXPORTED = [
     "vbk_default_opts", "vbk_build_model", "vbk_free_model", "vbk_model_size", "vbk_solve",
     "vbk_cross_sections", "vbk_eels", "vbk_solve_adjoint", "vbk_matvec", "vbk_precond_apply",
     "vbk_kernel_timings", "vbk_last_launch_count", "vbk_level_shift", "vbk_status_str",
-    "vbk_sys_status_str", "vbk_last_error", "vbk_matvec_noalloc",
+    "vbk_sys_status_str", "vbk_last_error", "vbk_matvec_noalloc", "vbk_matvec_variant",
 ]
 
 
@@ -96,6 +96,7 @@ def _load():
         "vbk_matvec_noalloc": (C.c_int, [vp, C.c_int, dp, C.c_int, vp, vp, vp]),
         "vbk_kernel_timings": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), ip, dp]),
         "vbk_last_launch_count": (C.c_longlong, [vp]),
+        "vbk_matvec_variant": (C.c_int, [vp, C.c_int]),
         "vbk_level_shift": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]),
         "vbk_status_str": (C.c_char_p, [C.c_int]),
         "vbk_sys_status_str": (C.c_char_p, [C.c_int]),
@@ -318,6 +319,10 @@ def vbk_kernel_timings(model: Model):
     ms = (C.c_double * cap)()
     n = _lib.vbk_kernel_timings(model.handle, cap, names, launches, ms)
     return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
+
+
+def vbk_matvec_variant(model: Model, precision=VBK_MIXED) -> int:
+    return int(_lib.vbk_matvec_variant(model.handle, int(precision)))
 
 
 def vbk_last_launch_count(model: Model) -> int:

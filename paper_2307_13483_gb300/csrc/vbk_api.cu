@@ -274,6 +274,7 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     dm.ent = (const DevEntry*)mem;
     dm.dent = (const DevEntry*)(mem + b1);
     dm.tab64 = (const double*)(mem + b1 + b2);
+    dm.ntab = (int)nt;
     dm.tab32 = (const float*)(mem + b1 + b2 + b3);
     m->desc = *d;
     m->desc.terms = m->terms.data();
@@ -938,6 +939,11 @@ int vbk_kernel_timings(const vbk_model* m, int cap, const char** names, int* lau
 }
 
 long long vbk_last_launch_count(const vbk_model* m) { return m ? m->launches : 0; }
+
+int vbk_matvec_variant(const vbk_model* m, int precision) {
+    if (!m) return -1;
+    return m->mv_variant[precision == VBK_MIXED ? 0 : 1];
+}
 
 const char* vbk_status_str(int code) {
     switch (code) {

@@ -83,6 +83,7 @@ struct DevModel {
     const DevEntry* dent;
     const double* tab64;
     const float* tab32;
+    int ntab;  // entries of tab64 / tab32
     // coefficient columns of the off-diagonal stencil points: pc[k][nu] = coef_k * prod_m
     // (q_m^pow)_{n_m, n_m + delta_m}, zero where the neighbour leaves the basis (energy-independent)
     const double* pc64;

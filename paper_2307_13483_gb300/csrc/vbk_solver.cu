@@ -262,29 +262,43 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
 
 // Windowed variant: the CTA stages, for each of its S systems and each state plane, the window
 // of x its TPB*EPT elements reach (contiguous, [nu0 + lmin, nu0 + T + lmax)) in shared memory,
-// so every neighbour is read from shared memory and x crosses L2 about (1 + (lmax-lmin)/T)
-// times.  Same contract as k_matvec2.
-template <class R, int S, int EPT>
-__global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
-                                                     const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x,
+// together with the per-mode oscillator tables, so every neighbour and every coefficient factor
+// is read from shared memory; global traffic is the window (about (1 + (lmax-lmin)/T) x), the
+// diagonal table and y.  Coefficients are formed on the fly as coef * prod_m tab_m[n_m]; a
+// neighbour outside the basis has a zero factor, and its window slot holds a finite value.
+// Same contract as k_matvec2.
+constexpr int MV_TAB_SMEM = 8192;  // most oscillator-table entries staged in shared memory
+
+template <class R, int S, int EPT, int M>
+__global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, int W_alloc, const int* __restrict__ sys_e, Sel sel,
+                                                     int nlist, const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x,
                                                      long long xs, cx<R>* __restrict__ y, long long ys,
                                                      const double2* __restrict__ b, double2* __restrict__ part, int red) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R>* win = reinterpret_cast<cx<R>*>(smraw);
+    __shared__ R pcoef[MV_MAXPTS];
     __shared__ int plin[MV_MAXPTS];
     __shared__ int pdp[MV_MAXPTS];
+    __shared__ short pcol[MV_MAXPTS][M];
     __shared__ cx<R> redsh[TPB / 32][S];
     constexpr int T = TPB * EPT;
     const int Nnu = md.Nnu, N = md.N, ns = md.ns;
     const int nchunk = (Nnu + T - 1) / T;
     const int d = blockIdx.x / nchunk;
     const int nu0 = (blockIdx.x - d * nchunk) * T;
-    const int lmin = md.lmin[d], W = T + md.lmax[d] - lmin, base = nu0 + lmin;
+    const int lmin = md.lmin[d], W = W_alloc, base = nu0 + lmin;
     const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
+    // dynamic shared memory: S * ns windows of W entries, then the oscillator tables
+    R* stab = reinterpret_cast<R*>(win + (long long)S * ns * W_alloc);
+    const R* gtab = tabp<R>(md);
+    for (int k = threadIdx.x; k < md.ntab; k += blockDim.x) stab[k] = gtab[k];
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
         const DevEntry& e = md.ent[pb + k];
         plin[k] = e.lin;  // window position of the neighbour: (nu + lin) - base = rel + lin
         pdp[k] = e.dp;
+        pcoef[k] = (R)e.coef;
+#pragma unroll
+        for (int m = 0; m < M; ++m) pcol[k][m] = (short)e.col[m];
     }
     int sy[S];
 #pragma unroll
@@ -314,13 +328,14 @@ __global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, const int* __
     cx<R> loc[S];
 #pragma unroll
     for (int t = 0; t < S; ++t) loc[t] = mkc<R>(0, 0);
-    const R* pc = pcp<R>(md) + (long long)pb * Nnu;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int nu = nu0 + threadIdx.x + e * TPB;
         if (nu >= Nnu) break;
         const int i = d * Nnu + nu;
         const int rel = nu - base;
+        int n[MAXM];
+        decode<M>(md, nu, n);
         cx<R> acc[S], xi[S];
 #pragma unroll
         for (int t = 0; t < S; ++t) {
@@ -332,16 +347,18 @@ __global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, const int* __
             }
         }
         for (int k = 0; k < np; ++k) {
-            const R c = __ldg(pc + (long long)k * Nnu + nu);
-            if (c != (R)0) {
-                const int widx = pdp[k] * W + rel + plin[k];
+            R c = pcoef[k];
 #pragma unroll
-                for (int t = 0; t < S; ++t)
-                    if (sy[t] >= 0) {
-                        const cx<R> v = win[(long long)t * ns * W + widx];
-                        acc[t].x = fma(-c, v.x, acc[t].x);
-                        acc[t].y = fma(-c, v.y, acc[t].y);
-                    }
+            for (int m = 0; m < M; ++m) {
+                const int col = pcol[k][m];
+                if (col >= 0) c *= stab[col + n[m]];
+            }
+            const int widx = pdp[k] * W + rel + plin[k];
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                const cx<R> v = win[(long long)t * ns * W + widx];
+                acc[t].x = fma(-c, v.x, acc[t].x);
+                acc[t].y = fma(-c, v.y, acc[t].y);
             }
         }
 #pragma unroll
@@ -1326,13 +1343,17 @@ inline int block_partials(const DevPlanBuf& pb) {
 constexpr int MV_NVAR = 8;
 inline int mv_ept(int v) { return v < 4 ? 1 : (v == 4 || v == 5) ? 4 : v == 6 ? 2 : 1; }
 inline int mv_sys(int v) { return v < 4 ? (1 << v) : (v == 4 ? 1 : v == 5 ? 2 : v == 6 ? 4 : 8); }
-inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
-    if (v < 4) return 0;
+inline int mv_window(const DevModel& md, int v) {
     int lr = 0;
     for (int d = 0; d < md.ns; ++d) lr = std::max(lr, md.lmax[d] - md.lmin[d]);
-    const long long W = (long long)TPB * mv_ept(v) + lr;
-    const long long bytes = (long long)mv_sys(v) * md.ns * W * (long long)c;
-    return bytes > 96 * 1024 ? -1 : (int)bytes;
+    return TPB * mv_ept(v) + lr;
+}
+inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
+    if (v < 4) return 0;
+    if (md.ntab > MV_TAB_SMEM) return -1;  // the oscillator tables must fit the shared-memory copy
+    const long long W = mv_window(md, v);
+    const long long bytes = (long long)mv_sys(v) * md.ns * W * (long long)c + (long long)md.ntab * (long long)(c / 2) + 16;
+    return bytes > 150 * 1024 ? -1 : (int)bytes;
 }
 inline bool mv_valid(const DevModel& md, int v, size_t c) {
     if (c == 16 && mv_sys(v) > 4) return false;  // FP64: at most 4 systems per thread
@@ -1347,8 +1368,17 @@ template <class T, int S, int EPT>
 void go_tiled(Runner& rn, const char* name, const DevModel& md, dim3 g, size_t smem, const int* sys_e, Sel sel,
               unsigned nlist, const cx<T>* diag, const cx<T>* x, long long xs, cx<T>* y, long long ys, const double2* b,
               double2* part, int red) {
-    rn.go_smem(name, k_matvec_tiled<T, S, EPT>, g, dim3(TPB), smem, md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part,
-               red);
+    const int Wa = TPB * EPT + [&] {
+        int lr = 0;
+        for (int d = 0; d < md.ns; ++d) lr = std::max(lr, md.lmax[d] - md.lmin[d]);
+        return lr;
+    }();
+    switch (md.M) {
+        case 1: rn.go_smem(name, k_matvec_tiled<T, S, EPT, 1>, g, dim3(TPB), smem, md, Wa, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 2: rn.go_smem(name, k_matvec_tiled<T, S, EPT, 2>, g, dim3(TPB), smem, md, Wa, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 3: rn.go_smem(name, k_matvec_tiled<T, S, EPT, 3>, g, dim3(TPB), smem, md, Wa, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        default: rn.go_smem(name, k_matvec_tiled<T, S, EPT, 4>, g, dim3(TPB), smem, md, Wa, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+    }
 }
 
 template <class T>
@@ -1376,18 +1406,24 @@ void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, co
 }
 
 // Opt the windowed variants in to the shared memory they need (outside any capture).
+template <class T, int S, int EPT>
+cudaError_t tiled_optin(const DevModel& md, int need) {
+    switch (md.M) {
+        case 1: return cudaFuncSetAttribute(k_matvec_tiled<T, S, EPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        case 2: return cudaFuncSetAttribute(k_matvec_tiled<T, S, EPT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        case 3: return cudaFuncSetAttribute(k_matvec_tiled<T, S, EPT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        default: return cudaFuncSetAttribute(k_matvec_tiled<T, S, EPT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    }
+}
 template <class T> int prepare_matvec(const DevModel& md) {
     const int need[4] = {mv_tiled_smem(md, 4, sizeof(cx<T>)), mv_tiled_smem(md, 5, sizeof(cx<T>)),
                          mv_tiled_smem(md, 6, sizeof(cx<T>)), mv_tiled_smem(md, 7, sizeof(cx<T>))};
     cudaError_t ce = cudaSuccess;
-    if (need[0] > 48 * 1024) ce = cudaFuncSetAttribute(k_matvec_tiled<T, 1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[0]);
-    if (need[1] > 48 * 1024 && ce == cudaSuccess)
-        ce = cudaFuncSetAttribute(k_matvec_tiled<T, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[1]);
-    if (need[2] > 48 * 1024 && ce == cudaSuccess)
-        ce = cudaFuncSetAttribute(k_matvec_tiled<T, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[2]);
+    if (need[0] > 0) ce = tiled_optin<T, 1, 4>(md, need[0]);
+    if (need[1] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 2, 4>(md, need[1]);
+    if (need[2] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 4, 2>(md, need[2]);
     if constexpr (sizeof(T) == 4)
-        if (need[3] > 48 * 1024 && ce == cudaSuccess)
-            ce = cudaFuncSetAttribute(k_matvec_tiled<T, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, need[3]);
+        if (need[3] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 8, 1>(md, need[3]);
     return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "matvec shared-memory opt-in");
 }
 
