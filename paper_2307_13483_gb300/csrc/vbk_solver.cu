@@ -260,6 +260,125 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
 }
 
 
+
+// Register-blocked batched matvec: one thread owns EPT consecutive elements of one state and S
+// systems.  For every stencil point it loads the EPT coefficients once and the EPT neighbours of
+// each system from one base address, so the instruction count per element-system is a few per
+// point; neighbour indices are clamped only for groups at the ends of the vector (their
+// coefficients are zero there).  Same contract as k_matvec2; grid x = (state d, chunk of TPB*EPT
+// elements), y = groups of S systems.
+template <class R, int S, int EPT>
+__global__ void __launch_bounds__(TPB) k_matvec3(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
+                                                const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x, long long xs,
+                                                cx<R>* __restrict__ y, long long ys, const double2* __restrict__ b,
+                                                double2* __restrict__ part, int red) {
+    __shared__ int offs[MV_MAXPTS];
+    __shared__ cx<R> redsh[TPB / 32][S];
+    constexpr int T = TPB * EPT;
+    const int Nnu = md.Nnu, N = md.N;
+    const int nchunk = (Nnu + T - 1) / T;
+    const int d = blockIdx.x / nchunk;
+    const int nu0 = (blockIdx.x - d * nchunk) * T + threadIdx.x * EPT;
+    const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const DevEntry& e = md.ent[pb + k];
+        offs[k] = (e.dp - d) * Nnu + e.lin;
+    }
+    const cx<R>* xp[S];
+    int sy[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const int li = blockIdx.y * S + t;
+        int s = -1;
+        if (li < nlist) {
+            s = sel.list ? sel.list[li] : li;
+            if (s >= 0 && sel.act && !sel.act[s]) s = -1;
+        }
+        sy[t] = s;
+        xp[t] = x + (long long)(s < 0 ? 0 : s) * xs;
+    }
+    __syncthreads();
+    const int nv = min(EPT, Nnu - nu0);  // elements of this thread inside the plane
+    const int i0 = d * Nnu + nu0;
+    cx<R> acc[S][EPT], xi[S][EPT];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const cx<R>* dg = diag + (long long)sys_e[sy[t] < 0 ? 0 : sy[t]] * N;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            xi[t][e] = mkc<R>(0, 0);
+            acc[t][e] = mkc<R>(0, 0);
+            if (sy[t] >= 0 && e < nv) {
+                xi[t][e] = xp[t][i0 + e];
+                acc[t][e] = cmul<R>(dg[i0 + e], xi[t][e]);
+            }
+        }
+    }
+    if (nv > 0) {
+        const R* pc = pcp<R>(md) + (long long)pb * Nnu + nu0;
+        for (int k = 0; k < np; ++k) {
+            R c[EPT];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) c[e] = e < nv ? __ldg(pc + (long long)k * Nnu + e) : (R)0;
+            const int j0 = i0 + offs[k];
+            if (j0 >= 0 && j0 + EPT <= N) {
+#pragma unroll
+                for (int t = 0; t < S; ++t) {
+                    const cx<R>* xb = xp[t] + j0;
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        const cx<R> v = xb[e];
+                        acc[t][e].x = fma(-c[e], v.x, acc[t][e].x);
+                        acc[t][e].y = fma(-c[e], v.y, acc[t][e].y);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < S; ++t) {
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        const cx<R> v = xp[t][min(max(j0 + e, 0), N - 1)];
+                        acc[t][e].x = fma(-c[e], v.x, acc[t][e].x);
+                        acc[t][e].y = fma(-c[e], v.y, acc[t][e].y);
+                    }
+                }
+            }
+        }
+    }
+    cx<R> loc[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        loc[t] = mkc<R>(0, 0);
+        if (sy[t] < 0) continue;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            if (e >= nv) continue;
+            cx<R> out = acc[t][e];
+            if (b) {
+                const double2 bb = b[(long long)sy[t] * N + i0 + e];
+                out = mkc<R>((R)bb.x - out.x, (R)bb.y - out.y);
+            }
+            y[(long long)sy[t] * ys + i0 + e] = out;
+            if (red == 1) loc[t] = cfma<R>(xi[t][e], out, loc[t]);
+            else if (red == 2) loc[t].x += cabs2<R>(out);
+        }
+    }
+    if (red) {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const cx<R> v = warp_sum_c<R>(loc[t]);
+            if (lane == 0) redsh[w][t] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < S && sy[threadIdx.x] >= 0) {
+            cx<R> tot = mkc<R>(0, 0);
+            for (int q = 0; q < TPB / 32; ++q) tot = cadd<R>(tot, redsh[q][threadIdx.x]);
+            part[(long long)sy[threadIdx.x] * gridDim.x + blockIdx.x] = cvt_to_d<R>(tot);
+        }
+    }
+}
+
 // Windowed variant: the CTA stages, for each of its S systems and each state plane, the window
 // of x its TPB*EPT elements reach (contiguous, [nu0 + lmin, nu0 + T + lmax)) in shared memory,
 // together with the per-mode oscillator tables, so every neighbour and every coefficient factor
@@ -1338,25 +1457,32 @@ inline int block_partials(const DevPlanBuf& pb) {
 
 
 // Matvec variants (chosen per model and precision by the autotuner below):
-//   0..3  direct k_matvec2 with S = 1, 2, 4, 8 systems per thread
+//   0..3  register-blocked k_matvec3 with (S, EPT) = (1, 4), (2, 4), (4, 2), (2, 2)
 //   4..7  windowed k_matvec_tiled with (S, EPT) = (1, 4), (2, 4), (4, 2), (8, 1)
-constexpr int MV_NVAR = 8;
-inline int mv_ept(int v) { return v < 4 ? 1 : (v == 4 || v == 5) ? 4 : v == 6 ? 2 : 1; }
-inline int mv_sys(int v) { return v < 4 ? (1 << v) : (v == 4 ? 1 : v == 5 ? 2 : v == 6 ? 4 : 8); }
+//   8..9  direct k_matvec2 with S = 1, 4
+constexpr int MV_NVAR = 10;
+inline int mv_ept(int v) {
+    static const int e[MV_NVAR] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1};
+    return e[v];
+}
+inline int mv_sys(int v) {
+    static const int sv[MV_NVAR] = {1, 2, 4, 2, 1, 2, 4, 8, 1, 4};
+    return sv[v];
+}
 inline int mv_window(const DevModel& md, int v) {
     int lr = 0;
     for (int d = 0; d < md.ns; ++d) lr = std::max(lr, md.lmax[d] - md.lmin[d]);
     return TPB * mv_ept(v) + lr;
 }
 inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
-    if (v < 4) return 0;
+    if (v < 4 || v >= 8) return 0;
     if (md.ntab > MV_TAB_SMEM) return -1;  // the oscillator tables must fit the shared-memory copy
     const long long W = mv_window(md, v);
     const long long bytes = (long long)mv_sys(v) * md.ns * W * (long long)c + (long long)md.ntab * (long long)(c / 2) + 16;
     return bytes > 150 * 1024 ? -1 : (int)bytes;
 }
 inline bool mv_valid(const DevModel& md, int v, size_t c) {
-    if (c == 16 && mv_sys(v) > 4) return false;  // FP64: at most 4 systems per thread
+    if (c == 16 && mv_sys(v) * mv_ept(v) > 8) return false;  // FP64: register budget
     return mv_tiled_smem(md, v, c) >= 0;
 }
 inline int matvec_partials_v(const DevModel& md, int v) {
@@ -1387,15 +1513,14 @@ void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, co
                      double2* part, int red) {
     const int S = mv_sys(v);
     const dim3 g((unsigned)matvec_partials_v(md, v), (nlist + S - 1) / S);
-    const size_t smem = v >= 4 ? (size_t)mv_tiled_smem(md, v, sizeof(cx<T>)) : 0;
+    const size_t smem = (v >= 4 && v < 8) ? (size_t)mv_tiled_smem(md, v, sizeof(cx<T>)) : 0;
     switch (v) {
-        case 0: rn.go(name, k_matvec2<T, 1>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
-        case 1: rn.go(name, k_matvec2<T, 2>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
-        case 2: rn.go(name, k_matvec2<T, 4>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
-        case 3:
-            if constexpr (sizeof(T) == 4)
-                rn.go(name, k_matvec2<T, 8>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red);
-            break;
+        case 0: rn.go(name, k_matvec3<T, 1, 4>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 1: rn.go(name, k_matvec3<T, 2, 4>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 2: rn.go(name, k_matvec3<T, 4, 2>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 3: rn.go(name, k_matvec3<T, 2, 2>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 8: rn.go(name, k_matvec2<T, 1>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
+        case 9: rn.go(name, k_matvec2<T, 4>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
         case 4: go_tiled<T, 1, 4>(rn, name, md, g, smem, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red); break;
         case 5: go_tiled<T, 2, 4>(rn, name, md, g, smem, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red); break;
         case 6: go_tiled<T, 4, 2>(rn, name, md, g, smem, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red); break;
@@ -1471,7 +1596,7 @@ template <class T, int M>
 void launch_matvec(Runner& rn, const char* name, const DevModel& md, const int* sys_e, Sel sel, unsigned nlist,
                    const cx<T>* diag, const cx<T>* x, long long xs, cx<T>* y, long long ys, const double2* b, double2* part,
                    int red, int variant) {
-    launch_matvec_v<T>(rn, variant < 0 ? (sizeof(T) == 4 ? 3 : 2) : variant, name, md, sys_e, sel, nlist, diag, x, xs, y, ys, b,
+    launch_matvec_v<T>(rn, variant < 0 ? (sizeof(T) == 4 ? 1 : 3) : variant, name, md, sys_e, sel, nlist, diag, x, xs, y, ys, b,
                        part, red);
 }
 inline int matvec_partials(const DevModel& md, int variant) { return matvec_partials_v(md, variant); }
@@ -1518,7 +1643,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     const size_t NN = (size_t)N;
     const int nb_e = (int)cdiv_u(N, TPB);       // element-wise kernels
     int nb_mv = matvec_partials(md, mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0 ? 0 : mdl->mv_variant[sizeof(R) == 4 ? 0 : 1]);
-    const int nb_mv_max = matvec_partials(md, 0);  // the largest partial count of any variant
+    int nb_mv_max = 0;  // the largest partial count of any variant
+    for (int v = 0; v < MV_NVAR; ++v) nb_mv_max = std::max(nb_mv_max, matvec_partials(md, v));
     const int nb_v = (int)cdiv_u(N, VCHUNK);    // basis-vector kernels
     const int nb_b = block ? block_partials(pbuf) : 0;
     const int nslot = std::max(std::max(nb_e, nb_mv_max), std::max(nb_b, nb_v * (mres + 1)));
@@ -1680,7 +1806,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cudaMemsetAsync(olist, 0xff, nsys * sizeof(int), st);  // -1: no system
             cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
-                  it == 0 ? nb_e : matvec_partials(md, std::max(0, mdl->mv_variant[1] < 0 ? 2 : mdl->mv_variant[1])),
+                  it == 0 ? nb_e : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
                   it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
             cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -1710,7 +1836,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     }
                 }
                 const int mvv = mdl->mv_variant[sizeof(R) == 4 ? 0 : 1];
-                nb_mv = matvec_partials(md, mvv < 0 ? (sizeof(R) == 4 ? 3 : 2) : mvv);
+                nb_mv = matvec_partials(md, mvv < 0 ? (sizeof(R) == 4 ? 1 : 3) : mvv);
                 // one COCG iteration for the systems of the inner list
                 auto cocg_iter = [&](unsigned ny) {
                     const Sel sc{ilist, inner};
@@ -2182,7 +2308,7 @@ int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* 
     rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
           (float2*)nullptr);
     const Sel none{nullptr, nullptr};
-    launch_matvec_v<double>(rn, 2, "matvec_fp64", m->dm, (const int*)se, none, (unsigned)nsys, (const double2*)d64, x,
+    launch_matvec_v<double>(rn, 9, "matvec_fp64", m->dm, (const int*)se, none, (unsigned)nsys, (const double2*)d64, x,
                             (long long)N, y, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
     if ((ce = cudaGetLastError()) != cudaSuccess) return vbk_cuda_fail(ce, "noalloc: kernels");
     if (rn.first_error != cudaSuccess) return VBK_ERR_CUDA;
