@@ -1482,7 +1482,7 @@ inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
     return bytes > 150 * 1024 ? -1 : (int)bytes;
 }
 inline bool mv_valid(const DevModel& md, int v, size_t c) {
-    if (c == 16 && mv_sys(v) * mv_ept(v) > 8) return false;  // FP64: register budget
+    if (c == 16 && (mv_sys(v) * mv_ept(v) > 8 || v == 7)) return false;  // FP64: register budget
     return mv_tiled_smem(md, v, c) >= 0;
 }
 inline int matvec_partials_v(const DevModel& md, int v) {
