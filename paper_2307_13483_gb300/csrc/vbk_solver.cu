@@ -996,6 +996,280 @@ __global__ void __launch_bounds__(TPB) k_cocg_p(int N, Sel sel, const SysState* 
     p[o] = cfma<R>(be, p[o], z[o]);
 }
 
+
+// ------------------------------------------------ persistent COCG (point preconditioners)
+// Grid-stride kernels over work items drawn from a device-side list of active systems, so the
+// grids are static and one CUDA graph serves a whole solve.  The per-system scalar steps run in
+// the last work item of each system (its partials are complete once the per-system counter
+// `done` reaches the item count; the writer side fences before counting), so an iteration is
+// three launches: matvec (+ alpha), update (+ beta, convergence, next list), p update.
+struct DList {
+    const int* list;
+    const int* count;
+};
+
+// Sum n partials of one system with the lanes of one warp (L2 reads; the writers fenced).
+__device__ __forceinline__ double2 warp_psum_cg(const double2* p, int n) {
+    const int lane = threadIdx.x & 31;
+    double2 a = make_double2(0.0, 0.0);
+    for (int k = lane; k < n; k += 32) {
+        const double2 v = __ldcg(p + k);
+        a.x += v.x;
+        a.y += v.y;
+    }
+    return warp_sum2(a);
+}
+
+// one matvec work item: S systems x EPT*TPB elements of state d (register-blocked, as k_matvec3)
+template <class R, int S, int EPT>
+__device__ __forceinline__ void pmatvec_item(const DevModel& md, const int* sys_e, const int* sy, int d, int nu0,
+                                             const int* offs, int np, const cx<R>* diag, const cx<R>* x, cx<R>* y,
+                                             cx<R> (&loc)[S]) {
+    const int Nnu = md.Nnu, N = md.N;
+    const int nv = min(EPT, Nnu - nu0);
+    const int i0 = d * Nnu + nu0;
+    const cx<R>* xp[S];
+    cx<R> acc[S][EPT], xi[S][EPT];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        xp[t] = x + (long long)(sy[t] < 0 ? 0 : sy[t]) * N;
+        const cx<R>* dg = diag + (long long)sys_e[sy[t] < 0 ? 0 : sy[t]] * N;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            xi[t][e] = mkc<R>(0, 0);
+            acc[t][e] = mkc<R>(0, 0);
+            if (sy[t] >= 0 && e < nv) {
+                xi[t][e] = xp[t][i0 + e];
+                acc[t][e] = cmul<R>(dg[i0 + e], xi[t][e]);
+            }
+        }
+    }
+    if (nv > 0) {
+        const R* pc = pcp<R>(md) + (long long)md.ebeg[d] * Nnu + nu0;
+        for (int k = 0; k < np; ++k) {
+            R c[EPT];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) c[e] = e < nv ? __ldg(pc + (long long)k * Nnu + e) : (R)0;
+            const int j0 = i0 + offs[k];
+            if (j0 >= 0 && j0 + EPT <= N) {
+#pragma unroll
+                for (int t = 0; t < S; ++t) {
+                    const cx<R>* xb = xp[t] + j0;
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        const cx<R> v = xb[e];
+                        acc[t][e].x = fma(-c[e], v.x, acc[t][e].x);
+                        acc[t][e].y = fma(-c[e], v.y, acc[t][e].y);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < S; ++t) {
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        const cx<R> v = xp[t][min(max(j0 + e, 0), N - 1)];
+                        acc[t][e].x = fma(-c[e], v.x, acc[t][e].x);
+                        acc[t][e].y = fma(-c[e], v.y, acc[t][e].y);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        loc[t] = mkc<R>(0, 0);
+        if (sy[t] < 0) continue;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            if (e >= nv) continue;
+            y[(long long)sy[t] * N + i0 + e] = acc[t][e];
+            loc[t] = cfma<R>(xi[t][e], acc[t][e], loc[t]);
+        }
+    }
+}
+
+// q = A p and p^T q; the last item of a system sets alpha = rho / p^T q (breakdown: retire).
+template <class R, int S, int EPT>
+__global__ void __launch_bounds__(TPB) k_pmatvec(DevModel md, const int* __restrict__ sys_e, DList L,
+                                                const cx<R>* __restrict__ diag, const cx<R>* __restrict__ p,
+                                                cx<R>* __restrict__ q, double2* __restrict__ part, int* __restrict__ done,
+                                                SysState* __restrict__ st, int* __restrict__ act, int* __restrict__ outer) {
+    __shared__ int offs[MAXS][MV_MAXPTS];
+    __shared__ cx<R> redsh[TPB / 32][S];
+    __shared__ int lastf[S];
+    constexpr int T = TPB * EPT;
+    const int Nnu = md.Nnu;
+    const int nchunk = (Nnu + T - 1) / T;
+    const int nxb = md.ns * nchunk;  // items (and partials) per system group
+    for (int dd = 0; dd < md.ns; ++dd) {
+        const int pb = md.ebeg[dd], np = min(md.ebeg[dd + 1] - pb, MV_MAXPTS);
+        for (int k = threadIdx.x; k < np; k += blockDim.x) {
+            const DevEntry& e = md.ent[pb + k];
+            offs[dd][k] = (e.dp - dd) * Nnu + e.lin;
+        }
+    }
+    __syncthreads();
+    const int cnt = *L.count;
+    const int ngr = (cnt + S - 1) / S;
+    const int nitems = ngr * nxb;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int g = item / nxb, xb = item - g * nxb;
+        const int d = xb / nchunk;
+        const int nu0 = (xb - d * nchunk) * T + threadIdx.x * EPT;
+        int sy[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const int pos = g * S + t;
+            sy[t] = pos < cnt ? L.list[pos] : -1;
+        }
+        const int np = min(md.ebeg[d + 1] - md.ebeg[d], MV_MAXPTS);
+        cx<R> loc[S];
+        pmatvec_item<R, S, EPT>(md, sys_e, sy, d, nu0, offs[d], np, diag, p, q, loc);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const cx<R> v = warp_sum_c<R>(loc[t]);
+            if (lane == 0) redsh[w][t] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < S) {
+            const int t = threadIdx.x, sid = sy[t];
+            lastf[t] = 0;
+            if (sid >= 0) {
+                cx<R> tot = mkc<R>(0, 0);
+                for (int qq = 0; qq < TPB / 32; ++qq) tot = cadd<R>(tot, redsh[qq][t]);
+                part[(long long)sid * nxb + xb] = cvt_to_d<R>(tot);
+                __threadfence();
+                lastf[t] = atomicAdd(done + sid, 1) == nxb - 1;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            if (!lastf[t]) continue;  // uniform across the block
+            if (w == 0) {
+                __threadfence();
+                const int sid = sy[t];
+                const double2 pq = warp_psum_cg(part + (long long)sid * nxb, nxb);
+                if (lane == 0) {
+                    done[sid] = 0;
+                    SysState& Sx = st[sid];
+                    const double den = pq.x * pq.x + pq.y * pq.y;
+                    if (!(den > 0.0) || !isfinite(den)) {
+                        Sx.status = isfinite(den) ? VBK_SYS_BREAKDOWN : VBK_SYS_NAN;
+                        Sx.alpha = make_double2(0.0, 0.0);
+                        act[sid] = 0;
+                        outer[sid] = 0;
+                    } else {
+                        Sx.alpha = cdiv<double>(Sx.rho, pq);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// x += alpha p, r -= alpha q, z = B^-1 r (point), partials ||r||^2 and r^T z; the last item of a
+// system forms beta, tests convergence and appends the system to the next list.
+template <class R, int EPT>
+__global__ void __launch_bounds__(TPB) k_pupdate(int N, const int* __restrict__ sys_e, DList L, int pmode,
+                                                const cx<R>* __restrict__ diag, cx<R>* __restrict__ x, cx<R>* __restrict__ r,
+                                                const cx<R>* __restrict__ p, const cx<R>* __restrict__ q, cx<R>* __restrict__ z,
+                                                double2* __restrict__ part_rr, double2* __restrict__ part_rz,
+                                                int* __restrict__ done, SysState* __restrict__ st, int* __restrict__ act,
+                                                int* __restrict__ outer, int max_iter, int* __restrict__ next_list,
+                                                int* __restrict__ next_count) {
+    __shared__ cx<R> sh[32];
+    __shared__ int lastf;
+    constexpr int T = TPB * EPT;
+    const int nub = (N + T - 1) / T;
+    const int cnt = *L.count;
+    const int nitems = cnt * nub;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int pos = item / nub, ub = item - pos * nub;
+        const int s = L.list[pos];
+        const bool on = act[s] != 0;  // a breakdown in this iteration's matvec retired it
+        cx<R> lrr = mkc<R>(0, 0), lrz = mkc<R>(0, 0);
+        if (on) {
+            const cx<R> al = cvt_from_d<R>(st[s].alpha);
+            const long long so = (long long)s * N;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                const int i = ub * T + e * TPB + threadIdx.x;
+                if (i >= N) continue;
+                const long long o = so + i;
+                x[o] = cfma<R>(al, p[o], x[o]);
+                const cx<R> rn = csub<R>(r[o], cmul<R>(al, q[o]));
+                r[o] = rn;
+                lrr.x += cabs2<R>(rn);
+                const cx<R> zi = pmode == 0 ? cdiv<R>(rn, diag[(long long)sys_e[s] * N + i]) : rn;
+                z[o] = zi;
+                lrz = cfma<R>(rn, zi, lrz);
+            }
+        }
+        const double2 trr = block_sum_c<R>(lrr, sh);
+        const double2 trz = block_sum_c<R>(lrz, sh);
+        if (threadIdx.x == 0) {
+            lastf = 0;
+            if (on) {
+                part_rr[(long long)s * nub + ub] = trr;
+                part_rz[(long long)s * nub + ub] = trz;
+                __threadfence();
+                lastf = atomicAdd(done + s, 1) == nub - 1;
+            }
+        }
+        __syncthreads();
+        if (lastf && threadIdx.x < 32) {
+            __threadfence();
+            const double rr = warp_psum_cg(part_rr + (long long)s * nub, nub).x;
+            const double2 rz = warp_psum_cg(part_rz + (long long)s * nub, nub);
+            if (threadIdx.x == 0) {
+                done[s] = 0;
+                SysState& Sx = st[s];
+                Sx.iters += 1;
+                Sx.cycle_iters += 1;
+                const double rn = sqrt(rr);
+                Sx.inres = rn;
+                const double den = Sx.rho.x * Sx.rho.x + Sx.rho.y * Sx.rho.y;
+                if (!isfinite(rn) || !isfinite(rz.x) || !isfinite(rz.y) || rn <= Sx.target || Sx.iters >= max_iter) {
+                    act[s] = 0;  // the FP64 residual decides
+                } else if (!(rz.x * rz.x + rz.y * rz.y > 0.0) || !(den > 0.0)) {
+                    Sx.status = VBK_SYS_BREAKDOWN;
+                    act[s] = 0;
+                    outer[s] = 0;
+                } else {
+                    Sx.beta = cdiv<double>(rz, Sx.rho);
+                    Sx.rho = rz;
+                    next_list[atomicAdd(next_count, 1)] = s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// p = z + beta p for the systems of the next list
+template <class R, int EPT>
+__global__ void __launch_bounds__(TPB) k_pp(int N, DList L, const SysState* __restrict__ st, const cx<R>* __restrict__ z,
+                                           cx<R>* __restrict__ p) {
+    constexpr int T = TPB * EPT;
+    const int nub = (N + T - 1) / T;
+    const int cnt = *L.count;
+    const int nitems = cnt * nub;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int pos = item / nub, ub = item - pos * nub;
+        const int s = L.list[pos];
+        const cx<R> be = cvt_from_d<R>(st[s].beta);
+        const long long so = (long long)s * N;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int i = ub * T + e * TPB + threadIdx.x;
+            if (i < N) p[so + i] = cfma<R>(be, p[so + i], z[so + i]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------- GMRES
 // Restarted GMRES(m) with right preconditioning (Sec. III.A; Saad & Schultz): Arnoldi
 // A B^-1 V_n = V_{n+1} H_n with classical Gram-Schmidt applied twice (CGS2), the
@@ -1653,7 +1927,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     bytes += carve_size<cx<R>>(mixed ? (size_t)nE * NN : 1);          // diagR
     bytes += carve_size<double2>((size_t)nsys * NN);                  // r64
     bytes += carve_size<SysState>(nsys);
-    bytes += 5 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
+    bytes += 7 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
     bytes += 3 * carve_size<double2>((size_t)nsys * nslot);           // partial buffers
     if (block) bytes += carve_size<cx<R>>((size_t)nE * NN * (bp.p + 1));
     if (method == VBK_COCG) {
@@ -1688,6 +1962,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     int* olist = carve<int>(p, nsys);
     int* ilist = carve<int>(p, nsys);
     int* alll = carve<int>(p, nsys);
+    int* ilist2 = carve<int>(p, nsys);  // second list of the persistent COCG iterations
+    int* done = carve<int>(p, nsys);    // per-system work-item counters (self-resetting)
     int* pfail = carve<int>(p, nE);
     int* sys_e = carve<int>(p, nsys);
     int* cnt = carve<int>(p, 4);
@@ -1721,7 +1997,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     int rc = VBK_OK;
     int* hcnt = nullptr;
     double* dE = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr, pgexec = nullptr;
+    long long p_per_launch = 0;
     std::vector<int> ones(nsys, 1), iota(nsys);
     for (int k = 0; k < nsys; ++k) iota[k] = k;
     std::vector<SysState> hst(nsys);
@@ -1746,7 +2023,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cudaMemcpyAsync(ilist, iota.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemsetAsync(sst, 0, nsys * sizeof(SysState), st) != cudaSuccess ||
             cudaMemsetAsync(job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) != cudaSuccess ||
-            cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess) {
+            cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(done, 0, nsys * sizeof(int), st) != cudaSuccess) {
             fail(vbk_cuda_fail(cudaGetLastError(), "solver set-up copies"));
             break;
         }
@@ -1861,7 +2139,99 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 };
                 const int K = std::max(1, o.check_every);
                 int k = 0;
-                if (!rn.timing) {
+                if (!block) {
+                    // persistent iterations: static grids over the device-side lists (A = ilist with
+                    // count cnt[0], B = ilist2 with count cnt[1]); K (even) iterations per CUDA graph,
+                    // captured once per solve and relaunched until list A is empty.  With timing on,
+                    // the same kernels are launched directly (an event pair each).
+                    const int K2 = K + (K & 1);
+                    int sms = 0;
+                    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, mdl->device);
+                    if (sms <= 0) sms = 148;
+                    auto grid_of = [&](auto kern) {
+                        int nb = 0;
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, TPB, 0);
+                        return (unsigned)(std::max(1, nb) * sms);
+                    };
+                    const int v = mvv;
+                    const int pS = (v == 0) ? 1 : (v == 2) ? 4 : 2, pE = (v == 0 || v == 1) ? 4 : 2;
+                    const unsigned g_mv = pS == 1   ? grid_of(k_pmatvec<R, 1, 4>)
+                                          : pS == 4 ? grid_of(k_pmatvec<R, 4, 2>)
+                                          : pE == 4 ? grid_of(k_pmatvec<R, 2, 4>)
+                                                    : grid_of(k_pmatvec<R, 2, 2>);
+                    const unsigned g_up = grid_of(k_pupdate<R, 4>), g_pp = grid_of(k_pp<R, 4>);
+                    auto piter = [&](int t) {
+                        const DList cur{t % 2 == 0 ? ilist : ilist2, cnt + (t % 2)};
+                        const DList nxt{t % 2 == 0 ? ilist2 : ilist, cnt + 1 - (t % 2)};
+                        cudaMemsetAsync(cnt + 1 - (t % 2), 0, sizeof(int), rn.st);
+                        if (pS == 1)
+                            rn.go("matvec", k_pmatvec<R, 1, 4>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                                  (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
+                        else if (pS == 4)
+                            rn.go("matvec", k_pmatvec<R, 4, 2>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                                  (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
+                        else if (pE == 4)
+                            rn.go("matvec", k_pmatvec<R, 2, 4>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                                  (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
+                        else
+                            rn.go("matvec", k_pmatvec<R, 2, 2>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                                  (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
+                        rn.go("cocg_update", k_pupdate<R, 4>, dim3(g_up), dim3(TPB), N, (const int*)sys_e, cur, pmode,
+                              (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z, partC, partB, done, sst, inner,
+                              outer, o.max_iter, (int*)nxt.list, (int*)nxt.count);
+                        rn.go("cocg_p", k_pp<R, 4>, dim3(g_pp), dim3(TPB), N, nxt, (const SysState*)sst, (const cx<R>*)z, pv);
+                    };
+                    if (!rn.timing && !pgexec) {
+                        const long long l0 = mdl->launches;
+                        if (!mdl->cap_stream &&
+                            cudaStreamCreateWithFlags(&mdl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "capture stream"));
+                            break;
+                        }
+                        if (cudaStreamBeginCapture(mdl->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "graph capture"));
+                            break;
+                        }
+                        rn.st = mdl->cap_stream;
+                        for (int t = 0; t < K2; ++t) piter(t);
+                        rn.st = st;
+                        cudaGraph_t graph = nullptr;
+                        const cudaError_t ce = cudaStreamEndCapture(mdl->cap_stream, &graph);
+                        p_per_launch = mdl->launches - l0;
+                        mdl->launches = l0;
+                        if (ce != cudaSuccess || rn.first_error != cudaSuccess) {
+                            if (graph) cudaGraphDestroy(graph);
+                            fail(ce != cudaSuccess ? vbk_cuda_fail(ce, "graph capture") : VBK_ERR_CUDA);
+                            break;
+                        }
+                        if (cudaGraphInstantiate(&pgexec, graph, 0) != cudaSuccess) {
+                            cudaGraphDestroy(graph);
+                            pgexec = nullptr;
+                            fail(vbk_cuda_fail(cudaGetLastError(), "graph instantiation"));
+                            break;
+                        }
+                        cudaGraphDestroy(graph);
+                    }
+                    for (;;) {
+                        if (rn.timing) {
+                            for (int t = 0; t < K2; ++t) piter(t);
+                        } else {
+                            if (cudaGraphLaunch(pgexec, st) != cudaSuccess) {
+                                fail(vbk_cuda_fail(cudaGetLastError(), "graph launch"));
+                                break;
+                            }
+                            mdl->launches += p_per_launch;
+                        }
+                        k += K2;
+                        cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+                        if (cudaStreamSynchronize(st) != cudaSuccess) {
+                            fail(vbk_cuda_fail(cudaGetLastError(), "COCG iterations"));
+                            break;
+                        }
+                        rn.flush();
+                        if (hcnt[0] == 0 || k > o.max_iter + K2) break;
+                    }
+                } else if (!rn.timing) {
                     // K iterations as one CUDA graph (grids sized for the active systems; systems that
                     // retire inside a chunk leave their CTAs at once), relaunched until none is active and
                     // re-captured when the active count has halved
@@ -2060,6 +2430,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
     cudaStreamSynchronize(st);
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (pgexec) cudaGraphExecDestroy(pgexec);
     if (hcnt) cudaFreeHost(hcnt);
     return rc;
 }
