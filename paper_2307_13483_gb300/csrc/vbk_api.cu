@@ -594,6 +594,19 @@ int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
     vbk_model* m = new (std::nothrow) vbk_model();
     if (!m) return VBK_ERR_OOM;
     cudaGetDevice(&m->device);
+    {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = m->device;
+        if (cudaMemPoolCreate(&m->pool, &props) == cudaSuccess) {
+            unsigned long long thr = ~0ULL;
+            cudaMemPoolSetAttribute(m->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        } else {
+            cudaGetLastError();
+            m->pool = nullptr;  // fall back to the device's default pool
+        }
+    }
     int rc = build(desc, m);
     if (rc) {
         vbk_free_model(m);
@@ -607,6 +620,10 @@ void vbk_free_model(vbk_model* m) {
     if (!m) return;
     if (m->dev_mem) cudaFree(m->dev_mem);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->pool) {
+        cudaDeviceSynchronize();  // outstanding frees of this model's calls complete before the pool goes
+        cudaMemPoolDestroy(m->pool);
+    }
     delete m;
 }
 
@@ -683,7 +700,7 @@ int vbk_solve(vbk_model* m, int n_eps, const double* eps_i, int n_vi, const int*
     b.st = st;
     const size_t bbytes = (size_t)job.nsys * N * sizeof(double2);
     const size_t extra = (size_t)n_eps * sizeof(double) + (size_t)n_vi * sizeof(int) + 512;
-    VBK_CUDA(cudaMallocAsync(&b.p, bbytes + extra, st));
+    VBK_CUDA(vbk_alloc(m, &b.p, bbytes + extra, st));
     double2* b64 = (double2*)b.p;
     double* deps = (double*)((char*)b.p + bbytes);
     int* dvf = (int*)((char*)deps + (((size_t)n_eps * sizeof(double) + 255) & ~size_t(255)));
@@ -720,7 +737,7 @@ int vbk_cross_sections(vbk_model* m, int n_eps, const double* eps_i, int n_vi, c
     b.st = st;
     const size_t s1 = ((size_t)n_eps * 8 + 255) & ~size_t(255), s2 = (Etot.size() * 8 + 255) & ~size_t(255),
                  s3 = ((size_t)n_vf * 4 + 255) & ~size_t(255), s4 = ((size_t)n_vf * 8 + 255) & ~size_t(255);
-    VBK_CUDA(cudaMallocAsync(&b.p, s1 + s2 + s3 + s4, st));
+    VBK_CUDA(vbk_alloc(m, &b.p, s1 + s2 + s3 + s4, st));
     char* p = (char*)b.p;
     VBK_CUDA(cudaMemcpyAsync(p, eps_i, n_eps * 8, cudaMemcpyHostToDevice, st));
     VBK_CUDA(cudaMemcpyAsync(p + s1, Etot.data(), Etot.size() * 8, cudaMemcpyHostToDevice, st));
@@ -757,7 +774,7 @@ int vbk_eels(vbk_model* m, int n_eps, int n_vi, const int* vi, int n_vf, const i
     b.st = st;
     const size_t s1 = ((size_t)n_de * 8 + 255) & ~size_t(255), s2 = ((size_t)n_vf * 8 + 255) & ~size_t(255),
                  s3 = ((size_t)n_vi * 8 + 255) & ~size_t(255);
-    VBK_CUDA(cudaMallocAsync(&b.p, s1 + s2 + s3, st));
+    VBK_CUDA(vbk_alloc(m, &b.p, s1 + s2 + s3, st));
     char* p = (char*)b.p;
     VBK_CUDA(cudaMemcpyAsync(p, de, n_de * 8, cudaMemcpyHostToDevice, st));
     VBK_CUDA(cudaMemcpyAsync(p + s1, Ef.data(), n_vf * 8, cudaMemcpyHostToDevice, st));
@@ -847,7 +864,7 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
     }
     DevBuf b;
     b.st = st;
-    VBK_CUDA(cudaMallocAsync(&b.p, tot, st));
+    VBK_CUDA(vbk_alloc(m, &b.p, tot, st));
     char* p = (char*)b.p;
     auto P = [&](int k) { return p + off[k]; };
     VBK_CUDA(cudaMemsetAsync(P(0), 0, sizes[0], st));
@@ -864,7 +881,7 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
     const long long nt = (long long)n_eps * n_vi * n_vf;
     std::vector<double> sig_dummy;  // sigma itself is not needed here
     double* dsig = nullptr;
-    VBK_CUDA(cudaMallocAsync((void**)&dsig, std::max<long long>(1, nt) * sizeof(double), st));
+    VBK_CUDA(vbk_alloc(m, (void**)&dsig, std::max<long long>(1, nt) * sizeof(double), st));
     k_sigma<<<cdiv_u(nt, 128), 128, 0, st>>>(m->dm, n_eps, n_vi, n_vf, (const double*)P(4), (const double*)P(5),
                                              (const double2*)psi_dev, (const int*)P(6), (const double*)P(7), dsig,
                                              (double2*)P(2));

@@ -125,6 +125,7 @@ struct vbk_model {
     int device = 0;
     cudaStream_t cap_stream = nullptr;  // library-owned stream used only to capture CUDA graphs
     int mv_variant[2] = {-1, -1};       // autotuned matvec variant per precision (FP32, FP64); -1: untuned
+    cudaMemPool_t pool = nullptr;       // library-owned stream-ordered pool (keeps its memory between calls)
 };
 
 // --------------------------------------------------------------------------- level shift
@@ -213,6 +214,11 @@ __host__ __device__ inline double vbk_amplitude(double eps, double a, double b, 
 }
 
 // --------------------------------------------------------------------------- helpers
+// Stream-ordered allocation from the model's own pool: workspace freed at the end of a call stays
+// reserved in the pool (release threshold: unlimited), so repeated solves do not map memory again.
+inline cudaError_t vbk_alloc(const vbk_model* m, void** p, size_t bytes, cudaStream_t st) {
+    return m->pool ? cudaMallocFromPoolAsync(p, bytes, m->pool, st) : cudaMallocAsync(p, bytes, st);
+}
 void vbk_set_error(const std::string& msg);
 int vbk_cuda_fail(cudaError_t e, const char* what);
 #define VBK_CUDA(call)                                             \

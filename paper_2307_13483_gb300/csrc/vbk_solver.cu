@@ -1688,7 +1688,7 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
         all.insert(all.end(), bp.ent_dc.begin(), bp.ent_dc.end());
     all.insert(all.end(), run_off.begin(), run_off.end());
     all.insert(all.end(), run_c0.begin(), run_c0.end());
-    VBK_CUDA(cudaMallocAsync(&out->mem, all.size() * sizeof(int), st));
+    VBK_CUDA(vbk_alloc(m, &out->mem, all.size() * sizeof(int), st));
     int* p = (int*)out->mem;
     VBK_CUDA(cudaMemcpyAsync(p, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     out->pd.chain_off = p;
@@ -1943,7 +1943,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     }
     char* wsbase = nullptr;
     {
-        cudaError_t e = cudaMallocAsync((void**)&wsbase, bytes, st);
+        cudaError_t e = vbk_alloc(mdl, (void**)&wsbase, bytes, st);
         if (e != cudaSuccess) {
             if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
             vbk_set_error("workspace allocation of " + std::to_string(bytes) + " bytes failed");
@@ -2011,7 +2011,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             fail(VBK_ERR_OOM);
             break;
         }
-        if (cudaMallocAsync((void**)&dE, std::max(1, nE) * sizeof(double), st) != cudaSuccess) {
+        if (vbk_alloc(mdl, (void**)&dE, std::max(1, nE) * sizeof(double), st) != cudaSuccess) {
             fail(VBK_ERR_OOM);
             break;
         }
@@ -2508,7 +2508,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
                    2 * carve_size<cx<R>>(mixed ? (size_t)nsys * N : 1) + carve_size<int>(nsys) + carve_size<double>(nE) +
                    carve_size<int>(nE) + (block ? carve_size<cx<R>>((size_t)nE * N * (bp.p + 1)) : 0);
     char* base = nullptr;
-    if (cudaMallocAsync((void**)&base, bytes, st) != cudaSuccess) {
+    if (vbk_alloc(m, (void**)&base, bytes, st) != cudaSuccess) {
         if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
         cudaGetLastError();
         vbk_set_error("operator workspace allocation failed");
