@@ -1045,34 +1045,39 @@ __device__ __forceinline__ void pmatvec_item(const DevModel& md, const int* sys_
         }
     }
     if (nv > 0) {
+        // stencil points in batches of PB: all coefficient and neighbour loads of a batch are
+        // issued before its FMAs (memory-level parallelism; short critical path)
+        constexpr int PB = 4;
         const R* pc = pcp<R>(md) + (long long)md.ebeg[d] * Nnu + nu0;
-        for (int k = 0; k < np; ++k) {
-            R c[EPT];
+        const bool interior = nv == EPT;
+        for (int k0 = 0; k0 < np; k0 += PB) {
+            R c[PB][EPT];
+            cx<R> v[PB][S][EPT];
 #pragma unroll
-            for (int e = 0; e < EPT; ++e) c[e] = e < nv ? __ldg(pc + (long long)k * Nnu + e) : (R)0;
-            const int j0 = i0 + offs[k];
-            if (j0 >= 0 && j0 + EPT <= N) {
+            for (int kk = 0; kk < PB; ++kk) {
+                const int k = k0 + kk;
+                const bool okk = k < np;
+                const int j0 = i0 + (okk ? offs[k] : 0);
+                const bool fast = interior && j0 >= 0 && j0 + EPT <= N;
 #pragma unroll
-                for (int t = 0; t < S; ++t) {
-                    const cx<R>* xb = xp[t] + j0;
+                for (int e = 0; e < EPT; ++e) c[kk][e] = (okk && e < nv) ? __ldg(pc + (long long)k * Nnu + e) : (R)0;
 #pragma unroll
-                    for (int e = 0; e < EPT; ++e) {
-                        const cx<R> v = xb[e];
-                        acc[t][e].x = fma(-c[e], v.x, acc[t][e].x);
-                        acc[t][e].y = fma(-c[e], v.y, acc[t][e].y);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int t = 0; t < S; ++t) {
+                for (int t = 0; t < S; ++t)
 #pragma unroll
                     for (int e = 0; e < EPT; ++e) {
-                        const cx<R> v = xp[t][min(max(j0 + e, 0), N - 1)];
-                        acc[t][e].x = fma(-c[e], v.x, acc[t][e].x);
-                        acc[t][e].y = fma(-c[e], v.y, acc[t][e].y);
+                        const int j = fast ? j0 + e : min(max(j0 + e, 0), N - 1);
+                        v[kk][t][e] = xp[t][j];
                     }
-                }
             }
+#pragma unroll
+            for (int kk = 0; kk < PB; ++kk)
+#pragma unroll
+                for (int t = 0; t < S; ++t)
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        acc[t][e].x = fma(-c[kk][e], v[kk][t][e].x, acc[t][e].x);
+                        acc[t][e].y = fma(-c[kk][e], v[kk][t][e].y, acc[t][e].y);
+                    }
         }
     }
 #pragma unroll
@@ -1180,7 +1185,7 @@ __global__ void __launch_bounds__(TPB) k_pupdate(int N, const int* __restrict__ 
                                                 int* __restrict__ done, SysState* __restrict__ st, int* __restrict__ act,
                                                 int* __restrict__ outer, int max_iter, int* __restrict__ next_list,
                                                 int* __restrict__ next_count) {
-    __shared__ cx<R> sh[32];
+    __shared__ R red3[TPB / 32][3];
     __shared__ int lastf;
     constexpr int T = TPB * EPT;
     const int nub = (N + T - 1) / T;
@@ -1208,13 +1213,31 @@ __global__ void __launch_bounds__(TPB) k_pupdate(int N, const int* __restrict__ 
                 lrz = cfma<R>(rn, zi, lrz);
             }
         }
-        const double2 trr = block_sum_c<R>(lrr, sh);
-        const double2 trz = block_sum_c<R>(lrz, sh);
+        // one block reduction of (||r||^2, r^T z)
+        R a0 = lrr.x, a1 = lrz.x, a2 = lrz.y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, o);
+            a1 += __shfl_down_sync(0xffffffffu, a1, o);
+            a2 += __shfl_down_sync(0xffffffffu, a2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red3[threadIdx.x >> 5][0] = a0;
+            red3[threadIdx.x >> 5][1] = a1;
+            red3[threadIdx.x >> 5][2] = a2;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             lastf = 0;
             if (on) {
-                part_rr[(long long)s * nub + ub] = trr;
-                part_rz[(long long)s * nub + ub] = trz;
+                R b0 = 0, b1 = 0, b2 = 0;
+                for (int w = 0; w < TPB / 32; ++w) {
+                    b0 += red3[w][0];
+                    b1 += red3[w][1];
+                    b2 += red3[w][2];
+                }
+                part_rr[(long long)s * nub + ub] = make_double2((double)b0, 0.0);
+                part_rz[(long long)s * nub + ub] = make_double2((double)b1, (double)b2);
                 __threadfence();
                 lastf = atomicAdd(done + s, 1) == nub - 1;
             }
@@ -2159,7 +2182,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                                           : pS == 4 ? grid_of(k_pmatvec<R, 4, 2>)
                                           : pE == 4 ? grid_of(k_pmatvec<R, 2, 4>)
                                                     : grid_of(k_pmatvec<R, 2, 2>);
-                    const unsigned g_up = grid_of(k_pupdate<R, 4>), g_pp = grid_of(k_pp<R, 4>);
+                    const unsigned g_up = grid_of(k_pupdate<R, 8>), g_pp = grid_of(k_pp<R, 4>);
                     auto piter = [&](int t) {
                         const DList cur{t % 2 == 0 ? ilist : ilist2, cnt + (t % 2)};
                         const DList nxt{t % 2 == 0 ? ilist2 : ilist, cnt + 1 - (t % 2)};
@@ -2176,7 +2199,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                         else
                             rn.go("matvec", k_pmatvec<R, 2, 2>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
                                   (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
-                        rn.go("cocg_update", k_pupdate<R, 4>, dim3(g_up), dim3(TPB), N, (const int*)sys_e, cur, pmode,
+                        rn.go("cocg_update", k_pupdate<R, 8>, dim3(g_up), dim3(TPB), N, (const int*)sys_e, cur, pmode,
                               (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z, partC, partB, done, sst, inner,
                               outer, o.max_iter, (int*)nxt.list, (int*)nxt.count);
                         rn.go("cocg_p", k_pp<R, 4>, dim3(g_pp), dim3(TPB), N, nxt, (const SysState*)sst, (const cx<R>*)z, pv);
