@@ -125,10 +125,13 @@ typedef struct {
                           the Krylov loop then launches kernels directly instead of as graphs */
     int autotune;      /* 1: on the first solve of a model, time the matvec kernel variants on
                           the batch and keep the fastest (per precision) for later calls       */
+    int resident;      /* 1: FP32 COCG with a point preconditioner runs each inner solve of a
+                          system in one thread block (vectors p, q in shared memory) when
+                          2 N * 8 bytes + tables fit; 0: grid-wide kernels                   */
 } vbk_opts;
 
 /* Fills `o` with defaults: GMRES, VBK_MIXED, Jacobi, restart 64, max_iter 20000,
- * max_refine 40, tol 1e-8, inner_tol 1e-5, check_every 8, timing 0, autotune 1. */
+ * max_refine 40, tol 1e-8, inner_tol 1e-5, check_every 8, timing 0, autotune 1, resident 1. */
 void vbk_default_opts(vbk_opts* o);
 
 typedef struct {

@@ -61,6 +61,7 @@ class vbk_opts(C.Structure):
         ("check_every", C.c_int),
         ("timing", C.c_int),
         ("autotune", C.c_int),
+        ("resident", C.c_int),
     ]
 
 

@@ -579,6 +579,7 @@ void vbk_default_opts(vbk_opts* o) {
     o->check_every = 8;
     o->timing = 0;
     o->autotune = 1;
+    o->resident = 1;
 }
 
 int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {

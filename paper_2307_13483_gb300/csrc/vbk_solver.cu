@@ -1293,6 +1293,198 @@ __global__ void __launch_bounds__(TPB) k_pp(int N, DList L, const SysState* __re
     }
 }
 
+
+// --------------------------------------------------- resident COCG (one CTA per system)
+// The whole inner solve of one system runs in one CTA: p and q live in shared memory (q is
+// overwritten by z = B^-1 r once consumed), x, r and the diagonal table stay in global memory
+// (L2-resident for the systems in flight), and the scalars come from block reductions.  No
+// grid-wide synchronisation is needed because the systems are independent; a converged system
+// frees its SM for the next one.  The iteration count is bounded by max_iter.
+constexpr int RTPB = 1024;
+
+template <int M>
+__global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const int* __restrict__ sys_e,
+                                                          const int* __restrict__ list, int pmode,
+                                                          const float2* __restrict__ diag, float2* __restrict__ x,
+                                                          float2* __restrict__ r, const float2* __restrict__ p0,
+                                                          SysState* __restrict__ st, int* __restrict__ act,
+                                                          int* __restrict__ outer, int max_iter) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = md.N, Nnu = md.Nnu;
+    float2* P = reinterpret_cast<float2*>(smraw);
+    float2* Q = P + N;
+    float* stab = reinterpret_cast<float*>(Q + N);
+    __shared__ float pcoef[MAXS][64];
+    __shared__ int poff[MAXS][64];
+    __shared__ short pcol[MAXS][64][MAXM];
+    __shared__ int npt[MAXS];
+    __shared__ float red[RTPB / 32][3];
+    __shared__ float2 bc[2];  // broadcast: alpha, beta
+    __shared__ int stop;
+    const int s = list[blockIdx.x];
+    const int tid = threadIdx.x;
+    const long long so = (long long)s * N;
+    const float2* dg = diag + (long long)sys_e[s] * N;
+    for (int k = tid; k < md.ntab; k += RTPB) stab[k] = md.tab32[k];
+    for (int d = 0; d < md.ns; ++d) {
+        const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, 64);
+        if (tid == 0) npt[d] = np;
+        for (int k = tid; k < np; k += RTPB) {
+            const DevEntry& e = md.ent[pb + k];
+            pcoef[d][k] = (float)e.coef;
+            poff[d][k] = (e.dp - d) * Nnu + e.lin;
+#pragma unroll
+            for (int m = 0; m < MAXM; ++m) pcol[d][k][m] = (short)e.col[m];
+        }
+    }
+    for (int i = tid; i < N; i += RTPB) P[i] = p0[so + i];
+    double rho_d = 0.0, rho_i = 0.0;
+    if (tid == 0) {
+        rho_d = st[s].rho.x;
+        rho_i = st[s].rho.y;
+    }
+    __syncthreads();
+    const int lane = tid & 31, wid = tid >> 5;
+    auto block_red3 = [&](float a0, float a1, float a2) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_down_sync(0xffffffffu, a0, o);
+            a1 += __shfl_down_sync(0xffffffffu, a1, o);
+            a2 += __shfl_down_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            red[wid][0] = a0;
+            red[wid][1] = a1;
+            red[wid][2] = a2;
+        }
+        __syncthreads();
+    };
+    const int budget = max(0, max_iter - st[s].iters);
+    for (int it = 0; it < budget; ++it) {
+        // q = A p and p^T q
+        float pq_x = 0.f, pq_y = 0.f;
+        for (int i = tid; i < N; i += RTPB) {
+            const int d = i / Nnu, nu = i - d * Nnu;
+            int n[MAXM];
+            decode<M>(md, nu, n);
+            const float2 pi = P[i];
+            float2 acc = cmul<float>(dg[i], pi);
+            const int np = npt[d];
+            for (int k = 0; k < np; ++k) {
+                float c = pcoef[d][k];
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const int col = pcol[d][k][m];
+                    if (col >= 0) c *= stab[col + n[m]];
+                }
+                const float2 v = P[min(max(i + poff[d][k], 0), N - 1)];
+                acc.x = fmaf(-c, v.x, acc.x);
+                acc.y = fmaf(-c, v.y, acc.y);
+            }
+            Q[i] = acc;
+            pq_x += pi.x * acc.x - pi.y * acc.y;
+            pq_y += pi.x * acc.y + pi.y * acc.x;
+        }
+        block_red3(pq_x, pq_y, 0.f);
+        if (tid == 0) {
+            double ax = 0.0, ay = 0.0;
+            for (int w = 0; w < RTPB / 32; ++w) {
+                ax += red[w][0];
+                ay += red[w][1];
+            }
+            const double den = ax * ax + ay * ay;
+            SysState& S = st[s];
+            stop = 0;
+            if (!(den > 0.0) || !isfinite(den)) {
+                S.status = isfinite(den) ? VBK_SYS_BREAKDOWN : VBK_SYS_NAN;
+                act[s] = 0;
+                outer[s] = 0;
+                stop = 1;
+            } else {
+                const double al_x = (rho_d * ax + rho_i * ay) / den, al_y = (rho_i * ax - rho_d * ay) / den;
+                bc[0] = make_float2((float)al_x, (float)al_y);
+            }
+        }
+        __syncthreads();
+        if (stop) break;
+        // x += alpha p, r -= alpha q, z = B^-1 r (into Q), ||r||^2, r^T z
+        const float2 al = bc[0];
+        float rr = 0.f, rz_x = 0.f, rz_y = 0.f;
+        for (int i = tid; i < N; i += RTPB) {
+            const float2 pi = P[i], qi = Q[i];
+            float2 xv = x[so + i];
+            xv.x += al.x * pi.x - al.y * pi.y;
+            xv.y += al.x * pi.y + al.y * pi.x;
+            x[so + i] = xv;
+            float2 rn = r[so + i];
+            rn.x -= al.x * qi.x - al.y * qi.y;
+            rn.y -= al.x * qi.y + al.y * qi.x;
+            r[so + i] = rn;
+            const float2 zi = pmode == 0 ? cdiv<float>(rn, dg[i]) : rn;
+            Q[i] = zi;
+            rr += rn.x * rn.x + rn.y * rn.y;
+            rz_x += rn.x * zi.x - rn.y * zi.y;
+            rz_y += rn.x * zi.y + rn.y * zi.x;
+        }
+        block_red3(rr, rz_x, rz_y);
+        if (tid == 0) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (int w = 0; w < RTPB / 32; ++w) {
+                a0 += red[w][0];
+                a1 += red[w][1];
+                a2 += red[w][2];
+            }
+            SysState& S = st[s];
+            S.iters += 1;
+            S.cycle_iters += 1;
+            const double rn = sqrt(a0);
+            S.inres = rn;
+            const double den = rho_d * rho_d + rho_i * rho_i;
+            stop = 0;
+            if (!isfinite(rn) || !isfinite(a1) || !isfinite(a2) || rn <= S.target || S.iters >= max_iter) {
+                act[s] = 0;  // the FP64 residual decides
+                stop = 1;
+            } else if (!(a1 * a1 + a2 * a2 > 0.0) || !(den > 0.0)) {
+                S.status = VBK_SYS_BREAKDOWN;
+                act[s] = 0;
+                outer[s] = 0;
+                stop = 1;
+            } else {
+                const double bx = (a1 * rho_d + a2 * rho_i) / den, by = (a2 * rho_d - a1 * rho_i) / den;
+                bc[1] = make_float2((float)bx, (float)by);
+                rho_d = a1;
+                rho_i = a2;
+                S.rho = make_double2(a1, a2);
+                S.beta = make_double2(bx, by);
+            }
+        }
+        __syncthreads();
+        if (stop) break;
+        // p = z + beta p
+        const float2 be = bc[1];
+        for (int i = tid; i < N; i += RTPB) {
+            const float2 pi = P[i], zi = Q[i];
+            P[i] = make_float2(zi.x + be.x * pi.x - be.y * pi.y, zi.y + be.x * pi.y + be.y * pi.x);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) act[s] = 0;
+}
+
+// shared memory of the resident kernel: p, q and the oscillator tables (FP32)
+inline size_t resident_smem(const DevModel& md) { return (size_t)2 * md.N * sizeof(float2) + (size_t)md.ntab * sizeof(float) + 16; }
+inline bool resident_ok(const DevModel& md) {
+    if (resident_smem(md) > 220 * 1024) return false;
+    for (int d = 0; d < md.ns; ++d)
+        if (md.ebeg[d + 1] - md.ebeg[d] > 64) return false;
+    return true;
+}
+template <int M> int prepare_resident(const DevModel& md) {
+    const cudaError_t ce =
+        cudaFuncSetAttribute(k_cocg_resident<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)resident_smem(md));
+    return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "resident COCG shared-memory opt-in");
+}
+
 // ---------------------------------------------------------------------------- GMRES
 // Restarted GMRES(m) with right preconditioning (Sec. III.A; Saad & Schultz): Arnoldi
 // A B^-1 V_n = V_{n+1} H_n with classical Gram-Schmidt applied twice (CGS2), the
@@ -1935,6 +2127,13 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
     }
     const bool tune = o.autotune != 0;
+    // FP32 COCG with a point preconditioner and a system small enough for shared memory:
+    // one CTA per system (k_cocg_resident)
+    bool resident = sizeof(R) == 4 && method == VBK_COCG && pspan <= 0 && resident_ok(md) && o.resident != 0;
+    if (resident && prepare_resident<M>(md) != VBK_OK) {
+        cudaGetLastError();
+        resident = false;
+    }
 
     // ---- workspace
     const size_t NN = (size_t)N;
@@ -2162,7 +2361,13 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 };
                 const int K = std::max(1, o.check_every);
                 int k = 0;
-                if (!block) {
+                if (!block && resident) {
+                    // one CTA per system runs the whole inner solve (list = ilist from the outer check)
+                    rn.go_smem("cocg_resident", k_cocg_resident<M>, dim3(n_in), dim3(RTPB), resident_smem(md), md,
+                               (const int*)sys_e, (const int*)ilist, pmode, reinterpret_cast<const float2*>(diagR),
+                               reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), reinterpret_cast<const float2*>(pv),
+                               sst, inner, outer, o.max_iter);
+                } else if (!block) {
                     // persistent iterations: static grids over the device-side lists (A = ilist with
                     // count cnt[0], B = ilist2 with count cnt[1]); K (even) iterations per CUDA graph,
                     // captured once per solve and relaunched until list A is empty.  With timing on,

@@ -72,7 +72,7 @@ def test_host_level_shift_rejects_bad_arguments(lib):
 def test_default_options(lib):
     o = lib.vbk_default_opts()
     assert (o.method, o.precision, o.precond_span, o.restart) == (lib.VBK_GMRES, lib.VBK_MIXED, 0, 64)
-    assert o.tol == 1e-8 and o.inner_tol == 1e-5 and o.check_every == 8 and o.timing == 0 and o.autotune == 1
+    assert o.tol == 1e-8 and o.inner_tol == 1e-5 and o.check_every == 8 and o.timing == 0 and o.autotune == 1 and o.resident == 1
     o2 = lib.vbk_default_opts(method="cocg", precision="fp64", tol=1e-10)
     assert (o2.method, o2.precision, o2.tol) == (lib.VBK_COCG, lib.VBK_FP64, 1e-10)
 

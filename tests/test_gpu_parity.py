@@ -307,14 +307,16 @@ def test_uneven_batch_with_several_initial_states(vbk):
                 assert res <= 1e-9 * 1.05
 
 
-def test_full_size_batched_sampled(vbk):
-    """The 80 x 80 basis (N = 12,800) over 256 energies in (0, 3] eV, in the launch configuration
-    of the benchmark: every system's true residual is checked by the oracle in complex128, and
-    cross sections of sampled energies are compared with sparse-LU solutions."""
+@pytest.mark.parametrize("span,resident", [(0, 1), (0, 0), (0x5, 1)])
+def test_full_size_batched_sampled(vbk, span, resident):
+    """The 80 x 80 basis (N = 12,800) over 256 energies in (0, 3] eV, in the launch configurations
+    of the benchmark (Jacobi: one thread block per system, or grid-wide kernels; M^g): every
+    system's true residual is checked by the oracle in complex128, and cross sections of sampled
+    energies are compared with sparse-LU solutions."""
     spec = w.WORKLOADS["ci2d_batched"]
     desc, eps, vi = spec["model"](), spec["eps"], spec["vi"]
     model = vbk.Model(desc)
-    opts = vbk.vbk_default_opts(method="cocg", precision="mixed", precond_span=0x5, tol=1e-8)
+    opts = vbk.vbk_default_opts(method="cocg", precision="mixed", precond_span=span, tol=1e-8, resident=resident)
     psi, stats = vbk.vbk_solve(model, eps, vi, opts)
     assert all(s["status"] == "converged" for s in stats)
     psi_h = psi.cpu().numpy()
