@@ -192,6 +192,8 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     dm.N = m->N;
     dm.nmu = m->nmu;
     dm.nchan = (int)m->chans.size();
+    for (int k = 0; k < MAXM; ++k) dm.fd_nb[k] = make_fastdiv(k < m->M ? m->nb[k] : 1);
+    dm.fd_nnu = make_fastdiv(m->Nnu);
     for (int k = 0; k < MAXM; ++k) {
         dm.nb[k] = k < m->M ? m->nb[k] : 1;
         dm.stride[k] = k < m->M ? m->stride[k] : 0;
@@ -223,6 +225,7 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         dm.ch_l[c] = m->chans[c].l;
         dm.ch_a[c] = m->chans[c].a;
         dm.ch_b[c] = m->chans[c].b;
+        dm.ch_sb[c] = std::sqrt(m->chans[c].b);
     }
     for (int k = 0; k < MAXCH; ++k) dm.mu_d[k] = mu_d[k];
     // coefficient columns of the stencil points (Sec. III: "all energy factors and square roots can

@@ -72,8 +72,44 @@ struct DevEntry {
     int delta[MAXM];
 };
 
+// Exact unsigned division by an invariant divisor with a multiply and shifts (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", PLDI 1994): for d >= 2,
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
+// n / d = (t + ((n - t) >> 1)) >> (l - 1); d = 1 is the identity.
+struct FastDiv {
+    unsigned m;
+    int l;  // 0: divisor 1
+    int d;
+};
+inline FastDiv make_fastdiv(int d) {
+    FastDiv f;
+    f.d = d;
+    if (d <= 1) {
+        f.m = 0;
+        f.l = 0;
+        return f;
+    }
+    int l = 0;
+    while ((1LL << l) < d) ++l;
+    f.l = l;
+    f.m = (unsigned)((((unsigned long long)1 << 32) * (((unsigned long long)1 << l) - (unsigned long long)d)) /
+                         (unsigned long long)d + 1ULL);
+    return f;
+}
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+    if (f.l == 0) return n;
+#ifdef __CUDA_ARCH__
+    const unsigned t = __umulhi(f.m, n);
+#else
+    const unsigned t = (unsigned)(((unsigned long long)f.m * n) >> 32);
+#endif
+    return (t + ((n - t) >> 1)) >> (f.l - 1);
+}
+
 struct DevModel {
     int ns, M, Nnu, N, nmu, nchan;
+    FastDiv fd_nb[MAXM];  // division by n_basis[m]
+    FastDiv fd_nnu;       // division by Nnu
     int nb[MAXM], stride[MAXM];
     double omega[MAXM];
     int ebeg[MAXS + 1];  // off-diagonal stencil points of output state d: [ebeg[d], ebeg[d+1])
@@ -89,7 +125,7 @@ struct DevModel {
     const double* pc64;
     const float* pc32;
     int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
-    double ch_a[MAXCH], ch_b[MAXCH];
+    double ch_a[MAXCH], ch_b[MAXCH], ch_sb[MAXCH];  // ch_sb = sqrt(b)
     int mu_d[MAXCH];  // discrete state coupled to partial wave mu
 };
 
@@ -203,6 +239,35 @@ __host__ __device__ inline double2 vbk_level_shift_eval(double eps, double a, do
     }
     double im = 0.0;
     if (eps > 0.0) im = -0.5 * a * pow(eps, l + 0.5) * exp(-b * eps);
+    return make_double2(a / (2.0 * PI) * p, im);
+}
+
+// The same transform with one square root: sb = sqrt(b) given, sqrt(b |eps|) = sb sqrt(|eps|).
+__host__ __device__ inline double2 vbk_level_shift_eval_sb(double eps, double a, double b, double sb, int l) {
+    const double PI = 3.14159265358979323846;
+    const double SQRT_PI = 1.7724538509055160;
+    const double sq = sqrt(fabs(eps));
+    double t;
+    if (eps > 0.0)
+        t = 2.0 * SQRT_PI * sq * vbk_dawson(sb * sq);
+    else if (eps < 0.0)
+        t = PI * sq * vbk_erfcx(sb * sq);
+    else
+        t = 0.0;
+    double g = SQRT_PI;  // Gamma(1/2)
+    double bp = sb;      // b^(k+1/2)
+    double p = -g / bp + t;
+    for (int k = 1; k <= l; ++k) {
+        g *= (k - 0.5);
+        bp *= b;
+        p = -g / bp + eps * p;
+    }
+    double im = 0.0;
+    if (eps > 0.0) {
+        double el = sq;  // eps^(l+1/2)
+        for (int k = 0; k < l; ++k) el *= eps;
+        im = -0.5 * a * el * exp(-b * eps);
+    }
     return make_double2(a / (2.0 * PI) * p, im);
 }
 

@@ -93,11 +93,12 @@ template <> __device__ __forceinline__ const float* tabp<float>(const DevModel& 
 template <> __device__ __forceinline__ const double* tabp<double>(const DevModel& md) { return md.tab64; }
 
 template <int M> __device__ __forceinline__ void decode(const DevModel& md, int nu, int (&n)[MAXM]) {
-    int rem = nu;
+    unsigned rem = (unsigned)nu;
 #pragma unroll
     for (int m = M - 1; m >= 0; --m) {
-        n[m] = rem % md.nb[m];
-        rem /= md.nb[m];
+        const unsigned q = fdiv(rem, md.fd_nb[m]);
+        n[m] = (int)(rem - q * (unsigned)md.nb[m]);
+        rem = q;
     }
 #pragma unroll
     for (int m = M; m < MAXM; ++m) n[m] = 0;
@@ -129,11 +130,11 @@ __device__ __forceinline__ bool point_coef(const DevEntry& en, const int (&n)[MA
 // FP32 copy for the inner iterations.
 template <int M>
 __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, double2* __restrict__ d64,
-                             float2* __restrict__ d32) {
+                             float2* __restrict__ d32, float2* __restrict__ dinv32) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nE * md.N) return;
     const int e = (int)(t / md.N), i = (int)(t - (long long)e * md.N);
-    const int d = i / md.Nnu, nu = i - d * md.Nnu;
+    const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * md.Nnu;
     int n[MAXM];
     decode<M>(md, nu, n);
     double en = 0.0;
@@ -149,12 +150,19 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
     }
     for (int c = 0; c < md.nchan; ++c) {
         if (md.ch_d[c] != d) continue;
-        const double2 F = vbk_level_shift_eval(eps, md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+        const double2 F = vbk_level_shift_eval_sb(eps, md.ch_a[c], md.ch_b[c], md.ch_sb[c], md.ch_l[c]);
         re -= F.x;
         im -= F.y;
     }
     d64[t] = make_double2(re, im);
-    if (d32) d32[t] = make_float2((float)re, (float)im);
+    if (d32) {
+        const float2 f = make_float2((float)re, (float)im);
+        d32[t] = f;
+        if (dinv32) {  // 1 / diag in FP32 for the Jacobi step of the FP32 iterations
+            const float den = f.x * f.x + f.y * f.y;
+            dinv32[t] = make_float2(f.x / den, -f.y / den);
+        }
+    }
 }
 
 // Batched matvec y = A x (or y = b - A x): one thread owns one element of one state and applies
@@ -1305,8 +1313,9 @@ constexpr int RTPB = 1024;
 template <int M>
 __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const int* __restrict__ sys_e,
                                                           const int* __restrict__ list, int pmode,
-                                                          const float2* __restrict__ diag, float2* __restrict__ x,
-                                                          float2* __restrict__ r, const float2* __restrict__ p0,
+                                                          const float2* __restrict__ diag, const float2* __restrict__ dinv,
+                                                          float2* __restrict__ x, float2* __restrict__ r,
+                                                          const float2* __restrict__ p0,
                                                           SysState* __restrict__ st, int* __restrict__ act,
                                                           int* __restrict__ outer, int max_iter) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1325,6 +1334,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     const int tid = threadIdx.x;
     const long long so = (long long)s * N;
     const float2* dg = diag + (long long)sys_e[s] * N;
+    const float2* di = dinv + (long long)sys_e[s] * N;
     for (int k = tid; k < md.ntab; k += RTPB) stab[k] = md.tab32[k];
     for (int d = 0; d < md.ns; ++d) {
         const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, 64);
@@ -1364,12 +1374,13 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
         // q = A p and p^T q
         float pq_x = 0.f, pq_y = 0.f;
         for (int i = tid; i < N; i += RTPB) {
-            const int d = i / Nnu, nu = i - d * Nnu;
+            const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * Nnu;
             int n[MAXM];
             decode<M>(md, nu, n);
             const float2 pi = P[i];
             float2 acc = cmul<float>(dg[i], pi);
             const int np = npt[d];
+#pragma unroll 4
             for (int k = 0; k < np; ++k) {
                 float c = pcoef[d][k];
 #pragma unroll
@@ -1420,7 +1431,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
             rn.x -= al.x * qi.x - al.y * qi.y;
             rn.y -= al.x * qi.y + al.y * qi.x;
             r[so + i] = rn;
-            const float2 zi = pmode == 0 ? cdiv<float>(rn, dg[i]) : rn;
+            const float2 zi = pmode == 0 ? cmul<float>(rn, di[i]) : rn;
             Q[i] = zi;
             rr += rn.x * rn.x + rn.y * rn.y;
             rz_x += rn.x * zi.x - rn.y * zi.y;
@@ -2147,6 +2158,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     size_t bytes = 0;
     bytes += carve_size<double2>((size_t)nE * NN);                    // diag64
     bytes += carve_size<cx<R>>(mixed ? (size_t)nE * NN : 1);          // diagR
+    bytes += carve_size<float2>(mixed ? (size_t)nE * NN : 1);         // 1/diag (FP32)
     bytes += carve_size<double2>((size_t)nsys * NN);                  // r64
     bytes += carve_size<SysState>(nsys);
     bytes += 7 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
@@ -2177,6 +2189,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     double2* diag64 = carve<double2>(p, (size_t)nE * NN);
     cx<R>* diagR = carve<cx<R>>(p, mixed ? (size_t)nE * NN : 1);
     if (!mixed) diagR = reinterpret_cast<cx<R>*>(diag64);
+    float2* dinvR = carve<float2>(p, mixed ? (size_t)nE * NN : 1);
+    if (!mixed) dinvR = nullptr;
     double2* r64 = carve<double2>(p, (size_t)nsys * NN);
     SysState* sst = carve<SysState>(p, nsys);
     int* outer = carve<int>(p, nsys);
@@ -2252,7 +2266,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         // energy tables (FP64 + inner-precision copy)
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), md, nE, (const double*)dE,
-              diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr);
+              diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR);
         if (block) {
             rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), md, pbuf.pd, nE,
                   (const cx<R>*)diagR, F, pfail);
@@ -2365,7 +2379,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     // one CTA per system runs the whole inner solve (list = ilist from the outer check)
                     rn.go_smem("cocg_resident", k_cocg_resident<M>, dim3(n_in), dim3(RTPB), resident_smem(md), md,
                                (const int*)sys_e, (const int*)ilist, pmode, reinterpret_cast<const float2*>(diagR),
-                               reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), reinterpret_cast<const float2*>(pv),
+                               (const float2*)dinvR, reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), reinterpret_cast<const float2*>(pv),
                                sst, inner, outer, o.max_iter);
                 } else if (!block) {
                     // persistent iterations: static grids over the device-side lists (A = ilist with
@@ -2767,7 +2781,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
         rc = vbk_cuda_fail(cudaGetLastError(), "operator set-up");
     } else {
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
-              mixed ? d32 : (float2*)nullptr);
+              mixed ? d32 : (float2*)nullptr, (float2*)nullptr);
         const dim3 ge(cdiv_u(N, TPB), (unsigned)nsys);
         if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
         if (op == 0) {
@@ -2905,7 +2919,7 @@ int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* 
         return vbk_cuda_fail(ce, "noalloc: copies into scratch");
     Runner rn{m, st, false, {}, {}};
     rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
-          (float2*)nullptr);
+          (float2*)nullptr, (float2*)nullptr);
     const Sel none{nullptr, nullptr};
     launch_matvec_v<double>(rn, 9, "matvec_fp64", m->dm, (const int*)se, none, (unsigned)nsys, (const double2*)d64, x,
                             (long long)N, y, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
