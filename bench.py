@@ -115,6 +115,11 @@ def kernel_bytes_per_unit(name, N, nmu, c, p_band):
         return (2 * c + (p_band + 1) * c / nmu) * N  # r in, z out, L D L^T factor shared by the waves
     if name == "point_precond":
         return (2 * c + c / nmu) * N
+    if name == "cocg_resident":
+        # one COCG iteration (matvec x in / y out, updates of x, r, p, q, z: (2 + 7) c N) plus the
+        # diagonal and reciprocal tables shared by the n_mu waves; p and q stay in shared memory
+        # and x, r in L2 across iterations, so DRAM traffic is far below this algorithmic figure
+        return (9 * c + 2 * c / nmu) * N
     return None
 
 
