@@ -297,6 +297,7 @@ struct SysState {
     double bnorm;    // ||b|| (FP64)
     double rnorm;    // ||b - A x|| of the last FP64 residual
     double scale;    // ||r|| used to scale the inner right-hand side
+    double inv_scale;  // 1 / scale (computed once per refinement step)
     double target;   // inner stopping threshold relative to the (unit) inner rhs
     double2 rho;     // COCG r^T z
     double2 alpha;

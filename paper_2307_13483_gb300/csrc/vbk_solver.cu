@@ -248,7 +248,10 @@ __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restr
             }
             y[(long long)sy[t] * ys + i] = out;
             if (red == 1) loc[t] = cmul<R>(xi[t], out);
-            else if (red == 2) loc[t] = mkc<R>(cabs2<R>(out), 0);
+            else if (red == 2) {
+                const float ox = (float)out.x, oy = (float)out.y;  // norm for the stopping test: FP32 suffices
+                loc[t] = mkc<R>((R)(ox * ox + oy * oy), 0);
+            }
         }
     }
     if (red) {
@@ -368,7 +371,10 @@ __global__ void __launch_bounds__(TPB) k_matvec3(DevModel md, const int* __restr
             }
             y[(long long)sy[t] * ys + i0 + e] = out;
             if (red == 1) loc[t] = cfma<R>(xi[t][e], out, loc[t]);
-            else if (red == 2) loc[t].x += cabs2<R>(out);
+            else if (red == 2) {
+                const float ox = (float)out.x, oy = (float)out.y;  // norm for the stopping test: FP32 suffices
+                loc[t].x += (R)(ox * ox + oy * oy);
+            }
         }
     }
     if (red) {
@@ -498,7 +504,10 @@ __global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, int W_alloc, 
             }
             y[(long long)sy[t] * ys + i] = out;
             if (red == 1) loc[t] = cfma<R>(xi[t], out, loc[t]);
-            else if (red == 2) loc[t].x += cabs2<R>(out);
+            else if (red == 2) {
+                const float ox = (float)out.x, oy = (float)out.y;  // norm for the stopping test: FP32 suffices
+                loc[t].x += (R)(ox * ox + oy * oy);
+            }
         }
     }
     if (red) {
@@ -794,7 +803,8 @@ __global__ void __launch_bounds__(TPB) k_copy_b(int N, Sel sel, const double2* _
     if (i < N) {
         const double2 v = b[(long long)s * N + i];
         r[(long long)s * N + i] = v;
-        loc.x = v.x * v.x + v.y * v.y;
+        const float fx = (float)v.x, fy = (float)v.y;  // the stopping test needs |b| to ~1e-7 only
+        loc.x = (double)(fx * fx + fy * fy);
     }
     const double2 tot = block_sum2(loc, sh);
     if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
@@ -841,6 +851,7 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
         return;
     }
     S.scale = rn;
+    S.inv_scale = 1.0 / rn;
     S.target = fmax(inner_tol, 0.3 * tol * S.bnorm / rn);
     S.j = 0;
     S.cycle_iters = 0;
@@ -859,9 +870,15 @@ __global__ void __launch_bounds__(TPB) k_inner_rhs(int N, Sel sel, const SysStat
     if (s < 0 || (sel.act && !sel.act[s])) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double inv = 1.0 / st[s].scale;
     const double2 v = r[(long long)s * N + i];
-    out[(long long)s * os + i] = cvt_from_d<R>(make_double2(v.x * inv, v.y * inv));
+    if constexpr (sizeof(R) == 4) {
+        // narrow first, scale in FP32: no FP64 arithmetic per element
+        const float inv = (float)st[s].inv_scale;
+        out[(long long)s * os + i] = make_float2((float)v.x * inv, (float)v.y * inv);
+    } else {
+        const double inv = st[s].inv_scale;
+        out[(long long)s * os + i] = cvt_from_d<R>(make_double2(v.x * inv, v.y * inv));
+    }
 }
 
 // x += ||r|| d (FP64 accumulation of the inner correction)
