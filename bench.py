@@ -123,6 +123,21 @@ def kernel_bytes_per_unit(name, N, nmu, c, p_band):
     return None
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel
+    source changed since the counters were taken."""
+    import hashlib
+
+    rec = (load_json(os.path.join("profiles", "ncu_traffic.json")) or {}).get(kernel)
+    if not rec:
+        return None
+    path = os.path.join(ROOT, rec["source_file"])
+    if not os.path.exists(path) or hashlib.sha1(open(path, "rb").read()).hexdigest() != rec["source_sha1"]:
+        return None
+    scale = {"B": 1, "kB": 1e3, "MB": 1e6}[rec.get("traffic_unit", "B")]
+    return rec["traffic_bytes_per_launch"] * scale
+
+
 def roofline(model_N, nmu, stats, timings, opts, peaks):
     c = 8 if opts.precision == 1 else 16
     units = sum(s["iterations"] for s in stats)
@@ -141,8 +156,9 @@ def roofline(model_N, nmu, stats, timings, opts, peaks):
                 "traffic": None, "peak_source": peak_note}
     total_bytes = bpu * units
     achieved = total_bytes / (ms * 1e-3) / 1e9
+    traffic = measured_traffic(name)
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_note,
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_note,
             "bytes_per_launch": round(total_bytes / launches), "launches": launches,
             "avg_launch_us": round(ms * 1e3 / launches, 2), "share_of_step": None}
 
