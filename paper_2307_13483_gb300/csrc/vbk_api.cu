@@ -1039,10 +1039,11 @@ int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* bp) {
         bp->ent_dc[k] = (int)dc;
         p = std::max<int>(p, (int)std::llabs(dc));
     }
-    if (p > PMAX) {
-        g_last_error = "block preconditioner bandwidth " + std::to_string(p) + " exceeds the supported " + std::to_string(PMAX);
+    if (p > PWMAX) {
+        g_last_error = "block preconditioner bandwidth " + std::to_string(p) + " exceeds the supported " + std::to_string(PWMAX);
         return VBK_ERR_UNSUPPORTED;
     }
     bp->p = p;
+    bp->wide = p > PMAX;
     return VBK_OK;
 }

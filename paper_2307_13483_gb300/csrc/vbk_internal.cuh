@@ -19,7 +19,8 @@
 #define MAXM VBK_MAX_MODES
 #define MAXS VBK_MAX_STATES
 #define MAXCH VBK_MAX_CHANNELS
-#define PMAX 16  // widest band handled by the thread-per-block LDL^T kernels
+#define PMAX 16    // widest band handled by the thread-per-block LDL^T kernels
+#define PWMAX 160  // widest band handled by the cooperative (one CTA / one warp per block) LDL^T kernels
 
 // ------------------------------------------------------------------------------- complex
 template <class R> struct cx_t;
@@ -330,6 +331,7 @@ struct BlockPlan {
     int L = 1;      // chain (block) length
     int nblk = 0;   // blocks per energy
     int p = 0;      // half bandwidth in chain order
+    bool wide = false;  // p > PMAX: cooperative factor and warp-per-block solves
     std::vector<int> ent_dc;  // per off-diagonal stencil point: chain offset (0 = outside block)
 };
 int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* plan);

@@ -538,6 +538,8 @@ struct PlanDev {
     int nrun, runlen, cs_run;
     const int* run_off;
     const int* run_c0;
+    // wide bands (p > PMAX): row stride of the band storage (p + 1 rounded up to 4 entries)
+    int ps;
 };
 
 // B = L D L^T of every block of every energy (Sec. III.B: factors computed once and stored).
@@ -765,6 +767,289 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
         const double2 t = block_sum_c<R>(lrz, sh);
         if (threadIdx.x == 0) part_rz[(long long)s * gridDim.x + blockIdx.x] = t;
     }
+}
+
+// --------------------------------------------------------- wide-band block preconditioner
+// Blocks whose half bandwidth p exceeds PMAX (the states x two-dimensional bend blocks of a
+// CO2-type model: chain length 3 * 20 * 20 with p = 120) are factored by one CTA per block and
+// solved by one warp per (system, block).  The factor is kept twice, as rows and as columns of
+// the band, so that both triangular sweeps stream contiguous rows:
+//   Frow[e][blk][c][o] = L(c, c - o),   Fcol[e][blk][c][o] = L(c + o, c)   (o = 1..p),
+//   Frow[e][blk][c][0] = Fcol[e][blk][c][0] = 1 / D_c,
+// each row padded to ps >= p + 1 entries (a multiple of 4).  Per energy the buffer holds the
+// Frow rows of all blocks followed by the Fcol rows (2 N ps entries).
+constexpr int WF_THREADS = 1024;  // threads of the factor kernel
+constexpr int WF_SLOTS = 13;      // window slots per thread: (PWMAX + 1)(PWMAX + 2) / 2 <= 13 * 1024
+constexpr int WA_WARPS = 4;       // warps (systems) per CTA of the solve kernel
+constexpr int WA_RING = 256;      // ring of pending right-hand-side entries per warp (> PWMAX)
+constexpr int WA_K = (PWMAX + 31) / 32;  // band entries per lane and step
+static_assert((PWMAX + 1) * (PWMAX + 2) / 2 <= WF_SLOTS * WF_THREADS, "factor window does not fit the slots");
+static_assert(WA_RING > PWMAX && (WA_RING & (WA_RING - 1)) == 0, "ring must exceed the band and be a power of two");
+
+template <class R> constexpr int wa_depth() { return sizeof(R) == 4 ? 16 : 8; }  // columns prefetched ahead
+
+// B's band in row storage before factoring: Frow[e][blk][c][o] = B(c, c - o) for o = 0..p, the
+// entries of A(E_e) whose row and column lie in the block (Sec. III.B).  The buffer must be
+// zero beforehand.  One thread per chain position.
+template <class R, int M>
+__global__ void __launch_bounds__(TPB) k_block_band(DevModel md, PlanDev pl, int nE, const cx<R>* __restrict__ diag,
+                                                   cx<R>* __restrict__ Frow) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per_e = (long long)pl.nblk * pl.L;
+    if (t >= (long long)nE * per_e) return;
+    const int e = (int)(t / per_e);
+    const long long rem = t - (long long)e * per_e;
+    const int blk = (int)(rem / pl.L), c = (int)(rem - (long long)blk * pl.L);
+    const int i = pl.fixed_base[blk] + pl.chain_off[c];
+    const int d = i / md.Nnu, nu = i - d * md.Nnu;
+    int n[MAXM];
+    decode<M>(md, nu, n);
+    cx<R>* row = Frow + (long long)e * 2 * pl.nblk * pl.L * pl.ps + ((long long)blk * pl.L + c) * pl.ps;
+    row[0] = diag[(long long)e * md.N + i];
+    const R* tab = tabp<R>(md);
+    for (int k = md.ebeg[d]; k < md.ebeg[d + 1]; ++k) {
+        const int dc = pl.ent_dc[k];
+        if (dc >= 0 || dc < -pl.p || c + dc < 0) continue;
+        R cf;
+        if (point_coef<R, M>(md.ent[k], n, md, tab, cf)) row[-dc].x -= cf;
+    }
+}
+
+// B = L D L^T of one block per CTA (grid: blocks x energies), right-looking over the chain.
+// The active window (rows and columns k..k+p of the partly reduced block, lower triangle)
+// lives in shared memory, packed by diagonals: diagonal o holds the p + 1 - o entries
+// (j + o, j) in a ring indexed by j mod (p + 1 - o).  Step k takes column k out of the
+// window, writes L(k + a, k) = W(k + a, k) / D_k to both band layouts, applies the rank-one
+// update W(k + a, k + b) -= L(k + a, k) D_k L(k + b, k) and lets row k + p + 1 of B enter in
+// the ring positions column k vacated.  Frow holds B's band on entry (k_block_band) and is
+// overwritten in place: row c is read before any L entry of it is written.
+template <class R>
+__global__ void __launch_bounds__(WF_THREADS, 1) k_block_factor_wide(PlanDev pl, cx<R>* __restrict__ F,
+                                                                    int* __restrict__ fail) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int p = pl.p, L = pl.L, ps = pl.ps;
+    const int T = (p + 1) * (p + 2) / 2;
+    cx<R>* W = reinterpret_cast<cx<R>*>(smem_raw);
+    cx<R>* colk = W + T;         // column k of the window (p + 1 entries)
+    cx<R>* lcol = colk + p + 1;  // L(k + a, k), lcol[0] = 1 / D_k
+    __shared__ cx<R> inv_sh;
+    __shared__ int bad_sh;
+    const int e = blockIdx.y, blk = blockIdx.x;
+    cx<R>* Fr = F + (long long)e * 2 * pl.nblk * L * ps + (long long)blk * L * ps;
+    cx<R>* Fc = Fr + (long long)pl.nblk * L * ps;
+    // slot s = threadIdx.x + q * WF_THREADS of the packed window: diagonal o and b = j - k
+    int meta[WF_SLOTS];
+#pragma unroll
+    for (int q = 0; q < WF_SLOTS; ++q) {
+        const int s = threadIdx.x + q * WF_THREADS;
+        meta[q] = -1;
+        if (s < T) {
+            int o = 0, base = 0;
+            while (base + (p + 1 - o) <= s) {
+                base += p + 1 - o;
+                ++o;
+            }
+            const int j = s - base;  // the window starts at k = 0, so b = j
+            meta[q] = o | (j << 16);
+            W[s] = (j + o < L) ? Fr[(long long)(j + o) * ps + o] : mkc<R>(0, 0);
+        }
+    }
+    if (threadIdx.x == 0) bad_sh = 0;
+    __syncthreads();
+    for (int k = 0; k < L; ++k) {
+        // column k leaves the window; row k + p + 1 of B enters in the vacated slots
+#pragma unroll
+        for (int q = 0; q < WF_SLOTS; ++q) {
+            const int mt = meta[q];
+            if (mt >= 0 && (mt >> 16) == 0) {
+                const int s = threadIdx.x + q * WF_THREADS, o = mt & 0xffff;
+                const cx<R> v = W[s];
+                colk[o] = v;
+                const int inew = k + p + 1;
+                W[s] = inew < L ? Fr[(long long)inew * ps + o] : mkc<R>(0, 0);
+                if (o == 0) {
+                    const R a2 = cabs2<R>(v);
+                    cx<R> inv = mkc<R>(0, 0);
+                    if (!(a2 > (R)0) || !isfinite(a2))
+                        bad_sh = 1;
+                    else
+                        inv = mkc<R>(v.x / a2, -v.y / a2);
+                    inv_sh = inv;
+                }
+            }
+        }
+        __syncthreads();
+        const cx<R> inv = inv_sh;
+        for (int a = threadIdx.x; a <= p; a += WF_THREADS) {
+            const cx<R> l = a == 0 ? inv : cmul<R>(colk[a], inv);
+            lcol[a] = l;
+            Fc[(long long)k * ps + a] = l;
+            if (k + a < L) Fr[(long long)(k + a) * ps + a] = l;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < WF_SLOTS; ++q) {
+            const int mt = meta[q];
+            if (mt < 0) continue;
+            const int o = mt & 0xffff, b = mt >> 16;
+            if (b > 0) {
+                const int s = threadIdx.x + q * WF_THREADS;
+                W[s] = csub<R>(W[s], cmul<R>(colk[b + o], lcol[b]));
+                meta[q] = o | ((b - 1) << 16);
+            } else {
+                meta[q] = o | ((p - o) << 16);  // the entering entry (k + p + 1, k + p + 1 - o)
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && bad_sh) atomicExch(fail + e, 1);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <int BYTES> __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// z = B^-1 r for the wide-band blocks: one warp per (system, block), WA_WARPS systems of the
+// selection per CTA (grid: blocks x ceil(n_sel / WA_WARPS)), so that the systems sharing an
+// energy read each band row once from DRAM.  Both sweeps are right-looking: once w_c (z_c) is
+// final, lane l subtracts its multiples from the pending entries c +- o, o = l + 1 + 32 j, kept
+// in a shared-memory ring.  Band rows are streamed DEPTH rows ahead into shared memory with
+// cp.async; right-hand-side entries enter the ring the same way.  Optional partials
+// part[s * nblk + blk] = sum_c w_c^2 / D_c = (r^T z restricted to the block).
+template <class R>
+__global__ void __launch_bounds__(WA_WARPS * 32) k_block_apply_wide(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
+                                                                   int nsel, const cx<R>* __restrict__ F,
+                                                                   const cx<R>* __restrict__ r, long long rs,
+                                                                   cx<R>* __restrict__ z, long long zs,
+                                                                   double2* __restrict__ part) {
+    constexpr int DEPTH = wa_depth<R>();
+    constexpr int CPL = 16 / sizeof(cx<R>);  // entries per 16-byte copy
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int li = blockIdx.y * WA_WARPS + wid;
+    if (li >= nsel) return;  // warp-uniform: the kernel has no CTA-wide barrier
+    const int s = sel.list ? sel.list[li] : li;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
+    const int blk = blockIdx.x, L = pl.L, p = pl.p, ps = pl.ps;
+    cx<R>* wbase = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)wid * (DEPTH * ps + WA_RING);
+    cx<R>* rows = wbase;                 // DEPTH band rows
+    cx<R>* acc = wbase + DEPTH * ps;     // pending entries, position c at acc[c % WA_RING]
+    const int e = sys_e[s];
+    const cx<R>* Fr = F + (long long)e * 2 * pl.nblk * L * ps + (long long)blk * L * ps;
+    const cx<R>* Fc = Fr + (long long)pl.nblk * L * ps;
+    const cx<R>* rv = r + (long long)s * rs;
+    cx<R>* zv = z + (long long)s * zs;
+    const int base = pl.fixed_base[blk];
+    const int nchunk = ps / CPL;  // 16-byte pieces per band row
+    auto fetch_row = [&](const cx<R>* src, int slot) {
+        for (int q = lane; q < nchunk; q += 32) cp_async16(rows + slot * ps + q * CPL, src + q * CPL);
+    };
+    // ---- forward sweep: w = L^-1 r, v = D^-1 w (stored in z)
+    for (int i = lane; i < WA_RING; i += 32) acc[i] = i < L ? rv[base + pl.chain_off[i]] : mkc<R>(0, 0);
+    for (int c = 0; c < DEPTH; ++c) {
+        if (c < L) fetch_row(Fc + (long long)c * ps, c);
+        cp_async_commit();
+    }
+    int off_next = 0;  // chain offset of position c + WA_RING (lane c % 32 holds the next 32)
+    int off_cur = 0;   // chain offset of position c
+    cx<R> rz = mkc<R>(0, 0);
+    for (int c = 0; c < L; ++c) {
+        if ((c & 31) == 0) {
+            off_cur = c + lane < L ? pl.chain_off[c + lane] : 0;
+            off_next = c + WA_RING + lane < L ? pl.chain_off[c + WA_RING + lane] : 0;
+        }
+        const int oc = __shfl_sync(0xffffffffu, off_cur, c & 31);
+        const int on = __shfl_sync(0xffffffffu, off_next, c & 31);
+        cp_async_wait<DEPTH - 1>();
+        __syncwarp();
+        const cx<R>* col = rows + (c % DEPTH) * ps;
+        const cx<R> w = acc[c & (WA_RING - 1)];
+        cx<R> f[WA_K];
+#pragma unroll
+        for (int j = 0; j < WA_K; ++j) {
+            const int o = lane + 1 + 32 * j;
+            f[j] = o <= p ? col[o] : mkc<R>(0, 0);
+        }
+        const cx<R> dinv = col[0];
+        __syncwarp();  // every lane has read column c and acc[c] before they are refilled
+        if (lane == 0) {
+            const cx<R> v = cmul<R>(w, dinv);
+            rz = cfma<R>(w, v, rz);
+            zv[base + oc] = v;
+            if (c + WA_RING < L)
+                cp_async_small<sizeof(cx<R>)>(acc + (c & (WA_RING - 1)), rv + base + on);
+            else
+                acc[c & (WA_RING - 1)] = mkc<R>(0, 0);
+        }
+        if (c + DEPTH < L) fetch_row(Fc + (long long)(c + DEPTH) * ps, c % DEPTH);
+        cp_async_commit();
+#pragma unroll
+        for (int j = 0; j < WA_K; ++j) {
+            const int o = lane + 1 + 32 * j;
+            if (o <= p && c + o < L) {
+                cx<R>& a = acc[(c + o) & (WA_RING - 1)];
+                a = csub<R>(a, cmul<R>(f[j], w));
+            }
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    __threadfence_block();
+    // ---- backward sweep: z = L^-T v
+    for (int i = lane; i < WA_RING; i += 32) {
+        const int c = L - 1 - i;
+        if (c >= 0) acc[c & (WA_RING - 1)] = zv[base + pl.chain_off[c]];
+    }
+    for (int q = 0; q < DEPTH; ++q) {
+        const int c = L - 1 - q;
+        if (c >= 0) fetch_row(Fr + (long long)c * ps, q);
+        cp_async_commit();
+    }
+    for (int c = L - 1, q = 0; c >= 0; --c, ++q) {
+        if ((q & 31) == 0) {
+            off_cur = c - lane >= 0 ? pl.chain_off[c - lane] : 0;
+            off_next = c - WA_RING - lane >= 0 ? pl.chain_off[c - WA_RING - lane] : 0;
+        }
+        const int oc = __shfl_sync(0xffffffffu, off_cur, q & 31);
+        const int on = __shfl_sync(0xffffffffu, off_next, q & 31);
+        cp_async_wait<DEPTH - 1>();
+        __syncwarp();
+        const cx<R>* row = rows + (q % DEPTH) * ps;
+        const cx<R> zc = acc[c & (WA_RING - 1)];
+        cx<R> f[WA_K];
+#pragma unroll
+        for (int j = 0; j < WA_K; ++j) {
+            const int o = lane + 1 + 32 * j;
+            f[j] = o <= p ? row[o] : mkc<R>(0, 0);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            zv[base + oc] = zc;
+            if (c - WA_RING >= 0)
+                cp_async_small<sizeof(cx<R>)>(acc + (c & (WA_RING - 1)), zv + base + on);
+            else
+                acc[c & (WA_RING - 1)] = mkc<R>(0, 0);
+        }
+        if (c - DEPTH >= 0) fetch_row(Fr + (long long)(c - DEPTH) * ps, q % DEPTH);
+        cp_async_commit();
+#pragma unroll
+        for (int j = 0; j < WA_K; ++j) {
+            const int o = lane + 1 + 32 * j;
+            if (o <= p && c - o >= 0) {
+                cx<R>& a = acc[(c - o) & (WA_RING - 1)];
+                a = csub<R>(a, cmul<R>(f[j], zc));
+            }
+        }
+    }
+    cp_async_wait<0>();
+    if (part && lane == 0) part[(long long)s * pl.nblk + blk] = cvt_to_d<R>(rz);
 }
 
 // Point preconditioners: mode 0 -> z = r / diag (Jacobi), mode -1 -> z = r.  Optional r^T z.
@@ -1862,8 +2147,15 @@ struct DevPlanBuf {
     PlanDev pd{};
     void* mem = nullptr;
     bool staged = false;  // chains gathered through shared memory (k_block_staged)
+    bool wide = false;    // p > PMAX: k_block_factor_wide / k_block_apply_wide
     int P = 0;            // register window of the staged kernel (>= p)
 };
+
+// Entries of the factor buffer of one energy: L * (p + 1) * nblk for the narrow kernels, two
+// band copies of N rows of stride ps for the wide ones.
+inline size_t factor_entries(const BlockPlan& bp, size_t N) {
+    return bp.wide ? 2 * N * (size_t)((bp.p + 1 + 3) & ~3) : N * (size_t)(bp.p + 1);
+}
 
 // Host tables of a block plan: element offset of every chain position, base element of
 // every block, and (when the chain contains the fastest mode) its contiguous runs.
@@ -1900,6 +2192,8 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
     out->pd.nblk = bp.nblk;
     out->pd.p = bp.p;
     out->pd.span = span;
+    out->pd.ps = (bp.p + 1 + 3) & ~3;
+    out->wide = bp.wide;
     const bool last_in_chain = (span >> m->M) & 1;
     out->staged = false;
     if (last_in_chain) {
@@ -1912,7 +2206,7 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
         out->pd.nrun = (int)run_c0.size();
         out->pd.cs_run = (span & 1) ? m->ns : 1;
         const size_t tile = (size_t)bp.L * (32 + 1) * 16;  // worst case (FP64)
-        out->staged = tile <= 160 * 1024 && bp.p <= 16;
+        out->staged = tile <= 160 * 1024 && bp.p <= PMAX;
         out->P = bp.p <= 2 ? 2 : bp.p <= 4 ? 4 : bp.p <= 8 ? 8 : 16;
     }
     if (run_c0.empty()) {
@@ -1945,7 +2239,24 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
 }
 
 // Launches the block preconditioner z = B^-1 r (optionally fused with the COCG update).
+template <class R> size_t wide_factor_smem(const PlanDev& pd) {
+    return ((size_t)(pd.p + 1) * (pd.p + 2) / 2 + 2 * (size_t)(pd.p + 1)) * sizeof(cx<R>);
+}
+template <class R> size_t wide_apply_smem(const PlanDev& pd) {
+    return (size_t)WA_WARPS * ((size_t)wa_depth<R>() * pd.ps + WA_RING) * sizeof(cx<R>);
+}
 template <class R> int prepare_staged(const DevPlanBuf& pb) {
+    if (pb.wide) {
+        const size_t f = wide_factor_smem<R>(pb.pd), a = wide_apply_smem<R>(pb.pd);
+        if (f > 227 * 1024 || a > 227 * 1024) {
+            vbk_set_error("block preconditioner band too wide for shared memory in this precision");
+            return VBK_ERR_UNSUPPORTED;
+        }
+        cudaError_t ce = cudaFuncSetAttribute(k_block_factor_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f);
+        if (ce == cudaSuccess)
+            ce = cudaFuncSetAttribute(k_block_apply_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a);
+        return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "wide block preconditioner shared-memory opt-in");
+    }
     if (!pb.staged) return VBK_OK;
     const size_t smem = (size_t)pb.pd.L * (SG + 1) * sizeof(cx<R>);
     if (smem <= 48 * 1024) return VBK_OK;
@@ -1969,6 +2280,7 @@ inline unsigned cdiv_u(long long a, long long b);
 template <class R> int prepare_staged(const DevPlanBuf& pb);
 
 inline int block_partials(const DevPlanBuf& pb) {
+    if (pb.wide) return pb.pd.nblk;
     return pb.staged ? (int)((pb.pd.nblk + 31) / 32) : (int)((pb.pd.nblk + BTPB - 1) / BTPB);
 }
 
@@ -2118,6 +2430,23 @@ void launch_matvec(Runner& rn, const char* name, const DevModel& md, const int* 
 }
 inline int matvec_partials(const DevModel& md, int variant) { return matvec_partials_v(md, variant); }
 
+// L D L^T factors of every block of every energy (Sec. III.B: computed once per energy and
+// stored): thread-per-block kernel for narrow bands, band assembly + one CTA per block for
+// wide ones.
+template <class R, int M>
+void factor_blocks(Runner& rn, const DevModel& md, const DevPlanBuf& pb, int nE, const cx<R>* diag, cx<R>* F, int* fail) {
+    if (!pb.wide) {
+        rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * pb.pd.nblk, 64)), dim3(64), md, pb.pd, nE,
+              diag, F, fail);
+        return;
+    }
+    const size_t per_e = 2 * (size_t)md.N * pb.pd.ps;
+    cudaMemsetAsync(F, 0, (size_t)nE * per_e * sizeof(cx<R>), rn.st);
+    rn.go("block_band", k_block_band<R, M>, dim3(cdiv_u((long long)nE * md.N, TPB)), dim3(TPB), md, pb.pd, nE, diag, F);
+    rn.go_smem("block_factor_wide", k_block_factor_wide<R>, dim3(pb.pd.nblk, nE), dim3(WF_THREADS),
+               wide_factor_smem<R>(pb.pd), pb.pd, F, fail);
+}
+
 template <class R, int M> struct Solver {
     static int run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vbk_stats* stats, cudaStream_t st);
 };
@@ -2180,7 +2509,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     bytes += carve_size<SysState>(nsys);
     bytes += 7 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
     bytes += 3 * carve_size<double2>((size_t)nsys * nslot);           // partial buffers
-    if (block) bytes += carve_size<cx<R>>((size_t)nE * NN * (bp.p + 1));
+    if (block) bytes += carve_size<cx<R>>((size_t)nE * factor_entries(bp, NN));
     if (method == VBK_COCG) {
         bytes += 5 * carve_size<cx<R>>((size_t)nsys * NN);            // x r p q z
     } else {
@@ -2223,7 +2552,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     double2* partA = carve<double2>(p, (size_t)nsys * nslot);
     double2* partB = carve<double2>(p, (size_t)nsys * nslot);
     double2* partC = carve<double2>(p, (size_t)nsys * nslot);
-    cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * NN * (bp.p + 1)) : nullptr;
+    cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * factor_entries(bp, NN)) : nullptr;
     cx<R>*x = nullptr, *r = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr, *V = nullptr, *w = nullptr;
     double2 *H = nullptr, *g = nullptr, *h1 = nullptr, *h2 = nullptr, *yv = nullptr, *sn = nullptr;
     double *cs = nullptr, *invh = nullptr;
@@ -2284,10 +2613,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         // energy tables (FP64 + inner-precision copy)
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), md, nE, (const double*)dE,
               diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR);
-        if (block) {
-            rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), md, pbuf.pd, nE,
-                  (const cx<R>*)diagR, F, pfail);
-        }
+        if (block) factor_blocks<R, M>(rn, md, pbuf, nE, (const cx<R>*)diagR, F, pfail);
         if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) {
             fail(vbk_cuda_fail(ce, "set-up kernels"));
             break;
@@ -2719,6 +3045,12 @@ void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny
         rn.go("cocg_update", k_cocg_update<R>, dim3(cdiv_u(N, TPB), ny), dim3(TPB), N, sel, sst, sys_e, 1,
               (const cx<R>*)nullptr, x, r, p, q, z, part_rr, (double2*)nullptr);
     }
+    if (pb.wide) {
+        if (ny == 0) return;
+        rn.go_smem("block_apply_wide", k_block_apply_wide<R>, dim3(pb.pd.nblk, cdiv_u(ny, WA_WARPS)), dim3(WA_WARPS * 32),
+                   wide_apply_smem<R>(pb.pd), pb.pd, sys_e, sel, (int)ny, F, (const cx<R>*)r, rs, z, zs, part_rz);
+        return;
+    }
     rn.go("block_apply", k_block_apply<R>, dim3((pb.pd.nblk + BTPB - 1) / BTPB, ny), dim3(BTPB), pb.pd, sys_e, sel, F,
           (const cx<R>*)r, rs, z, zs, part_rz);
 }
@@ -2765,7 +3097,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     }
     size_t bytes = carve_size<double2>((size_t)nE * N) + carve_size<float2>(mixed ? (size_t)nE * N : 1) +
                    2 * carve_size<cx<R>>(mixed ? (size_t)nsys * N : 1) + carve_size<int>(nsys) + carve_size<double>(nE) +
-                   carve_size<int>(nE) + (block ? carve_size<cx<R>>((size_t)nE * N * (bp.p + 1)) : 0);
+                   carve_size<int>(nE) + (block ? carve_size<cx<R>>((size_t)nE * factor_entries(bp, N)) : 0);
     char* base = nullptr;
     if (vbk_alloc(m, (void**)&base, bytes, st) != cudaSuccess) {
         if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
@@ -2781,7 +3113,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     int* se = carve<int>(p, nsys);
     double* dE = carve<double>(p, nE);
     int* pfail = carve<int>(p, nE);
-    cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * N * (bp.p + 1)) : nullptr;
+    cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * factor_entries(bp, N)) : nullptr;
     if (!mixed) {
         xr = reinterpret_cast<cx<R>*>(const_cast<double2*>(x));
         yr = reinterpret_cast<cx<R>*>(y);
@@ -2806,8 +3138,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
                                 yr, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0,
                                 variant >= 0 ? variant : m->mv_variant[sizeof(R) == 4 ? 0 : 1]);
         } else if (block) {
-            rn.go("block_factor", k_block_factor<R, M>, dim3(cdiv_u((long long)nE * bp.nblk, 64)), dim3(64), m->dm, pbuf.pd, nE,
-                  diagR, F, pfail);
+            factor_blocks<R, M>(rn, m->dm, pbuf, nE, diagR, F, pfail);
             block_precond<R>(rn, pbuf, N, none, (unsigned)nsys, (const int*)se, (const cx<R>*)F, (const SysState*)nullptr, 0,
                              nullptr, xr, (long long)N, nullptr, nullptr, yr, (long long)N, nullptr, nullptr);
         } else {
