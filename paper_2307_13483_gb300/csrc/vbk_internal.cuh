@@ -300,6 +300,7 @@ struct SysState {
     double scale;    // ||r|| used to scale the inner right-hand side
     double inv_scale;  // 1 / scale (computed once per refinement step)
     double target;   // inner stopping threshold relative to the (unit) inner rhs
+    double pscale;   // scale of the previous inner solve (0: none yet)
     double2 rho;     // COCG r^T z
     double2 alpha;
     double2 beta;

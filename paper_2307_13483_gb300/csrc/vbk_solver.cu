@@ -780,13 +780,15 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
 // Frow rows of all blocks followed by the Fcol rows (2 N ps entries).
 constexpr int WF_THREADS = 1024;  // threads of the factor kernel
 constexpr int WF_SLOTS = 13;      // window slots per thread: (PWMAX + 1)(PWMAX + 2) / 2 <= 13 * 1024
-constexpr int WA_WARPS = 4;       // warps (systems) per CTA of the solve kernel
+constexpr int WA_WARPS = 2;       // warps (systems) per CTA of the solve kernel
+constexpr int WA_PB = 8;          // chain positions per panel of the solve kernel
 constexpr int WA_RING = 256;      // ring of pending right-hand-side entries per warp (> PWMAX)
-constexpr int WA_K = (PWMAX + 31) / 32;  // band entries per lane and step
 static_assert((PWMAX + 1) * (PWMAX + 2) / 2 <= WF_SLOTS * WF_THREADS, "factor window does not fit the slots");
-static_assert(WA_RING > PWMAX && (WA_RING & (WA_RING - 1)) == 0, "ring must exceed the band and be a power of two");
+// A refilled ring slot must not be touched by a panel update (which covers 32 KP positions
+// past the panel) before the copy that refills it has been waited for, NP panels later.
+static_assert(WA_RING >= (3 + 1) * WA_PB + 32 * ((PWMAX + 31) / 32) - 1 && (WA_RING & (WA_RING - 1)) == 0,
+              "pending ring too small for the band, the panel and the prefetch distance");
 
-template <class R> constexpr int wa_depth() { return sizeof(R) == 4 ? 16 : 8; }  // columns prefetched ahead
 
 // B's band in row storage before factoring: Frow[e][blk][c][o] = B(c, c - o) for o = 0..p, the
 // entries of A(E_e) whose row and column lie in the block (Sec. III.B).  The buffer must be
@@ -917,139 +919,161 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // z = B^-1 r for the wide-band blocks: one warp per (system, block), WA_WARPS systems of the
-// selection per CTA (grid: blocks x ceil(n_sel / WA_WARPS)), so that the systems sharing an
-// energy read each band row once from DRAM.  Both sweeps are right-looking: once w_c (z_c) is
-// final, lane l subtracts its multiples from the pending entries c +- o, o = l + 1 + 32 j, kept
-// in a shared-memory ring.  Band rows are streamed DEPTH rows ahead into shared memory with
-// cp.async; right-hand-side entries enter the ring the same way.  Optional partials
-// part[s * nblk + blk] = sum_c w_c^2 / D_c = (r^T z restricted to the block).
-template <class R>
+// selection per CTA (grid: blocks x ceil(n_sel / WA_WARPS)); systems sharing an energy read
+// the same band rows, which L2 then serves once from DRAM.  Both triangular sweeps walk the
+// chain in panels of WA_PB positions: the panel's own WA_PB x WA_PB triangle is solved by
+// lanes 0..WA_PB-1 with shuffles, then every lane subtracts the panel's contribution from
+// the pending entries it owns (positions panel end + lane + 32 m), WA_PB band rows at a time.
+// Pending entries live in a shared-memory ring of WA_RING positions.  Band rows stream into a
+// per-warp ring of NP panels with cp.async, NP - 1 panels ahead; right-hand-side entries
+// enter the pending ring the same way.  Shared-memory rows are padded with zeros to
+// 32 KP + WA_PB entries, so the panel update needs no band-edge tests.  Optional partials
+// part[s * nblk + blk] = sum_c w_c^2 / D_c (r^T z restricted to the block, w = L^-1 r).
+template <class R> constexpr int wa_np() { return sizeof(R) == 4 ? 3 : 2; }
+__host__ __device__ constexpr int wa_pss(int kp) { return 32 * kp + WA_PB; }
+
+template <class R, int KP>
 __global__ void __launch_bounds__(WA_WARPS * 32) k_block_apply_wide(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
                                                                    int nsel, const cx<R>* __restrict__ F,
                                                                    const cx<R>* __restrict__ r, long long rs,
                                                                    cx<R>* __restrict__ z, long long zs,
                                                                    double2* __restrict__ part) {
-    constexpr int DEPTH = wa_depth<R>();
+    constexpr int NP = wa_np<R>(), PB = WA_PB, PSS = wa_pss(KP), RM = WA_RING - 1;
     constexpr int CPL = 16 / sizeof(cx<R>);  // entries per 16-byte copy
+    constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int li = blockIdx.y * WA_WARPS + wid;
     if (li >= nsel) return;  // warp-uniform: the kernel has no CTA-wide barrier
     const int s = sel.list ? sel.list[li] : li;
     if (s < 0 || (sel.act && !sel.act[s])) return;
-    const int blk = blockIdx.x, L = pl.L, p = pl.p, ps = pl.ps;
-    cx<R>* wbase = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)wid * (DEPTH * ps + WA_RING);
-    cx<R>* rows = wbase;                 // DEPTH band rows
-    cx<R>* acc = wbase + DEPTH * ps;     // pending entries, position c at acc[c % WA_RING]
+    const int blk = blockIdx.x, L = pl.L, ps = pl.ps;
+    cx<R>* rows = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)wid * (NP * PB * PSS + WA_RING);
+    cx<R>* acc = rows + NP * PB * PSS;
     const int e = sys_e[s];
     const cx<R>* Fr = F + (long long)e * 2 * pl.nblk * L * ps + (long long)blk * L * ps;
     const cx<R>* Fc = Fr + (long long)pl.nblk * L * ps;
     const cx<R>* rv = r + (long long)s * rs;
     cx<R>* zv = z + (long long)s * zs;
     const int base = pl.fixed_base[blk];
-    const int nchunk = ps / CPL;  // 16-byte pieces per band row
-    auto fetch_row = [&](const cx<R>* src, int slot) {
-        for (int q = lane; q < nchunk; q += 32) cp_async16(rows + slot * ps + q * CPL, src + q * CPL);
+    const int nchunk = ps / CPL;
+    const int npan = (L + PB - 1) / PB;
+    for (int i = lane; i < NP * PB * PSS; i += 32) rows[i] = mkc<R>(0, 0);
+    __syncwarp();
+    // band rows of panel k into ring slot k % NP; dir = +1: Fcol rows k PB + i, dir = -1: Frow
+    // rows L - 1 - k PB - i
+    auto fetch_panel = [&](const cx<R>* Fb, int k, int dir) {
+        cx<R>* dst = rows + (k % NP) * PB * PSS;
+        for (int i = 0; i < PB; ++i) {
+            const int row = dir > 0 ? k * PB + i : L - 1 - k * PB - i;
+            if (row < 0 || row >= L) break;
+            const cx<R>* src = Fb + (long long)row * ps;
+            for (int q = lane; q < nchunk; q += 32) cp_async16(dst + i * PSS + q * CPL, src + q * CPL);
+        }
     };
-    // ---- forward sweep: w = L^-1 r, v = D^-1 w (stored in z)
+    cx<R> rz = mkc<R>(0, 0);
+    // ---- forward sweep: w = L^-1 r (panels ascending), v = D^-1 w stored in z
     for (int i = lane; i < WA_RING; i += 32) acc[i] = i < L ? rv[base + pl.chain_off[i]] : mkc<R>(0, 0);
-    for (int c = 0; c < DEPTH; ++c) {
-        if (c < L) fetch_row(Fc + (long long)c * ps, c);
+    for (int k = 0; k < NP; ++k) {
+        if (k < npan) fetch_panel(Fc, k, 1);
         cp_async_commit();
     }
-    int off_next = 0;  // chain offset of position c + WA_RING (lane c % 32 holds the next 32)
-    int off_cur = 0;   // chain offset of position c
-    cx<R> rz = mkc<R>(0, 0);
-    for (int c = 0; c < L; ++c) {
-        if ((c & 31) == 0) {
-            off_cur = c + lane < L ? pl.chain_off[c + lane] : 0;
-            off_next = c + WA_RING + lane < L ? pl.chain_off[c + WA_RING + lane] : 0;
-        }
-        const int oc = __shfl_sync(0xffffffffu, off_cur, c & 31);
-        const int on = __shfl_sync(0xffffffffu, off_next, c & 31);
-        cp_async_wait<DEPTH - 1>();
+    for (int k = 0; k < npan; ++k) {
+        const int c0 = k * PB, np = min(PB, L - c0);
+        const cx<R>* prow = rows + (k % NP) * PB * PSS;
+        const int off_c = lane < np ? pl.chain_off[c0 + lane] : 0;
+        const bool refill = lane < PB && c0 + lane + WA_RING < L;
+        const int off_r = refill ? pl.chain_off[c0 + lane + WA_RING] : 0;
+        cp_async_wait<NP - 1>();
         __syncwarp();
-        const cx<R>* col = rows + (c % DEPTH) * ps;
-        const cx<R> w = acc[c & (WA_RING - 1)];
-        cx<R> f[WA_K];
+        cx<R> val = lane < np ? acc[(c0 + lane) & RM] : mkc<R>(0, 0);
+        cx<R> wj[PB];
 #pragma unroll
-        for (int j = 0; j < WA_K; ++j) {
-            const int o = lane + 1 + 32 * j;
-            f[j] = o <= p ? col[o] : mkc<R>(0, 0);
+        for (int j = 0; j < PB; ++j) {
+            wj[j].x = __shfl_sync(FULL, val.x, j);
+            wj[j].y = __shfl_sync(FULL, val.y, j);
+            if (lane > j && lane < np) val = csub<R>(val, cmul<R>(prow[j * PSS + lane - j], wj[j]));
         }
-        const cx<R> dinv = col[0];
-        __syncwarp();  // every lane has read column c and acc[c] before they are refilled
-        if (lane == 0) {
-            const cx<R> v = cmul<R>(w, dinv);
-            rz = cfma<R>(w, v, rz);
-            zv[base + oc] = v;
-            if (c + WA_RING < L)
-                cp_async_small<sizeof(cx<R>)>(acc + (c & (WA_RING - 1)), rv + base + on);
+        if (lane < np) {
+            const cx<R> v = cmul<R>(val, prow[lane * PSS]);
+            rz = cfma<R>(val, v, rz);
+            zv[base + off_c] = v;
+        }
+        if (lane < PB) {  // position c0 + lane is final: its ring slot takes position c0 + lane + WA_RING
+            if (refill)
+                cp_async_small<sizeof(cx<R>)>(acc + ((c0 + lane) & RM), rv + base + off_r);
             else
-                acc[c & (WA_RING - 1)] = mkc<R>(0, 0);
+                acc[(c0 + lane) & RM] = mkc<R>(0, 0);
         }
-        if (c + DEPTH < L) fetch_row(Fc + (long long)(c + DEPTH) * ps, c % DEPTH);
-        cp_async_commit();
 #pragma unroll
-        for (int j = 0; j < WA_K; ++j) {
-            const int o = lane + 1 + 32 * j;
-            if (o <= p && c + o < L) {
-                cx<R>& a = acc[(c + o) & (WA_RING - 1)];
-                a = csub<R>(a, cmul<R>(f[j], w));
+        for (int m = 0; m < KP; ++m) {
+            const int t = lane + 32 * m;
+            cx<R> sum = mkc<R>(0, 0);
+#pragma unroll
+            for (int j = 0; j < PB; ++j) sum = cfma<R>(prow[j * PSS + PB + t - j], wj[j], sum);
+            if (c0 + PB + t < L) {
+                cx<R>& a = acc[(c0 + PB + t) & RM];
+                a = csub<R>(a, sum);
             }
         }
+        __syncwarp();  // every lane is done with the panel's rows
+        if (k + NP < npan) fetch_panel(Fc, k + NP, 1);
+        cp_async_commit();
     }
     cp_async_wait<0>();
     __syncwarp();
-    __threadfence_block();
-    // ---- backward sweep: z = L^-T v
+    // ---- backward sweep: z = L^-T v (panels descending)
     for (int i = lane; i < WA_RING; i += 32) {
         const int c = L - 1 - i;
-        if (c >= 0) acc[c & (WA_RING - 1)] = zv[base + pl.chain_off[c]];
+        if (c >= 0) acc[c & RM] = zv[base + pl.chain_off[c]];
     }
-    for (int q = 0; q < DEPTH; ++q) {
-        const int c = L - 1 - q;
-        if (c >= 0) fetch_row(Fr + (long long)c * ps, q);
+    for (int k = 0; k < NP; ++k) {
+        if (k < npan) fetch_panel(Fr, k, -1);
         cp_async_commit();
     }
-    for (int c = L - 1, q = 0; c >= 0; --c, ++q) {
-        if ((q & 31) == 0) {
-            off_cur = c - lane >= 0 ? pl.chain_off[c - lane] : 0;
-            off_next = c - WA_RING - lane >= 0 ? pl.chain_off[c - WA_RING - lane] : 0;
-        }
-        const int oc = __shfl_sync(0xffffffffu, off_cur, q & 31);
-        const int on = __shfl_sync(0xffffffffu, off_next, q & 31);
-        cp_async_wait<DEPTH - 1>();
+    for (int k = 0; k < npan; ++k) {
+        const int c1 = L - 1 - k * PB, np = min(PB, c1 + 1);
+        const cx<R>* prow = rows + (k % NP) * PB * PSS;
+        const int off_c = lane < np ? pl.chain_off[c1 - lane] : 0;
+        const bool refill = lane < PB && c1 - lane - WA_RING >= 0;
+        const int off_r = refill ? pl.chain_off[c1 - lane - WA_RING] : 0;
+        cp_async_wait<NP - 1>();
         __syncwarp();
-        const cx<R>* row = rows + (q % DEPTH) * ps;
-        const cx<R> zc = acc[c & (WA_RING - 1)];
-        cx<R> f[WA_K];
+        cx<R> val = lane < np ? acc[(c1 - lane) & RM] : mkc<R>(0, 0);
+        cx<R> zj[PB];
 #pragma unroll
-        for (int j = 0; j < WA_K; ++j) {
-            const int o = lane + 1 + 32 * j;
-            f[j] = o <= p ? row[o] : mkc<R>(0, 0);
+        for (int j = 0; j < PB; ++j) {
+            zj[j].x = __shfl_sync(FULL, val.x, j);
+            zj[j].y = __shfl_sync(FULL, val.y, j);
+            if (lane > j && lane < np) val = csub<R>(val, cmul<R>(prow[j * PSS + lane - j], zj[j]));
         }
-        __syncwarp();
-        if (lane == 0) {
-            zv[base + oc] = zc;
-            if (c - WA_RING >= 0)
-                cp_async_small<sizeof(cx<R>)>(acc + (c & (WA_RING - 1)), zv + base + on);
+        if (lane < np) zv[base + off_c] = val;
+        if (lane < PB) {
+            if (refill)
+                cp_async_small<sizeof(cx<R>)>(acc + ((c1 - lane) & RM), zv + base + off_r);
             else
-                acc[c & (WA_RING - 1)] = mkc<R>(0, 0);
+                acc[(c1 - lane) & RM] = mkc<R>(0, 0);
         }
-        if (c - DEPTH >= 0) fetch_row(Fr + (long long)(c - DEPTH) * ps, q % DEPTH);
-        cp_async_commit();
 #pragma unroll
-        for (int j = 0; j < WA_K; ++j) {
-            const int o = lane + 1 + 32 * j;
-            if (o <= p && c - o >= 0) {
-                cx<R>& a = acc[(c - o) & (WA_RING - 1)];
-                a = csub<R>(a, cmul<R>(f[j], zc));
+        for (int m = 0; m < KP; ++m) {
+            const int t = lane + 32 * m;
+            cx<R> sum = mkc<R>(0, 0);
+#pragma unroll
+            for (int j = 0; j < PB; ++j) sum = cfma<R>(prow[j * PSS + PB + t - j], zj[j], sum);
+            if (c1 - PB - t >= 0) {
+                cx<R>& a = acc[(c1 - PB - t) & RM];
+                a = csub<R>(a, sum);
             }
         }
+        __syncwarp();
+        if (k + NP < npan) fetch_panel(Fr, k + NP, -1);
+        cp_async_commit();
     }
     cp_async_wait<0>();
-    if (part && lane == 0) part[(long long)s * pl.nblk + blk] = cvt_to_d<R>(rz);
+    if (part) {
+        rz = warp_sum_c<R>(rz);
+        if (lane == 0) part[(long long)s * pl.nblk + blk] = cvt_to_d<R>(rz);
+    }
 }
 
 // Point preconditioners: mode 0 -> z = r / diag (Jacobi), mode -1 -> z = r.  Optional r^T z.
@@ -1135,6 +1159,7 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
         outer[s] = 0;
         return;
     }
+    S.pscale = S.scale;
     S.scale = rn;
     S.inv_scale = 1.0 / rn;
     S.target = fmax(inner_tol, 0.3 * tol * S.bnorm / rn);
@@ -1186,8 +1211,13 @@ __global__ void __launch_bounds__(TPB) k_accumulate(int N, Sel sel, const SysSta
 // Two-term preconditioned COCG (Sec. III.A; van der Vorst & Melissen):
 //   q = A p; alpha = rho / p^T q; x += alpha p; r -= alpha q; z = B^-1 r; rho' = r^T z;
 //   beta = rho'/rho; p = z + beta p.
+// rho = r^T z of a new inner solve.  With `cont` the search direction of the previous inner
+// solve carries over (a reliable update: the recursive residual has just been replaced by the
+// true FP64 residual): p = z + gamma p_old with gamma = (rho / rho_old) (scale / scale_old),
+// the COCG beta of the unscaled recurrences expressed in the new inner scale; gamma = 0 starts
+// afresh (p = z).
 __global__ void k_cocg_start(int nsys, SysState* __restrict__ st, const int* __restrict__ act,
-                             const double2* __restrict__ part_rz, int nb) {
+                             const double2* __restrict__ part_rz, int nb, int cont) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys || !act[s]) return;
     double2 rz = make_double2(0.0, 0.0);
@@ -1195,8 +1225,18 @@ __global__ void k_cocg_start(int nsys, SysState* __restrict__ st, const int* __r
         rz.x += part_rz[(long long)s * nb + k].x;
         rz.y += part_rz[(long long)s * nb + k].y;
     }
-    st[s].rho = rz;
-    st[s].beta = make_double2(0.0, 0.0);
+    SysState& S = st[s];
+    double2 g = make_double2(0.0, 0.0);
+    const double den = S.rho.x * S.rho.x + S.rho.y * S.rho.y;
+    if (cont && S.pscale > 0.0 && den > 0.0 && isfinite(den)) {
+        g = cdiv<double>(rz, S.rho);
+        const double f = S.scale / S.pscale;
+        g.x *= f;
+        g.y *= f;
+        if (!isfinite(g.x) || !isfinite(g.y)) g = make_double2(0.0, 0.0);
+    }
+    S.rho = rz;
+    S.beta = g;
 }
 
 // per-system scalars: one warp per system sums its partials (lanes strided, then shuffles)
@@ -2239,11 +2279,20 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
 }
 
 // Launches the block preconditioner z = B^-1 r (optionally fused with the COCG update).
+template <class R> cudaError_t wide_apply_attr(int kp, int smem) {
+    switch (kp) {
+        case 1: return cudaFuncSetAttribute(k_block_apply_wide<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 2: return cudaFuncSetAttribute(k_block_apply_wide<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 3: return cudaFuncSetAttribute(k_block_apply_wide<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 4: return cudaFuncSetAttribute(k_block_apply_wide<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        default: return cudaFuncSetAttribute(k_block_apply_wide<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+}
 template <class R> size_t wide_factor_smem(const PlanDev& pd) {
     return ((size_t)(pd.p + 1) * (pd.p + 2) / 2 + 2 * (size_t)(pd.p + 1)) * sizeof(cx<R>);
 }
 template <class R> size_t wide_apply_smem(const PlanDev& pd) {
-    return (size_t)WA_WARPS * ((size_t)wa_depth<R>() * pd.ps + WA_RING) * sizeof(cx<R>);
+    return (size_t)WA_WARPS * ((size_t)wa_np<R>() * WA_PB * wa_pss((pd.p + 31) / 32) + WA_RING) * sizeof(cx<R>);
 }
 template <class R> int prepare_staged(const DevPlanBuf& pb) {
     if (pb.wide) {
@@ -2254,7 +2303,7 @@ template <class R> int prepare_staged(const DevPlanBuf& pb) {
         }
         cudaError_t ce = cudaFuncSetAttribute(k_block_factor_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f);
         if (ce == cudaSuccess)
-            ce = cudaFuncSetAttribute(k_block_apply_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a);
+            ce = wide_apply_attr<R>((pb.pd.p + 31) / 32, (int)a);
         return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "wide block preconditioner shared-memory opt-in");
     }
     if (!pb.staged) return VBK_OK;
@@ -2677,14 +2726,23 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             const Sel so2{olist, outer};
 
             if (method == VBK_COCG) {
-                // r = rhs, x = 0, z = B^-1 r, p = z, rho = r^T z
+                // r = rhs, x = 0, z = B^-1 r, p = z, rho = r^T z.  With a block preconditioner the
+                // search direction carries over from the previous inner solve (k_cocg_start):
+                // hard problems (thousands of iterations) then keep their Krylov progress across
+                // the FP64 residual refreshes instead of restarting.
                 rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst,
                       (const double2*)r64, r, (long long)N);
                 cudaMemsetAsync(x, 0, (size_t)nsys * NN * sizeof(cx<R>), st);
                 precond(si, n_in, r, N, z, N, partB);
                 rn.go("cocg_start", k_cocg_start, dim3(gs), dim3(128), nsys, sst, (const int*)inner, (const double2*)partB,
-                      nb_rz);
-                cudaMemcpyAsync(pv, z, (size_t)nsys * NN * sizeof(cx<R>), cudaMemcpyDeviceToDevice, st);
+                      nb_rz, block ? 1 : 0);
+                if (block) {
+                    if (it == 0) cudaMemsetAsync(pv, 0, (size_t)nsys * NN * sizeof(cx<R>), st);
+                    rn.go("cocg_p", k_cocg_p<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst, (const cx<R>*)z,
+                          pv);
+                } else {
+                    cudaMemcpyAsync(pv, z, (size_t)nsys * NN * sizeof(cx<R>), cudaMemcpyDeviceToDevice, st);
+                }
                 if (tune && mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0) {
                     if (int trc = tune_matvec<R>(rn, mdl, (const int*)sys_e, si, n_in, (const cx<R>*)diagR, (const cx<R>*)pv,
                                                  (long long)N, q, (long long)N, (const double2*)nullptr, partA, 1)) {
@@ -3047,8 +3105,19 @@ void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny
     }
     if (pb.wide) {
         if (ny == 0) return;
-        rn.go_smem("block_apply_wide", k_block_apply_wide<R>, dim3(pb.pd.nblk, cdiv_u(ny, WA_WARPS)), dim3(WA_WARPS * 32),
-                   wide_apply_smem<R>(pb.pd), pb.pd, sys_e, sel, (int)ny, F, (const cx<R>*)r, rs, z, zs, part_rz);
+        const dim3 g(pb.pd.nblk, cdiv_u(ny, WA_WARPS));
+        const size_t smem = wide_apply_smem<R>(pb.pd);
+        auto launch = [&](auto kern) {
+            rn.go_smem("block_apply_wide", kern, g, dim3(WA_WARPS * 32), smem, pb.pd, sys_e, sel, (int)ny, F,
+                       (const cx<R>*)r, rs, z, zs, part_rz);
+        };
+        switch ((pb.pd.p + 31) / 32) {
+            case 1: launch(k_block_apply_wide<R, 1>); break;
+            case 2: launch(k_block_apply_wide<R, 2>); break;
+            case 3: launch(k_block_apply_wide<R, 3>); break;
+            case 4: launch(k_block_apply_wide<R, 4>); break;
+            default: launch(k_block_apply_wide<R, 5>); break;
+        }
         return;
     }
     rn.go("block_apply", k_block_apply<R>, dim3((pb.pd.nblk + BTPB - 1) / BTPB, ny), dim3(BTPB), pb.pd, sys_e, sel, F,
