@@ -1045,5 +1045,9 @@ int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* bp) {
     }
     bp->p = p;
     bp->wide = p > PMAX;
+    if (bp->wide) {
+        bp->S = 4 * ((p + 7) / 8);  // levels of S >= p / 2 chain positions: block pentadiagonal
+        bp->K = (bp->L + bp->S - 1) / bp->S;
+    }
     return VBK_OK;
 }

@@ -332,7 +332,8 @@ struct BlockPlan {
     int L = 1;      // chain (block) length
     int nblk = 0;   // blocks per energy
     int p = 0;      // half bandwidth in chain order
-    bool wide = false;  // p > PMAX: cooperative factor and warp-per-block solves
+    bool wide = false;  // p > PMAX: level-blocked factor (levels of S chain positions, K levels)
+    int S = 0, K = 0;
     std::vector<int> ent_dc;  // per off-diagonal stencil point: chain offset (0 = outside block)
 };
 int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* plan);

@@ -538,8 +538,8 @@ struct PlanDev {
     int nrun, runlen, cs_run;
     const int* run_off;
     const int* run_c0;
-    // wide bands (p > PMAX): row stride of the band storage (p + 1 rounded up to 4 entries)
-    int ps;
+    // wide bands (p > PMAX): level size and level count of the block-pentadiagonal form
+    int S, K;
 };
 
 // B = L D L^T of every block of every energy (Sec. III.B: factors computed once and stored).
@@ -770,309 +770,287 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
 }
 
 // --------------------------------------------------------- wide-band block preconditioner
-// Blocks whose half bandwidth p exceeds PMAX (the states x two-dimensional bend blocks of a
-// CO2-type model: chain length 3 * 20 * 20 with p = 120) are factored by one CTA per block and
-// solved by one warp per (system, block).  The factor is kept twice, as rows and as columns of
-// the band, so that both triangular sweeps stream contiguous rows:
-//   Frow[e][blk][c][o] = L(c, c - o),   Fcol[e][blk][c][o] = L(c + o, c)   (o = 1..p),
-//   Frow[e][blk][c][0] = Fcol[e][blk][c][0] = 1 / D_c,
-// each row padded to ps >= p + 1 entries (a multiple of 4).  Per energy the buffer holds the
-// Frow rows of all blocks followed by the Fcol rows (2 N ps entries).
-constexpr int WF_THREADS = 1024;  // threads of the factor kernel
-constexpr int WF_SLOTS = 13;      // window slots per thread: (PWMAX + 1)(PWMAX + 2) / 2 <= 13 * 1024
-constexpr int WA_WARPS = 2;       // warps (systems) per CTA of the solve kernel
-constexpr int WA_PB = 8;          // chain positions per panel of the solve kernel
-constexpr int WA_RING = 256;      // ring of pending right-hand-side entries per warp (> PWMAX)
-static_assert((PWMAX + 1) * (PWMAX + 2) / 2 <= WF_SLOTS * WF_THREADS, "factor window does not fit the slots");
-// A refilled ring slot must not be touched by a panel update (which covers 32 KP positions
-// past the panel) before the copy that refills it has been waited for, NP panels later.
-static_assert(WA_RING >= (3 + 1) * WA_PB + 32 * ((PWMAX + 31) / 32) - 1 && (WA_RING & (WA_RING - 1)) == 0,
-              "pending ring too small for the band, the panel and the prefetch distance");
+// Blocks whose chain half bandwidth p exceeds PMAX (the states x two-dimensional bend blocks of
+// a CO2-type model: 3 * 20 * 20 = 1200 unknowns with p = 120) are factored in LEVELS of S
+// consecutive chain positions, S = 4 ceil(p / 8) >= p / 2, so that B is block pentadiagonal
+// with S x S blocks: B = L D L^T with L unit block-lower (blocks L_{k+1,k}, L_{k+2,k}) and D
+// block diagonal (dense complex symmetric S x S).  The last level is padded with identity
+// rows.  Per energy and block the factor holds, for every level k, five S x S blocks:
+//   [0] D_k^-1 stored transposed, [1], [2] Lf_j = L_{k,k-j}^T, [3], [4] Lb_j = L_{k+j,k}
+// (all row-major), so that thread i of a solve reads column i of each (coalesced).  Both
+// triangular sweeps are then dense block products, K = ceil(L / S) sequential steps instead
+// of L scalar ones.  After the factors, each energy holds a workspace of 9 S x S blocks per
+// block (the Schur-complement window during the factorization).
+constexpr int LF_THREADS = 256;  // threads of the level factorization
+constexpr int LV_SMAX = 80;      // largest level (p <= 160 = PWMAX)
+static_assert(4 * ((PWMAX + 7) / 8) <= LV_SMAX, "PWMAX needs a larger level size");
 
+__host__ __device__ inline int level_size(int p) { return 4 * ((p + 7) / 8); }
+__host__ __device__ inline long long level_factor_entries(int nblk, int K, int S) {
+    return (long long)nblk * S * S * (5LL * K + 9);
+}
 
-// B's band in row storage before factoring: Frow[e][blk][c][o] = B(c, c - o) for o = 0..p, the
-// entries of A(E_e) whose row and column lie in the block (Sec. III.B).  The buffer must be
-// zero beforehand.  One thread per chain position.
+// Rows of level a of B (chain positions a S .. a S + S - 1) into the window blocks W(a, a),
+// W(a, a - 1), W(a, a - 2) (those with a - j >= 0): Wslot(a, b) = W + ((a % 3) * 3 + b % 3) S^2.
 template <class R, int M>
-__global__ void __launch_bounds__(TPB) k_block_band(DevModel md, PlanDev pl, int nE, const cx<R>* __restrict__ diag,
-                                                   cx<R>* __restrict__ Frow) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long per_e = (long long)pl.nblk * pl.L;
-    if (t >= (long long)nE * per_e) return;
-    const int e = (int)(t / per_e);
-    const long long rem = t - (long long)e * per_e;
-    const int blk = (int)(rem / pl.L), c = (int)(rem - (long long)blk * pl.L);
-    const int i = pl.fixed_base[blk] + pl.chain_off[c];
-    const int d = i / md.Nnu, nu = i - d * md.Nnu;
-    int n[MAXM];
-    decode<M>(md, nu, n);
-    cx<R>* row = Frow + (long long)e * 2 * pl.nblk * pl.L * pl.ps + ((long long)blk * pl.L + c) * pl.ps;
-    row[0] = diag[(long long)e * md.N + i];
+__device__ void level_assemble(const DevModel& md, const PlanDev& pl, int e, int blk, int a, const cx<R>* __restrict__ diag,
+                               cx<R>* __restrict__ W) {
+    const int S = pl.S, L = pl.L;
+    const long long S2 = (long long)S * S;
+    for (int j = 0; j <= 2 && a - j >= 0; ++j) {
+        cx<R>* Wb = W + ((a % 3) * 3 + (a - j) % 3) * S2;
+        for (long long t = threadIdx.x; t < S2; t += blockDim.x) Wb[t] = mkc<R>(0, 0);
+    }
+    __syncthreads();
     const R* tab = tabp<R>(md);
-    for (int k = md.ebeg[d]; k < md.ebeg[d + 1]; ++k) {
-        const int dc = pl.ent_dc[k];
-        if (dc >= 0 || dc < -pl.p || c + dc < 0) continue;
-        R cf;
-        if (point_coef<R, M>(md.ent[k], n, md, tab, cf)) row[-dc].x -= cf;
+    for (int r = threadIdx.x; r < S; r += blockDim.x) {
+        const int c = a * S + r;
+        cx<R>* Waa = W + ((a % 3) * 3 + a % 3) * S2;
+        if (c >= L) {  // padding: identity
+            Waa[(long long)r * S + r] = mkc<R>(1, 0);
+            continue;
+        }
+        const int i = pl.fixed_base[blk] + pl.chain_off[c];
+        const int d = i / md.Nnu, nu = i - d * md.Nnu;
+        int n[MAXM];
+        decode<M>(md, nu, n);
+        Waa[(long long)r * S + r] = diag[(long long)e * md.N + i];
+        for (int k = md.ebeg[d]; k < md.ebeg[d + 1]; ++k) {
+            const int dc = pl.ent_dc[k];
+            if (dc == 0) continue;
+            const int cp = c + dc;
+            if (cp < 0 || cp >= L) continue;
+            const int b = cp / S;
+            if (b < a - 2 || b > a) continue;
+            R cf;
+            if (point_coef<R, M>(md.ent[k], n, md, tab, cf)) {
+                cx<R>& dst = W[((a % 3) * 3 + b % 3) * S2 + (long long)r * S + (cp - b * S)];
+                dst.x -= cf;
+            }
+        }
     }
 }
 
-// B = L D L^T of one block per CTA (grid: blocks x energies), right-looking over the chain.
-// The active window (rows and columns k..k+p of the partly reduced block, lower triangle)
-// lives in shared memory, packed by diagonals: diagonal o holds the p + 1 - o entries
-// (j + o, j) in a ring indexed by j mod (p + 1 - o).  Step k takes column k out of the
-// window, writes L(k + a, k) = W(k + a, k) / D_k to both band layouts, applies the rank-one
-// update W(k + a, k + b) -= L(k + a, k) D_k L(k + b, k) and lets row k + p + 1 of B enter in
-// the ring positions column k vacated.  Frow holds B's band on entry (k_block_band) and is
-// overwritten in place: row c is read before any L entry of it is written.
-template <class R>
-__global__ void __launch_bounds__(WF_THREADS, 1) k_block_factor_wide(PlanDev pl, cx<R>* __restrict__ F,
-                                                                    int* __restrict__ fail) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int p = pl.p, L = pl.L, ps = pl.ps;
-    const int T = (p + 1) * (p + 2) / 2;
-    cx<R>* W = reinterpret_cast<cx<R>*>(smem_raw);
-    cx<R>* colk = W + T;         // column k of the window (p + 1 entries)
-    cx<R>* lcol = colk + p + 1;  // L(k + a, k), lcol[0] = 1 / D_k
-    __shared__ cx<R> inv_sh;
-    __shared__ int bad_sh;
-    const int e = blockIdx.y, blk = blockIdx.x;
-    cx<R>* Fr = F + (long long)e * 2 * pl.nblk * L * ps + (long long)blk * L * ps;
-    cx<R>* Fc = Fr + (long long)pl.nblk * L * ps;
-    // slot s = threadIdx.x + q * WF_THREADS of the packed window: diagonal o and b = j - k
-    int meta[WF_SLOTS];
-#pragma unroll
-    for (int q = 0; q < WF_SLOTS; ++q) {
-        const int s = threadIdx.x + q * WF_THREADS;
-        meta[q] = -1;
-        if (s < T) {
-            int o = 0, base = 0;
-            while (base + (p + 1 - o) <= s) {
-                base += p + 1 - o;
-                ++o;
-            }
-            const int j = s - base;  // the window starts at k = 0, so b = j
-            meta[q] = o | (j << 16);
-            W[s] = (j + o < L) ? Fr[(long long)(j + o) * ps + o] : mkc<R>(0, 0);
+// C = X Y for S x S matrices in shared memory (row-major), 2 x 2 output tiles per thread;
+// `emit(r, c, v)` receives every entry of C.
+template <class R, class Emit>
+__device__ __forceinline__ void level_gemm(int S, const cx<R>* X, const cx<R>* Y, Emit emit) {
+    const int nt = S / 2;
+    for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) {
+        const int r0 = (t / nt) * 2, c0 = (t % nt) * 2;
+        cx<R> a00 = mkc<R>(0, 0), a01 = a00, a10 = a00, a11 = a00;
+        for (int m = 0; m < S; ++m) {
+            const cx<R> x0 = X[r0 * S + m], x1 = X[(r0 + 1) * S + m];
+            const cx<R> y0 = Y[m * S + c0], y1 = Y[m * S + c0 + 1];
+            a00 = cfma<R>(x0, y0, a00);
+            a01 = cfma<R>(x0, y1, a01);
+            a10 = cfma<R>(x1, y0, a10);
+            a11 = cfma<R>(x1, y1, a11);
         }
+        emit(r0, c0, a00);
+        emit(r0, c0 + 1, a01);
+        emit(r0 + 1, c0, a10);
+        emit(r0 + 1, c0 + 1, a11);
     }
+}
+
+// Block L D L^T of one preconditioner block per CTA (grid: blocks x energies), right-looking
+// over levels (Sec. III.B: the factors are computed once per energy and stored):
+//   D_k^-1 by Gauss-Jordan elimination with partial pivoting,
+//   L_{k+j,k} = W(k+j, k) D_k^-1 (j = 1, 2),
+//   W(k+i, k+j) -= L_{k+i,k} W(k+j, k)^T (1 <= j <= i <= 2),
+// then the rows of level k + 3 enter the window.  A zero pivot sets fail[e].
+template <class R, int M>
+__global__ void __launch_bounds__(LF_THREADS) k_level_factor(DevModel md, PlanDev pl, const cx<R>* __restrict__ diag,
+                                                            cx<R>* __restrict__ F, int* __restrict__ fail) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<R>* sm = reinterpret_cast<cx<R>*>(smem_raw);  // 2 S^2 entries
+    __shared__ int piv_sh, bad_sh;
+    __shared__ cx<R> pinv_sh;
+    const int S = pl.S, K = pl.K, blk = blockIdx.x, e = blockIdx.y;
+    const long long S2 = (long long)S * S;
+    cx<R>* Fe = F + (long long)e * level_factor_entries(pl.nblk, K, S);
+    cx<R>* Out = Fe + (long long)blk * K * 5 * S2;
+    cx<R>* W = Fe + (long long)pl.nblk * K * 5 * S2 + (long long)blk * 9 * S2;
+    auto slot = [&](int a, int b) { return W + ((a % 3) * 3 + b % 3) * S2; };
+    auto out = [&](int k, int part) { return Out + ((long long)k * 5 + part) * S2; };
     if (threadIdx.x == 0) bad_sh = 0;
-    __syncthreads();
-    for (int k = 0; k < L; ++k) {
-        // column k leaves the window; row k + p + 1 of B enters in the vacated slots
+    for (int a = 0; a < 3 && a < K; ++a) level_assemble<R, M>(md, pl, e, blk, a, diag, W);
+    for (int k = 0; k < K; ++k) {
+        __syncthreads();
+        // ---- D_k^-1: [D | I] -> [I | D^-1] in shared memory (row stride 2 S)
+        cx<R>* aug = sm;
+        const cx<R>* D = slot(k, k);
+        for (long long t = threadIdx.x; t < 2 * S2; t += blockDim.x) {
+            const int r = (int)(t / (2 * S)), c = (int)(t - (long long)r * 2 * S);
+            aug[t] = c < S ? D[(long long)r * S + c] : mkc<R>(c - S == r ? 1 : 0, 0);
+        }
+        __syncthreads();
+        for (int m = 0; m < S; ++m) {
+            if (threadIdx.x < 32) {
+                R best = (R)-1;
+                int bi = m;
+                for (int r = m + threadIdx.x; r < S; r += 32) {
+                    const R v = cabs2<R>(aug[(long long)r * 2 * S + m]);
+                    if (v > best) {
+                        best = v;
+                        bi = r;
+                    }
+                }
 #pragma unroll
-        for (int q = 0; q < WF_SLOTS; ++q) {
-            const int mt = meta[q];
-            if (mt >= 0 && (mt >> 16) == 0) {
-                const int s = threadIdx.x + q * WF_THREADS, o = mt & 0xffff;
-                const cx<R> v = W[s];
-                colk[o] = v;
-                const int inew = k + p + 1;
-                W[s] = inew < L ? Fr[(long long)inew * ps + o] : mkc<R>(0, 0);
-                if (o == 0) {
-                    const R a2 = cabs2<R>(v);
-                    cx<R> inv = mkc<R>(0, 0);
-                    if (!(a2 > (R)0) || !isfinite(a2))
+                for (int o = 16; o > 0; o >>= 1) {
+                    const R ob = __shfl_down_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    piv_sh = bi;
+                    const cx<R> pv = aug[(long long)bi * 2 * S + m];
+                    const R a2 = cabs2<R>(pv);
+                    if (!(a2 > (R)0) || !isfinite(a2)) {
                         bad_sh = 1;
-                    else
-                        inv = mkc<R>(v.x / a2, -v.y / a2);
-                    inv_sh = inv;
+                        pinv_sh = mkc<R>(0, 0);
+                    } else {
+                        pinv_sh = mkc<R>(pv.x / a2, -pv.y / a2);
+                    }
                 }
             }
-        }
-        __syncthreads();
-        const cx<R> inv = inv_sh;
-        for (int a = threadIdx.x; a <= p; a += WF_THREADS) {
-            const cx<R> l = a == 0 ? inv : cmul<R>(colk[a], inv);
-            lcol[a] = l;
-            Fc[(long long)k * ps + a] = l;
-            if (k + a < L) Fr[(long long)(k + a) * ps + a] = l;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < WF_SLOTS; ++q) {
-            const int mt = meta[q];
-            if (mt < 0) continue;
-            const int o = mt & 0xffff, b = mt >> 16;
-            if (b > 0) {
-                const int s = threadIdx.x + q * WF_THREADS;
-                W[s] = csub<R>(W[s], cmul<R>(colk[b + o], lcol[b]));
-                meta[q] = o | ((b - 1) << 16);
-            } else {
-                meta[q] = o | ((p - o) << 16);  // the entering entry (k + p + 1, k + p + 1 - o)
+            __syncthreads();
+            const int pr = piv_sh;
+            const cx<R> pinv = pinv_sh;
+            for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
+                const cx<R> vp = aug[(long long)pr * 2 * S + c];
+                if (pr != m) aug[(long long)pr * 2 * S + c] = aug[(long long)m * 2 * S + c];
+                aug[(long long)m * 2 * S + c] = cmul<R>(vp, pinv);
             }
+            __syncthreads();
+            const int w = 2 * S - m - 1;  // columns m + 1 .. 2 S - 1
+            for (long long t = threadIdx.x; t < (long long)S * w; t += blockDim.x) {
+                const int r = (int)(t / w), c = m + 1 + (int)(t - (long long)r * w);
+                if (r == m) continue;
+                const cx<R> f = aug[(long long)r * 2 * S + m];
+                aug[(long long)r * 2 * S + c] = csub<R>(aug[(long long)r * 2 * S + c], cmul<R>(f, aug[(long long)m * 2 * S + c]));
+            }
+            __syncthreads();
+        }
+        cx<R>* Dt = out(k, 0);
+        for (long long t = threadIdx.x; t < S2; t += blockDim.x) {
+            const int r = (int)(t / S), c = (int)(t - (long long)r * S);
+            Dt[(long long)c * S + r] = aug[(long long)r * 2 * S + S + c];  // transposed
         }
         __syncthreads();
+        if (k + 3 < K) level_assemble<R, M>(md, pl, e, blk, k + 3, diag, W);
+        // ---- L_{k+j,k} = W(k+j, k) D^-1
+        cx<R>* X = sm;
+        cx<R>* Y = sm + S2;
+        for (int j = 1; j <= 2 && k + j < K; ++j) {
+            __syncthreads();
+            const cx<R>* A = slot(k + j, k);
+            for (long long t = threadIdx.x; t < S2; t += blockDim.x) {
+                const int r = (int)(t / S), c = (int)(t - (long long)r * S);
+                X[t] = A[t];
+                Y[t] = Dt[(long long)c * S + r];
+            }
+            __syncthreads();
+            cx<R>* Lb = out(k, 2 + j);
+            cx<R>* Lf = out(k + j, j);
+            level_gemm<R>(S, X, Y, [&](int r, int c, cx<R> v) {
+                Lb[(long long)r * S + c] = v;
+                Lf[(long long)c * S + r] = v;
+            });
+        }
+        // ---- Schur complements W(k+i, k+j) -= L_{k+i,k} W(k+j, k)^T
+        for (int i = 1; i <= 2 && k + i < K; ++i)
+            for (int j = 1; j <= i; ++j) {
+                __syncthreads();
+                const cx<R>* A = out(k, 2 + i);
+                const cx<R>* B = slot(k + j, k);
+                for (long long t = threadIdx.x; t < S2; t += blockDim.x) {
+                    const int r = (int)(t / S), c = (int)(t - (long long)r * S);
+                    X[t] = A[t];
+                    Y[(long long)c * S + r] = B[t];
+                }
+                __syncthreads();
+                cx<R>* C = slot(k + i, k + j);
+                level_gemm<R>(S, X, Y, [&](int r, int c, cx<R> v) {
+                    C[(long long)r * S + c] = csub<R>(C[(long long)r * S + c], v);
+                });
+            }
     }
+    __syncthreads();
     if (threadIdx.x == 0 && bad_sh) atomicExch(fail + e, 1);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-template <int BYTES> __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// z = B^-1 r for the wide-band blocks: one warp per (system, block), WA_WARPS systems of the
-// selection per CTA (grid: blocks x ceil(n_sel / WA_WARPS)); systems sharing an energy read
-// the same band rows, which L2 then serves once from DRAM.  Both triangular sweeps walk the
-// chain in panels of WA_PB positions: the panel's own WA_PB x WA_PB triangle is solved by
-// lanes 0..WA_PB-1 with shuffles, then every lane subtracts the panel's contribution from
-// the pending entries it owns (positions panel end + lane + 32 m), WA_PB band rows at a time.
-// Pending entries live in a shared-memory ring of WA_RING positions.  Band rows stream into a
-// per-warp ring of NP panels with cp.async, NP - 1 panels ahead; right-hand-side entries
-// enter the pending ring the same way.  Shared-memory rows are padded with zeros to
-// 32 KP + WA_PB entries, so the panel update needs no band-edge tests.  Optional partials
-// part[s * nblk + blk] = sum_c w_c^2 / D_c (r^T z restricted to the block, w = L^-1 r).
-template <class R> constexpr int wa_np() { return sizeof(R) == 4 ? 3 : 2; }
-__host__ __device__ constexpr int wa_pss(int kp) { return 32 * kp + WA_PB; }
-
-template <class R, int KP>
-__global__ void __launch_bounds__(WA_WARPS * 32) k_block_apply_wide(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
-                                                                   int nsel, const cx<R>* __restrict__ F,
-                                                                   const cx<R>* __restrict__ r, long long rs,
-                                                                   cx<R>* __restrict__ z, long long zs,
-                                                                   double2* __restrict__ part) {
-    constexpr int NP = wa_np<R>(), PB = WA_PB, PSS = wa_pss(KP), RM = WA_RING - 1;
-    constexpr int CPL = 16 / sizeof(cx<R>);  // entries per 16-byte copy
-    constexpr unsigned FULL = 0xffffffffu;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int li = blockIdx.y * WA_WARPS + wid;
-    if (li >= nsel) return;  // warp-uniform: the kernel has no CTA-wide barrier
-    const int s = sel.list ? sel.list[li] : li;
+// z = B^-1 r for the level-blocked factors: one CTA per (block, selected system), thread i < S
+// owns row i of every level.  Forward: w_k = r_k - sum_j L_{k,k-j} w_{k-j}, u_k = D_k^-1 w_k
+// (stored in z); backward: z_k = u_k - sum_j L_{k+j,k}^T z_{k+j}.  Optional partials
+// part[s * nblk + blk] = sum_k w_k^T u_k (= r^T z restricted to the block).
+template <class R>
+__global__ void __launch_bounds__(96) k_level_apply(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
+                                                   const cx<R>* __restrict__ F, const cx<R>* __restrict__ r, long long rs,
+                                                   cx<R>* __restrict__ z, long long zs, double2* __restrict__ part) {
+    __shared__ cx<R> ring[3][LV_SMAX];
+    __shared__ cx<R> sh[32];
+    const int s = sel_sys(sel);
     if (s < 0 || (sel.act && !sel.act[s])) return;
-    const int blk = blockIdx.x, L = pl.L, ps = pl.ps;
-    cx<R>* rows = reinterpret_cast<cx<R>*>(smem_raw) + (size_t)wid * (NP * PB * PSS + WA_RING);
-    cx<R>* acc = rows + NP * PB * PSS;
+    const int S = pl.S, K = pl.K, L = pl.L, blk = blockIdx.x, i = threadIdx.x;
+    const long long S2 = (long long)S * S;
     const int e = sys_e[s];
-    const cx<R>* Fr = F + (long long)e * 2 * pl.nblk * L * ps + (long long)blk * L * ps;
-    const cx<R>* Fc = Fr + (long long)pl.nblk * L * ps;
+    const cx<R>* Out = F + (long long)e * level_factor_entries(pl.nblk, K, S) + (long long)blk * K * 5 * S2;
     const cx<R>* rv = r + (long long)s * rs;
     cx<R>* zv = z + (long long)s * zs;
     const int base = pl.fixed_base[blk];
-    const int nchunk = ps / CPL;
-    const int npan = (L + PB - 1) / PB;
-    for (int i = lane; i < NP * PB * PSS; i += 32) rows[i] = mkc<R>(0, 0);
-    __syncwarp();
-    // band rows of panel k into ring slot k % NP; dir = +1: Fcol rows k PB + i, dir = -1: Frow
-    // rows L - 1 - k PB - i
-    auto fetch_panel = [&](const cx<R>* Fb, int k, int dir) {
-        cx<R>* dst = rows + (k % NP) * PB * PSS;
-        for (int i = 0; i < PB; ++i) {
-            const int row = dir > 0 ? k * PB + i : L - 1 - k * PB - i;
-            if (row < 0 || row >= L) break;
-            const cx<R>* src = Fb + (long long)row * ps;
-            for (int q = lane; q < nchunk; q += 32) cp_async16(dst + i * PSS + q * CPL, src + q * CPL);
-        }
-    };
+    const bool row = i < S;
     cx<R> rz = mkc<R>(0, 0);
-    // ---- forward sweep: w = L^-1 r (panels ascending), v = D^-1 w stored in z
-    for (int i = lane; i < WA_RING; i += 32) acc[i] = i < L ? rv[base + pl.chain_off[i]] : mkc<R>(0, 0);
-    for (int k = 0; k < NP; ++k) {
-        if (k < npan) fetch_panel(Fc, k, 1);
-        cp_async_commit();
-    }
-    for (int k = 0; k < npan; ++k) {
-        const int c0 = k * PB, np = min(PB, L - c0);
-        const cx<R>* prow = rows + (k % NP) * PB * PSS;
-        const int off_c = lane < np ? pl.chain_off[c0 + lane] : 0;
-        const bool refill = lane < PB && c0 + lane + WA_RING < L;
-        const int off_r = refill ? pl.chain_off[c0 + lane + WA_RING] : 0;
-        cp_async_wait<NP - 1>();
-        __syncwarp();
-        cx<R> val = lane < np ? acc[(c0 + lane) & RM] : mkc<R>(0, 0);
-        cx<R> wj[PB];
-#pragma unroll
-        for (int j = 0; j < PB; ++j) {
-            wj[j].x = __shfl_sync(FULL, val.x, j);
-            wj[j].y = __shfl_sync(FULL, val.y, j);
-            if (lane > j && lane < np) val = csub<R>(val, cmul<R>(prow[j * PSS + lane - j], wj[j]));
-        }
-        if (lane < np) {
-            const cx<R> v = cmul<R>(val, prow[lane * PSS]);
-            rz = cfma<R>(val, v, rz);
-            zv[base + off_c] = v;
-        }
-        if (lane < PB) {  // position c0 + lane is final: its ring slot takes position c0 + lane + WA_RING
-            if (refill)
-                cp_async_small<sizeof(cx<R>)>(acc + ((c0 + lane) & RM), rv + base + off_r);
-            else
-                acc[(c0 + lane) & RM] = mkc<R>(0, 0);
-        }
-#pragma unroll
-        for (int m = 0; m < KP; ++m) {
-            const int t = lane + 32 * m;
-            cx<R> sum = mkc<R>(0, 0);
-#pragma unroll
-            for (int j = 0; j < PB; ++j) sum = cfma<R>(prow[j * PSS + PB + t - j], wj[j], sum);
-            if (c0 + PB + t < L) {
-                cx<R>& a = acc[(c0 + PB + t) & RM];
-                a = csub<R>(a, sum);
+    for (int k = 0; k < K; ++k) {
+        const int c = k * S + i;
+        const bool valid = row && c < L;
+        const int el = valid ? base + pl.chain_off[c] : 0;
+        cx<R> acc = valid ? rv[el] : mkc<R>(0, 0);
+        if (row) {
+            for (int j = 1; j <= 2 && k - j >= 0; ++j) {
+                const cx<R>* Lf = Out + ((long long)k * 5 + j) * S2 + i;
+                const cx<R>* wv = ring[(k - j) % 3];
+#pragma unroll 4
+                for (int m = 0; m < S; ++m) acc = csub<R>(acc, cmul<R>(Lf[(long long)m * S], wv[m]));
             }
+            ring[k % 3][i] = acc;
         }
-        __syncwarp();  // every lane is done with the panel's rows
-        if (k + NP < npan) fetch_panel(Fc, k + NP, 1);
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    __syncwarp();
-    // ---- backward sweep: z = L^-T v (panels descending)
-    for (int i = lane; i < WA_RING; i += 32) {
-        const int c = L - 1 - i;
-        if (c >= 0) acc[c & RM] = zv[base + pl.chain_off[c]];
-    }
-    for (int k = 0; k < NP; ++k) {
-        if (k < npan) fetch_panel(Fr, k, -1);
-        cp_async_commit();
-    }
-    for (int k = 0; k < npan; ++k) {
-        const int c1 = L - 1 - k * PB, np = min(PB, c1 + 1);
-        const cx<R>* prow = rows + (k % NP) * PB * PSS;
-        const int off_c = lane < np ? pl.chain_off[c1 - lane] : 0;
-        const bool refill = lane < PB && c1 - lane - WA_RING >= 0;
-        const int off_r = refill ? pl.chain_off[c1 - lane - WA_RING] : 0;
-        cp_async_wait<NP - 1>();
-        __syncwarp();
-        cx<R> val = lane < np ? acc[(c1 - lane) & RM] : mkc<R>(0, 0);
-        cx<R> zj[PB];
-#pragma unroll
-        for (int j = 0; j < PB; ++j) {
-            zj[j].x = __shfl_sync(FULL, val.x, j);
-            zj[j].y = __shfl_sync(FULL, val.y, j);
-            if (lane > j && lane < np) val = csub<R>(val, cmul<R>(prow[j * PSS + lane - j], zj[j]));
+        __syncthreads();
+        if (row) {
+            const cx<R>* Dt = Out + (long long)k * 5 * S2 + i;
+            const cx<R>* wv = ring[k % 3];
+            cx<R> u = mkc<R>(0, 0);
+#pragma unroll 4
+            for (int m = 0; m < S; ++m) u = cfma<R>(Dt[(long long)m * S], wv[m], u);
+            rz = cfma<R>(acc, u, rz);
+            if (valid) zv[el] = u;
         }
-        if (lane < np) zv[base + off_c] = val;
-        if (lane < PB) {
-            if (refill)
-                cp_async_small<sizeof(cx<R>)>(acc + ((c1 - lane) & RM), zv + base + off_r);
-            else
-                acc[(c1 - lane) & RM] = mkc<R>(0, 0);
-        }
-#pragma unroll
-        for (int m = 0; m < KP; ++m) {
-            const int t = lane + 32 * m;
-            cx<R> sum = mkc<R>(0, 0);
-#pragma unroll
-            for (int j = 0; j < PB; ++j) sum = cfma<R>(prow[j * PSS + PB + t - j], zj[j], sum);
-            if (c1 - PB - t >= 0) {
-                cx<R>& a = acc[(c1 - PB - t) & RM];
-                a = csub<R>(a, sum);
+    }
+    __syncthreads();
+    for (int k = K - 1; k >= 0; --k) {
+        const int c = k * S + i;
+        const bool valid = row && c < L;
+        const int el = valid ? base + pl.chain_off[c] : 0;
+        cx<R> acc = valid ? zv[el] : mkc<R>(0, 0);
+        if (row) {
+            for (int j = 1; j <= 2 && k + j < K; ++j) {
+                const cx<R>* Lb = Out + ((long long)k * 5 + 2 + j) * S2 + i;
+                const cx<R>* zr = ring[(k + j) % 3];
+#pragma unroll 4
+                for (int m = 0; m < S; ++m) acc = csub<R>(acc, cmul<R>(Lb[(long long)m * S], zr[m]));
             }
+            ring[k % 3][i] = acc;
+            if (valid) zv[el] = acc;
         }
-        __syncwarp();
-        if (k + NP < npan) fetch_panel(Fr, k + NP, -1);
-        cp_async_commit();
+        __syncthreads();
     }
-    cp_async_wait<0>();
     if (part) {
-        rz = warp_sum_c<R>(rz);
-        if (lane == 0) part[(long long)s * pl.nblk + blk] = cvt_to_d<R>(rz);
+        const double2 tot = block_sum_c<R>(rz, sh);
+        if (threadIdx.x == 0) part[(long long)s * pl.nblk + blk] = tot;
     }
 }
 
@@ -2187,14 +2165,14 @@ struct DevPlanBuf {
     PlanDev pd{};
     void* mem = nullptr;
     bool staged = false;  // chains gathered through shared memory (k_block_staged)
-    bool wide = false;    // p > PMAX: k_block_factor_wide / k_block_apply_wide
+    bool wide = false;    // p > PMAX: k_level_factor / k_level_apply
     int P = 0;            // register window of the staged kernel (>= p)
 };
 
-// Entries of the factor buffer of one energy: L * (p + 1) * nblk for the narrow kernels, two
-// band copies of N rows of stride ps for the wide ones.
+// Entries of the factor buffer of one energy: L * (p + 1) * nblk for the narrow kernels, the
+// level blocks and the factorization window for the wide ones.
 inline size_t factor_entries(const BlockPlan& bp, size_t N) {
-    return bp.wide ? 2 * N * (size_t)((bp.p + 1 + 3) & ~3) : N * (size_t)(bp.p + 1);
+    return bp.wide ? (size_t)level_factor_entries(bp.nblk, bp.K, bp.S) : N * (size_t)(bp.p + 1);
 }
 
 // Host tables of a block plan: element offset of every chain position, base element of
@@ -2232,7 +2210,8 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
     out->pd.nblk = bp.nblk;
     out->pd.p = bp.p;
     out->pd.span = span;
-    out->pd.ps = (bp.p + 1 + 3) & ~3;
+    out->pd.S = bp.S;
+    out->pd.K = bp.K;
     out->wide = bp.wide;
     const bool last_in_chain = (span >> m->M) & 1;
     out->staged = false;
@@ -2279,32 +2258,13 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
 }
 
 // Launches the block preconditioner z = B^-1 r (optionally fused with the COCG update).
-template <class R> cudaError_t wide_apply_attr(int kp, int smem) {
-    switch (kp) {
-        case 1: return cudaFuncSetAttribute(k_block_apply_wide<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case 2: return cudaFuncSetAttribute(k_block_apply_wide<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case 3: return cudaFuncSetAttribute(k_block_apply_wide<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        case 4: return cudaFuncSetAttribute(k_block_apply_wide<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        default: return cudaFuncSetAttribute(k_block_apply_wide<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    }
-}
-template <class R> size_t wide_factor_smem(const PlanDev& pd) {
-    return ((size_t)(pd.p + 1) * (pd.p + 2) / 2 + 2 * (size_t)(pd.p + 1)) * sizeof(cx<R>);
-}
-template <class R> size_t wide_apply_smem(const PlanDev& pd) {
-    return (size_t)WA_WARPS * ((size_t)wa_np<R>() * WA_PB * wa_pss((pd.p + 31) / 32) + WA_RING) * sizeof(cx<R>);
-}
 template <class R> int prepare_staged(const DevPlanBuf& pb) {
     if (pb.wide) {
-        const size_t f = wide_factor_smem<R>(pb.pd), a = wide_apply_smem<R>(pb.pd);
-        if (f > 227 * 1024 || a > 227 * 1024) {
+        if (pb.pd.S > LV_SMAX || 2 * (size_t)pb.pd.S * pb.pd.S * sizeof(cx<R>) > 220 * 1024) {
             vbk_set_error("block preconditioner band too wide for shared memory in this precision");
             return VBK_ERR_UNSUPPORTED;
         }
-        cudaError_t ce = cudaFuncSetAttribute(k_block_factor_wide<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f);
-        if (ce == cudaSuccess)
-            ce = wide_apply_attr<R>((pb.pd.p + 31) / 32, (int)a);
-        return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "wide block preconditioner shared-memory opt-in");
+        return VBK_OK;
     }
     if (!pb.staged) return VBK_OK;
     const size_t smem = (size_t)pb.pd.L * (SG + 1) * sizeof(cx<R>);
@@ -2489,11 +2449,16 @@ void factor_blocks(Runner& rn, const DevModel& md, const DevPlanBuf& pb, int nE,
               diag, F, fail);
         return;
     }
-    const size_t per_e = 2 * (size_t)md.N * pb.pd.ps;
-    cudaMemsetAsync(F, 0, (size_t)nE * per_e * sizeof(cx<R>), rn.st);
-    rn.go("block_band", k_block_band<R, M>, dim3(cdiv_u((long long)nE * md.N, TPB)), dim3(TPB), md, pb.pd, nE, diag, F);
-    rn.go_smem("block_factor_wide", k_block_factor_wide<R>, dim3(pb.pd.nblk, nE), dim3(WF_THREADS),
-               wide_factor_smem<R>(pb.pd), pb.pd, F, fail);
+    const size_t smem = 2 * (size_t)pb.pd.S * pb.pd.S * sizeof(cx<R>);
+    const cudaError_t ce = cudaFuncSetAttribute(k_level_factor<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        if (rn.first_error == cudaSuccess) rn.first_error = ce;
+        vbk_set_error("level factorization shared-memory opt-in failed");
+        return;
+    }
+    rn.go_smem("block_factor_wide", k_level_factor<R, M>, dim3(pb.pd.nblk, nE), dim3(LF_THREADS), smem, md, pb.pd, diag, F,
+               fail);
 }
 
 template <class R, int M> struct Solver {
@@ -3105,19 +3070,8 @@ void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny
     }
     if (pb.wide) {
         if (ny == 0) return;
-        const dim3 g(pb.pd.nblk, cdiv_u(ny, WA_WARPS));
-        const size_t smem = wide_apply_smem<R>(pb.pd);
-        auto launch = [&](auto kern) {
-            rn.go_smem("block_apply_wide", kern, g, dim3(WA_WARPS * 32), smem, pb.pd, sys_e, sel, (int)ny, F,
-                       (const cx<R>*)r, rs, z, zs, part_rz);
-        };
-        switch ((pb.pd.p + 31) / 32) {
-            case 1: launch(k_block_apply_wide<R, 1>); break;
-            case 2: launch(k_block_apply_wide<R, 2>); break;
-            case 3: launch(k_block_apply_wide<R, 3>); break;
-            case 4: launch(k_block_apply_wide<R, 4>); break;
-            default: launch(k_block_apply_wide<R, 5>); break;
-        }
+        rn.go("block_apply_wide", k_level_apply<R>, dim3(pb.pd.nblk, ny), dim3(32 * ((pb.pd.S + 31) / 32)), pb.pd, sys_e, sel,
+              F, (const cx<R>*)r, rs, z, zs, part_rz);
         return;
     }
     rn.go("block_apply", k_block_apply<R>, dim3((pb.pd.nblk + BTPB - 1) / BTPB, ny), dim3(BTPB), pb.pd, sys_e, sel, F,
