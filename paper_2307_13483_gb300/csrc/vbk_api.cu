@@ -1048,6 +1048,10 @@ int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* bp) {
     if (bp->wide) {
         bp->S = 4 * ((p + 7) / 8);  // levels of S >= p / 2 chain positions: block pentadiagonal
         bp->K = (bp->L + bp->S - 1) / bp->S;
+        if (bp->nblk > 65535) {
+            g_last_error = "wide-band block preconditioner with more than 65535 blocks";
+            return VBK_ERR_UNSUPPORTED;
+        }
     }
     return VBK_OK;
 }

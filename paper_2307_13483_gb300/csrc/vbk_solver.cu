@@ -776,7 +776,7 @@ __global__ void __launch_bounds__(STPB) k_block_staged(PlanDev pl, const int* __
 // with S x S blocks: B = L D L^T with L unit block-lower (blocks L_{k+1,k}, L_{k+2,k}) and D
 // block diagonal (dense complex symmetric S x S).  The last level is padded with identity
 // rows.  Per energy and block the factor holds, for every level k, five S x S blocks:
-//   [0] D_k^-1 stored transposed, [1], [2] Lf_j = L_{k,k-j}^T, [3], [4] Lb_j = L_{k+j,k}
+//   [0] D_k^-1 (symmetrized), [1], [2] Lf_j = L_{k,k-j}^T, [3], [4] Lb_j = L_{k+j,k}
 // (all row-major), so that thread i of a solve reads column i of each (coalesced).  Both
 // triangular sweeps are then dense block products, K = ceil(L / S) sequential steps instead
 // of L scalar ones.  After the factors, each energy holds a workspace of 9 S x S blocks per
@@ -936,10 +936,13 @@ __global__ void __launch_bounds__(LF_THREADS) k_level_factor(DevModel md, PlanDe
             }
             __syncthreads();
         }
+        // D_k^-1 is complex symmetric; its symmetric part is stored so that the preconditioner
+        // L^-T D^-1 L^-1 stays exactly symmetric under rounding (COCG relies on it)
         cx<R>* Dt = out(k, 0);
         for (long long t = threadIdx.x; t < S2; t += blockDim.x) {
             const int r = (int)(t / S), c = (int)(t - (long long)r * S);
-            Dt[(long long)c * S + r] = aug[(long long)r * 2 * S + S + c];  // transposed
+            const cx<R> a = aug[(long long)r * 2 * S + S + c], b = aug[(long long)c * 2 * S + S + r];
+            Dt[t] = mkc<R>((R)0.5 * (a.x + b.x), (R)0.5 * (a.y + b.y));
         }
         __syncthreads();
         if (k + 3 < K) level_assemble<R, M>(md, pl, e, blk, k + 3, diag, W);
@@ -984,19 +987,29 @@ __global__ void __launch_bounds__(LF_THREADS) k_level_factor(DevModel md, PlanDe
     if (threadIdx.x == 0 && bad_sh) atomicExch(fail + e, 1);
 }
 
-// z = B^-1 r for the level-blocked factors: one CTA per (block, selected system), thread i < S
-// owns row i of every level.  Forward: w_k = r_k - sum_j L_{k,k-j} w_{k-j}, u_k = D_k^-1 w_k
-// (stored in z); backward: z_k = u_k - sum_j L_{k+j,k}^T z_{k+j}.  Optional partials
+// z = B^-1 r for the level-blocked factors: one CTA per (selected system, block) of
+// 4 * RW threads (grid: systems x blocks, systems fastest, so that the systems sharing an
+// energy read each block's factors while they are in L2), RW = 32 ceil(S / 32): thread (q, i) sums quarter q of the inner index for row
+// i of every level block product (4 x more loads in flight than one thread per row), and
+// quarter 0 combines.  Forward: w_k = r_k - sum_j L_{k,k-j} w_{k-j}, u_k = D_k^-1 w_k (stored
+// in z); backward: z_k = u_k - sum_j L_{k+j,k}^T z_{k+j}.  Optional partials
 // part[s * nblk + blk] = sum_k w_k^T u_k (= r^T z restricted to the block).
+constexpr int LA_RWMAX = 96;  // rows per quarter (>= LV_SMAX, a multiple of 32)
 template <class R>
-__global__ void __launch_bounds__(96) k_level_apply(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
-                                                   const cx<R>* __restrict__ F, const cx<R>* __restrict__ r, long long rs,
-                                                   cx<R>* __restrict__ z, long long zs, double2* __restrict__ part) {
-    __shared__ cx<R> ring[3][LV_SMAX];
+__global__ void __launch_bounds__(4 * LA_RWMAX) k_level_apply(PlanDev pl, const int* __restrict__ sys_e, Sel sel,
+                                                             const cx<R>* __restrict__ F, const cx<R>* __restrict__ r,
+                                                             long long rs, cx<R>* __restrict__ z, long long zs,
+                                                             double2* __restrict__ part) {
+    __shared__ cx<R> ring[3][LA_RWMAX];
+    __shared__ cx<R> red[4][LA_RWMAX];   // partials of w (forward) and z (backward)
+    __shared__ cx<R> redu[4][LA_RWMAX];  // partials of u: quarter 0 may still read them while
+                                         // the next level's w partials are written
     __shared__ cx<R> sh[32];
-    const int s = sel_sys(sel);
+    const int s = sel.list ? sel.list[blockIdx.x] : (int)blockIdx.x;
     if (s < 0 || (sel.act && !sel.act[s])) return;
-    const int S = pl.S, K = pl.K, L = pl.L, blk = blockIdx.x, i = threadIdx.x;
+    const int S = pl.S, K = pl.K, L = pl.L, blk = blockIdx.y;
+    const int RW = blockDim.x >> 2, i = threadIdx.x % RW, q = threadIdx.x / RW;
+    const int Q = S >> 2, m0 = q * Q;  // this thread's quarter of the inner index
     const long long S2 = (long long)S * S;
     const int e = sys_e[s];
     const cx<R>* Out = F + (long long)e * level_factor_entries(pl.nblk, K, S) + (long long)blk * K * 5 * S2;
@@ -1005,46 +1018,56 @@ __global__ void __launch_bounds__(96) k_level_apply(PlanDev pl, const int* __res
     const int base = pl.fixed_base[blk];
     const bool row = i < S;
     cx<R> rz = mkc<R>(0, 0);
+    // partial sum over this quarter of M[m][i] v[m] (M row-major S x S, v in shared memory)
+    auto quarter = [&](const cx<R>* M, const cx<R>* v, cx<R> acc) {
+        const cx<R>* col = M + (long long)m0 * S + i;
+#pragma unroll 10
+        for (int m = 0; m < Q; ++m) acc = cfma<R>(col[(long long)m * S], v[m0 + m], acc);
+        return acc;
+    };
     for (int k = 0; k < K; ++k) {
         const int c = k * S + i;
-        const bool valid = row && c < L;
+        const bool valid = row && q == 0 && c < L;
         const int el = valid ? base + pl.chain_off[c] : 0;
-        cx<R> acc = valid ? rv[el] : mkc<R>(0, 0);
-        if (row) {
-            for (int j = 1; j <= 2 && k - j >= 0; ++j) {
-                const cx<R>* Lf = Out + ((long long)k * 5 + j) * S2 + i;
-                const cx<R>* wv = ring[(k - j) % 3];
-#pragma unroll 4
-                for (int m = 0; m < S; ++m) acc = csub<R>(acc, cmul<R>(Lf[(long long)m * S], wv[m]));
-            }
-            ring[k % 3][i] = acc;
+        const cx<R> rk = valid ? rv[el] : mkc<R>(0, 0);
+        cx<R> part_w = mkc<R>(0, 0);
+        if (row)
+            for (int j = 1; j <= 2 && k - j >= 0; ++j)
+                part_w = quarter(Out + ((long long)k * 5 + j) * S2, ring[(k - j) % 3], part_w);
+        red[q][i] = part_w;
+        __syncthreads();
+        cx<R> w = mkc<R>(0, 0);
+        if (row && q == 0) {
+            w = csub<R>(csub<R>(csub<R>(csub<R>(rk, red[0][i]), red[1][i]), red[2][i]), red[3][i]);
+            ring[k % 3][i] = w;
         }
         __syncthreads();
-        if (row) {
-            const cx<R>* Dt = Out + (long long)k * 5 * S2 + i;
-            const cx<R>* wv = ring[k % 3];
-            cx<R> u = mkc<R>(0, 0);
-#pragma unroll 4
-            for (int m = 0; m < S; ++m) u = cfma<R>(Dt[(long long)m * S], wv[m], u);
-            rz = cfma<R>(acc, u, rz);
+        cx<R> part_u = mkc<R>(0, 0);
+        if (row) part_u = quarter(Out + (long long)k * 5 * S2, ring[k % 3], part_u);
+        redu[q][i] = part_u;
+        __syncthreads();
+        if (row && q == 0) {
+            const cx<R> u = cadd<R>(cadd<R>(cadd<R>(redu[0][i], redu[1][i]), redu[2][i]), redu[3][i]);
+            rz = cfma<R>(w, u, rz);
             if (valid) zv[el] = u;
         }
     }
     __syncthreads();
     for (int k = K - 1; k >= 0; --k) {
         const int c = k * S + i;
-        const bool valid = row && c < L;
+        const bool valid = row && q == 0 && c < L;
         const int el = valid ? base + pl.chain_off[c] : 0;
-        cx<R> acc = valid ? zv[el] : mkc<R>(0, 0);
-        if (row) {
-            for (int j = 1; j <= 2 && k + j < K; ++j) {
-                const cx<R>* Lb = Out + ((long long)k * 5 + 2 + j) * S2 + i;
-                const cx<R>* zr = ring[(k + j) % 3];
-#pragma unroll 4
-                for (int m = 0; m < S; ++m) acc = csub<R>(acc, cmul<R>(Lb[(long long)m * S], zr[m]));
-            }
-            ring[k % 3][i] = acc;
-            if (valid) zv[el] = acc;
+        const cx<R> uk = valid ? zv[el] : mkc<R>(0, 0);
+        cx<R> part_z = mkc<R>(0, 0);
+        if (row)
+            for (int j = 1; j <= 2 && k + j < K; ++j)
+                part_z = quarter(Out + ((long long)k * 5 + 2 + j) * S2, ring[(k + j) % 3], part_z);
+        red[q][i] = part_z;
+        __syncthreads();
+        if (row && q == 0) {
+            const cx<R> zk = csub<R>(csub<R>(csub<R>(csub<R>(uk, red[0][i]), red[1][i]), red[2][i]), red[3][i]);
+            ring[k % 3][i] = zk;
+            if (valid) zv[el] = zk;
         }
         __syncthreads();
     }
@@ -3070,8 +3093,8 @@ void block_precond(Runner& rn, const DevPlanBuf& pb, int N, Sel sel, unsigned ny
     }
     if (pb.wide) {
         if (ny == 0) return;
-        rn.go("block_apply_wide", k_level_apply<R>, dim3(pb.pd.nblk, ny), dim3(32 * ((pb.pd.S + 31) / 32)), pb.pd, sys_e, sel,
-              F, (const cx<R>*)r, rs, z, zs, part_rz);
+        rn.go("block_apply_wide", k_level_apply<R>, dim3(ny, pb.pd.nblk), dim3(4 * 32 * ((pb.pd.S + 31) / 32)), pb.pd, sys_e,
+              sel, F, (const cx<R>*)r, rs, z, zs, part_rz);
         return;
     }
     rn.go("block_apply", k_block_apply<R>, dim3((pb.pd.nblk + BTPB - 1) / BTPB, ny), dim3(BTPB), pb.pd, sys_e, sel, F,
