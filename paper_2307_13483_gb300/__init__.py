@@ -11,6 +11,7 @@ raises if it has not been built (``python -m paper_2307_13483_gb300.build`` or
 from __future__ import annotations
 
 import ctypes as C
+from collections.abc import Sequence
 import os
 
 import numpy as np
@@ -67,6 +68,37 @@ class vbk_opts(C.Structure):
 
 class vbk_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double)]
+
+
+_STATS_DTYPE = np.dtype({"names": ["status", "iterations", "refinements", "rel_residual"],
+                         "formats": ["<i4", "<i4", "<i4", "<f8"], "offsets": [0, 4, 8, 16], "itemsize": 24})
+
+
+class SolveStats(Sequence):
+    """Per-system results of a solve: item k is a dict (status name, iterations, refinements,
+    rel_residual), built on access; the fields are also numpy arrays (``.status`` holds the
+    VBK_SYS_* codes) over the library's own result buffer."""
+
+    def __init__(self, buf):
+        assert C.sizeof(vbk_stats) == _STATS_DTYPE.itemsize
+        self._buf = buf
+        self._a = np.frombuffer(buf, dtype=_STATS_DTYPE)
+
+    def __len__(self):
+        return self._a.size
+
+    def __getitem__(self, k):
+        if isinstance(k, slice):
+            return [self[i] for i in range(*k.indices(len(self)))]
+        r = self._a[k]
+        code = int(r["status"])
+        return dict(status=SYS_STATUS.get(code, code), iterations=int(r["iterations"]), refinements=int(r["refinements"]),
+                    rel_residual=float(r["rel_residual"]))
+
+    def __getattr__(self, name):
+        if name in _STATS_DTYPE.names:
+            return self._a[name]
+        raise AttributeError(name)
 
 
 EXPORTED = [
@@ -229,9 +261,7 @@ def vbk_solve(model: Model, eps_i, vi, opts: vbk_opts | None = None, psi=None, s
     rc = _lib.vbk_solve(model.handle, eps.size, _dptr(eps), vis.shape[0], _iptr(vis), C.byref(o), _tensor_ptr(psi), st,
                         _stream(stream))
     _check(rc, "vbk_solve", allow=() if check else (VBK_ERR_NOT_CONVERGED,))
-    stats = [dict(status=SYS_STATUS.get(s.status, s.status), iterations=s.iterations, refinements=s.refinements,
-                  rel_residual=s.rel_residual) for s in st]
-    return psi, stats
+    return psi, SolveStats(st)
 
 
 def vbk_cross_sections(model: Model, eps_i, vi, psi, vf, stream=None, want_t=False):
@@ -276,9 +306,7 @@ def vbk_solve_adjoint(model: Model, eps_i, vi, psi, vf, dL_dsigma, theta_ids, op
                                 _tensor_ptr(psi), vfs.shape[0], _iptr(vfs), _tensor_ptr(dl), th.size, _iptr(th),
                                 _dptr(grad), st, _stream(stream))
     _check(rc, "vbk_solve_adjoint", allow=() if check else (VBK_ERR_NOT_CONVERGED,))
-    stats = [dict(status=SYS_STATUS.get(s.status, s.status), iterations=s.iterations, refinements=s.refinements,
-                  rel_residual=s.rel_residual) for s in st]
-    return grad, stats
+    return grad, SolveStats(st)
 
 
 def vbk_matvec(model: Model, E, x, precision=VBK_FP64, variant=-1, stream=None):

@@ -226,6 +226,8 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         dm.ch_a[c] = m->chans[c].a;
         dm.ch_b[c] = m->chans[c].b;
         dm.ch_sb[c] = std::sqrt(m->chans[c].b);
+        dm.ch_isb[c] = 1.0 / dm.ch_sb[c];
+        dm.ch_ib[c] = 1.0 / m->chans[c].b;
     }
     for (int k = 0; k < MAXCH; ++k) dm.mu_d[k] = mu_d[k];
     // coefficient columns of the stencil points (Sec. III: "all energy factors and square roots can
@@ -628,6 +630,7 @@ void vbk_free_model(vbk_model* m) {
         cudaDeviceSynchronize();  // outstanding frees of this model's calls complete before the pool goes
         cudaMemPoolDestroy(m->pool);
     }
+    if (m->hpin) cudaFreeHost(m->hpin);
     delete m;
 }
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/vbk.h"
+#include "vbk_erfcx_table.h"
 
 #define MAXM VBK_MAX_MODES
 #define MAXS VBK_MAX_STATES
@@ -127,6 +128,7 @@ struct DevModel {
     const float* pc32;
     int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
     double ch_a[MAXCH], ch_b[MAXCH], ch_sb[MAXCH];  // ch_sb = sqrt(b)
+    double ch_isb[MAXCH], ch_ib[MAXCH];            // 1 / sqrt(b), 1 / b
     int mu_d[MAXCH];  // discrete state coupled to partial wave mu
 };
 
@@ -163,7 +165,27 @@ struct vbk_model {
     cudaStream_t cap_stream = nullptr;  // library-owned stream used only to capture CUDA graphs
     int mv_variant[2] = {-1, -1};       // autotuned matvec variant per precision (FP32, FP64); -1: untuned
     cudaMemPool_t pool = nullptr;       // library-owned stream-ordered pool (keeps its memory between calls)
+    void* hpin = nullptr;               // library-owned pinned host staging buffer (grown on demand)
+    size_t hpin_bytes = 0;
 };
+
+// The model's pinned staging buffer with at least `bytes` bytes (callers have synchronised every
+// copy that used the previous contents before they return).
+inline void* vbk_pinned(vbk_model* m, size_t bytes) {
+    if (m->hpin_bytes < bytes) {
+        if (m->hpin) cudaFreeHost(m->hpin);
+        m->hpin = nullptr;
+        m->hpin_bytes = 0;
+        const size_t want = bytes < (size_t)65536 ? (size_t)65536 : bytes * 2;
+        if (cudaMallocHost(&m->hpin, want) != cudaSuccess) {
+            cudaGetLastError();
+            m->hpin = nullptr;
+            return nullptr;
+        }
+        m->hpin_bytes = want;
+    }
+    return m->hpin;
+}
 
 // --------------------------------------------------------------------------- level shift
 // Dawson's integral D(x) = exp(-x^2) int_0^x exp(t^2) dt.  Taylor series for |x| < 0.5;
@@ -205,15 +227,34 @@ __host__ __device__ inline double vbk_dawson(double x) {
     return x < 0 ? -r : r;
 }
 
-// exp(y^2) erfc(y), y >= 0
+// erfcx(y) = exp(y^2) erfc(y), y >= 0.  Below 16: piecewise degree-12 polynomials on intervals
+// of width 1/2 (interpolation at Chebyshev points of each interval, coefficients computed in
+// 40-digit arithmetic by gen_erfcx_table.py; relative error ~1e-15).  From 16: the asymptotic
+// series erfcx(y) = 1 / (y sqrt(pi)) sum_k (-1)^k (2k - 1)!! / (2 y^2)^k, 9 terms (the first
+// omitted term is below 1e-16 there).
+static __device__ const double vbk_erfcx_c_dev[VBK_ERFCX_NINT * (VBK_ERFCX_DEG + 1)] = {VBK_ERFCX_COEFFS};
+static const double vbk_erfcx_c_host[VBK_ERFCX_NINT * (VBK_ERFCX_DEG + 1)] = {VBK_ERFCX_COEFFS};
 __host__ __device__ inline double vbk_erfcx(double y) {
+    if (y < 0.5 * VBK_ERFCX_NINT) {
 #ifdef __CUDA_ARCH__
-    return erfcx(y);
+        const double* C = vbk_erfcx_c_dev;
 #else
-    if (y < 25.0) return std::exp(y * y) * std::erfc(y);
-    double y2 = y * y;  // asymptotic series, relative error < 1e-16 for y >= 25
-    return 0.56418958354775628 / y * (1.0 - 0.5 / y2 + 0.75 / (y2 * y2) - 1.875 / (y2 * y2 * y2));
+        const double* C = vbk_erfcx_c_host;
 #endif
+        const int k = y > 0.0 ? (int)(2.0 * y) : 0;
+        const double t = 4.0 * y - (double)(2 * k + 1);
+        const double* c = C + k * (VBK_ERFCX_DEG + 1);
+        double r = c[VBK_ERFCX_DEG];
+        for (int p = VBK_ERFCX_DEG - 1; p >= 0; --p) r = fma(r, t, c[p]);
+        return r;
+    }
+    const double u = 0.5 / (y * y);
+    double s = 1.0, term = 1.0;
+    for (int k = 1; k <= 8; ++k) {
+        term *= -(2.0 * k - 1.0) * u;
+        s += term;
+    }
+    return 0.56418958354775628 / y * s;
 }
 
 // F[f](eps) for f(x) = (a / 2 pi) x^(l+1/2) exp(-b x), x > 0 (Eq. IntF with the widths of
@@ -243,8 +284,11 @@ __host__ __device__ inline double2 vbk_level_shift_eval(double eps, double a, do
     return make_double2(a / (2.0 * PI) * p, im);
 }
 
-// The same transform with one square root: sb = sqrt(b) given, sqrt(b |eps|) = sb sqrt(|eps|).
-__host__ __device__ inline double2 vbk_level_shift_eval_sb(double eps, double a, double b, double sb, int l) {
+// The same transform from precomputed channel constants sb = sqrt(b), isb = 1 / sqrt(b),
+// ib = 1 / b: one square root and no division per evaluation (sqrt(b |eps|) = sb sqrt(|eps|),
+// Gamma(k + 1/2) b^-(k+1/2) built up by multiplications).
+__host__ __device__ inline double2 vbk_level_shift_core(double eps, double a, double b, double sb, double isb, double ib,
+                                                        int l) {
     const double PI = 3.14159265358979323846;
     const double SQRT_PI = 1.7724538509055160;
     const double sq = sqrt(fabs(eps));
@@ -255,13 +299,13 @@ __host__ __device__ inline double2 vbk_level_shift_eval_sb(double eps, double a,
         t = PI * sq * vbk_erfcx(sb * sq);
     else
         t = 0.0;
-    double g = SQRT_PI;  // Gamma(1/2)
-    double bp = sb;      // b^(k+1/2)
-    double p = -g / bp + t;
+    double g = SQRT_PI;  // Gamma(k + 1/2), k = 0
+    double ibp = isb;    // b^-(k+1/2)
+    double p = t - g * ibp;
     for (int k = 1; k <= l; ++k) {
         g *= (k - 0.5);
-        bp *= b;
-        p = -g / bp + eps * p;
+        ibp *= ib;
+        p = eps * p - g * ibp;
     }
     double im = 0.0;
     if (eps > 0.0) {
@@ -269,7 +313,10 @@ __host__ __device__ inline double2 vbk_level_shift_eval_sb(double eps, double a,
         for (int k = 0; k < l; ++k) el *= eps;
         im = -0.5 * a * el * exp(-b * eps);
     }
-    return make_double2(a / (2.0 * PI) * p, im);
+    return make_double2(a * (0.5 / PI) * p, im);
+}
+__host__ __device__ inline double2 vbk_level_shift_eval_sb(double eps, double a, double b, double sb, int l) {
+    return vbk_level_shift_core(eps, a, b, sb, 1.0 / sb, 1.0 / b, l);
 }
 
 // f(eps) = sqrt(Gamma(eps) / 2 pi), zero for eps <= 0 (reading: closed channels do not couple)

@@ -150,7 +150,8 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
     }
     for (int c = 0; c < md.nchan; ++c) {
         if (md.ch_d[c] != d) continue;
-        const double2 F = vbk_level_shift_eval_sb(eps, md.ch_a[c], md.ch_b[c], md.ch_sb[c], md.ch_l[c]);
+        const double2 F =
+            vbk_level_shift_core(eps, md.ch_a[c], md.ch_b[c], md.ch_sb[c], md.ch_isb[c], md.ch_ib[c], md.ch_l[c]);
         re -= F.x;
         im -= F.y;
     }
@@ -1103,21 +1104,20 @@ __global__ void __launch_bounds__(TPB) k_point_precond(int N, const int* __restr
 
 // ------------------------------------------------------------------- refinement (FP64)
 // First outer step: r = b (x = 0), partial ||r||^2.
-__global__ void __launch_bounds__(TPB) k_copy_b(int N, Sel sel, const double2* __restrict__ b,
-                                               double2* __restrict__ r, double2* __restrict__ part) {
-    __shared__ double2 sh[32];
-    const int s = sel_sys(sel);
-    if (s < 0 || (sel.act && !sel.act[s])) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double2 loc = make_double2(0.0, 0.0);
-    if (i < N) {
-        const double2 v = b[(long long)s * N + i];
-        r[(long long)s * N + i] = v;
-        const float fx = (float)v.x, fy = (float)v.y;  // the stopping test needs |b| to ~1e-7 only
-        loc.x = (double)(fx * fx + fy * fy);
+// ||b||^2 of every system: one thread block per system (grid: nsys), one partial each.  FP32
+// accumulation: the stopping test needs ||b|| to ~1e-7 only.
+__global__ void __launch_bounds__(TPB) k_rhs_norm(int N, const double2* __restrict__ b, double2* __restrict__ part) {
+    __shared__ float2 sh[32];
+    const int s = blockIdx.x;
+    const double2* bs = b + (long long)s * N;
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double2 v = bs[i];
+        const float fx = (float)v.x, fy = (float)v.y;
+        acc = fmaf(fx, fx, fmaf(fy, fy, acc));
     }
-    const double2 tot = block_sum2(loc, sh);
-    if (threadIdx.x == 0) part[(long long)s * gridDim.x + blockIdx.x] = tot;
+    const double2 tot = block_sum_c<float>(make_float2(acc, 0.f), sh);
+    if (threadIdx.x == 0) part[s] = tot;
 }
 
 // Outer convergence test on the FP64 residual (stopping rule of Sec. III, true residual).
@@ -1658,7 +1658,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
                                                           const int* __restrict__ list, int pmode,
                                                           const float2* __restrict__ diag, const float2* __restrict__ dinv,
                                                           float2* __restrict__ x, float2* __restrict__ r,
-                                                          const float2* __restrict__ p0,
+                                                          const double2* __restrict__ res, double2* __restrict__ x64,
                                                           SysState* __restrict__ st, int* __restrict__ act,
                                                           int* __restrict__ outer, int max_iter) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -1670,9 +1670,8 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     __shared__ int poff[MAXS][64];
     __shared__ short pcol[MAXS][64][MAXM];
     __shared__ int npt[MAXS];
-    __shared__ float red[RTPB / 32][3];
-    __shared__ float2 bc[2];  // broadcast: alpha, beta
-    __shared__ int stop;
+    __shared__ float redA[RTPB / 32][3], redB[RTPB / 32][3];  // per-warp partials of the two reductions
+    static_assert(RTPB == 1024, "one partial per lane in the final warp sums");
     const int s = list[blockIdx.x];
     const int tid = threadIdx.x;
     const long long so = (long long)s * N;
@@ -1690,29 +1689,57 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
             for (int m = 0; m < MAXM; ++m) pcol[d][k][m] = (short)e.col[m];
         }
     }
-    for (int i = tid; i < N; i += RTPB) P[i] = p0[so + i];
-    double rho_d = 0.0, rho_i = 0.0;
-    if (tid == 0) {
-        rho_d = st[s].rho.x;
-        rho_i = st[s].rho.y;
-    }
+    // per-system scalars, kept identical in every thread: each reduction ends with one barrier
+    // after which every warp sums the per-warp partials itself (no serial thread-0 section)
+    const SysState S0 = st[s];
+    const float target2 = (float)(S0.target * S0.target);
+    int iters = S0.iters;
+    float rr = 0.f;
+    int status = -1;  // -1: stopped normally (the FP64 residual decides)
     __syncthreads();
     const int lane = tid & 31, wid = tid >> 5;
-    auto block_red3 = [&](float a0, float a1, float a2) {
+    auto all_sum3 = [&](float (*buf)[3], float a0, float a1, float a2) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_down_sync(0xffffffffu, a0, o);
-            a1 += __shfl_down_sync(0xffffffffu, a1, o);
-            a2 += __shfl_down_sync(0xffffffffu, a2, o);
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
         }
         if (lane == 0) {
-            red[wid][0] = a0;
-            red[wid][1] = a1;
-            red[wid][2] = a2;
+            buf[wid][0] = a0;
+            buf[wid][1] = a1;
+            buf[wid][2] = a2;
         }
         __syncthreads();
+        float3 t = make_float3(buf[lane][0], buf[lane][1], buf[lane][2]);  // RTPB / 32 == 32 partials
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+            t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+            t.z += __shfl_xor_sync(0xffffffffu, t.z, o);
+        }
+        return t;
     };
-    const int budget = max(0, max_iter - st[s].iters);
+    // start of the inner solve: r = (b - A x64) / scale in FP32 (narrowed first, scaled in
+    // FP32), x = 0, z = B^-1 r, p = z, rho = r^T z
+    float2 rho, beta = make_float2(0.f, 0.f);
+    {
+        const float inv = (float)S0.inv_scale;
+        float rz_x = 0.f, rz_y = 0.f;
+        for (int i = tid; i < N; i += RTPB) {
+            const double2 v = res[so + i];
+            const float2 rn = make_float2((float)v.x * inv, (float)v.y * inv);
+            r[so + i] = rn;
+            const float2 zi = pmode == 0 ? cmul<float>(rn, di[i]) : rn;
+            P[i] = zi;
+            rz_x += rn.x * zi.x - rn.y * zi.y;
+            rz_y += rn.x * zi.y + rn.y * zi.x;
+        }
+        const float3 t = all_sum3(redB, 0.f, rz_x, rz_y);
+        rho = make_float2(t.y, t.z);
+    }
+    bool wrote_x = false;
+    const int budget = max(0, max_iter - iters);
     for (int it = 0; it < budget; ++it) {
         // q = A p and p^T q
         float pq_x = 0.f, pq_y = 0.f;
@@ -1739,34 +1766,18 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
             pq_x += pi.x * acc.x - pi.y * acc.y;
             pq_y += pi.x * acc.y + pi.y * acc.x;
         }
-        block_red3(pq_x, pq_y, 0.f);
-        if (tid == 0) {
-            double ax = 0.0, ay = 0.0;
-            for (int w = 0; w < RTPB / 32; ++w) {
-                ax += red[w][0];
-                ay += red[w][1];
-            }
-            const double den = ax * ax + ay * ay;
-            SysState& S = st[s];
-            stop = 0;
-            if (!(den > 0.0) || !isfinite(den)) {
-                S.status = isfinite(den) ? VBK_SYS_BREAKDOWN : VBK_SYS_NAN;
-                act[s] = 0;
-                outer[s] = 0;
-                stop = 1;
-            } else {
-                const double al_x = (rho_d * ax + rho_i * ay) / den, al_y = (rho_i * ax - rho_d * ay) / den;
-                bc[0] = make_float2((float)al_x, (float)al_y);
-            }
+        const float3 pq = all_sum3(redA, pq_x, pq_y, 0.f);
+        const float den = pq.x * pq.x + pq.y * pq.y;
+        if (!(den > 0.f) || !isfinite(den)) {
+            status = isfinite(den) ? VBK_SYS_BREAKDOWN : VBK_SYS_NAN;
+            break;
         }
-        __syncthreads();
-        if (stop) break;
+        const float2 al = make_float2((rho.x * pq.x + rho.y * pq.y) / den, (rho.y * pq.x - rho.x * pq.y) / den);
         // x += alpha p, r -= alpha q, z = B^-1 r (into Q), ||r||^2, r^T z
-        const float2 al = bc[0];
-        float rr = 0.f, rz_x = 0.f, rz_y = 0.f;
+        float rr_l = 0.f, rz_x = 0.f, rz_y = 0.f;
         for (int i = tid; i < N; i += RTPB) {
             const float2 pi = P[i], qi = Q[i];
-            float2 xv = x[so + i];
+            float2 xv = it == 0 ? make_float2(0.f, 0.f) : x[so + i];
             xv.x += al.x * pi.x - al.y * pi.y;
             xv.y += al.x * pi.y + al.y * pi.x;
             x[so + i] = xv;
@@ -1776,53 +1787,53 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
             r[so + i] = rn;
             const float2 zi = pmode == 0 ? cmul<float>(rn, di[i]) : rn;
             Q[i] = zi;
-            rr += rn.x * rn.x + rn.y * rn.y;
+            rr_l += rn.x * rn.x + rn.y * rn.y;
             rz_x += rn.x * zi.x - rn.y * zi.y;
             rz_y += rn.x * zi.y + rn.y * zi.x;
         }
-        block_red3(rr, rz_x, rz_y);
-        if (tid == 0) {
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-            for (int w = 0; w < RTPB / 32; ++w) {
-                a0 += red[w][0];
-                a1 += red[w][1];
-                a2 += red[w][2];
-            }
-            SysState& S = st[s];
-            S.iters += 1;
-            S.cycle_iters += 1;
-            const double rn = sqrt(a0);
-            S.inres = rn;
-            const double den = rho_d * rho_d + rho_i * rho_i;
-            stop = 0;
-            if (!isfinite(rn) || !isfinite(a1) || !isfinite(a2) || rn <= S.target || S.iters >= max_iter) {
-                act[s] = 0;  // the FP64 residual decides
-                stop = 1;
-            } else if (!(a1 * a1 + a2 * a2 > 0.0) || !(den > 0.0)) {
-                S.status = VBK_SYS_BREAKDOWN;
-                act[s] = 0;
-                outer[s] = 0;
-                stop = 1;
-            } else {
-                const double bx = (a1 * rho_d + a2 * rho_i) / den, by = (a2 * rho_d - a1 * rho_i) / den;
-                bc[1] = make_float2((float)bx, (float)by);
-                rho_d = a1;
-                rho_i = a2;
-                S.rho = make_double2(a1, a2);
-                S.beta = make_double2(bx, by);
-            }
+        const float3 sums = all_sum3(redB, rr_l, rz_x, rz_y);
+        wrote_x = true;
+        iters += 1;
+        rr = sums.x;
+        if (!isfinite(sums.x) || !isfinite(sums.y) || !isfinite(sums.z) || sums.x <= target2 || iters >= max_iter) break;
+        const float rden = rho.x * rho.x + rho.y * rho.y;
+        if (!(sums.y * sums.y + sums.z * sums.z > 0.f) || !(rden > 0.f)) {
+            status = VBK_SYS_BREAKDOWN;
+            break;
         }
-        __syncthreads();
-        if (stop) break;
+        beta = make_float2((sums.y * rho.x + sums.z * rho.y) / rden, (sums.z * rho.x - sums.y * rho.y) / rden);
+        rho = make_float2(sums.y, sums.z);
         // p = z + beta p
-        const float2 be = bc[1];
         for (int i = tid; i < N; i += RTPB) {
             const float2 pi = P[i], zi = Q[i];
-            P[i] = make_float2(zi.x + be.x * pi.x - be.y * pi.y, zi.y + be.x * pi.y + be.y * pi.x);
+            P[i] = make_float2(zi.x + beta.x * pi.x - beta.y * pi.y, zi.y + beta.x * pi.y + beta.y * pi.x);
         }
         __syncthreads();
     }
-    if (tid == 0) act[s] = 0;
+    // the correction of this refinement step: x64 += scale x (each thread its own elements)
+    if (wrote_x) {
+        const double sc = S0.scale;
+        for (int i = tid; i < N; i += RTPB) {
+            const float2 xv = x[so + i];
+            double2 X = x64[so + i];
+            X.x += sc * (double)xv.x;
+            X.y += sc * (double)xv.y;
+            x64[so + i] = X;
+        }
+    }
+    if (tid == 0) {
+        SysState& S = st[s];
+        S.cycle_iters += iters - S0.iters;
+        S.iters = iters;
+        S.inres = sqrt((double)rr);
+        S.rho = make_double2(rho.x, rho.y);
+        S.beta = make_double2(beta.x, beta.y);
+        if (status >= 0) {
+            S.status = status;
+            outer[s] = 0;
+        }
+        act[s] = 0;
+    }
 }
 
 // shared memory of the resident kernel: p, q and the oscillator tables (FP32)
@@ -2544,7 +2555,10 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     bytes += carve_size<float2>(mixed ? (size_t)nE * NN : 1);         // 1/diag (FP32)
     bytes += carve_size<double2>((size_t)nsys * NN);                  // r64
     bytes += carve_size<SysState>(nsys);
-    bytes += 7 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(nsys) + carve_size<int>(4);
+    // energies and the per-system index arrays set from the host: one block, one copy
+    const size_t small_bytes = (size_t)nE * sizeof(double) + 5 * (size_t)nsys * sizeof(int);
+    bytes += carve_size<char>(small_bytes);
+    bytes += 3 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(4);
     bytes += 3 * carve_size<double2>((size_t)nsys * nslot);           // partial buffers
     if (block) bytes += carve_size<cx<R>>((size_t)nE * factor_entries(bp, NN));
     if (method == VBK_COCG) {
@@ -2576,15 +2590,17 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     if (!mixed) dinvR = nullptr;
     double2* r64 = carve<double2>(p, (size_t)nsys * NN);
     SysState* sst = carve<SysState>(p, nsys);
-    int* outer = carve<int>(p, nsys);
+    char* smallp = carve<char>(p, small_bytes);
+    double* dE = reinterpret_cast<double*>(smallp);
+    int* sys_e = reinterpret_cast<int*>(smallp + (size_t)nE * sizeof(double));
+    int* outer = sys_e + nsys;
+    int* alll = outer + nsys;
+    int* olist = alll + nsys;
+    int* ilist = olist + nsys;
     int* inner = carve<int>(p, nsys);
-    int* olist = carve<int>(p, nsys);
-    int* ilist = carve<int>(p, nsys);
-    int* alll = carve<int>(p, nsys);
     int* ilist2 = carve<int>(p, nsys);  // second list of the persistent COCG iterations
     int* done = carve<int>(p, nsys);    // per-system work-item counters (self-resetting)
     int* pfail = carve<int>(p, nE);
-    int* sys_e = carve<int>(p, nsys);
     int* cnt = carve<int>(p, 4);
     double2* partA = carve<double2>(p, (size_t)nsys * nslot);
     double2* partB = carve<double2>(p, (size_t)nsys * nslot);
@@ -2614,32 +2630,36 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     }
 
     int rc = VBK_OK;
-    int* hcnt = nullptr;
-    double* dE = nullptr;
     cudaGraphExec_t gexec = nullptr, pgexec = nullptr;
     long long p_per_launch = 0;
-    std::vector<int> ones(nsys, 1), iota(nsys);
-    for (int k = 0; k < nsys; ++k) iota[k] = k;
-    std::vector<SysState> hst(nsys);
+    // pinned staging (model-owned, reused): [host counters | set-up block | per-system states]
+    const size_t o_stage = 256, o_hst = o_stage + ((small_bytes + 255) & ~size_t(255));
+    char* hp = static_cast<char*>(vbk_pinned(mdl, o_hst + (size_t)nsys * sizeof(SysState)));
+    int* hcnt = reinterpret_cast<int*>(hp);
+    SysState* hst = hp ? reinterpret_cast<SysState*>(hp + o_hst) : nullptr;
     auto fail = [&](int code) {
         rc = code;
         return code;
     };
     do {
-        if (cudaMallocHost((void**)&hcnt, 4 * sizeof(int)) != cudaSuccess) {
+        if (!hp) {
+            vbk_set_error("pinned host staging buffer allocation failed");
             fail(VBK_ERR_OOM);
             break;
         }
-        if (vbk_alloc(mdl, (void**)&dE, std::max(1, nE) * sizeof(double), st) != cudaSuccess) {
-            fail(VBK_ERR_OOM);
-            break;
+        {
+            char* stage = hp + o_stage;
+            std::memcpy(stage, job.E.data(), (size_t)nE * sizeof(double));
+            int* si = reinterpret_cast<int*>(stage + (size_t)nE * sizeof(double));
+            std::memcpy(si, job.sys_e.data(), (size_t)nsys * sizeof(int));
+            for (int k = 0; k < nsys; ++k) {
+                si[nsys + k] = 1;      // outer
+                si[2 * nsys + k] = k;  // all systems
+                si[3 * nsys + k] = k;  // outer list
+                si[4 * nsys + k] = k;  // inner list
+            }
         }
-        if (cudaMemcpyAsync(dE, job.E.data(), nE * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(sys_e, job.sys_e.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(outer, ones.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(alll, iota.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(olist, iota.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(ilist, iota.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(smallp, hp + o_stage, small_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemsetAsync(sst, 0, nsys * sizeof(SysState), st) != cudaSuccess ||
             cudaMemsetAsync(job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) != cudaSuccess ||
             cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess ||
@@ -2662,7 +2682,6 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         const unsigned gs = cdiv_u(nsys, 128);
         const unsigned gw = cdiv_u(nsys, 4);  // warp-per-system kernels, 4 warps per block
         const int pmode = pspan < 0 ? -1 : (block ? 1 : 0);
-        const Sel sel_all{alll, outer};
         unsigned n_out = (unsigned)nsys;  // systems in olist (host copy)
         unsigned n_in = (unsigned)nsys;   // upper bound of systems in ilist
         // z = B^-1 src for the systems of `sel` (+ optional r^T z partials)
@@ -2679,8 +2698,10 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         for (int it = 0; it <= o.max_refine + 1; ++it) {
             // FP64 residual r = b - A x
             const Sel so{olist, outer};
+            // the first residual is b itself (x = 0): only its norm is computed, and the first
+            // inner solve reads b directly
             if (it == 0)
-                rn.go("copy_b", k_copy_b, dim3(nb_e, nsys), dim3(TPB), N, sel_all, job.b64, r64, partA);
+                rn.go("rhs_norm", k_rhs_norm, dim3(nsys), dim3(TPB), N, job.b64, partA);
             else
             {
                 if (tune && mdl->mv_variant[1] < 0) {
@@ -2700,7 +2721,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cudaMemsetAsync(olist, 0xff, nsys * sizeof(int), st);  // -1: no system
             cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
-                  it == 0 ? nb_e : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
+                  it == 0 ? 1 : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
                   it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
             cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -2713,13 +2734,21 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             const Sel si{ilist, inner};
             const Sel so2{olist, outer};
 
-            if (method == VBK_COCG) {
+            const double2* res = it == 0 ? job.b64 : (const double2*)r64;  // the current FP64 residual
+            if (method == VBK_COCG && resident && !block) {
+                // one CTA per system runs the whole inner solve: scaled residual in, FP64
+                // correction out (list = ilist from the outer check)
+                rn.go_smem("cocg_resident", k_cocg_resident<M>, dim3(n_in), dim3(RTPB), resident_smem(md), md,
+                           (const int*)sys_e, (const int*)ilist, pmode, reinterpret_cast<const float2*>(diagR),
+                           (const float2*)dinvR, reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), res, job.x64,
+                           sst, inner, outer, o.max_iter);
+            } else if (method == VBK_COCG) {
                 // r = rhs, x = 0, z = B^-1 r, p = z, rho = r^T z.  With a block preconditioner the
                 // search direction carries over from the previous inner solve (k_cocg_start):
                 // hard problems (thousands of iterations) then keep their Krylov progress across
                 // the FP64 residual refreshes instead of restarting.
-                rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst,
-                      (const double2*)r64, r, (long long)N);
+                rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst, res, r,
+                      (long long)N);
                 cudaMemsetAsync(x, 0, (size_t)nsys * NN * sizeof(cx<R>), st);
                 precond(si, n_in, r, N, z, N, partB);
                 rn.go("cocg_start", k_cocg_start, dim3(gs), dim3(128), nsys, sst, (const int*)inner, (const double2*)partB,
@@ -2764,13 +2793,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 };
                 const int K = std::max(1, o.check_every);
                 int k = 0;
-                if (!block && resident) {
-                    // one CTA per system runs the whole inner solve (list = ilist from the outer check)
-                    rn.go_smem("cocg_resident", k_cocg_resident<M>, dim3(n_in), dim3(RTPB), resident_smem(md), md,
-                               (const int*)sys_e, (const int*)ilist, pmode, reinterpret_cast<const float2*>(diagR),
-                               (const float2*)dinvR, reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), reinterpret_cast<const float2*>(pv),
-                               sst, inner, outer, o.max_iter);
-                } else if (!block) {
+                if (!block) {
                     // persistent iterations: static grids over the device-side lists (A = ilist with
                     // count cnt[0], B = ilist2 with count cnt[1]); K (even) iterations per CUDA graph,
                     // captured once per solve and relaunched until list A is empty.  With timing on,
@@ -2954,8 +2977,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             } else {
                 // one GMRES(m) cycle on the scaled residual
                 const long long ldV = (long long)(mres + 1) * N;
-                rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst,
-                      (const double2*)r64, V, ldV);
+                rn.go("inner_rhs", k_inner_rhs<R>, dim3(nb_e, n_in), dim3(TPB), N, si, (const SysState*)sst, res, V, ldV);
                 rn.go("gmres_start", k_gmres_cycle_start, dim3(gs), dim3(128), nsys, mres, (const int*)inner, g);
                 if (tune && mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0) {
                     if (int trc = tune_matvec<R>(rn, mdl, (const int*)sys_e, si, n_in, (const cx<R>*)diagR, (const cx<R>*)V, ldV,
@@ -3031,7 +3053,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         if (rc) break;
         // results
-        if (cudaMemcpyAsync(hst.data(), sst, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(hst, sst, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             fail(vbk_cuda_fail(cudaGetLastError(), "result copy"));
             break;
@@ -3056,13 +3078,11 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         if (!all_ok) rc = VBK_ERR_NOT_CONVERGED;
     } while (0);
-    if (dE) cudaFreeAsync(dE, st);
     cudaFreeAsync(wsbase, st);
     if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
     cudaStreamSynchronize(st);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (pgexec) cudaGraphExecDestroy(pgexec);
-    if (hcnt) cudaFreeHost(hcnt);
     return rc;
 }
 
