@@ -247,13 +247,51 @@ int build(const vbk_model_desc* d, vbk_model* m) {
             pc[k * m->Nnu + nu] = c;
         }
     }
-    // one device allocation: entries | diagonal entries | tab64 | tab32 | pc64 | pc32
+    // descriptors and primary-mode coefficient rows of the one-block-per-system kernel
+    std::vector<int4> rdesc(std::max<size_t>(1, offd.size()), make_int4(0, 0, 0, -1));
+    std::vector<float> rct;
+    int rhalo = 0, rok = 1;
+    for (size_t k = 0; k < offd.size(); ++k) {
+        const DevEntry& e = offd[k].e;
+        const int d = offd[k].d;
+        int m1 = -1, m2 = 255, col2 = -1, nmodes = 0;
+        for (int mm = 0; mm < m->M; ++mm) {
+            if (e.col[mm] < 0) continue;
+            ++nmodes;
+            if (m1 < 0) {
+                m1 = mm;
+            } else if (m2 == 255) {
+                m2 = mm;
+                col2 = e.col[mm];
+            }
+        }
+        if (nmodes > 2) rok = 0;
+        const int mp = m1 < 0 ? 0 : m1;
+        const int off = (int)rct.size();
+        for (int n = 0; n < m->nb[mp]; ++n) {
+            double c = e.coef;
+            if (m1 >= 0) {
+                const int nn = n + e.delta[m1];
+                c = (nn >= 0 && nn < m->nb[m1]) ? c * m->tab[e.col[m1] + n] : 0.0;
+            }
+            rct.push_back((float)c);
+        }
+        const int poff = (e.dp - d) * m->Nnu + e.lin;
+        rdesc[k] = make_int4(mp | (m2 << 8), off, poff, col2);
+        rhalo = std::max(rhalo, std::max(-(d * m->Nnu + poff), (d + 1) * m->Nnu - 1 + poff - (m->N - 1)));
+    }
+    if (rct.empty()) rct.push_back(0.0f);
+    dm.nrct = (int)rct.size();
+    dm.rhalo = rhalo;
+    dm.rok = rok;
+    // one device allocation: entries | diagonal entries | tab64 | tab32 | pc64 | pc32 | rdesc | rct
     const size_t ne = std::max<size_t>(1, offd.size()), nd = std::max<size_t>(1, diagp.size()), nt = m->tab.size();
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b1 = al(ne * sizeof(DevEntry)), b2 = al(nd * sizeof(DevEntry)), b3 = al(nt * sizeof(double)),
-                 b4 = al(nt * sizeof(float)), b5 = al(npc * sizeof(double)), b6 = al(npc * sizeof(float));
+                 b4 = al(nt * sizeof(float)), b5 = al(npc * sizeof(double)), b6 = al(npc * sizeof(float)),
+                 b7 = al(rdesc.size() * sizeof(int4)), b8 = al(rct.size() * sizeof(float));
     char* mem = nullptr;
-    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6);
+    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8);
     if (err != cudaSuccess) return vbk_cuda_fail(err, "model tables");
     m->dev_mem = mem;
     std::vector<DevEntry> he(ne), hd(nd);
@@ -275,6 +313,14 @@ int build(const vbk_model_desc* d, vbk_model* m) {
             return vbk_cuda_fail(err, "model coefficient upload");
         dm.pc64 = (const double*)(mem + b1 + b2 + b3 + b4);
         dm.pc32 = (const float*)(mem + b1 + b2 + b3 + b4 + b5);
+    }
+    {
+        char* base = mem + b1 + b2 + b3 + b4 + b5 + b6;
+        if ((err = cudaMemcpy(base, rdesc.data(), rdesc.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(base + b7, rct.data(), rct.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return vbk_cuda_fail(err, "model descriptor upload");
+        dm.rdesc = (const int4*)base;
+        dm.rct = (const float*)(base + b7);
     }
     dm.ent = (const DevEntry*)mem;
     dm.dent = (const DevEntry*)(mem + b1);

@@ -126,6 +126,15 @@ struct DevModel {
     // (q_m^pow)_{n_m, n_m + delta_m}, zero where the neighbour leaves the basis (energy-independent)
     const double* pc64;
     const float* pc32;
+    // the same stencil for the one-block-per-system kernel: per point a descriptor
+    // (x: primary mode | secondary mode << 8 (255: none), y: offset of its coefficient row in
+    // rct, z: neighbour offset (dp - d) Nnu + lin, w: tab32 column of the secondary mode or -1)
+    // and rct[y + n] = coef (q^k)_{n, n + delta} of the primary mode (zero where it leaves the basis)
+    const int4* rdesc;
+    const float* rct;
+    int nrct;
+    int rhalo;   // largest distance a neighbour index falls outside [0, N)
+    int rok;     // 1 if no point involves more than two modes
     int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
     double ch_a[MAXCH], ch_b[MAXCH], ch_sb[MAXCH];  // ch_sb = sqrt(b)
     double ch_isb[MAXCH], ch_ib[MAXCH];            // 1 / sqrt(b), 1 / b

@@ -1653,6 +1653,14 @@ __global__ void __launch_bounds__(TPB) k_pp(int N, DList L, const SysState* __re
 // frees its SM for the next one.  The iteration count is bounded by max_iter.
 constexpr int RTPB = 1024;
 
+// n[m] for a runtime mode index m without dynamic register indexing
+template <int M> __device__ __forceinline__ int nsel(const int (&n)[MAXM], int m) {
+    int r = n[0];
+#pragma unroll
+    for (int k = 1; k < M; ++k) r = (m == k) ? n[k] : r;
+    return r;
+}
+
 template <int M>
 __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const int* __restrict__ sys_e,
                                                           const int* __restrict__ list, int pmode,
@@ -1662,13 +1670,12 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
                                                           SysState* __restrict__ st, int* __restrict__ act,
                                                           int* __restrict__ outer, int max_iter) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int N = md.N, Nnu = md.Nnu;
-    float2* P = reinterpret_cast<float2*>(smraw);
-    float2* Q = P + N;
+    const int N = md.N, Nnu = md.Nnu, H = md.rhalo;
+    float2* P = reinterpret_cast<float2*>(smraw) + H;  // p with H zero entries on either side
+    float2* Q = P + N + H;
     float* stab = reinterpret_cast<float*>(Q + N);
-    __shared__ float pcoef[MAXS][64];
-    __shared__ int poff[MAXS][64];
-    __shared__ short pcol[MAXS][64][MAXM];
+    float* sct = stab + md.ntab;
+    __shared__ int4 sdesc[MAXS][64];
     __shared__ int npt[MAXS];
     __shared__ float redA[RTPB / 32][3], redB[RTPB / 32][3];  // per-warp partials of the two reductions
     static_assert(RTPB == 1024, "one partial per lane in the final warp sums");
@@ -1678,16 +1685,12 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     const float2* dg = diag + (long long)sys_e[s] * N;
     const float2* di = dinv + (long long)sys_e[s] * N;
     for (int k = tid; k < md.ntab; k += RTPB) stab[k] = md.tab32[k];
+    for (int k = tid; k < md.nrct; k += RTPB) sct[k] = md.rct[k];
+    for (int k = tid; k < H; k += RTPB) P[-1 - k] = P[N + k] = make_float2(0.f, 0.f);
     for (int d = 0; d < md.ns; ++d) {
         const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, 64);
         if (tid == 0) npt[d] = np;
-        for (int k = tid; k < np; k += RTPB) {
-            const DevEntry& e = md.ent[pb + k];
-            pcoef[d][k] = (float)e.coef;
-            poff[d][k] = (e.dp - d) * Nnu + e.lin;
-#pragma unroll
-            for (int m = 0; m < MAXM; ++m) pcol[d][k][m] = (short)e.col[m];
-        }
+        for (int k = tid; k < np; k += RTPB) sdesc[d][k] = md.rdesc[pb + k];
     }
     // per-system scalars, kept identical in every thread: each reduction ends with one barrier
     // after which every warp sums the per-warp partials itself (no serial thread-0 section)
@@ -1750,15 +1753,13 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
             const float2 pi = P[i];
             float2 acc = cmul<float>(dg[i], pi);
             const int np = npt[d];
+            const int4* dsc = sdesc[d];
 #pragma unroll 4
             for (int k = 0; k < np; ++k) {
-                float c = pcoef[d][k];
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const int col = pcol[d][k][m];
-                    if (col >= 0) c *= stab[col + n[m]];
-                }
-                const float2 v = P[min(max(i + poff[d][k], 0), N - 1)];
+                const int4 q = dsc[k];
+                float c = sct[q.y + nsel<M>(n, q.x & 255)];
+                if (q.w >= 0) c *= stab[q.w + nsel<M>(n, q.x >> 8)];
+                const float2 v = P[i + q.z];  // neighbours outside [0, N) read the zero halo
                 acc.x = fmaf(-c, v.x, acc.x);
                 acc.y = fmaf(-c, v.y, acc.y);
             }
@@ -1836,10 +1837,13 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     }
 }
 
-// shared memory of the resident kernel: p, q and the oscillator tables (FP32)
-inline size_t resident_smem(const DevModel& md) { return (size_t)2 * md.N * sizeof(float2) + (size_t)md.ntab * sizeof(float) + 16; }
+// shared memory of the resident kernel: p (with its halo), q, the oscillator tables and the
+// primary-mode coefficient rows (FP32)
+inline size_t resident_smem(const DevModel& md) {
+    return (size_t)(2 * md.N + 2 * md.rhalo) * sizeof(float2) + (size_t)(md.ntab + md.nrct) * sizeof(float) + 16;
+}
 inline bool resident_ok(const DevModel& md) {
-    if (resident_smem(md) > 220 * 1024) return false;
+    if (!md.rok || resident_smem(md) > 220 * 1024) return false;
     for (int d = 0; d < md.ns; ++d)
         if (md.ebeg[d + 1] - md.ebeg[d] > 64) return false;
     return true;
