@@ -197,41 +197,55 @@ inline void* vbk_pinned(vbk_model* m, size_t bytes) {
 }
 
 // --------------------------------------------------------------------------- level shift
-// Dawson's integral D(x) = exp(-x^2) int_0^x exp(t^2) dt.  Taylor series for |x| < 0.5;
-// otherwise Rybicki's sampling-theorem method (G. B. Rybicki, Computers in Physics 3, 85
-// (1989)): D(x) = lim_{h->0} pi^-1/2 sum_{n odd} exp(-(x - n h)^2) / n, here with h = 1/4
-// (aliasing error ~exp(-(pi/2h)^2) ~ 1e-17), the sum centred on the even integer n0 nearest
-// x/h and the Gaussian factors generated by exact multiplicative recurrences.
+// Dawson's integral D(x) = exp(-x^2) int_0^x exp(t^2) dt, odd in x.  |x| < 1/2: Taylor series
+// D(x) = x sum_k (-2 x^2)^k / (2k + 1)!!, 14 terms (truncation below 1e-16); 1/2 <= |x| < 16:
+// piecewise degree-12 polynomials on intervals of width 1/2 (interpolation at Chebyshev points,
+// coefficients computed in 40-digit arithmetic by gen_erfcx_table.py; relative error ~3e-15);
+// from 16: the asymptotic series D(x) = 1/(2x) sum_k (2k - 1)!! / (2 x^2)^k, 9 terms.
+static __device__ const double vbk_dawson_c_dev[VBK_ERFCX_NINT * (VBK_ERFCX_DEG + 1)] = {VBK_DAWSON_COEFFS};
+static const double vbk_dawson_c_host[VBK_ERFCX_NINT * (VBK_ERFCX_DEG + 1)] = {VBK_DAWSON_COEFFS};
 __host__ __device__ inline double vbk_dawson(double x) {
-    double ax = fabs(x);
+    const double ax = fabs(x);
     double r;
     if (ax < 0.5) {
-        double x2 = ax * ax, term = ax, sum = ax;
-        for (int k = 1; k < 22; ++k) {
-            term *= -2.0 * x2 / (2.0 * k + 1.0);
+        const double u = ax * ax;
+        // (-2)^k / (2k + 1)!!, k = 0..13 (quotients of exact constants, folded at compile time)
+        const double cs[14] = {1.0,
+                               -2.0 / 3.0,
+                               4.0 / 15.0,
+                               -8.0 / 105.0,
+                               16.0 / 945.0,
+                               -32.0 / 10395.0,
+                               64.0 / 135135.0,
+                               -128.0 / 2027025.0,
+                               256.0 / 34459425.0,
+                               -512.0 / 654729075.0,
+                               1024.0 / 13749310575.0,
+                               -2048.0 / 316234143225.0,
+                               4096.0 / 7905853580625.0,
+                               -8192.0 / 213458046676875.0};
+        r = cs[13];
+        for (int k = 12; k >= 0; --k) r = fma(r, u, cs[k]);
+        r *= ax;
+    } else if (ax < 0.5 * VBK_ERFCX_NINT) {
+#ifdef __CUDA_ARCH__
+        const double* C = vbk_dawson_c_dev;
+#else
+        const double* C = vbk_dawson_c_host;
+#endif
+        const int k = (int)(2.0 * ax);
+        const double t = 4.0 * ax - (double)(2 * k + 1);
+        const double* c = C + k * (VBK_ERFCX_DEG + 1);
+        r = c[VBK_ERFCX_DEG];
+        for (int p = VBK_ERFCX_DEG - 1; p >= 0; --p) r = fma(r, t, c[p]);
+    } else {
+        const double u = 0.5 / (ax * ax);
+        double sum = 1.0, term = 1.0;
+        for (int k = 1; k <= 8; ++k) {
+            term *= (2.0 * k - 1.0) * u;
             sum += term;
         }
-        r = sum;
-    } else {
-        const double h = 0.25;
-        double n0 = 2.0 * rint(0.5 * ax / h);
-        double xp = ax - n0 * h;           // |xp| <= h
-        double e1 = exp(2.0 * xp * h);     // exp(2 xp h)
-        double e2 = e1 * e1, ie1 = 1.0 / e1, ie2 = ie1 * ie1;
-        double pk = e1, qk = ie1;          // exp(+-2 xp h (2k-1))
-        double ck = 0.93941306281347581;   // exp(-h^2)          = exp(-(2k-1)^2 h^2), k = 1
-        double rk = 0.60653065971263342;   // exp(-8 h^2 k), k=1 = exp(-1/2)
-        const double q = 0.60653065971263342;
-        double sum = 0.0;
-        for (int k = 1; k <= 14; ++k) {
-            double odd = 2.0 * k - 1.0;
-            sum += ck * (pk / (n0 + odd) + qk / (n0 - odd));
-            pk *= e2;
-            qk *= ie2;
-            ck *= rk;   // c_{k+1} = c_k exp(-8 k h^2)
-            rk *= q;
-        }
-        r = exp(-xp * xp) * sum * 0.56418958354775628;  // 1/sqrt(pi)
+        r = 0.5 / ax * sum;
     }
     return x < 0 ? -r : r;
 }
