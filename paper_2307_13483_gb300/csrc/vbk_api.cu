@@ -247,40 +247,51 @@ int build(const vbk_model_desc* d, vbk_model* m) {
             pc[k * m->Nnu + nu] = c;
         }
     }
-    // descriptors and primary-mode coefficient rows of the one-block-per-system kernel
-    std::vector<int4> rdesc(std::max<size_t>(1, offd.size()), make_int4(0, 0, 0, -1));
-    std::vector<float> rct;
+    // descriptors and primary-mode coefficient rows of the one-block-per-system kernel, the
+    // points of each state grouped by primary mode
+    std::vector<int4> rdesc;
+    std::vector<float2> rct;
     int rhalo = 0, rok = 1;
-    for (size_t k = 0; k < offd.size(); ++k) {
-        const DevEntry& e = offd[k].e;
-        const int d = offd[k].d;
-        int m1 = -1, m2 = 255, col2 = -1, nmodes = 0;
-        for (int mm = 0; mm < m->M; ++mm) {
-            if (e.col[mm] < 0) continue;
-            ++nmodes;
-            if (m1 < 0) {
-                m1 = mm;
-            } else if (m2 == 255) {
-                m2 = mm;
-                col2 = e.col[mm];
+    for (int d = 0; d < m->ns; ++d) {
+        dm.rbeg[d] = (int)rdesc.size();
+        for (int mg = 0; mg < MAXM; ++mg) dm.rcnt[d][mg] = 0;
+        for (int mg = 0; mg < m->M; ++mg)
+            for (size_t k = 0; k < offd.size(); ++k) {
+                if (offd[k].d != d) continue;
+                const DevEntry& e = offd[k].e;
+                int m1 = -1, m2 = 0, col2 = -1, nmodes = 0;
+                for (int mm = 0; mm < m->M; ++mm) {
+                    if (e.col[mm] < 0) continue;
+                    ++nmodes;
+                    if (m1 < 0) {
+                        m1 = mm;
+                    } else if (col2 < 0) {
+                        m2 = mm;
+                        col2 = e.col[mm];
+                    }
+                }
+                if ((m1 < 0 ? 0 : m1) != mg) continue;
+                if (nmodes > 2) rok = 0;
+                const int off = (int)rct.size();
+                for (int n = 0; n < m->nb[mg]; ++n) {
+                    double c = e.coef;
+                    if (m1 >= 0) {
+                        const int nn = n + e.delta[m1];
+                        c = (nn >= 0 && nn < m->nb[m1]) ? c * m->tab[e.col[m1] + n] : 0.0;
+                    }
+                    rct.push_back(make_float2((float)-c, (float)-c));
+                }
+                const int poff = (e.dp - d) * m->Nnu + e.lin;
+                rdesc.push_back(make_int4(off * 8, poff * 8, col2, m2));
+                dm.rcnt[d][mg] += 1;
+                rhalo = std::max(rhalo, std::max(-(d * m->Nnu + poff), (d + 1) * m->Nnu - 1 + poff - (m->N - 1)));
             }
-        }
-        if (nmodes > 2) rok = 0;
-        const int mp = m1 < 0 ? 0 : m1;
-        const int off = (int)rct.size();
-        for (int n = 0; n < m->nb[mp]; ++n) {
-            double c = e.coef;
-            if (m1 >= 0) {
-                const int nn = n + e.delta[m1];
-                c = (nn >= 0 && nn < m->nb[m1]) ? c * m->tab[e.col[m1] + n] : 0.0;
-            }
-            rct.push_back((float)c);
-        }
-        const int poff = (e.dp - d) * m->Nnu + e.lin;
-        rdesc[k] = make_int4(mp | (m2 << 8), off, poff, col2);
-        rhalo = std::max(rhalo, std::max(-(d * m->Nnu + poff), (d + 1) * m->Nnu - 1 + poff - (m->N - 1)));
+        if ((int)rdesc.size() - dm.rbeg[d] > 64) rok = 0;
     }
-    if (rct.empty()) rct.push_back(0.0f);
+    dm.rbeg[m->ns] = (int)rdesc.size();
+    if (rdesc.empty()) rdesc.push_back(make_int4(0, 0, -1, 0));
+    if (rct.empty()) rct.push_back(make_float2(0.f, 0.f));
+    if (rdesc.size() > (size_t)MAXS * 64) rok = 0;
     dm.nrct = (int)rct.size();
     dm.rhalo = rhalo;
     dm.rok = rok;
@@ -289,9 +300,10 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b1 = al(ne * sizeof(DevEntry)), b2 = al(nd * sizeof(DevEntry)), b3 = al(nt * sizeof(double)),
                  b4 = al(nt * sizeof(float)), b5 = al(npc * sizeof(double)), b6 = al(npc * sizeof(float)),
-                 b7 = al(rdesc.size() * sizeof(int4)), b8 = al(rct.size() * sizeof(float));
+                 b7 = al(rdesc.size() * sizeof(int4)), b8 = al(rct.size() * sizeof(float2)),
+                 b9 = al(npc * sizeof(float2));
     char* mem = nullptr;
-    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8);
+    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8 + b9);
     if (err != cudaSuccess) return vbk_cuda_fail(err, "model tables");
     m->dev_mem = mem;
     std::vector<DevEntry> he(ne), hd(nd);
@@ -317,10 +329,18 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     {
         char* base = mem + b1 + b2 + b3 + b4 + b5 + b6;
         if ((err = cudaMemcpy(base, rdesc.data(), rdesc.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (err = cudaMemcpy(base + b7, rct.data(), rct.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+            (err = cudaMemcpy(base + b7, rct.data(), rct.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
             return vbk_cuda_fail(err, "model descriptor upload");
         dm.rdesc = (const int4*)base;
-        dm.rct = (const float*)(base + b7);
+        dm.rct = (const float2*)(base + b7);
+        std::vector<float2> pcs(npc);
+        for (size_t k = 0; k < npc; ++k) {
+            const float h = (float)pc[k];
+            pcs[k] = make_float2(h, (float)(pc[k] - (double)h));
+        }
+        if ((err = cudaMemcpy(base + b7 + b8, pcs.data(), npc * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return vbk_cuda_fail(err, "model coefficient upload");
+        dm.pcs = (const float2*)(base + b7 + b8);
     }
     dm.ent = (const DevEntry*)mem;
     dm.dent = (const DevEntry*)(mem + b1);

@@ -126,15 +126,20 @@ struct DevModel {
     // (q_m^pow)_{n_m, n_m + delta_m}, zero where the neighbour leaves the basis (energy-independent)
     const double* pc64;
     const float* pc32;
-    // the same stencil for the one-block-per-system kernel: per point a descriptor
-    // (x: primary mode | secondary mode << 8 (255: none), y: offset of its coefficient row in
-    // rct, z: neighbour offset (dp - d) Nnu + lin, w: tab32 column of the secondary mode or -1)
-    // and rct[y + n] = coef (q^k)_{n, n + delta} of the primary mode (zero where it leaves the basis)
+    const float2* pcs;  // the same columns as double-float pairs (hi = (float)c, lo = (float)(c - hi))
+    // the same stencil for the one-block-per-system kernel, points of state d grouped by their
+    // primary mode m (rbeg[d] + sum of rcnt[d][< m] ...): per point a descriptor (x: byte offset
+    // of its coefficient row in rct, y: byte offset (8 ((dp - d) Nnu + lin)) of the neighbour,
+    // z: tab32 column of a secondary mode or -1, w: that mode) and the row
+    // rct[x / 8 + n] = -(coef (q^k)_{n, n + delta}) twice (a packed pair; zero where the neighbour
+    // leaves the basis), n the primary-mode index
     const int4* rdesc;
-    const float* rct;
+    const float2* rct;
     int nrct;
+    int rbeg[MAXS + 1];
+    int rcnt[MAXS][MAXM];
     int rhalo;   // largest distance a neighbour index falls outside [0, N)
-    int rok;     // 1 if no point involves more than two modes
+    int rok;     // 1 if no point involves more than two modes and no state more than 64 points
     int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
     double ch_a[MAXCH], ch_b[MAXCH], ch_sb[MAXCH];  // ch_sb = sqrt(b)
     double ch_isb[MAXCH], ch_ib[MAXCH];            // 1 / sqrt(b), 1 / b

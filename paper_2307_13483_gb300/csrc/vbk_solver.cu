@@ -130,7 +130,7 @@ __device__ __forceinline__ bool point_coef(const DevEntry& en, const int (&n)[MA
 // FP32 copy for the inner iterations.
 template <int M>
 __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, double2* __restrict__ d64,
-                             float2* __restrict__ d32, float2* __restrict__ dinv32) {
+                             float2* __restrict__ d32, float2* __restrict__ dinv32, float4* __restrict__ dsp) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nE * md.N) return;
     const int e = (int)(t / md.N), i = (int)(t - (long long)e * md.N);
@@ -155,7 +155,11 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
         re -= F.x;
         im -= F.y;
     }
-    d64[t] = make_double2(re, im);
+    if (d64) d64[t] = make_double2(re, im);
+    if (dsp) {  // double-float pair (hi, lo) of the FP64 value for the double-float residual
+        const float hr = (float)re, hi = (float)im;
+        dsp[t] = make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+    }
     if (d32) {
         const float2 f = make_float2((float)re, (float)im);
         d32[t] = f;
@@ -1113,8 +1117,10 @@ __global__ void __launch_bounds__(TPB) k_rhs_norm(int N, const double2* __restri
     float acc = 0.f;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const double2 v = bs[i];
-        const float fx = (float)v.x, fy = (float)v.y;
-        acc = fmaf(fx, fx, fmaf(fy, fy, acc));
+        if ((__double_as_longlong(v.x) | __double_as_longlong(v.y)) != 0) {  // b is mostly zero
+            const float fx = (float)v.x, fy = (float)v.y;
+            acc = fmaf(fx, fx, fmaf(fy, fy, acc));
+        }
     }
     const double2 tot = block_sum_c<float>(make_float2(acc, 0.f), sh);
     if (threadIdx.x == 0) part[s] = tot;
@@ -1651,7 +1657,160 @@ __global__ void __launch_bounds__(TPB) k_pp(int N, DList L, const SysState* __re
 // (L2-resident for the systems in flight), and the scalars come from block reductions.  No
 // grid-wide synchronisation is needed because the systems are independent; a converged system
 // frees its SM for the next one.  The iteration count is bounded by max_iter.
+// ------------------------------------------------------------------ double-float arithmetic
+// Unevaluated sums hi + lo of two floats (Dekker 1971 products with a fused multiply-add;
+// Knuth's TwoSum): the residual b - A x of the FP32 refinement path is formed with ~48-bit
+// significands on the FP32 pipes, which GB300 runs ~64x faster than its FP64 pipe.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// (sh, sl) += (ah + al) (xh + xl), the al xl term (~2^-48 relative) dropped
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float xh, float xl) {
+    const float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);
+    e = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
+    float sum, t;
+    df_two_sum(sh, p, sum, t);
+    sh = sum;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+// renormalised pair (s, l) with s = fl(h + l)
+__device__ __forceinline__ float2 df_norm(float h, float l) {
+    const float sum = __fadd_rn(h, l);
+    return make_float2(sum, __fsub_rn(l, __fsub_rn(sum, h)));
+}
+
+// r = b - A x for the FP32 refinement path in double-float arithmetic.  x, r and the diagonal
+// are (re hi, im hi, re lo, im lo) quadruples, b is FP64 (split where nonzero); the energy-independent stencil
+// coefficients come as (hi, lo) pairs.  Register blocking as in k_matvec3 (S systems x EPT
+// consecutive elements per thread, coefficients loaded once for the S systems); one
+// ||r||^2 partial (of the hi parts, FP32) per thread block and system.
+template <int S, int EPT>
+__global__ void __launch_bounds__(TPB) k_residual_df(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
+                                                    const float4* __restrict__ dsp, const float4* __restrict__ xs,
+                                                    const double2* __restrict__ b64, float4* __restrict__ rs,
+                                                    double2* __restrict__ part) {
+    __shared__ int offs[MV_MAXPTS];
+    __shared__ float redsh[TPB / 32][S];
+    constexpr int T = TPB * EPT;
+    const int Nnu = md.Nnu, N = md.N;
+    const int nchunk = (Nnu + T - 1) / T;
+    const int d = blockIdx.x / nchunk;
+    const int nu0 = (blockIdx.x - d * nchunk) * T + threadIdx.x * EPT;
+    const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const DevEntry& e = md.ent[pb + k];
+        offs[k] = (e.dp - d) * Nnu + e.lin;
+    }
+    int sy[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const int li = blockIdx.y * S + t;
+        int s = -1;
+        if (li < nlist) {
+            s = sel.list ? sel.list[li] : li;
+            if (s >= 0 && sel.act && !sel.act[s]) s = -1;
+        }
+        sy[t] = s;
+    }
+    __syncthreads();
+    const int nv = min(EPT, Nnu - nu0);
+    const int i0 = d * Nnu + nu0;
+    float rh[S][EPT], rl[S][EPT], ih[S][EPT], il[S][EPT];  // r = (rh + rl) + i (ih + il)
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const long long so = (long long)(sy[t] < 0 ? 0 : sy[t]) * N;
+        const float4* dg = dsp + (long long)sys_e[sy[t] < 0 ? 0 : sy[t]] * N;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            rh[t][e] = rl[t][e] = ih[t][e] = il[t][e] = 0.f;
+            if (sy[t] >= 0 && e < nv) {
+                const float4 x = xs[so + i0 + e], g = dg[i0 + e];
+                const double2 b = b64[so + i0 + e];
+                if ((__double_as_longlong(b.x) | __double_as_longlong(b.y)) != 0) {  // b is mostly zero
+                    rh[t][e] = (float)b.x;
+                    ih[t][e] = (float)b.y;
+                    rl[t][e] = (float)(b.x - (double)rh[t][e]);
+                    il[t][e] = (float)(b.y - (double)ih[t][e]);
+                }
+                df_fma(rh[t][e], rl[t][e], -g.x, -g.z, x.x, x.z);
+                df_fma(rh[t][e], rl[t][e], g.y, g.w, x.y, x.w);
+                df_fma(ih[t][e], il[t][e], -g.x, -g.z, x.y, x.w);
+                df_fma(ih[t][e], il[t][e], -g.y, -g.w, x.x, x.z);
+            }
+        }
+    }
+    if (nv > 0) {
+        const float2* pc = md.pcs + (long long)pb * Nnu + nu0;
+        for (int k = 0; k < np; ++k) {
+            float2 c[EPT];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) c[e] = e < nv ? __ldg(pc + (long long)k * Nnu + e) : make_float2(0.f, 0.f);
+            const int j0 = i0 + offs[k];
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                const float4* xb = xs + (long long)(sy[t] < 0 ? 0 : sy[t]) * N;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    const float4 v = xb[min(max(j0 + e, 0), N - 1)];  // zero coefficient outside the basis
+                    df_fma(rh[t][e], rl[t][e], c[e].x, c[e].y, v.x, v.z);
+                    df_fma(ih[t][e], il[t][e], c[e].x, c[e].y, v.y, v.w);
+                }
+            }
+        }
+    }
+    float loc[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        loc[t] = 0.f;
+        if (sy[t] < 0) continue;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            if (e >= nv) continue;
+            const float2 re = df_norm(rh[t][e], rl[t][e]), im = df_norm(ih[t][e], il[t][e]);
+            rs[(long long)sy[t] * N + i0 + e] = make_float4(re.x, im.x, re.y, im.y);
+            loc[t] = fmaf(re.x, re.x, fmaf(im.x, im.x, loc[t]));
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        float v = loc[t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) redsh[w][t] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < S && sy[threadIdx.x] >= 0) {
+        float tot = 0.f;
+        for (int q = 0; q < TPB / 32; ++q) tot += redsh[q][threadIdx.x];
+        part[(long long)sy[threadIdx.x] * gridDim.x + blockIdx.x] = make_double2((double)tot, 0.0);
+    }
+}
+constexpr int DF_S = 2, DF_EPT = 4;
+inline int df_partials(const DevModel& md) { return md.ns * ((md.Nnu + TPB * DF_EPT - 1) / (TPB * DF_EPT)); }
+
+// x64 = hi + lo of the double-float solution (every system)
+__global__ void __launch_bounds__(TPB) k_df_out(long long n, const float4* __restrict__ xs, double2* __restrict__ x64) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = xs[i];
+    x64[i] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+}
+
 constexpr int RTPB = 1024;
+
+// a * b + c on both halves of a float pair with one packed FP32x2 instruction
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+          "l"(*reinterpret_cast<unsigned long long*>(&c)));
+    return *reinterpret_cast<float2*>(&r);
+}
 
 // n[m] for a runtime mode index m without dynamic register indexing
 template <int M> __device__ __forceinline__ int nsel(const int (&n)[MAXM], int m) {
@@ -1666,17 +1825,16 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
                                                           const int* __restrict__ list, int pmode,
                                                           const float2* __restrict__ diag, const float2* __restrict__ dinv,
                                                           float2* __restrict__ x, float2* __restrict__ r,
-                                                          const double2* __restrict__ res, double2* __restrict__ x64,
+                                                          const double2* __restrict__ res_d, const float4* __restrict__ res_s,
+                                                          float4* __restrict__ xs,
                                                           SysState* __restrict__ st, int* __restrict__ act,
                                                           int* __restrict__ outer, int max_iter) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int N = md.N, Nnu = md.Nnu, H = md.rhalo;
+    const int N = md.N, H = md.rhalo;
     float2* P = reinterpret_cast<float2*>(smraw) + H;  // p with H zero entries on either side
     float2* Q = P + N + H;
-    float* stab = reinterpret_cast<float*>(Q + N);
-    float* sct = stab + md.ntab;
-    __shared__ int4 sdesc[MAXS][64];
-    __shared__ int npt[MAXS];
+    float2* sct = Q + N;                                 // coefficient rows (packed pairs)
+    __shared__ int4 sdesc[MAXS * 64];
     __shared__ float redA[RTPB / 32][3], redB[RTPB / 32][3];  // per-warp partials of the two reductions
     static_assert(RTPB == 1024, "one partial per lane in the final warp sums");
     const int s = list[blockIdx.x];
@@ -1684,19 +1842,14 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     const long long so = (long long)s * N;
     const float2* dg = diag + (long long)sys_e[s] * N;
     const float2* di = dinv + (long long)sys_e[s] * N;
-    for (int k = tid; k < md.ntab; k += RTPB) stab[k] = md.tab32[k];
     for (int k = tid; k < md.nrct; k += RTPB) sct[k] = md.rct[k];
     for (int k = tid; k < H; k += RTPB) P[-1 - k] = P[N + k] = make_float2(0.f, 0.f);
-    for (int d = 0; d < md.ns; ++d) {
-        const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, 64);
-        if (tid == 0) npt[d] = np;
-        for (int k = tid; k < np; k += RTPB) sdesc[d][k] = md.rdesc[pb + k];
-    }
+    for (int k = tid; k < md.rbeg[md.ns]; k += RTPB) sdesc[k] = md.rdesc[k];
     // per-system scalars, kept identical in every thread: each reduction ends with one barrier
     // after which every warp sums the per-warp partials itself (no serial thread-0 section)
-    const SysState S0 = st[s];
-    const float target2 = (float)(S0.target * S0.target);
-    int iters = S0.iters;
+    // (fields read where they are needed: nothing of the state stays live across the loop)
+    const float target2 = (float)(st[s].target * st[s].target);
+    int iters = st[s].iters;
     float rr = 0.f;
     int status = -1;  // -1: stopped normally (the FP64 residual decides)
     __syncthreads();
@@ -1723,15 +1876,22 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
         }
         return t;
     };
-    // start of the inner solve: r = (b - A x64) / scale in FP32 (narrowed first, scaled in
-    // FP32), x = 0, z = B^-1 r, p = z, rho = r^T z
+    // start of the inner solve: r = (b - A x) / scale in FP32 (the hi part of the double-float
+    // residual, scaled in FP32), x = 0, z = B^-1 r, p = z, rho = r^T z
     float2 rho, beta = make_float2(0.f, 0.f);
     {
-        const float inv = (float)S0.inv_scale;
+        const float inv = (float)st[s].inv_scale;
         float rz_x = 0.f, rz_y = 0.f;
         for (int i = tid; i < N; i += RTPB) {
-            const double2 v = res[so + i];
-            const float2 rn = make_float2((float)v.x * inv, (float)v.y * inv);
+            float2 rn = make_float2(0.f, 0.f);
+            if (res_d) {  // the first residual: b (FP64, mostly zero)
+                const double2 v = res_d[so + i];
+                if ((__double_as_longlong(v.x) | __double_as_longlong(v.y)) != 0)
+                    rn = make_float2((float)v.x * inv, (float)v.y * inv);
+            } else {
+                const float4 v = res_s[so + i];
+                rn = make_float2(v.x * inv, v.y * inv);
+            }
             r[so + i] = rn;
             const float2 zi = pmode == 0 ? cmul<float>(rn, di[i]) : rn;
             P[i] = zi;
@@ -1747,21 +1907,29 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
         // q = A p and p^T q
         float pq_x = 0.f, pq_y = 0.f;
         for (int i = tid; i < N; i += RTPB) {
-            const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * Nnu;
+            const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * md.Nnu;
             int n[MAXM];
             decode<M>(md, nu, n);
             const float2 pi = P[i];
             float2 acc = cmul<float>(dg[i], pi);
-            const int np = npt[d];
-            const int4* dsc = sdesc[d];
+            const char* Pi = reinterpret_cast<const char*>(P + i);
+            int k = md.rbeg[d];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {  // points grouped by primary mode: no per-point mode select
+                const int kend = k + md.rcnt[d][m];
+                const char* row = reinterpret_cast<const char*>(sct) + n[m] * 8;
 #pragma unroll 4
-            for (int k = 0; k < np; ++k) {
-                const int4 q = dsc[k];
-                float c = sct[q.y + nsel<M>(n, q.x & 255)];
-                if (q.w >= 0) c *= stab[q.w + nsel<M>(n, q.x >> 8)];
-                const float2 v = P[i + q.z];  // neighbours outside [0, N) read the zero halo
-                acc.x = fmaf(-c, v.x, acc.x);
-                acc.y = fmaf(-c, v.y, acc.y);
+                for (; k < kend; ++k) {
+                    const int4 q = sdesc[k];
+                    float2 cc = *reinterpret_cast<const float2*>(row + q.x);  // (-c, -c)
+                    if (q.z >= 0) {
+                        const float t = md.tab32[q.z + nsel<M>(n, q.w)];
+                        cc.x *= t;
+                        cc.y *= t;
+                    }
+                    // neighbours outside [0, N) read the zero halo
+                    acc = ffma2(cc, *reinterpret_cast<const float2*>(Pi + q.y), acc);
+                }
             }
             Q[i] = acc;
             pq_x += pi.x * acc.x - pi.y * acc.y;
@@ -1811,20 +1979,23 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
         }
         __syncthreads();
     }
-    // the correction of this refinement step: x64 += scale x (each thread its own elements)
+    // the correction of this refinement step: x += scale d in double-float (each thread its own
+    // elements; scale split once into hi + lo floats)
     if (wrote_x) {
-        const double sc = S0.scale;
+        const double sc = st[s].scale;
+        const float sh = (float)sc, sl = (float)(sc - (double)sh);
         for (int i = tid; i < N; i += RTPB) {
-            const float2 xv = x[so + i];
-            double2 X = x64[so + i];
-            X.x += sc * (double)xv.x;
-            X.y += sc * (double)xv.y;
-            x64[so + i] = X;
+            const float2 dv = x[so + i];
+            float4 X = xs[so + i];
+            df_fma(X.x, X.z, sh, sl, dv.x, 0.f);
+            df_fma(X.y, X.w, sh, sl, dv.y, 0.f);
+            const float2 re = df_norm(X.x, X.z), im = df_norm(X.y, X.w);
+            xs[so + i] = make_float4(re.x, im.x, re.y, im.y);
         }
     }
     if (tid == 0) {
         SysState& S = st[s];
-        S.cycle_iters += iters - S0.iters;
+        S.cycle_iters += iters - S.iters;
         S.iters = iters;
         S.inres = sqrt((double)rr);
         S.rho = make_double2(rho.x, rho.y);
@@ -1840,7 +2011,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
 // shared memory of the resident kernel: p (with its halo), q, the oscillator tables and the
 // primary-mode coefficient rows (FP32)
 inline size_t resident_smem(const DevModel& md) {
-    return (size_t)(2 * md.N + 2 * md.rhalo) * sizeof(float2) + (size_t)(md.ntab + md.nrct) * sizeof(float) + 16;
+    return (size_t)(2 * md.N + 2 * md.rhalo + md.nrct) * sizeof(float2) + 16;
 }
 inline bool resident_ok(const DevModel& md) {
     if (!md.rok || resident_smem(md) > 220 * 1024) return false;
@@ -2543,6 +2714,10 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         cudaGetLastError();
         resident = false;
     }
+    // The resident FP32 path refines in double-float arithmetic: the solution accumulates as
+    // (hi, lo) float pairs and b - A x is formed on the FP32 pipes (k_residual_df); psi is
+    // converted to FP64 once at the end.
+    const bool dfr = resident;
 
     // ---- workspace
     const size_t NN = (size_t)N;
@@ -2554,7 +2729,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     const int nb_b = block ? block_partials(pbuf) : 0;
     const int nslot = std::max(std::max(nb_e, nb_mv_max), std::max(nb_b, nb_v * (mres + 1)));
     size_t bytes = 0;
-    bytes += carve_size<double2>((size_t)nE * NN);                    // diag64
+    bytes += carve_size<double2>(dfr ? 1 : (size_t)nE * NN);         // diag64 (diagonal split in df mode)
+    if (dfr) bytes += carve_size<float4>((size_t)nE * NN) + 2 * carve_size<float4>((size_t)nsys * NN);  // dsp, xs, rs
     bytes += carve_size<cx<R>>(mixed ? (size_t)nE * NN : 1);          // diagR
     bytes += carve_size<float2>(mixed ? (size_t)nE * NN : 1);         // 1/diag (FP32)
     bytes += carve_size<double2>((size_t)nsys * NN);                  // r64
@@ -2587,7 +2763,13 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
     }
     char* p = wsbase;
-    double2* diag64 = carve<double2>(p, (size_t)nE * NN);
+    double2* diag64 = carve<double2>(p, dfr ? 1 : (size_t)nE * NN);
+    float4 *dsp = nullptr, *xs = nullptr, *rsp = nullptr;
+    if (dfr) {
+        dsp = carve<float4>(p, (size_t)nE * NN);
+        xs = carve<float4>(p, (size_t)nsys * NN);
+        rsp = carve<float4>(p, (size_t)nsys * NN);
+    }
     cx<R>* diagR = carve<cx<R>>(p, mixed ? (size_t)nE * NN : 1);
     if (!mixed) diagR = reinterpret_cast<cx<R>*>(diag64);
     float2* dinvR = carve<float2>(p, mixed ? (size_t)nE * NN : 1);
@@ -2665,7 +2847,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         if (cudaMemcpyAsync(smallp, hp + o_stage, small_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemsetAsync(sst, 0, nsys * sizeof(SysState), st) != cudaSuccess ||
-            cudaMemsetAsync(job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) != cudaSuccess ||
+            cudaMemsetAsync(dfr ? (void*)xs : (void*)job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) != cudaSuccess ||
             cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(done, 0, nsys * sizeof(int), st) != cudaSuccess) {
             fail(vbk_cuda_fail(cudaGetLastError(), "solver set-up copies"));
@@ -2673,7 +2855,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         // energy tables (FP64 + inner-precision copy)
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), md, nE, (const double*)dE,
-              diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR);
+              dfr ? (double2*)nullptr : diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR, dsp);
         if (block) factor_blocks<R, M>(rn, md, pbuf, nE, (const cx<R>*)diagR, F, pfail);
         if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) {
             fail(vbk_cuda_fail(ce, "set-up kernels"));
@@ -2706,6 +2888,10 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             // inner solve reads b directly
             if (it == 0)
                 rn.go("rhs_norm", k_rhs_norm, dim3(nsys), dim3(TPB), N, job.b64, partA);
+            else if (dfr)
+                rn.go("residual_df", k_residual_df<DF_S, DF_EPT>,
+                      dim3(df_partials(md), cdiv_u(n_out, DF_S)), dim3(TPB), md, (const int*)sys_e, so, (int)n_out,
+                      (const float4*)dsp, (const float4*)xs, job.b64, rsp, partA);
             else
             {
                 if (tune && mdl->mv_variant[1] < 0) {
@@ -2725,7 +2911,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cudaMemsetAsync(olist, 0xff, nsys * sizeof(int), st);  // -1: no system
             cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
-                  it == 0 ? 1 : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
+                  it == 0 ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
                   it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
             cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -2740,12 +2926,13 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
 
             const double2* res = it == 0 ? job.b64 : (const double2*)r64;  // the current FP64 residual
             if (method == VBK_COCG && resident && !block) {
-                // one CTA per system runs the whole inner solve: scaled residual in, FP64
-                // correction out (list = ilist from the outer check)
+                // one CTA per system runs the whole inner solve: scaled double-float residual in,
+                // double-float correction out (list = ilist from the outer check)
                 rn.go_smem("cocg_resident", k_cocg_resident<M>, dim3(n_in), dim3(RTPB), resident_smem(md), md,
                            (const int*)sys_e, (const int*)ilist, pmode, reinterpret_cast<const float2*>(diagR),
-                           (const float2*)dinvR, reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), res, job.x64,
-                           sst, inner, outer, o.max_iter);
+                           (const float2*)dinvR, reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r),
+                           it == 0 ? job.b64 : (const double2*)nullptr, (const float4*)rsp, xs, sst, inner, outer,
+                           o.max_iter);
             } else if (method == VBK_COCG) {
                 // r = rhs, x = 0, z = B^-1 r, p = z, rho = r^T z.  With a block preconditioner the
                 // search direction carries over from the previous inner solve (k_cocg_start):
@@ -3056,6 +3243,9 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             }
         }
         if (rc) break;
+        if (dfr)
+            rn.go("df_out", k_df_out, dim3(cdiv_u((long long)nsys * N, TPB)), dim3(TPB), (long long)nsys * N, (const float4*)xs,
+                  job.x64);
         // results
         if (cudaMemcpyAsync(hst, sst, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
@@ -3200,7 +3390,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
         rc = vbk_cuda_fail(cudaGetLastError(), "operator set-up");
     } else {
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
-              mixed ? d32 : (float2*)nullptr, (float2*)nullptr);
+              mixed ? d32 : (float2*)nullptr, (float2*)nullptr, (float4*)nullptr);
         const dim3 ge(cdiv_u(N, TPB), (unsigned)nsys);
         if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
         if (op == 0) {
@@ -3337,7 +3527,7 @@ int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* 
         return vbk_cuda_fail(ce, "noalloc: copies into scratch");
     Runner rn{m, st, false, {}, {}};
     rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
-          (float2*)nullptr, (float2*)nullptr);
+          (float2*)nullptr, (float2*)nullptr, (float4*)nullptr);
     const Sel none{nullptr, nullptr};
     launch_matvec_v<double>(rn, 9, "matvec_fp64", m->dm, (const int*)se, none, (unsigned)nsys, (const double2*)d64, x,
                             (long long)N, y, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);
