@@ -387,7 +387,7 @@ struct SysState {
     int refines;     // FP64 residuals after the first
     int j;           // GMRES: steps in the current cycle
     int cycle_iters; // iterations in the current inner solve
-    int pad;
+    int last_cycle;  // iterations of the previous inner solve (orders the next launch)
 };
 
 // Internal solve over an explicit list of systems with dense FP64 right-hand sides.

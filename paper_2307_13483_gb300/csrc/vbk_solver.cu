@@ -1171,6 +1171,7 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
     S.inv_scale = 1.0 / rn;
     S.target = fmax(inner_tol, 0.3 * tol * S.bnorm / rn);
     S.j = 0;
+    S.last_cycle = S.cycle_iters;
     S.cycle_iters = 0;
     S.inres = 1.0;
     inner[s] = 1;
@@ -1180,6 +1181,31 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
 }
 
 // inner right-hand side r / ||r|| in the inner precision
+// Reorders the outer and inner lists of the next inner solve, longest expected solve first:
+// one CTA per system runs the whole inner solve in the resident kernel, and the hardware
+// starts CTAs in list order, so a long system started last leaves the other SMs idle.  Key:
+// iterations of the system's previous inner solve, then the system index (later first: in an
+// ascending energy grid, the higher energies with more open channels take longer), both
+// descending.  One CTA; rank by counting (the caller limits this to ORDER_MAX systems).
+constexpr int ORDER_MAX = 4096;
+__global__ void __launch_bounds__(1024) k_order_lists(int nsys, const SysState* __restrict__ st, const int* __restrict__ inner,
+                                                      int* __restrict__ olist, int* __restrict__ ilist) {
+    __shared__ int key[ORDER_MAX];
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) key[s] = inner[s] ? st[s].last_cycle : -1;
+    __syncthreads();
+    for (int s = threadIdx.x; s < nsys; s += blockDim.x) {
+        const int ks = key[s];
+        if (ks < 0) continue;
+        int pos = 0;
+        for (int t = 0; t < nsys; ++t) {
+            const int kt = key[t];
+            pos += (kt > ks) || (kt == ks && t > s);
+        }
+        olist[pos] = s;
+        ilist[pos] = s;
+    }
+}
+
 template <class R>
 __global__ void __launch_bounds__(TPB) k_inner_rhs(int N, Sel sel, const SysState* __restrict__ st,
                                                   const double2* __restrict__ r, cx<R>* __restrict__ out, long long os) {
@@ -2913,6 +2939,9 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
                   it == 0 ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
                   it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
+            if (resident && nsys <= ORDER_MAX)  // longest expected inner solve first (one CTA each)
+                rn.go("order_lists", k_order_lists, dim3(1), dim3(1024), nsys, (const SysState*)sst, (const int*)inner, olist,
+                      ilist);
             cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) {
                 fail(vbk_cuda_fail(cudaGetLastError(), "outer check"));
