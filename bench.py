@@ -163,6 +163,20 @@ def roofline(model_N, nmu, stats, timings, opts, peaks):
             "avg_launch_us": round(ms * 1e3 / launches, 2), "share_of_step": None}
 
 
+# ------------------------------------------------------------------------------ replicas
+def job_rate(t_step_ms, units_per_rank, world, dist=None, device="cpu"):
+    """Step time and whole-job throughput of `world` replicas.  Every rank solves its own copy
+    of the workload (the systems are independent: no data-path collective); the step time is
+    the maximum over ranks, and value = world * units / time."""
+    if dist is not None and world > 1:
+        import torch
+
+        tt = torch.tensor([float(t_step_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step_ms = float(tt.item())
+    return t_step_ms, world * units_per_rank / (t_step_ms * 1e-3)
+
+
 # ------------------------------------------------------------------------------ oracle
 def oracle_rate(desc, eps, vi, n_sample):
     """Oracle energies/s on a bounded, evenly spaced sample of the energy grid."""
@@ -271,13 +285,8 @@ def main():
         all_stats.extend(stats)
     barrier()
     clocks = sampler.stop()
-    t_step = sum(step_ms) / len(step_ms)
-    if dist is not None:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
     n_energies = eps.size * len(vi)
-    value = world * n_energies / (t_step * 1e-3)
+    t_step, value = job_rate(sum(step_ms) / len(step_ms), n_energies, world, dist, "cuda")
     converged = all(s["status"] == "converged" for s in all_stats)
     worst = max(s["rel_residual"] for s in all_stats)
     iters = [s["iterations"] for s in stats]

@@ -1,0 +1,59 @@
+"""The multi-GPU path of bench.py is replicas only: every rank solves its own copy of the
+workload and only the step time is reduced (maximum over ranks).  Checked here with two gloo
+ranks on the CPU, and the reference arm's rule that ranks other than 0 do no work."""
+
+import os
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t, v = bench.job_rate(2.0 + 3.0 * rank, 256, world, dist, "cpu")  # ranks take 2 ms and 5 ms
+        q.put((rank, t, v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_job_rate_takes_the_slowest_rank_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, t, v in res:
+        assert t == 5.0
+        assert v == pytest.approx(2 * 256 / 5e-3)
+
+
+def test_job_rate_single_rank():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.job_rate(4.0, 100, 1) == (4.0, 100 / 4e-3)
+
+
+def test_reference_arm_ranks_other_than_zero_do_no_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env, timeout=300)
+    assert out.returncode == 0
+    assert out.stdout.strip() == ""
