@@ -250,7 +250,8 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     // descriptors and primary-mode coefficient rows of the one-block-per-system kernel, the
     // points of each state grouped by primary mode
     std::vector<int4> rdesc;
-    std::vector<float2> rct;
+    std::vector<float2> rct, rctd;  // (-c, -c) and the double-float pair (hi, lo) of +c
+    int rsec = 0;
     int rhalo = 0, rok = 1;
     for (int d = 0; d < m->ns; ++d) {
         dm.rbeg[d] = (int)rdesc.size();
@@ -280,9 +281,12 @@ int build(const vbk_model_desc* d, vbk_model* m) {
                         c = (nn >= 0 && nn < m->nb[m1]) ? c * m->tab[e.col[m1] + n] : 0.0;
                     }
                     rct.push_back(make_float2((float)-c, (float)-c));
+                    const float ch = (float)c;
+                    rctd.push_back(make_float2(ch, (float)(c - (double)ch)));
                 }
                 const int poff = (e.dp - d) * m->Nnu + e.lin;
                 rdesc.push_back(make_int4(off * 8, poff * 8, col2, m2));
+                if (col2 >= 0) rsec = 1;
                 dm.rcnt[d][mg] += 1;
                 rhalo = std::max(rhalo, std::max(-(d * m->Nnu + poff), (d + 1) * m->Nnu - 1 + poff - (m->N - 1)));
             }
@@ -291,6 +295,8 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     dm.rbeg[m->ns] = (int)rdesc.size();
     if (rdesc.empty()) rdesc.push_back(make_int4(0, 0, -1, 0));
     if (rct.empty()) rct.push_back(make_float2(0.f, 0.f));
+    if (rctd.empty()) rctd.push_back(make_float2(0.f, 0.f));
+    dm.rsec = rsec;
     if (rdesc.size() > (size_t)MAXS * 64) rok = 0;
     dm.nrct = (int)rct.size();
     dm.rhalo = rhalo;
@@ -301,9 +307,9 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     const size_t b1 = al(ne * sizeof(DevEntry)), b2 = al(nd * sizeof(DevEntry)), b3 = al(nt * sizeof(double)),
                  b4 = al(nt * sizeof(float)), b5 = al(npc * sizeof(double)), b6 = al(npc * sizeof(float)),
                  b7 = al(rdesc.size() * sizeof(int4)), b8 = al(rct.size() * sizeof(float2)),
-                 b9 = al(npc * sizeof(float2));
+                 b9 = al(npc * sizeof(float2)), b10 = al(rctd.size() * sizeof(float2));
     char* mem = nullptr;
-    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8 + b9);
+    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8 + b9 + b10);
     if (err != cudaSuccess) return vbk_cuda_fail(err, "model tables");
     m->dev_mem = mem;
     std::vector<DevEntry> he(ne), hd(nd);
@@ -341,6 +347,10 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         if ((err = cudaMemcpy(base + b7 + b8, pcs.data(), npc * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
             return vbk_cuda_fail(err, "model coefficient upload");
         dm.pcs = (const float2*)(base + b7 + b8);
+        if ((err = cudaMemcpy(base + b7 + b8 + b9, rctd.data(), rctd.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return vbk_cuda_fail(err, "model coefficient upload");
+        dm.rctd = (const float2*)(base + b7 + b8 + b9);
     }
     dm.ent = (const DevEntry*)mem;
     dm.dent = (const DevEntry*)(mem + b1);

@@ -135,6 +135,8 @@ struct DevModel {
     // leaves the basis), n the primary-mode index
     const int4* rdesc;
     const float2* rct;
+    const float2* rctd;  // the same rows as double-float pairs (hi, lo) of +coef (q^k)_{n, n + delta}
+    int rsec;            // 1 if some point involves a secondary mode
     int nrct;
     int rbeg[MAXS + 1];
     int rcnt[MAXS][MAXM];

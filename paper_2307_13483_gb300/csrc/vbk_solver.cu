@@ -2034,6 +2034,92 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     }
 }
 
+// b - A x in double-float for one system per CTA (grid: the outer list; -1 entries return):
+// the whole split solution (re hi, im hi, re lo, im lo) of the system is staged once in shared
+// memory with a zero halo, so every x entry leaves L2/HBM once instead of once per stencil
+// point; coefficients come from the (hi, lo) rows of the primary mode (models whose points
+// involve a secondary mode use k_residual_df).  One ||r||^2 partial per system (part[s]).
+template <int M>
+__global__ void __launch_bounds__(RTPB, 1) k_residual_res(DevModel md, const int* __restrict__ sys_e,
+                                                         const int* __restrict__ list, const float4* __restrict__ dsp,
+                                                         const float4* __restrict__ xs, const double2* __restrict__ b64,
+                                                         float4* __restrict__ rs, double2* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = md.N, H = md.rhalo;
+    float4* X = reinterpret_cast<float4*>(smraw) + H;
+    float2* rows = reinterpret_cast<float2*>(X + N + H);
+    __shared__ int4 sdesc[MAXS * 64];
+    __shared__ float red[RTPB / 32];
+    const int s = list[blockIdx.x];
+    if (s < 0) return;
+    const int tid = threadIdx.x;
+    const long long so = (long long)s * N;
+    const float4* dg = dsp + (long long)sys_e[s] * N;
+    for (int k = tid; k < md.nrct; k += RTPB) rows[k] = md.rctd[k];
+    for (int k = tid; k < H; k += RTPB) X[-1 - k] = X[N + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = tid; k < md.rbeg[md.ns]; k += RTPB) sdesc[k] = md.rdesc[k];
+    for (int i = tid; i < N; i += RTPB) X[i] = xs[so + i];
+    __syncthreads();
+    float nrm = 0.f;
+    for (int i = tid; i < N; i += RTPB) {
+        const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * md.Nnu;
+        int n[MAXM];
+        decode<M>(md, nu, n);
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        const double2 bb = b64[so + i];
+        if ((__double_as_longlong(bb.x) | __double_as_longlong(bb.y)) != 0) {  // b is mostly zero
+            rh = (float)bb.x;
+            ih = (float)bb.y;
+            rl = (float)(bb.x - (double)rh);
+            il = (float)(bb.y - (double)ih);
+        }
+        const float4 x = X[i], g = dg[i];
+        df_fma(rh, rl, -g.x, -g.z, x.x, x.z);
+        df_fma(rh, rl, g.y, g.w, x.y, x.w);
+        df_fma(ih, il, -g.x, -g.z, x.y, x.w);
+        df_fma(ih, il, -g.y, -g.w, x.x, x.z);
+        int k = md.rbeg[d];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int kend = k + md.rcnt[d][m];
+            const float2* row = rows + n[m];
+#pragma unroll 4
+            for (; k < kend; ++k) {
+                const int4 q = sdesc[k];
+                const float2 c = row[q.x >> 3];
+                const float4 v = X[i + (q.y >> 3)];  // neighbours outside [0, N) read the zero halo
+                df_fma(rh, rl, c.x, c.y, v.x, v.z);
+                df_fma(ih, il, c.x, c.y, v.y, v.w);
+            }
+        }
+        const float2 re = df_norm(rh, rl), im = df_norm(ih, il);
+        rs[so + i] = make_float4(re.x, im.x, re.y, im.y);
+        nrm = fmaf(re.x, re.x, fmaf(im.x, im.x, nrm));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    if ((tid & 31) == 0) red[tid >> 5] = nrm;
+    __syncthreads();
+    if (tid < 32) {
+        float t = red[tid];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (tid == 0) part[s] = make_double2((double)t, 0.0);
+    }
+}
+inline size_t residual_res_smem(const DevModel& md) {
+    return (size_t)(md.N + 2 * md.rhalo) * sizeof(float4) + (size_t)md.nrct * sizeof(float2) + 16;
+}
+template <int M> bool prepare_residual_res(const DevModel& md) {
+    if (md.rsec || residual_res_smem(md) > 220 * 1024) return false;
+    if (cudaFuncSetAttribute(k_residual_res<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)residual_res_smem(md)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 // shared memory of the resident kernel: p (with its halo), q, the oscillator tables and the
 // primary-mode coefficient rows (FP32)
 inline size_t resident_smem(const DevModel& md) {
@@ -2744,6 +2830,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     // (hi, lo) float pairs and b - A x is formed on the FP32 pipes (k_residual_df); psi is
     // converted to FP64 once at the end.
     const bool dfr = resident;
+    // the double-float residual with one CTA per system when the split solution fits shared memory
+    const bool dfr_res = dfr && prepare_residual_res<M>(md);
 
     // ---- workspace
     const size_t NN = (size_t)N;
@@ -2914,6 +3002,9 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             // inner solve reads b directly
             if (it == 0)
                 rn.go("rhs_norm", k_rhs_norm, dim3(nsys), dim3(TPB), N, job.b64, partA);
+            else if (dfr_res)
+                rn.go_smem("residual_df", k_residual_res<M>, dim3(n_out), dim3(RTPB), residual_res_smem(md), md,
+                           (const int*)sys_e, (const int*)olist, (const float4*)dsp, (const float4*)xs, job.b64, rsp, partA);
             else if (dfr)
                 rn.go("residual_df", k_residual_df<DF_S, DF_EPT>,
                       dim3(df_partials(md), cdiv_u(n_out, DF_S)), dim3(TPB), md, (const int*)sys_e, so, (int)n_out,
@@ -2937,7 +3028,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cudaMemsetAsync(olist, 0xff, nsys * sizeof(int), st);  // -1: no system
             cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
-                  it == 0 ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
+                  it == 0 || dfr_res ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
                   it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
             if (resident && nsys <= ORDER_MAX)  // longest expected inner solve first (one CTA each)
                 rn.go("order_lists", k_order_lists, dim3(1), dim3(1024), nsys, (const SysState*)sst, (const int*)inner, olist,
