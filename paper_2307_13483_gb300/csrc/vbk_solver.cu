@@ -1864,6 +1864,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     __shared__ float redA[RTPB / 32][3], redB[RTPB / 32][3];  // per-warp partials of the two reductions
     static_assert(RTPB == 1024, "one partial per lane in the final warp sums");
     const int s = list[blockIdx.x];
+    if (s < 0) return;  // launched over more list slots than systems (speculative refinement round)
     const int tid = threadIdx.x;
     const long long so = (long long)s * N;
     const float2* dg = diag + (long long)sys_e[s] * N;
@@ -2832,6 +2833,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     const bool dfr = resident;
     // the double-float residual with one CTA per system when the split solution fits shared memory
     const bool dfr_res = dfr && prepare_residual_res<M>(md);
+    const bool spec = dfr_res && o.timing == 0;  // refinement rounds enqueued ahead of the host check
 
     // ---- workspace
     const size_t NN = (size_t)N;
@@ -3034,13 +3036,20 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 rn.go("order_lists", k_order_lists, dim3(1), dim3(1024), nsys, (const SysState*)sst, (const int*)inner, olist,
                       ilist);
             cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
-            if (cudaStreamSynchronize(st) != cudaSuccess) {
-                fail(vbk_cuda_fail(cudaGetLastError(), "outer check"));
-                break;
+            if (spec && it < 2) {
+                // the first two refinement rounds are enqueued without waiting for the count:
+                // the one-CTA-per-system kernels run over every list slot and slots past the
+                // count (-1) return at once; a solve takes at least two inner solves
+                n_out = n_in = (unsigned)nsys;
+            } else {
+                if (cudaStreamSynchronize(st) != cudaSuccess) {
+                    fail(vbk_cuda_fail(cudaGetLastError(), "outer check"));
+                    break;
+                }
+                rn.flush();
+                if (hcnt[0] == 0) break;
+                n_out = n_in = (unsigned)hcnt[0];
             }
-            rn.flush();
-            if (hcnt[0] == 0) break;
-            n_out = n_in = (unsigned)hcnt[0];
             const Sel si{ilist, inner};
             const Sel so2{olist, outer};
 
