@@ -301,15 +301,36 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     dm.nrct = (int)rct.size();
     dm.rhalo = rhalo;
     dm.rok = rok;
+    // energy-independent parts of the diagonal: E_nu per nu and the delta = 0 terms of U_dd per
+    // element (the same products as the off-diagonal coefficients, summed in point order)
+    std::vector<double> enu(m->Nnu), u0(m->N, 0.0);
+    for (int nu = 0; nu < m->Nnu; ++nu) {
+        double en = 0.0;
+        for (int mm = 0; mm < m->M; ++mm) en += dm.omega[mm] * ((nu / m->stride[mm]) % m->nb[mm] + 0.5);
+        enu[nu] = en;
+    }
+    for (int d = 0; d < m->ns; ++d)
+        for (int nu = 0; nu < m->Nnu; ++nu) {
+            double u = 0.0;
+            for (const HostEntry& h : diagp) {
+                if (h.d != d) continue;
+                double c = h.e.coef;
+                for (int mm = 0; mm < m->M; ++mm)
+                    if (h.e.col[mm] >= 0) c *= m->tab[h.e.col[mm] + (nu / m->stride[mm]) % m->nb[mm]];
+                u += c;
+            }
+            u0[(size_t)d * m->Nnu + nu] = u;
+        }
     // one device allocation: entries | diagonal entries | tab64 | tab32 | pc64 | pc32 | rdesc | rct
     const size_t ne = std::max<size_t>(1, offd.size()), nd = std::max<size_t>(1, diagp.size()), nt = m->tab.size();
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t b1 = al(ne * sizeof(DevEntry)), b2 = al(nd * sizeof(DevEntry)), b3 = al(nt * sizeof(double)),
                  b4 = al(nt * sizeof(float)), b5 = al(npc * sizeof(double)), b6 = al(npc * sizeof(float)),
                  b7 = al(rdesc.size() * sizeof(int4)), b8 = al(rct.size() * sizeof(float2)),
-                 b9 = al(npc * sizeof(float2)), b10 = al(rctd.size() * sizeof(float2));
+                 b9 = al(npc * sizeof(float2)), b10 = al(rctd.size() * sizeof(float2)),
+                 b11 = al(enu.size() * sizeof(double)), b12 = al(u0.size() * sizeof(double));
     char* mem = nullptr;
-    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8 + b9 + b10);
+    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8 + b9 + b10 + b11 + b12);
     if (err != cudaSuccess) return vbk_cuda_fail(err, "model tables");
     m->dev_mem = mem;
     std::vector<DevEntry> he(ne), hd(nd);
@@ -351,6 +372,12 @@ int build(const vbk_model_desc* d, vbk_model* m) {
             cudaSuccess)
             return vbk_cuda_fail(err, "model coefficient upload");
         dm.rctd = (const float2*)(base + b7 + b8 + b9);
+        char* b2base = base + b7 + b8 + b9 + b10;
+        if ((err = cudaMemcpy(b2base, enu.data(), enu.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(b2base + b11, u0.data(), u0.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return vbk_cuda_fail(err, "model diagonal upload");
+        dm.enu = (const double*)b2base;
+        dm.u0 = (const double*)(b2base + b11);
     }
     dm.ent = (const DevEntry*)mem;
     dm.dent = (const DevEntry*)(mem + b1);

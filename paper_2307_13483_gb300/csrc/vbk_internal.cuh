@@ -119,6 +119,8 @@ struct DevModel {
     int dbeg[MAXS + 1];  // diagonal parts (delta = 0, dp = d) of the terms of state d
     const DevEntry* ent;
     const DevEntry* dent;
+    const double* enu;  // E_nu = sum_m omega_m (n_m + 1/2), per nu
+    const double* u0;   // delta = 0 part of U_dd(nu) (the diagonal terms), per element (d, nu)
     const double* tab64;
     const float* tab32;
     int ntab;  // entries of tab64 / tab32

@@ -131,23 +131,13 @@ __device__ __forceinline__ bool point_coef(const DevEntry& en, const int (&n)[MA
 template <int M>
 __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, double2* __restrict__ d64,
                              float2* __restrict__ d32, float2* __restrict__ dinv32, float4* __restrict__ dsp) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)nE * md.N) return;
-    const int e = (int)(t / md.N), i = (int)(t - (long long)e * md.N);
+    const int e = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;  // grid: elements x energies
+    if (i >= md.N) return;
+    const long long t = (long long)e * md.N + i;
     const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * md.Nnu;
-    int n[MAXM];
-    decode<M>(md, nu, n);
-    double en = 0.0;
-#pragma unroll
-    for (int m = 0; m < M; ++m) en += md.omega[m] * (n[m] + 0.5);
-    const double eps = E[e] - en;
-    double re = eps, im = 0.0;
-    for (int k = md.dbeg[d]; k < md.dbeg[d + 1]; ++k) {
-        const DevEntry p = md.dent[k];
-        double c;
-        point_coef<double, M>(p, n, md, md.tab64, c);
-        re -= c;
-    }
+    // E_nu and the delta = 0 part of U_dd are energy-independent: tabulated at model build
+    const double eps = E[e] - md.enu[nu];
+    double re = eps - md.u0[i], im = 0.0;
     for (int c = 0; c < md.nchan; ++c) {
         if (md.ch_d[c] != d) continue;
         const double2 F =
@@ -2970,7 +2960,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             break;
         }
         // energy tables (FP64 + inner-precision copy)
-        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), md, nE, (const double*)dE,
+        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE,
               dfr ? (double2*)nullptr : diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR, dsp);
         if (block) factor_blocks<R, M>(rn, md, pbuf, nE, (const cx<R>*)diagR, F, pfail);
         if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) {
@@ -3518,7 +3508,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
         cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess) {
         rc = vbk_cuda_fail(cudaGetLastError(), "operator set-up");
     } else {
-        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
+        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), m->dm, nE, (const double*)dE, d64,
               mixed ? d32 : (float2*)nullptr, (float2*)nullptr, (float4*)nullptr);
         const dim3 ge(cdiv_u(N, TPB), (unsigned)nsys);
         if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
@@ -3655,7 +3645,7 @@ int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* 
         (ce = cudaMemcpyAsync(se, hse, nsys * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return vbk_cuda_fail(ce, "noalloc: copies into scratch");
     Runner rn{m, st, false, {}, {}};
-    rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u((long long)nE * N, TPB)), dim3(TPB), m->dm, nE, (const double*)dE, d64,
+    rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), m->dm, nE, (const double*)dE, d64,
           (float2*)nullptr, (float2*)nullptr, (float4*)nullptr);
     const Sel none{nullptr, nullptr};
     launch_matvec_v<double>(rn, 9, "matvec_fp64", m->dm, (const int*)se, none, (unsigned)nsys, (const double2*)d64, x,
