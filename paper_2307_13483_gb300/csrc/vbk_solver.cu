@@ -1808,12 +1808,23 @@ __global__ void __launch_bounds__(TPB) k_residual_df(DevModel md, const int* __r
 constexpr int DF_S = 2, DF_EPT = 4;
 inline int df_partials(const DevModel& md) { return md.ns * ((md.Nnu + TPB * DF_EPT - 1) / (TPB * DF_EPT)); }
 
-// x64 = hi + lo of the double-float solution (every system)
+// float -> double, exact, by moving the bit fields (integer pipes; GB300's FP64 pipe is the
+// scarce one); zeros, subnormals, infinities and NaNs take the conversion instruction
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f;
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(ex + (1023u - 127u)) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// x64 = hi + lo of the double-float solution (every system); the sum is exact in FP64
 __global__ void __launch_bounds__(TPB) k_df_out(long long n, const float4* __restrict__ xs, double2* __restrict__ x64) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 v = xs[i];
-    x64[i] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+    x64[i] = make_double2(f2d_exact(v.x) + f2d_exact(v.z), f2d_exact(v.y) + f2d_exact(v.w));
 }
 
 constexpr int RTPB = 1024;
@@ -2109,6 +2120,102 @@ template <int M> bool prepare_residual_res(const DevModel& md) {
         return false;
     }
     return true;
+}
+
+// y = A x (or b - A x) in FP32 for S systems per CTA (grid: groups of S list entries): each
+// system's x is staged once in shared memory with a zero halo (every x entry leaves L2/HBM once,
+// neighbours come from shared memory), coefficients from the primary-mode rows as in the
+// resident COCG kernel, shared by the S systems.  One partial per system: x^T y (red = 1) or
+// ||y||^2 (red = 2) in part[s].
+template <int M, int S>
+__global__ void __launch_bounds__(RTPB, 1) k_matvec_sys(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
+                                                       const float2* __restrict__ diag, const float2* __restrict__ x,
+                                                       long long xs, float2* __restrict__ y, long long ys,
+                                                       const double2* __restrict__ b, double2* __restrict__ part, int red) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = md.N, H = md.rhalo, NH = N + 2 * H;
+    float2* Xb = reinterpret_cast<float2*>(smraw) + H;  // system t: Xb + t * NH
+    float2* sct = reinterpret_cast<float2*>(smraw) + S * NH;
+    __shared__ int4 sdesc[MAXS * 64];
+    __shared__ float2 redsh[RTPB / 32];
+    const int tid = threadIdx.x;
+    int sy[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const int li = blockIdx.x * S + t;
+        int s = -1;
+        if (li < nlist) {
+            s = sel.list ? sel.list[li] : li;
+            if (s >= 0 && sel.act && !sel.act[s]) s = -1;
+        }
+        sy[t] = s;
+    }
+    for (int k = tid; k < md.nrct; k += RTPB) sct[k] = md.rct[k];
+    for (int k = tid; k < md.rbeg[md.ns]; k += RTPB) sdesc[k] = md.rdesc[k];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        float2* X = Xb + t * NH;
+        for (int k = tid; k < H; k += RTPB) X[-1 - k] = X[N + k] = make_float2(0.f, 0.f);
+        const float2* xv = x + (long long)(sy[t] < 0 ? 0 : sy[t]) * xs;
+        for (int i = tid; i < N; i += RTPB) X[i] = sy[t] < 0 ? make_float2(0.f, 0.f) : xv[i];
+    }
+    __syncthreads();
+    float2 loc[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) loc[t] = make_float2(0.f, 0.f);
+    for (int i = tid; i < N; i += RTPB) {
+        const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * md.Nnu;
+        int n[MAXM];
+        decode<M>(md, nu, n);
+        float2 acc[S], xi[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            xi[t] = Xb[t * NH + i];
+            acc[t] = sy[t] < 0 ? make_float2(0.f, 0.f) : cmul<float>(diag[(long long)sys_e[sy[t]] * N + i], xi[t]);
+        }
+        const char* Xi = reinterpret_cast<const char*>(Xb + i);
+        int k = md.rbeg[d];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int kend = k + md.rcnt[d][m];
+            const char* row = reinterpret_cast<const char*>(sct) + n[m] * 8;
+#pragma unroll 4
+            for (; k < kend; ++k) {
+                const int4 q = sdesc[k];
+                float2 cc = *reinterpret_cast<const float2*>(row + q.x);  // (-c, -c)
+                if (q.z >= 0) {
+                    const float tt = md.tab32[q.z + nsel<M>(n, q.w)];
+                    cc.x *= tt;
+                    cc.y *= tt;
+                }
+#pragma unroll
+                for (int t = 0; t < S; ++t)  // neighbours outside [0, N) read the zero halo
+                    acc[t] = ffma2(cc, *reinterpret_cast<const float2*>(Xi + (size_t)t * NH * 8 + q.y), acc[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            if (sy[t] < 0) continue;
+            float2 out = acc[t];
+            if (b) {
+                const double2 bb = b[(long long)sy[t] * N + i];
+                out = make_float2((float)bb.x - out.x, (float)bb.y - out.y);
+            }
+            y[(long long)sy[t] * ys + i] = out;
+            if (red == 1) loc[t] = cfma<float>(xi[t], out, loc[t]);
+            else if (red == 2) loc[t].x = fmaf(out.x, out.x, fmaf(out.y, out.y, loc[t].x));
+        }
+    }
+    if (red) {
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const double2 tot = block_sum_c<float>(loc[t], redsh);
+            if (tid == 0 && sy[t] >= 0) part[sy[t]] = tot;
+        }
+    }
+}
+inline size_t matvec_sys_smem(const DevModel& md, int S) {
+    return (size_t)(S * (md.N + 2 * md.rhalo) + md.nrct) * sizeof(float2) + 16;
 }
 
 // shared memory of the resident kernel: p (with its halo), q, the oscillator tables and the
@@ -2610,13 +2717,14 @@ inline int block_partials(const DevPlanBuf& pb) {
 //   0..3  register-blocked k_matvec3 with (S, EPT) = (1, 4), (2, 4), (4, 2), (2, 2)
 //   4..7  windowed k_matvec_tiled with (S, EPT) = (1, 4), (2, 4), (4, 2), (8, 1)
 //   8..9  direct k_matvec2 with S = 1, 4
-constexpr int MV_NVAR = 10;
+//   10..11 one / two systems per CTA with x in shared memory (k_matvec_sys, FP32)
+constexpr int MV_NVAR = 12;
 inline int mv_ept(int v) {
-    static const int e[MV_NVAR] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1};
+    static const int e[MV_NVAR] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1, 1, 1};
     return e[v];
 }
 inline int mv_sys(int v) {
-    static const int sv[MV_NVAR] = {1, 2, 4, 2, 1, 2, 4, 8, 1, 4};
+    static const int sv[MV_NVAR] = {1, 2, 4, 2, 1, 2, 4, 8, 1, 4, 1, 2};
     return sv[v];
 }
 inline int mv_window(const DevModel& md, int v) {
@@ -2632,10 +2740,12 @@ inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
     return bytes > 150 * 1024 ? -1 : (int)bytes;
 }
 inline bool mv_valid(const DevModel& md, int v, size_t c) {
+    if (v >= 10) return c == 8 && md.rok && matvec_sys_smem(md, v - 9) <= 220 * 1024;
     if (c == 16 && (mv_sys(v) * mv_ept(v) > 8 || v == 7)) return false;  // FP64: register budget
     return mv_tiled_smem(md, v, c) >= 0;
 }
 inline int matvec_partials_v(const DevModel& md, int v) {
+    if (v >= 10) return 1;
     const int T = TPB * mv_ept(v);
     return md.ns * ((md.Nnu + T - 1) / T);
 }
@@ -2664,6 +2774,25 @@ void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, co
     const int S = mv_sys(v);
     const dim3 g((unsigned)matvec_partials_v(md, v), (nlist + S - 1) / S);
     const size_t smem = (v >= 4 && v < 8) ? (size_t)mv_tiled_smem(md, v, sizeof(cx<T>)) : 0;
+    if (v >= 10) {
+        if constexpr (sizeof(T) == 4) {
+            const int Sv = v - 9;
+            const dim3 gs((nlist + Sv - 1) / Sv);
+            const size_t sm = matvec_sys_smem(md, Sv);
+            auto go = [&](auto kern) { rn.go_smem(name, kern, gs, dim3(RTPB), sm, md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); };
+            switch (md.M * 2 + (Sv - 1)) {
+                case 2: go(k_matvec_sys<1, 1>); break;
+                case 3: go(k_matvec_sys<1, 2>); break;
+                case 4: go(k_matvec_sys<2, 1>); break;
+                case 5: go(k_matvec_sys<2, 2>); break;
+                case 6: go(k_matvec_sys<3, 1>); break;
+                case 7: go(k_matvec_sys<3, 2>); break;
+                case 8: go(k_matvec_sys<4, 1>); break;
+                default: go(k_matvec_sys<4, 2>); break;
+            }
+        }
+        return;
+    }
     switch (v) {
         case 0: rn.go(name, k_matvec3<T, 1, 4>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
         case 1: rn.go(name, k_matvec3<T, 2, 4>, g, dim3(TPB), md, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); break;
@@ -2697,8 +2826,24 @@ template <class T> int prepare_matvec(const DevModel& md) {
     if (need[0] > 0) ce = tiled_optin<T, 1, 4>(md, need[0]);
     if (need[1] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 2, 4>(md, need[1]);
     if (need[2] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 4, 2>(md, need[2]);
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4) {
         if (need[3] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 8, 1>(md, need[3]);
+        for (int Sv = 1; Sv <= 2 && ce == cudaSuccess; ++Sv) {
+            if (!mv_valid(md, 9 + Sv, sizeof(cx<T>))) continue;
+            const int sm = (int)matvec_sys_smem(md, Sv);
+            auto opt = [&](auto kern) { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); };
+            switch (md.M * 2 + (Sv - 1)) {
+                case 2: ce = opt(k_matvec_sys<1, 1>); break;
+                case 3: ce = opt(k_matvec_sys<1, 2>); break;
+                case 4: ce = opt(k_matvec_sys<2, 1>); break;
+                case 5: ce = opt(k_matvec_sys<2, 2>); break;
+                case 6: ce = opt(k_matvec_sys<3, 1>); break;
+                case 7: ce = opt(k_matvec_sys<3, 2>); break;
+                case 8: ce = opt(k_matvec_sys<4, 1>); break;
+                default: ce = opt(k_matvec_sys<4, 2>); break;
+            }
+        }
+    }
     return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "matvec shared-memory opt-in");
 }
 
@@ -2737,6 +2882,11 @@ int tune_matvec(Runner& rn, vbk_model* mdl, const int* sys_e, Sel sel, unsigned 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     slot = bestv;
+    if (timing) {  // the chosen variant's best time over the whole batch (one launch, all systems of the list)
+        const int k = rn.id(sizeof(T) == 4 ? "matvec_tuned_fp32" : "matvec_tuned_fp64");
+        mdl->timers[k].launches += 1;
+        mdl->timers[k].ms += best;
+    }
     launch_matvec_v<T>(rn, bestv, "matvec_tune", md, sys_e, sel, nlist, diag, x, xs, y, ys, b, part, red);
     if (const cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) return vbk_cuda_fail(ce, "matvec tuner");
     return VBK_OK;
@@ -3124,21 +3274,23 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                                           : pE == 4 ? grid_of(k_pmatvec<R, 2, 4>)
                                                     : grid_of(k_pmatvec<R, 2, 2>);
                     const unsigned g_up = grid_of(k_pupdate<R, 8>), g_pp = grid_of(k_pp<R, 4>);
-                    auto piter = [&](int t) {
+                    // mvname: the first matvec of an inner solve (every system of the inner list
+                    // active) is timed under its own name when timing is on
+                    auto piter = [&](int t, const char* mvname = "matvec") {
                         const DList cur{t % 2 == 0 ? ilist : ilist2, cnt + (t % 2)};
                         const DList nxt{t % 2 == 0 ? ilist2 : ilist, cnt + 1 - (t % 2)};
                         cudaMemsetAsync(cnt + 1 - (t % 2), 0, sizeof(int), rn.st);
                         if (pS == 1)
-                            rn.go("matvec", k_pmatvec<R, 1, 4>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                            rn.go(mvname, k_pmatvec<R, 1, 4>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
                                   (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
                         else if (pS == 4)
-                            rn.go("matvec", k_pmatvec<R, 4, 2>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                            rn.go(mvname, k_pmatvec<R, 4, 2>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
                                   (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
                         else if (pE == 4)
-                            rn.go("matvec", k_pmatvec<R, 2, 4>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                            rn.go(mvname, k_pmatvec<R, 2, 4>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
                                   (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
                         else
-                            rn.go("matvec", k_pmatvec<R, 2, 2>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
+                            rn.go(mvname, k_pmatvec<R, 2, 2>, dim3(g_mv), dim3(TPB), md, (const int*)sys_e, cur,
                                   (const cx<R>*)diagR, (const cx<R>*)pv, q, partA, done, sst, inner, outer);
                         rn.go("cocg_update", k_pupdate<R, 8>, dim3(g_up), dim3(TPB), N, (const int*)sys_e, cur, pmode,
                               (const cx<R>*)diagR, x, r, (const cx<R>*)pv, (const cx<R>*)q, z, partC, partB, done, sst, inner,
@@ -3178,7 +3330,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     }
                     for (;;) {
                         if (rn.timing) {
-                            for (int t = 0; t < K2; ++t) piter(t);
+                            for (int t = 0; t < K2; ++t) piter(t, k == 0 && t == 0 ? "matvec_full" : "matvec");
                         } else {
                             if (cudaGraphLaunch(pgexec, st) != cudaSuccess) {
                                 fail(vbk_cuda_fail(cudaGetLastError(), "graph launch"));
