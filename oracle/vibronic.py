@@ -11,7 +11,9 @@ Everything here is the plain definition, in complex128 with NumPy/SciPy:
 * the level-shift factor F[f](eps) (Eq. IntF with the widths of Sec. II.B), written in
   closed form through Dawson's function and the scaled complementary error function,
 * the matrix A = E - H_ef = E - H_0 - U - F in the product basis (Eqs. H_ef, Amatrix),
-  assembled as Kronecker products (state index slowest, last mode fastest),
+  assembled as Kronecker products (state index slowest, last mode fastest); F is the
+  operator of Eq. F_gen, diagonal for the q-independent couplings of Sec. II.B and the
+  sandwich sum P F[f f'] P' of Eq. FE for the q-dependent couplings of Sec. II.C,
 * the right-hand side Phi (Sec. II.D), the solve (Eq. Ax=b) by direct LU,
 * T-matrix and cross section (Eqs. Td, crs, crs2), the 2D EELS sum (Eq. 2Dsp),
 * the gradient of a cross-section loss by a dense-LU adjoint.
@@ -23,6 +25,9 @@ Readings of the paper taken here (the CUDA path takes the same ones):
 * f_d^mu(eps) = sqrt(Gamma_d^mu(eps) / 2 pi) is real and non-negative, and zero for
   eps <= 0 (closed channel);
 * energies in eV; sigma is reported raw as 2 pi^3 |T|^2 / eps_i with eps_i in eV;
+* a q-dependent coupling V^mu_{d eps}(q) = f_d^mu(eps) P(q) is separable (Sec. II.C) and its
+  polynomial P(q) is a sum of products of truncated q matrices, like U; the channels of one
+  partial wave share l, so that F[f f'] has the closed form of one channel;
 * the EELS resolution function is a unit-area Gaussian of FWHM 10 meV.
 
 Parity status: every function here is pinned by tests under ``tests/`` against
@@ -155,14 +160,78 @@ def coupling_matrix(model: dict) -> sp.csr_matrix:
 
 
 def check_channels(model: dict):
+    """A state couples to a partial wave at most once, and the channels of one partial wave
+    share the exponent l (the closed form of F[f_c f_c'] in ``pair_level_shift`` needs it)."""
+    seen, l_of = set(), {}
+    for c in model["channels"]:
+        if (c["d"], c["mu"]) in seen:
+            raise ValueError("a state couples to a partial wave at most once")
+        seen.add((c["d"], c["mu"]))
+        if l_of.setdefault(c["mu"], c["l"]) != c["l"]:
+            raise ValueError("the channels of one partial wave must share l")
+
+
+def has_q_dependent_coupling(model: dict) -> bool:
+    """True for the generalized coupling (Sec. II.C): some partial wave couples to two states
+    or through a polynomial in q."""
     mus = [c["mu"] for c in model["channels"]]
-    if len(set(mus)) != len(mus):
-        raise ValueError("each partial wave must couple to a single discrete state")
+    return len(set(mus)) != len(mus) or any(c.get("terms") for c in model["channels"])
+
+
+def channel_polynomial(model: dict, c: int) -> sp.csr_matrix:
+    """P_c(q) of the coupling V^mu_{d eps}(q) = f_d^mu(eps) P_c(q) (Sec. II.C, separable in eps
+    and q): the sum of coef * prod_m q_m^pow over the channel's "terms", or the identity when it
+    lists none (the q-independent coupling of Sec. II.B).  Real symmetric, N_nu x N_nu."""
+    ch = model["channels"][c]
+    nv = int(np.prod(basis_shape(model)))
+    if not ch.get("terms"):
+        return sp.identity(nv, format="csr")
+    P = sp.csr_matrix((nv, nv))
+    for t in ch["terms"]:
+        P = P + t["coef"] * term_matrix(model, t["pow"])
+    return P.tocsr()
+
+
+def pair_level_shift(eps, ca: dict, cb: dict):
+    """F[f_a f_b](eps) for two channels of one partial wave (Eq. FE, transform of Eq. IntF).
+
+    With Gamma_c = a_c eps^(l+1/2) exp(-b_c eps) and f_c = sqrt(Gamma_c / 2 pi), the product is
+    f_a f_b = (sqrt(a_a a_b) / 2 pi) eps^(l+1/2) exp(-(b_a + b_b) eps / 2): the one-channel
+    form with a = sqrt(a_a a_b), b = (b_a + b_b) / 2, so ``level_shift`` applies (equal l)."""
+    if ca["l"] != cb["l"]:
+        raise ValueError("the channels of one partial wave must share l")
+    return level_shift(eps, math.sqrt(ca["a"] * cb["a"]), 0.5 * (ca["b"] + cb["b"]), ca["l"])
+
+
+def continuum_operator(model: dict, E: float) -> sp.csr_matrix:
+    """The level-shift operator F(E - H_0) over alpha = (d, nu), complex128 (Eq. FE).
+
+    For every partial wave mu and every ordered pair (c, c') of its channels, block (d_c, d_c')
+    receives P_c diag(F[f_c f_c'](E - E_nu)) P_c'.  The factors keep this order: F is a function
+    of E - H_0, which does not commute with q.  With q-independent couplings and one state per
+    partial wave this is diag(F[Gamma_d / 2 pi](E - E_nu)) on the diagonal blocks (Sec. II.B)."""
+    check_channels(model)
+    ns = model["n_states"]
+    nv = int(np.prod(basis_shape(model)))
+    en = level_energies(model)
+    chans = model["channels"]
+    P = [channel_polynomial(model, c) for c in range(len(chans))]
+    blocks = [[sp.csr_matrix((nv, nv), dtype=np.complex128) for _ in range(ns)] for _ in range(ns)]
+    for c, ca in enumerate(chans):
+        for cp, cb in enumerate(chans):
+            if ca["mu"] != cb["mu"]:
+                continue
+            g = sp.diags(pair_level_shift(E - en, ca, cb))
+            blocks[ca["d"]][cb["d"]] = blocks[ca["d"]][cb["d"]] + P[c] @ g @ P[cp]
+    return sp.bmat(blocks, format="csr")
 
 
 def continuum_diagonal(model: dict, E: float) -> np.ndarray:
-    """Diagonal of F(E - H_0): sum over the channels of state d of F[Gamma/2pi](E - E_nu)."""
+    """Diagonal of F(E - H_0) for q-independent couplings with one state per partial wave
+    (Sec. II.B): sum over the channels of state d of F[Gamma/2pi](E - E_nu)."""
     check_channels(model)
+    if has_q_dependent_coupling(model):
+        raise ValueError("F(E - H_0) is not diagonal for this coupling; use continuum_operator")
     ns = model["n_states"]
     en = level_energies(model)
     out = np.zeros((ns, en.size), dtype=np.complex128)
@@ -175,8 +244,8 @@ def a_matrix(model: dict, E: float) -> sp.csr_matrix:
     """A = E - H_0 - U - F(E - H_0) over alpha = (d, nu) (Eq. Amatrix), complex128."""
     ns = model["n_states"]
     en = np.tile(level_energies(model), ns)
-    diag = E - en - continuum_diagonal(model, E)
-    return (sp.diags(diag) - coupling_matrix(model)).tocsr().astype(np.complex128)
+    A = sp.diags((E - en).astype(np.complex128)) - coupling_matrix(model) - continuum_operator(model, E)
+    return A.tocsr().astype(np.complex128)
 
 
 # ----------------------------------------------------------------------------------------
@@ -187,16 +256,25 @@ def n_partial_waves(model: dict) -> int:
 
 
 def phi(model: dict, E: float, v, mu: int) -> np.ndarray:
-    """Phi^{v mu}_{d,nu} = <nu| V^mu_{d eps} |v> with eps = E - E_v (Sec. II.D).
+    """Phi^{v mu}_{d,nu} = <nu| V^mu_{d eps}(q) |v> with eps = E - E_v (Sec. II.D).
 
-    With q-independent couplings this is f_d^mu(E - E_v) on the single entry (d, v)."""
+    With V^mu_{d eps} = f_d^mu(eps) P_c(q) (Sec. II.C) this is f_d^mu(E - E_v) times column v of
+    P_c in the block of state d, summed over the channels c of mu; for q-independent couplings
+    it is f_d^mu(E - E_v) on the single entry (d, v)."""
     ns = model["n_states"]
     nv = int(np.prod(basis_shape(model)))
     out = np.zeros(ns * nv)
-    ev = float(level_energies(model)[flat_index(model, v)])
-    for c in model["channels"]:
-        if c["mu"] == mu:
-            out[c["d"] * nv + flat_index(model, v)] += coupling_amplitude(E - ev, c["a"], c["b"], c["l"])
+    iv = flat_index(model, v)
+    ev = float(level_energies(model)[iv])
+    for k, c in enumerate(model["channels"]):
+        if c["mu"] != mu:
+            continue
+        f = coupling_amplitude(E - ev, c["a"], c["b"], c["l"])
+        if c.get("terms"):
+            col = channel_polynomial(model, k)[:, iv].toarray().ravel()
+            out[c["d"] * nv:(c["d"] + 1) * nv] += f * col
+        else:
+            out[c["d"] * nv + iv] += f
     return out
 
 
@@ -286,26 +364,42 @@ def eels(model: dict, eps, vi, vf_list, sigma_ef: np.ndarray, de_grid, fwhm: flo
 def with_parameter(model: dict, theta: int, value: float) -> dict:
     """Copy of the model with parameter theta replaced.
 
-    theta < n_terms: coefficient of term theta; else channel c = (theta - n_terms) // 2,
-    its ``a`` (even) or ``b`` (odd)."""
+    theta < n_terms: coefficient of term theta; n_terms <= theta < n_terms + 2 n_channels:
+    channel c = (theta - n_terms) // 2, its ``a`` (even) or ``b`` (odd); beyond: the
+    coefficients of the channels' coupling polynomials, channel by channel in listed order."""
     import copy
 
     m = copy.deepcopy(model)
-    nt = len(m["terms"])
+    nt, nc = len(m["terms"]), len(m["channels"])
     if theta < nt:
         m["terms"][theta]["coef"] = value
-    else:
+    elif theta < nt + 2 * nc:
         c, which = divmod(theta - nt, 2)
         m["channels"][c]["ab"[which]] = value
+    else:
+        c, t = _poly_term(m, theta - nt - 2 * nc)
+        m["channels"][c]["terms"][t]["coef"] = value
     return m
 
 
+def _poly_term(model: dict, k: int):
+    for c, ch in enumerate(model["channels"]):
+        n = len(ch.get("terms") or [])
+        if k < n:
+            return c, k
+        k -= n
+    raise IndexError("parameter index beyond the coupling-polynomial terms")
+
+
 def get_parameter(model: dict, theta: int) -> float:
-    nt = len(model["terms"])
+    nt, nc = len(model["terms"]), len(model["channels"])
     if theta < nt:
         return float(model["terms"][theta]["coef"])
-    c, which = divmod(theta - nt, 2)
-    return float(model["channels"][c]["ab"[which]])
+    if theta < nt + 2 * nc:
+        c, which = divmod(theta - nt, 2)
+        return float(model["channels"][c]["ab"[which]])
+    c, t = _poly_term(model, theta - nt - 2 * nc)
+    return float(model["channels"][c]["terms"][t]["coef"])
 
 
 def loss(model: dict, eps, vi, vf_list, target) -> float:

@@ -18,7 +18,10 @@ Model dictionary format (all energies in eV, Sec. II):
 * ``channels``  discrete-state/continuum couplings with constant q-dependence
                 (Sec. II.B): {"d", "mu", "a", "b", "l"} gives the width
                 Gamma_d^mu(eps) = a * eps^(l+1/2) * exp(-b*eps) of state d into
-                partial wave mu.  Each partial wave couples to one state.
+                partial wave mu.  An optional "terms" list [{"coef", "pow"}] makes
+                the coupling q-dependent, V^mu_{d eps}(q) = f_d^mu(eps) P(q) with
+                P(q) = sum coef * prod_m q_m^pow[m] (Sec. II.C); a partial wave may
+                then couple to several states, whose channels share l.
 """
 
 from __future__ import annotations
@@ -166,6 +169,28 @@ def ecd86_model(n_g: int, n_u: int) -> dict:
             {"d": 1, "mu": 1, "a": 0.186, "b": 0.375, "l": 1},
         ],
     }
+
+
+def gen_ecd_model(n_g: int, n_u: int) -> dict:
+    """The generalized model of Sec. II.C with the parameter values of Tables I and II.
+
+    U is the ECD86 matrix of Table I; the coupling matrix is expanded to first order in q,
+      V = [[f_1^e (1 + lambda_1 q_g), f_1^o q_u], [f_2^e q_u, f_2^o (1 + lambda_2 q_g)]]
+    (rows d, columns mu = e, o), with 2 pi |f_d^mu|^2 = a eps^(l+1/2) exp(-b eps) from
+    Table II.  Both partial waves couple to both states.  Index d here is 0-based.
+    """
+    m = ecd86_model(n_g, n_u)
+    lam1, lam2 = 0.2, 0.1
+    one_plus = lambda lam: [{"coef": 1.0, "pow": [0, 0]}, {"coef": lam, "pow": [1, 0]}]  # noqa: E731
+    q_u = [{"coef": 1.0, "pow": [0, 1]}]
+    m["name"] = f"gen-ecd-{n_g}x{n_u}"
+    m["channels"] = [
+        {"d": 0, "mu": 0, "a": 0.07, "b": 0.25, "l": 0, "terms": one_plus(lam1)},
+        {"d": 1, "mu": 0, "a": 0.1, "b": 0.5, "l": 0, "terms": q_u},
+        {"d": 0, "mu": 1, "a": 0.186, "b": 0.375, "l": 1, "terms": q_u},
+        {"d": 1, "mu": 1, "a": 0.15, "b": 0.8, "l": 1, "terms": one_plus(lam2)},
+    ]
+    return m
 
 
 def eps_grid(eps_max: float, n: int) -> np.ndarray:
