@@ -35,6 +35,7 @@ extern "C" {
 #define VBK_MAX_MODES 4
 #define VBK_MAX_STATES 4
 #define VBK_MAX_CHANNELS 8
+#define VBK_MAX_CTERMS 32
 
 /* Return codes of the API calls. */
 #define VBK_OK 0
@@ -64,14 +65,30 @@ typedef struct {
     int pow[VBK_MAX_MODES];
 } vbk_term;
 
-/* Coupling of discrete state d to partial wave mu, independent of q (Sec. II.B):
- * width Gamma(eps) = a * eps^(l + 1/2) * exp(-b * eps), f = sqrt(Gamma / 2 pi) >= 0,
- * level shift F[Gamma/2pi](E - E_nu) (Eq. IntF).  Each mu couples to one state. */
+/* Coupling of discrete state d to partial wave mu (Sec. II.B): width
+ * Gamma(eps) = a * eps^(l + 1/2) * exp(-b * eps), f = sqrt(Gamma / 2 pi) >= 0.  Without
+ * polynomial terms (vbk_cterm) the coupling is independent of q and the channel adds the level
+ * shift F[Gamma/2pi](E - E_nu) (Eq. IntF) to the diagonal of its state.  A state couples to a
+ * partial wave at most once. */
 typedef struct {
     int d, mu;
     double a, b;
     int l;
 } vbk_channel;
+
+/* One term of the coupling polynomial P_c(q) of channel c, making the coupling q-dependent
+ * and separable, V^mu_{d eps}(q) = f_d^mu(eps) P_c(q) (Sec. II.C): coef * prod_m q_m^pow[m],
+ * powers as in vbk_term (products of truncated matrices).  A channel without terms has
+ * P_c = 1.  A partial wave whose channels carry terms, or that couples to two or more states,
+ * contributes the non-local operator F_dd' = sum_mu P_c F[f_c f_c'](E - H_0) P_c' over the
+ * ordered pairs (c, c') of its channels (Eq. FE, from Eq. F_gen), with
+ * f_c f_c' = (sqrt(a_c a_c') / 2 pi) eps^(l + 1/2) exp(-(b_c + b_c') eps / 2); the channels
+ * of such a wave must share l.  Phi^{v mu} then carries f_c(eps) P_c(q)|v> (Sec. II.D). */
+typedef struct {
+    int channel;
+    double coef;
+    int pow[VBK_MAX_MODES];
+} vbk_cterm;
 
 /* Model: states, harmonic modes (Eq. H0harm: omega[m], basis n = 0..n_basis[m]-1),
  * polynomial U and continuum channels.  Arrays are copied by vbk_build_model. */
@@ -84,6 +101,8 @@ typedef struct {
     const vbk_term* terms;         /* host, [n_terms]             */
     int n_channels;                /* 1..VBK_MAX_CHANNELS         */
     const vbk_channel* channels;   /* host, [n_channels]          */
+    int n_cterms;                  /* 0..VBK_MAX_CTERMS (0: every coupling independent of q) */
+    const vbk_cterm* cterms;       /* host, [n_cterms], or NULL when n_cterms = 0            */
 } vbk_model_desc;
 
 typedef struct vbk_model vbk_model;
@@ -144,8 +163,10 @@ typedef struct {
 /* Builds a model from the description (Sec. II; tables of Sec. III: oscillator matrix
  * elements and their truncated powers are precomputed once).  *out receives a handle.
  * Errors: VBK_ERR_INVALID_ARG for out-of-range sizes/indices, non-finite or non-positive
- * omega, b <= 0, a < 0, l < 0, a partial wave coupled to two states; VBK_ERR_NO_DEVICE,
- * VBK_ERR_OOM, VBK_ERR_CUDA. */
+ * omega, b <= 0, a < 0, l < 0, a state coupled twice to one partial wave, channels of a
+ * q-dependent partial wave with different l, a coupling term naming no channel;
+ * VBK_ERR_UNSUPPORTED when the q-dependent couplings need more than 64 polynomial points in
+ * all; VBK_ERR_NO_DEVICE, VBK_ERR_OOM, VBK_ERR_CUDA. */
 int vbk_build_model(const vbk_model_desc* desc, vbk_model** out);
 
 /* Releases the model and its device tables.  NULL is ignored. */
@@ -193,7 +214,8 @@ int vbk_eels(vbk_model* model, int n_eps, int n_vi, const int* vi, int n_vf, con
  *   dL/dtheta = Re sum [ sum_f w_f dPhi_f^T psi + lambda^T dPhi_i - lambda^T (dA/dtheta) psi ],
  *   w_f = dL/dsigma * 2 pi^3/eps_i * 2 conj(T_f).
  * theta_ids (host [n_theta]): k < n_terms is the coefficient of term k; n_terms + 2c and
- * n_terms + 2c + 1 are a and b of channel c.
+ * n_terms + 2c + 1 are a and b of channel c (VBK_ERR_UNSUPPORTED for a channel of a
+ * q-dependent partial wave, whose a and b enter the non-local level shift).
  *   grad      : host double [n_theta], written.
  *   stats     : host [n_eps * n_vi * n_mu] adjoint solve outcomes, or NULL.
  * Synchronises `stream`. */
@@ -203,15 +225,19 @@ int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi
                       double* grad, vbk_stats* stats, void* stream);
 
 /* y = A(E_k) x for a batch: the matrix-free operator of Sec. III (diagonal energy and
- * level-shift factors plus the q-polynomial stencils).
+ * level-shift factors plus the q-polynomial stencils; with q-dependent couplings also the
+ * non-local level shift of Eq. FE, applied as two stencil passes through the coupling
+ * polynomials with the pair transforms tabulated per energy; only variant 8 (or -1) then).
  *   E       : host [n_E] total energies.   n_vec : vectors per energy.
  *   x_dev, y_dev : device complex128 [n_E][n_vec][N].
  *   precision: VBK_FP64 computes in FP64; VBK_MIXED rounds x and the operator to FP32,
  *   computes in FP32 and widens y.
- *   variant : kernel variant, -1 = the model's autotuned choice; 0..3 = direct kernel with
- *   1, 2, 4, 8 systems per thread; 4..7 = shared-memory-windowed kernel with (systems,
- *   elements) per thread (1,4), (2,4), (4,2), (8,1).  VBK_ERR_INVALID_ARG if the variant
- *   does not fit this model and precision.  Asynchronous on `stream`. */
+ *   variant : kernel variant, -1 = the model's autotuned choice; 0..3 = register-blocked
+ *   kernel with (systems, elements) per thread (1,4), (2,4), (4,2), (2,2); 4..7 = shared-
+ *   memory-windowed kernel with (1,4), (2,4), (4,2), (8,1); 8, 9 = direct kernel with 1 or 4
+ *   systems per thread; 10, 11 = one or two systems per thread block with x in shared memory
+ *   (VBK_MIXED only).  VBK_ERR_INVALID_ARG if the variant does not fit this model and
+ *   precision.  Asynchronous on `stream`. */
 int vbk_matvec(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,
                void* y_dev, int precision, int variant, void* stream);
 
@@ -227,12 +253,15 @@ int vbk_matvec(vbk_model* model, int n_E, const double* E, int n_vec, const void
  * The first call on a device looks up the array's device address (set-up); make that first
  * call before any stream capture.  All calls share the array: calls that overlap on the GPU
  * (other streams, other host threads) race.  Synchronises `stream`.  No cudaMalloc, cudaFree
- * or allocating library routine is called. */
+ * or allocating library routine is called.  Models with q-dependent couplings (vbk_cterm, or a
+ * partial wave coupled to several states) need per-call tables of the non-local level shift
+ * that the array does not hold: VBK_ERR_UNSUPPORTED. */
 int vbk_matvec_noalloc(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,
                        void* y_dev, void* stream);
 
 /* z = B^-1 r with B the block-diagonal preconditioner `precond_span` of A(E_k) (Sec. III.B),
- * factored as L D L^T.  Shapes as in vbk_matvec.  Asynchronous on `stream`.  A zero pivot
+ * factored as L D L^T; its blocks include the entries of the non-local level shift (Eq. FE)
+ * that fall inside them.  Shapes as in vbk_matvec.  Asynchronous on `stream`.  A zero pivot
  * gives VBK_ERR_NOT_CONVERGED (and synchronises). */
 int vbk_precond_apply(vbk_model* model, int n_E, const double* E, int n_vec, int precond_span,
                       const void* r_dev, void* z_dev, int precision, void* stream);

@@ -36,6 +36,10 @@ class vbk_channel(C.Structure):
     _fields_ = [("d", C.c_int), ("mu", C.c_int), ("a", C.c_double), ("b", C.c_double), ("l", C.c_int)]
 
 
+class vbk_cterm(C.Structure):
+    _fields_ = [("channel", C.c_int), ("coef", C.c_double), ("pow", C.c_int * VBK_MAX_MODES)]
+
+
 class vbk_model_desc(C.Structure):
     _fields_ = [
         ("n_states", C.c_int),
@@ -46,6 +50,8 @@ class vbk_model_desc(C.Structure):
         ("terms", C.POINTER(vbk_term)),
         ("n_channels", C.c_int),
         ("channels", C.POINTER(vbk_channel)),
+        ("n_cterms", C.c_int),
+        ("cterms", C.POINTER(vbk_cterm)),
     ]
 
 
@@ -201,6 +207,14 @@ class Model:
                 int(c["d"]), int(c["mu"]), float(c["a"]), float(c["b"]), int(c["l"]))
         d.n_terms, d.terms = len(desc["terms"]), terms
         d.n_channels, d.channels = len(desc["channels"]), chans
+        # coupling polynomials of q-dependent channels (Sec. II.C), channel by channel
+        ct = [(k, t) for k, c in enumerate(desc["channels"]) for t in (c.get("terms") or [])]
+        cterms = (vbk_cterm * max(1, len(ct)))()
+        for j, (k, t) in enumerate(ct):
+            cterms[j].channel, cterms[j].coef = k, float(t["coef"])
+            for i, pw in enumerate(t["pow"]):
+                cterms[j].pow[i] = int(pw)
+        d.n_cterms, d.cterms = len(ct), cterms
         h = C.c_void_p()
         _check(_lib.vbk_build_model(C.byref(d), C.byref(h)), "vbk_build_model")
         self.handle = h

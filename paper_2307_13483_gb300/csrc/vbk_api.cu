@@ -85,9 +85,13 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         m->stride[k] = str;
         str *= d->n_basis[k];
     }
+    if (d->n_cterms < 0 || d->n_cterms > VBK_MAX_CTERMS || (d->n_cterms > 0 && !d->cterms))
+        return invalid("n_cterms out of range (0..VBK_MAX_CTERMS) or cterms missing");
     m->terms.assign(d->terms, d->terms + d->n_terms);
     m->chans.assign(d->channels, d->channels + d->n_channels);
-    int mu_d[VBK_MAX_CHANNELS];
+    m->cterms.assign(d->cterms, d->cterms + d->n_cterms);
+    int mu_d[VBK_MAX_CHANNELS], mu_cnt[VBK_MAX_CHANNELS] = {0}, mu_sw[VBK_MAX_CHANNELS] = {0};
+    bool dmu_seen[MAXS][VBK_MAX_CHANNELS] = {};
     for (int k = 0; k < VBK_MAX_CHANNELS; ++k) mu_d[k] = -1;
     int nmu = 0;
     for (const auto& c : m->chans) {
@@ -95,12 +99,34 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         if (c.mu < 0 || c.mu >= VBK_MAX_CHANNELS) return invalid("partial-wave index out of range");
         if (!(c.a >= 0.0) || !std::isfinite(c.a) || !(c.b > 0.0) || !std::isfinite(c.b) || c.l < 0 || c.l > 20)
             return invalid("channel parameters out of range (a >= 0, b > 0, 0 <= l <= 20)");
-        if (mu_d[c.mu] >= 0) return invalid("a partial wave may couple to a single state only");
+        if (dmu_seen[c.d][c.mu]) return invalid("a state couples to a partial wave at most once");
+        dmu_seen[c.d][c.mu] = true;
         mu_d[c.mu] = c.d;
+        mu_cnt[c.mu] += 1;
         nmu = std::max(nmu, c.mu + 1);
     }
     m->nmu = nmu;
     int kmax[MAXM] = {0};
+    // q-dependent couplings (Sec. II.C): a wave with two or more states, or a coupling polynomial
+    for (const auto& t : m->cterms) {
+        if (t.channel < 0 || t.channel >= (int)m->chans.size()) return invalid("coupling term names no channel");
+        if (!std::isfinite(t.coef)) return invalid("coupling term coefficient not finite");
+        for (int k = 0; k < m->M; ++k) {
+            if (t.pow[k] < 0 || t.pow[k] > 8) return invalid("coupling term power out of range (0..8)");
+            kmax[k] = std::max(kmax[k], t.pow[k]);
+        }
+        for (int k = m->M; k < VBK_MAX_MODES; ++k)
+            if (t.pow[k] != 0) return invalid("coupling term power given for a mode beyond n_modes");
+        mu_sw[m->chans[t.channel].mu] = 1;
+    }
+    for (int mu = 0; mu < VBK_MAX_CHANNELS; ++mu)
+        if (mu_cnt[mu] > 1) mu_sw[mu] = 1;
+    for (const auto& c : m->chans)
+        for (const auto& c2 : m->chans)
+            if (c.mu == c2.mu && mu_sw[c.mu] && c.l != c2.l)
+                return invalid("the channels of a q-dependent partial wave must share l");
+    for (int mu = 0; mu < VBK_MAX_CHANNELS; ++mu)
+        if (mu_sw[mu]) mu_d[mu] = -1;
     for (const auto& t : m->terms) {
         if (t.d < 0 || t.dp < 0 || t.d >= m->ns || t.dp >= m->ns || t.d > t.dp) return invalid("term state indices must satisfy 0 <= d <= dp < n_states");
         if (!std::isfinite(t.coef)) return invalid("term coefficient not finite");
@@ -230,6 +256,98 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         dm.ch_ib[c] = 1.0 / m->chans[c].b;
     }
     for (int k = 0; k < MAXCH; ++k) dm.mu_d[k] = mu_d[k];
+    // sandwich channels: points of the coupling polynomials (merged by offset), pair transforms
+    std::vector<double> spc;  // [point][nu]
+    {
+        for (int k = 0; k < MAXCH; ++k) {
+            dm.ch_sw[k] = 0;
+            dm.mu_sw[k] = mu_sw[k];
+            for (int k2 = 0; k2 < MAXCH; ++k2) dm.sc_pair[k][k2] = -1;
+        }
+        dm.nsc = 0;
+        dm.npair = 0;
+        int npts = 0;
+        dm.sc_pbeg[0] = 0;
+        for (int c = 0; c < dm.nchan; ++c) {
+            if (!mu_sw[m->chans[c].mu]) continue;
+            const int j = dm.nsc++;
+            dm.ch_sw[c] = 1;
+            dm.sc_ch[j] = c;
+            dm.sc_d[j] = m->chans[c].d;
+            dm.sc_mu[j] = m->chans[c].mu;
+            // columns of P_c keyed by the offset vector; no terms: P_c = 1
+            std::vector<std::pair<std::vector<int>, std::vector<double>>> cols;
+            auto column = [&](const std::vector<int>& delta) -> std::vector<double>& {
+                for (auto& pr : cols)
+                    if (pr.first == delta) return pr.second;
+                cols.emplace_back(delta, std::vector<double>(m->Nnu, 0.0));
+                return cols.back().second;
+            };
+            bool any = false;
+            for (const auto& t : m->cterms) {
+                if (t.channel != c) continue;
+                any = true;
+                int cnt[MAXM], o[MAXM];
+                long long ncomb = 1;
+                for (int k = 0; k < m->M; ++k) {
+                    cnt[k] = t.pow[k] + 1;
+                    ncomb *= cnt[k];
+                }
+                for (long long cb = 0; cb < ncomb; ++cb) {
+                    long long rem = cb;
+                    for (int k = m->M - 1; k >= 0; --k) {
+                        o[k] = (int)(rem % cnt[k]);
+                        rem /= cnt[k];
+                    }
+                    std::vector<int> delta(m->M, 0);
+                    for (int k = 0; k < m->M; ++k) delta[k] = t.pow[k] ? -t.pow[k] + 2 * o[k] : 0;
+                    std::vector<double>& col = column(delta);
+                    for (int nu = 0; nu < m->Nnu; ++nu) {
+                        double v = t.coef;
+                        for (int mm = 0; mm < m->M && v != 0.0; ++mm) {
+                            if (!t.pow[mm]) continue;
+                            const int n = (nu / m->stride[mm]) % m->nb[mm];
+                            const int nn = n + delta[mm];
+                            v = (nn >= 0 && nn < m->nb[mm])
+                                    ? v * m->tab[m->colbase[mm][t.pow[mm]] + o[mm] * m->nb[mm] + n]
+                                    : 0.0;
+                        }
+                        col[nu] += v;
+                    }
+                }
+            }
+            if (!any) column(std::vector<int>(m->M, 0)).assign(m->Nnu, 1.0);
+            for (auto& pr : cols) {
+                bool nz = false;
+                for (double v : pr.second) nz = nz || v != 0.0;
+                if (!nz) continue;
+                if (npts >= MAXSP)
+                    return (g_last_error = "the coupling polynomials have more than 64 points", VBK_ERR_UNSUPPORTED);
+                int lin = 0;
+                for (int k = 0; k < m->M; ++k) lin += pr.first[k] * m->stride[k];
+                dm.sp_lin[npts++] = lin;
+                m->sp_delta.push_back(pr.first);
+                spc.insert(spc.end(), pr.second.begin(), pr.second.end());
+            }
+            dm.sc_pbeg[j + 1] = npts;
+        }
+        for (int j = 0; j < dm.nsc; ++j)
+            for (int j2 = j; j2 < dm.nsc; ++j2) {
+                if (dm.sc_mu[j] != dm.sc_mu[j2]) continue;
+                if (dm.npair >= MAXPAIR)
+                    return (g_last_error = "more than 20 channel pairs of q-dependent partial waves", VBK_ERR_UNSUPPORTED);
+                const int p = dm.npair++;
+                dm.sc_pair[j][j2] = dm.sc_pair[j2][j] = p;
+                const vbk_channel &ca = m->chans[dm.sc_ch[j]], &cb = m->chans[dm.sc_ch[j2]];
+                // f_j f_j' = (sqrt(a_j a_j') / 2 pi) eps^(l+1/2) exp(-(b_j + b_j') eps / 2): one-channel form
+                dm.pr_l[p] = ca.l;
+                dm.pr_a[p] = j == j2 ? ca.a : std::sqrt(ca.a * cb.a);
+                dm.pr_b[p] = j == j2 ? ca.b : 0.5 * (ca.b + cb.b);
+                dm.pr_sb[p] = std::sqrt(dm.pr_b[p]);
+                dm.pr_isb[p] = 1.0 / dm.pr_sb[p];
+                dm.pr_ib[p] = 1.0 / dm.pr_b[p];
+            }
+    }
     // coefficient columns of the stencil points (Sec. III: "all energy factors and square roots can
     // be precalculated")
     const size_t npc = std::max<size_t>(1, offd.size()) * (size_t)m->Nnu;
@@ -379,6 +497,20 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         dm.enu = (const double*)b2base;
         dm.u0 = (const double*)(b2base + b11);
     }
+    if (!spc.empty()) {
+        const size_t bs = (spc.size() * sizeof(double) + 255) & ~size_t(255);
+        char* mem2 = nullptr;
+        if ((err = cudaMalloc((void**)&mem2, bs + spc.size() * sizeof(float))) != cudaSuccess)
+            return vbk_cuda_fail(err, "coupling polynomial tables");
+        m->dev_mem2 = mem2;
+        std::vector<float> s32(spc.size());
+        for (size_t k = 0; k < spc.size(); ++k) s32[k] = (float)spc[k];
+        if ((err = cudaMemcpy(mem2, spc.data(), spc.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(mem2 + bs, s32.data(), s32.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return vbk_cuda_fail(err, "coupling polynomial upload");
+        dm.spc64 = (const double*)mem2;
+        dm.spc32 = (const float*)(mem2 + bs);
+    }
     dm.ent = (const DevEntry*)mem;
     dm.dent = (const DevEntry*)(mem + b1);
     dm.tab64 = (const double*)(mem + b1 + b2);
@@ -387,6 +519,7 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     m->desc = *d;
     m->desc.terms = m->terms.data();
     m->desc.channels = m->chans.data();
+    m->desc.cterms = m->cterms.empty() ? nullptr : m->cterms.data();
     return VBK_OK;
 }
 
@@ -420,12 +553,61 @@ struct DevBuf {
 };
 
 // --------------------------------------------------------------------------- kernels
-// Dense right-hand sides Phi^{v_i mu} (Sec. II.D): f_{d(mu)}(E - E_vi) on entry (d(mu), v_i).
+// Phi^{v mu} of a q-dependent wave (Sec. II.C, II.D): sum over its channels j of
+// f_j(eps) (P_j |v>) in state d_j, i.e. w * f_j * (P_j)_{v + lin_k, v} at v + lin_k for every point
+// k of P_j (P_j symmetric), added to the vector g of one system.  The targets are distinct: the
+// offsets of one channel differ and the channels of one wave sit in different states.
+__device__ void sand_scatter(const DevModel& md, int mu, double eps, int v, double2 w, double2* __restrict__ g) {
+    for (int j = 0; j < md.nsc; ++j) {
+        if (md.sc_mu[j] != mu) continue;
+        const int c = md.sc_ch[j];
+        const double f = vbk_amplitude(eps, md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+        if (f == 0.0) continue;
+        double2* gd = g + (long long)md.sc_d[j] * md.Nnu;
+        for (int k = md.sc_pbeg[j]; k < md.sc_pbeg[j + 1]; ++k) {
+            const double cf = md.spc64[(long long)k * md.Nnu + v];
+            if (cf == 0.0) continue;
+            double2& t = gd[v + md.sp_lin[k]];
+            t.x += w.x * f * cf;
+            t.y += w.y * f * cf;
+        }
+    }
+}
+
+// <Phi^{v mu} | psi> of a q-dependent wave: sum_j f_j(eps) (P_j psi_(d_j))(v)  (Eq. crs2, real Phi).
+__device__ double2 sand_project(const DevModel& md, int mu, double eps, int v, const double2* __restrict__ ps) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < md.nsc; ++j) {
+        if (md.sc_mu[j] != mu) continue;
+        const int c = md.sc_ch[j];
+        const double f = vbk_amplitude(eps, md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+        if (f == 0.0) continue;
+        const double2* pd = ps + (long long)md.sc_d[j] * md.Nnu;
+        double2 t = make_double2(0.0, 0.0);
+        for (int k = md.sc_pbeg[j]; k < md.sc_pbeg[j + 1]; ++k) {
+            const double cf = md.spc64[(long long)k * md.Nnu + v];
+            if (cf == 0.0) continue;
+            const double2 x = pd[v + md.sp_lin[k]];
+            t.x += cf * x.x;
+            t.y += cf * x.y;
+        }
+        acc.x += f * t.x;
+        acc.y += f * t.y;
+    }
+    return acc;
+}
+
+// Dense right-hand sides Phi^{v_i mu} (Sec. II.D): f_{d(mu)}(E - E_vi) on entry (d(mu), v_i), or
+// the polynomial columns of a q-dependent wave (Sec. II.C).  b is zero on entry.
 __global__ void k_build_rhs(DevModel md, int nsys, int n_vi, const double* __restrict__ eps, const int* __restrict__ vflat,
                             double2* __restrict__ b) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     const int mu = s % md.nmu, i = (s / md.nmu) % n_vi, e = s / (md.nmu * n_vi);
+    if (md.mu_sw[mu]) {
+        sand_scatter(md, mu, eps[e], vflat[i], make_double2(1.0, 0.0), b + (long long)s * md.N);
+        return;
+    }
     const int d = md.mu_d[mu];
     if (d < 0) return;
     for (int c = 0; c < md.nchan; ++c)
@@ -457,7 +639,9 @@ __global__ void k_sigma(DevModel md, int n_eps, int n_vi, int n_vf, const double
         for (int mf = 0; mf < nmu; ++mf) {
             const int d = md.mu_d[mf], c = chan_of_mu(md, mf);
             double2 tv = make_double2(0.0, 0.0);
-            if (d >= 0 && c >= 0) {
+            if (md.mu_sw[mf]) {
+                tv = sand_project(md, mf, E - E_vf[f], vf_flat[f], ps);
+            } else if (d >= 0 && c >= 0) {
                 const double amp = vbk_amplitude(E - E_vf[f], md.ch_a[c], md.ch_b[c], md.ch_l[c]);
                 const double2 pv = ps[(long long)d * md.Nnu + vf_flat[f]];
                 tv = make_double2(amp * pv.x, amp * pv.y);
@@ -507,6 +691,10 @@ __global__ void k_adjoint_rhs(DevModel md, int n_eps, int n_vi, int n_vf, const 
             const double2 tv = T[((((long long)e * n_vi + i) * nmu + mi) * n_vf + f) * nmu + mf];
             const double2 w = make_double2(dl * pre * tv.x, -dl * pre * tv.y);
             W[(s * n_vf + f) * nmu + mf] = w;
+            if (md.mu_sw[mf]) {
+                sand_scatter(md, mf, E - E_vf[f], vf_flat[f], w, g + s * md.N);
+                continue;
+            }
             const int d = md.mu_d[mf], c = chan_of_mu(md, mf);
             if (d < 0 || c < 0) continue;
             const double amp = vbk_amplitude(E - E_vf[f], md.ch_a[c], md.ch_b[c], md.ch_l[c]);
@@ -728,6 +916,7 @@ int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
 void vbk_free_model(vbk_model* m) {
     if (!m) return;
     if (m->dev_mem) cudaFree(m->dev_mem);
+    if (m->dev_mem2) cudaFree(m->dev_mem2);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->pool) {
         cudaDeviceSynchronize();  // outstanding frees of this model's calls complete before the pool goes
@@ -941,6 +1130,10 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
             g.kind = 1 + (id - nterm) % 2;
             g.c = (id - nterm) / 2;
             if (g.kind == 1 && !(m->chans[g.c].a > 0.0)) return invalid("gradient in a needs a > 0");
+            if (m->dm.ch_sw[g.c]) {
+                g_last_error = "adjoint: gradients in a and b of a q-dependent channel are not available";
+                return VBK_ERR_UNSUPPORTED;
+            }
         }
         gps[k] = g;
     }
@@ -1145,6 +1338,30 @@ int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* bp) {
         bp->ent_dc[k] = (int)dc;
         p = std::max<int>(p, (int)std::llabs(dc));
     }
+    // entries of the sandwich operator (q-dependent couplings) that fall inside a block
+    bp->sw_combo.clear();
+    const DevModel& dm = m->dm;
+    for (int j = 0; j < dm.nsc; ++j)
+        for (int j2 = 0; j2 < dm.nsc; ++j2) {
+            const int pr = dm.sc_pair[j][j2];
+            if (pr < 0) continue;
+            for (int k = dm.sc_pbeg[j]; k < dm.sc_pbeg[j + 1]; ++k)
+                for (int k2 = dm.sc_pbeg[j2]; k2 < dm.sc_pbeg[j2 + 1]; ++k2) {
+                    const int dd = dm.sc_d[j2] - dm.sc_d[j];
+                    bool in = sd || dd == 0;
+                    long long dc = sd ? dd : 0;
+                    for (int mm = 0; mm < m->M && in; ++mm) {
+                        const int delta = m->sp_delta[k][mm] + m->sp_delta[k2][mm];
+                        if (span & (2 << mm))
+                            dc += (long long)delta * cstr[mm];
+                        else if (delta != 0)
+                            in = false;
+                    }
+                    if (!in || dc == 0) continue;  // dc = 0: on the diagonal (in the diagonal tables)
+                    bp->sw_combo.insert(bp->sw_combo.end(), {dm.sc_d[j], k, k2, pr, (int)dc});
+                    p = std::max<int>(p, (int)std::llabs(dc));
+                }
+        }
     if (p > PWMAX) {
         g_last_error = "block preconditioner bandwidth " + std::to_string(p) + " exceeds the supported " + std::to_string(PWMAX);
         return VBK_ERR_UNSUPPORTED;

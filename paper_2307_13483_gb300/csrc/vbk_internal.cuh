@@ -22,6 +22,8 @@
 #define MAXCH VBK_MAX_CHANNELS
 #define PMAX 16    // widest band handled by the thread-per-block LDL^T kernels
 #define PWMAX 160  // widest band handled by the cooperative (one CTA / one warp per block) LDL^T kernels
+#define MAXPAIR 20  // pair transforms of q-dependent channels (a wave couples to at most MAXS states)
+#define MAXSP 64    // polynomial points of all q-dependent channels
 
 // ------------------------------------------------------------------------------- complex
 template <class R> struct cx_t;
@@ -147,7 +149,32 @@ struct DevModel {
     int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
     double ch_a[MAXCH], ch_b[MAXCH], ch_sb[MAXCH];  // ch_sb = sqrt(b)
     double ch_isb[MAXCH], ch_ib[MAXCH];            // 1 / sqrt(b), 1 / b
-    int mu_d[MAXCH];  // discrete state coupled to partial wave mu
+    int mu_d[MAXCH];  // discrete state coupled to partial wave mu (-1: none, or a q-dependent wave)
+    // q-dependent continuum coupling (Sec. II.C, Eq. FE).  The channels of a partial wave that
+    // couples to several states or through a polynomial P_c(q) are "sandwich" channels
+    // j = 0..nsc-1: instead of a diagonal term they act as  F x = sum_j P_j w_j  with
+    // w_j = sum_j' g_(j,j') P_j' x_(d_j'),  g_(j,j')(nu) = F[f_j f_j'](E - E_nu) for j, j' of one wave.
+    int ch_sw[MAXCH];  // 1 if channel c is a sandwich channel
+    int mu_sw[MAXCH];  // 1 if partial wave mu has sandwich channels
+    int nsc, npair;
+    int sc_ch[MAXCH], sc_d[MAXCH], sc_mu[MAXCH];
+    int sc_pbeg[MAXCH + 1];     // polynomial points of sandwich channel j: [sc_pbeg[j], sc_pbeg[j + 1])
+    int sc_pair[MAXCH][MAXCH];  // pair-table index of (j, j') of one wave (symmetric), -1 otherwise
+    int pr_l[MAXPAIR];
+    // pair transform constants: a = sqrt(a_j a_j'), b = (b_j + b_j') / 2, sqrt(b), 1 / sqrt(b), 1 / b
+    double pr_a[MAXPAIR], pr_b[MAXPAIR], pr_sb[MAXPAIR], pr_isb[MAXPAIR], pr_ib[MAXPAIR];
+    int sp_lin[MAXSP];  // in-plane offset of polynomial point k (the offsets of one channel are distinct)
+    // spc[k][nu] = (P_j)_{nu, nu + lin_k} for point k of channel j, zero where nu + lin_k leaves the
+    // basis; P_j is symmetric, so the same column gives (P_j)_{nu + lin_k, nu}
+    const double* spc64;
+    const float* spc32;
+    // per-call buffers, set on a solver's or operator's own copy of the model (null in the model)
+    double2* sg64;   // g[e][pair][nu]
+    float2* sg32;
+    double2* sfd64;  // diagonal of the sandwich operator [e][N] (it is part of the diagonal tables)
+    float2* sfd32;
+    double2* sw64;   // w[list slot][j][nu]
+    float2* sw32;
 };
 
 // Host copy of a term, channel etc.
@@ -168,6 +195,9 @@ struct vbk_model {
     vbk_model_desc desc;  // with pointers into the vectors below
     std::vector<vbk_term> terms;
     std::vector<vbk_channel> chans;
+    std::vector<vbk_cterm> cterms;
+    void* dev_mem2 = nullptr;  // coefficient columns of the coupling polynomials (q-dependent channels)
+    std::vector<std::vector<int>> sp_delta;  // per polynomial point of a sandwich channel: offset per mode
     int M = 0, ns = 0, Nnu = 0, N = 0, nmu = 0;
     int nb[MAXM] = {0}, stride[MAXM] = {0};
     std::vector<double> tab;          // per-(mode, power, offset) columns of (q^k)_{n, n+delta}
@@ -414,6 +444,11 @@ struct BlockPlan {
     bool wide = false;  // p > PMAX: level-blocked factor (levels of S chain positions, K levels)
     int S = 0, K = 0;
     std::vector<int> ent_dc;  // per off-diagonal stencil point: chain offset (0 = outside block)
+    // entries of the sandwich operator inside a block (q-dependent couplings, Eq. FE): for row
+    // state d, points k of P_j (d_j = d) and k2 of P_j' (j' of the same wave), the entry
+    // (d, nu) -> (d_j', nu + lin_k + lin_k2) receives spc[k][nu] g_(j,j')(nu + lin_k) spc[k2][nu + lin_k];
+    // five ints each: d, k, k2, pair, chain offset (nonzero)
+    std::vector<int> sw_combo;
 };
 int vbk_make_block_plan(const vbk_model* m, int span, BlockPlan* plan);
 

@@ -139,11 +139,32 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
     const double eps = E[e] - md.enu[nu];
     double re = eps - md.u0[i], im = 0.0;
     for (int c = 0; c < md.nchan; ++c) {
-        if (md.ch_d[c] != d) continue;
+        if (md.ch_d[c] != d || md.ch_sw[c]) continue;
         const double2 F =
             vbk_level_shift_core(eps, md.ch_a[c], md.ch_b[c], md.ch_sb[c], md.ch_isb[c], md.ch_ib[c], md.ch_l[c]);
         re -= F.x;
         im -= F.y;
+    }
+    if (md.nsc) {
+        // diagonal of the sandwich operator (Eq. FE): sum_j sum_k (P_j)_{nu, nu+lin_k}^2 g_(j,j)(nu + lin_k),
+        // from the pair tables written by k_sand_table; part of diag(A), added back by the matvec
+        double fr = 0.0, fi = 0.0;
+        for (int j = 0; j < md.nsc; ++j) {
+            if (md.sc_d[j] != d) continue;
+            const double2* g = md.sg64 + ((long long)e * md.npair + md.sc_pair[j][j]) * md.Nnu;
+            for (int k = md.sc_pbeg[j]; k < md.sc_pbeg[j + 1]; ++k) {
+                const double c = md.spc64[(long long)k * md.Nnu + nu];
+                if (c != 0.0) {  // nonzero only where nu + lin_k lies in the basis
+                    const double2 gv = g[nu + md.sp_lin[k]];
+                    fr = fma(c * c, gv.x, fr);
+                    fi = fma(c * c, gv.y, fi);
+                }
+            }
+        }
+        re -= fr;
+        im -= fi;
+        md.sfd64[t] = make_double2(fr, fi);
+        if (md.sfd32) md.sfd32[t] = make_float2((float)fr, (float)fi);
     }
     if (d64) d64[t] = make_double2(re, im);
     if (dsp) {  // double-float pair (hi, lo) of the FP64 value for the double-float residual
@@ -172,6 +193,167 @@ constexpr int MV_MAXPTS = 256;
 template <class R> __device__ __forceinline__ const R* pcp(const DevModel& md);
 template <> __device__ __forceinline__ const float* pcp<float>(const DevModel& md) { return md.pc32; }
 template <> __device__ __forceinline__ const double* pcp<double>(const DevModel& md) { return md.pc64; }
+
+// --------------------------------------------------- q-dependent coupling (Sec. II.C, Eq. FE)
+// g[e][p][nu] = F[f_j f_j'](E_e - E_nu) for every pair p = (j, j') of sandwich channels of one
+// partial wave, in FP64 and (when requested) FP32.
+__global__ void k_sand_table(DevModel md, int nE, const double* __restrict__ E) {
+    const int e = blockIdx.y, nu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nu >= md.Nnu) return;
+    const double eps = E[e] - md.enu[nu];
+    for (int p = 0; p < md.npair; ++p) {
+        const double2 F = vbk_level_shift_core(eps, md.pr_a[p], md.pr_b[p], md.pr_sb[p], md.pr_isb[p], md.pr_ib[p], md.pr_l[p]);
+        const long long t = ((long long)e * md.npair + p) * md.Nnu + nu;
+        md.sg64[t] = F;
+        if (md.sg32) md.sg32[t] = to_f(F);
+    }
+}
+
+template <class R> __device__ __forceinline__ const R* spcp(const DevModel& md);
+template <> __device__ __forceinline__ const float* spcp<float>(const DevModel& md) { return md.spc32; }
+template <> __device__ __forceinline__ const double* spcp<double>(const DevModel& md) { return md.spc64; }
+template <class R> __device__ __forceinline__ const cx<R>* sgp(const DevModel& md);
+template <> __device__ __forceinline__ const float2* sgp<float>(const DevModel& md) { return md.sg32; }
+template <> __device__ __forceinline__ const double2* sgp<double>(const DevModel& md) { return md.sg64; }
+template <class R> __device__ __forceinline__ const cx<R>* sfdp(const DevModel& md);
+template <> __device__ __forceinline__ const float2* sfdp<float>(const DevModel& md) { return md.sfd32; }
+template <> __device__ __forceinline__ const double2* sfdp<double>(const DevModel& md) { return md.sfd64; }
+template <class R> __device__ __forceinline__ cx<R>* swp(const DevModel& md);
+template <> __device__ __forceinline__ float2* swp<float>(const DevModel& md) { return md.sw32; }
+template <> __device__ __forceinline__ double2* swp<double>(const DevModel& md) { return md.sw64; }
+
+// Inner half of the sandwich product, per system of the list (first pass of the staged stencil):
+//   u_j = P_j x_(d_j)   (polynomial points of channel j),
+//   w[slot][j][nu] = sum_j' g_(j,j')(nu) u_j'(nu)   over the channels j' of the same wave.
+// Grid: x = chunks of TPB levels nu, y = list slots.
+template <class R>
+__global__ void __launch_bounds__(TPB) k_sand_w(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
+                                               const cx<R>* __restrict__ x, long long xs) {
+    const int li = blockIdx.y, nu = blockIdx.x * TPB + threadIdx.x;
+    const int Nnu = md.Nnu;
+    if (nu >= Nnu || li >= nlist) return;
+    int s = sel.list ? sel.list[li] : li;
+    if (s < 0 || (sel.act && !sel.act[s])) return;
+    const int e = sys_e[s];
+    const cx<R>* xp = x + (long long)s * xs;
+    const R* pc = spcp<R>(md);
+    cx<R> u[MAXCH];
+#pragma unroll
+    for (int j = 0; j < MAXCH; ++j) {
+        u[j] = mkc<R>(0, 0);
+        if (j < md.nsc) {
+            const cx<R>* xd = xp + (long long)md.sc_d[j] * Nnu;
+            for (int k = md.sc_pbeg[j]; k < md.sc_pbeg[j + 1]; ++k) {
+                const R c = __ldg(pc + (long long)k * Nnu + nu);
+                if (c != (R)0) {
+                    const cx<R> v = xd[nu + md.sp_lin[k]];
+                    u[j].x = fma(c, v.x, u[j].x);
+                    u[j].y = fma(c, v.y, u[j].y);
+                }
+            }
+        }
+    }
+    const cx<R>* g = sgp<R>(md) + (long long)e * md.npair * Nnu + nu;
+    cx<R>* w = swp<R>(md) + (long long)li * md.nsc * Nnu + nu;
+#pragma unroll
+    for (int j = 0; j < MAXCH; ++j) {
+        if (j < md.nsc) {
+            cx<R> acc = mkc<R>(0, 0);
+#pragma unroll
+            for (int j2 = 0; j2 < MAXCH; ++j2) {
+                const int p = j2 < md.nsc ? md.sc_pair[j][j2] : -1;
+                if (p >= 0) acc = cfma<R>(g[(long long)p * Nnu], u[j2], acc);
+            }
+            w[(long long)j * Nnu] = acc;
+        }
+    }
+}
+
+// y = A x (or b - A x) for models with sandwich channels: the stencil of k_matvec2 (one system
+// per thread) plus the outer half of the sandwich product,
+//   y_d -= sum_{j: d_j = d} P_j w_j  and  y_d += diag(F_s) x_d
+// (the diagonal tables hold the whole diagonal of A, including that of the sandwich operator).
+// Reads w of the same list slot, written by k_sand_w.  Same grid and partials as k_matvec2<R, 1>.
+template <class R>
+__global__ void __launch_bounds__(TPB) k_matvec_sw(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
+                                                  const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x, long long xs,
+                                                  cx<R>* __restrict__ y, long long ys, const double2* __restrict__ b,
+                                                  double2* __restrict__ part, int red) {
+    __shared__ int offs[MV_MAXPTS];
+    __shared__ cx<R> redsh[TPB / 32];
+    const int nchunk = (md.Nnu + TPB - 1) / TPB;
+    const int d = blockIdx.x / nchunk;
+    const int nu = (blockIdx.x - d * nchunk) * TPB + threadIdx.x;
+    const int N = md.N, Nnu = md.Nnu;
+    const int pb = md.ebeg[d], np = min(md.ebeg[d + 1] - pb, MV_MAXPTS);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const DevEntry& e = md.ent[pb + k];
+        offs[k] = (e.dp - d) * Nnu + e.lin;
+    }
+    const int li = blockIdx.y;
+    int s = -1;
+    if (li < nlist) {
+        s = sel.list ? sel.list[li] : li;
+        if (s >= 0 && sel.act && !sel.act[s]) s = -1;
+    }
+    __syncthreads();
+    const bool on = s >= 0 && nu < Nnu;
+    const int i = d * Nnu + nu;
+    const cx<R>* xp = x + (long long)(s < 0 ? 0 : s) * xs;
+    cx<R> acc = mkc<R>(0, 0), xi = mkc<R>(0, 0);
+    if (on) {
+        const long long te = (long long)sys_e[s] * N + i;
+        xi = xp[i];
+        acc = cmul<R>(cadd<R>(diag[te], sfdp<R>(md)[te]), xi);
+        const R* pc = pcp<R>(md) + (long long)pb * Nnu + nu;
+        for (int k = 0; k < np; ++k) {
+            const R c = __ldg(pc + (long long)k * Nnu);
+            if (c != (R)0) {
+                const cx<R> v = xp[min(max(i + offs[k], 0), N - 1)];
+                acc.x = fma(-c, v.x, acc.x);
+                acc.y = fma(-c, v.y, acc.y);
+            }
+        }
+        const R* sp = spcp<R>(md);
+        for (int j = 0; j < md.nsc; ++j) {
+            if (md.sc_d[j] != d) continue;
+            const cx<R>* wj = swp<R>(md) + ((long long)li * md.nsc + j) * Nnu;
+            for (int k = md.sc_pbeg[j]; k < md.sc_pbeg[j + 1]; ++k) {
+                const R c = __ldg(sp + (long long)k * Nnu + nu);
+                if (c != (R)0) {
+                    const cx<R> v = wj[nu + md.sp_lin[k]];
+                    acc.x = fma(-c, v.x, acc.x);
+                    acc.y = fma(-c, v.y, acc.y);
+                }
+            }
+        }
+    }
+    cx<R> loc = mkc<R>(0, 0);
+    if (on) {
+        cx<R> out = acc;
+        if (b) {
+            const double2 bb = b[(long long)s * N + i];
+            out = mkc<R>((R)bb.x - out.x, (R)bb.y - out.y);
+        }
+        y[(long long)s * ys + i] = out;
+        if (red == 1) loc = cmul<R>(xi, out);
+        else if (red == 2) {
+            const float ox = (float)out.x, oy = (float)out.y;
+            loc = mkc<R>((R)(ox * ox + oy * oy), 0);
+        }
+    }
+    if (red) {
+        const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+        const cx<R> v = warp_sum_c<R>(loc);
+        if (lane == 0) redsh[wp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0 && s >= 0) {
+            cx<R> tot = mkc<R>(0, 0);
+            for (int q = 0; q < TPB / 32; ++q) tot = cadd<R>(tot, redsh[q]);
+            part[(long long)s * gridDim.x + blockIdx.x] = cvt_to_d<R>(tot);
+        }
+    }
+}
 
 template <class R, int S>
 __global__ void __launch_bounds__(TPB) k_matvec2(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
@@ -535,7 +717,31 @@ struct PlanDev {
     const int* run_c0;
     // wide bands (p > PMAX): level size and level count of the block-pentadiagonal form
     int S, K;
+    // sandwich entries inside a block (q-dependent couplings): 5 ints each (see BlockPlan::sw_combo)
+    const int* swc;
+    int nswc;
 };
+
+// Entries of the sandwich operator in row (d, nu) of a block (Eq. FE): for every combination of
+// a point k of P_j and a point k2 of P_j', the value spc[k][nu] g_(j,j')(nu + lin_k) spc[k2][nu + lin_k]
+// at chain offset dc; `add(dc, v)` receives -v (A = ... - F).  Zero coefficients mark neighbours
+// outside the basis.
+template <class R, class Add>
+__device__ __forceinline__ void sand_block_row(const DevModel& md, const PlanDev& pl, int e, int d, int nu, Add add) {
+    const R* sp = spcp<R>(md);
+    for (int t = 0; t < pl.nswc; ++t) {
+        const int* cb = pl.swc + 5 * t;
+        if (cb[0] != d) continue;
+        const int k = cb[1], k2 = cb[2];
+        const R c1 = sp[(long long)k * md.Nnu + nu];
+        if (c1 == (R)0) continue;
+        const int kap = nu + md.sp_lin[k];
+        const R c2 = sp[(long long)k2 * md.Nnu + kap];
+        if (c2 == (R)0) continue;
+        const cx<R> g = sgp<R>(md)[((long long)e * md.npair + cb[3]) * md.Nnu + kap];
+        add(cb[4], mkc<R>(-c1 * c2 * g.x, -c1 * c2 * g.y));
+    }
+}
 
 // B = L D L^T of every block of every energy (Sec. III.B: factors computed once and stored).
 // One thread per (energy, block); F[e][c][k][blk]: k = 0 holds 1/D_c, k >= 1 holds L_{c,c-k}.
@@ -567,6 +773,10 @@ __global__ void k_block_factor(DevModel md, PlanDev pl, int nE, const cx<R>* __r
             R cf;
             if (point_coef<R, M>(pt, n, md, tab, cf)) row[-dc].x -= cf;
         }
+        if (pl.nswc)
+            sand_block_row<R>(md, pl, e, d, nu, [&](int dc, cx<R> v) {
+                if (dc < 0 && dc >= -p && c + dc >= 0) row[-dc] = cadd<R>(row[-dc], v);
+            });
         // row[k] now holds B[c][c-k]; eliminate left to right
         for (int jj = max(0, c - p); jj < c; ++jj) {
             const int kj = c - jj;
@@ -823,6 +1033,15 @@ __device__ void level_assemble(const DevModel& md, const PlanDev& pl, int e, int
                 dst.x -= cf;
             }
         }
+        if (pl.nswc)
+            sand_block_row<R>(md, pl, e, d, nu, [&](int dc, cx<R> v) {
+                const int cp = c + dc;
+                if (cp < 0 || cp >= L) return;
+                const int b = cp / S;
+                if (b < a - 2 || b > a) return;
+                cx<R>& dst = W[((a % 3) * 3 + b % 3) * S2 + (long long)r * S + (cp - b * S)];
+                dst = cadd<R>(dst, v);
+            });
     }
 }
 
@@ -2652,9 +2871,9 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
         run_off.push_back(0);
     }
     const size_t n1 = chain.size(), n2 = base.size(), n3 = std::max<size_t>(1, bp.ent_dc.size()), n4 = run_off.size(),
-                 n5 = run_c0.size();
+                 n5 = run_c0.size(), n6 = bp.sw_combo.size();
     std::vector<int> all;
-    all.reserve(n1 + n2 + n3 + n4 + n5);
+    all.reserve(n1 + n2 + n3 + n4 + n5 + n6);
     all.insert(all.end(), chain.begin(), chain.end());
     all.insert(all.end(), base.begin(), base.end());
     if (bp.ent_dc.empty())
@@ -2663,6 +2882,7 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
         all.insert(all.end(), bp.ent_dc.begin(), bp.ent_dc.end());
     all.insert(all.end(), run_off.begin(), run_off.end());
     all.insert(all.end(), run_c0.begin(), run_c0.end());
+    all.insert(all.end(), bp.sw_combo.begin(), bp.sw_combo.end());
     VBK_CUDA(vbk_alloc(m, &out->mem, all.size() * sizeof(int), st));
     int* p = (int*)out->mem;
     VBK_CUDA(cudaMemcpyAsync(p, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -2671,6 +2891,8 @@ int upload_plan(const BlockPlan& bp, const vbk_model* m, cudaStream_t st, DevPla
     out->pd.ent_dc = p + n1 + n2;
     out->pd.run_off = p + n1 + n2 + n3;
     out->pd.run_c0 = p + n1 + n2 + n3 + n4;
+    out->pd.swc = p + n1 + n2 + n3 + n4 + n5;
+    out->pd.nswc = (int)(n6 / 5);
     // `all` must stay alive until the copy completes
     VBK_CUDA(cudaStreamSynchronize(st));
     return VBK_OK;
@@ -2740,11 +2962,13 @@ inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
     return bytes > 150 * 1024 ? -1 : (int)bytes;
 }
 inline bool mv_valid(const DevModel& md, int v, size_t c) {
+    if (md.nsc) return v == 8;  // sandwich channels: k_sand_w + k_matvec_sw, launched in place of variant 8
     if (v >= 10) return c == 8 && md.rok && matvec_sys_smem(md, v - 9) <= 220 * 1024;
     if (c == 16 && (mv_sys(v) * mv_ept(v) > 8 || v == 7)) return false;  // FP64: register budget
     return mv_tiled_smem(md, v, c) >= 0;
 }
 inline int matvec_partials_v(const DevModel& md, int v) {
+    if (md.nsc) v = 8;
     if (v >= 10) return 1;
     const int T = TPB * mv_ept(v);
     return md.ns * ((md.Nnu + T - 1) / T);
@@ -2771,6 +2995,14 @@ template <class T>
 void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, const int* sys_e, Sel sel, unsigned nlist,
                      const cx<T>* diag, const cx<T>* x, long long xs, cx<T>* y, long long ys, const double2* b,
                      double2* part, int red) {
+    if (md.nsc) {
+        // q-dependent coupling: the two passes of the sandwich product (whatever variant was asked)
+        if (nlist == 0) return;
+        rn.go("sandwich_w", k_sand_w<T>, dim3(cdiv_u(md.Nnu, TPB), nlist), dim3(TPB), md, sys_e, sel, (int)nlist, x, xs);
+        rn.go(name, k_matvec_sw<T>, dim3((unsigned)matvec_partials_v(md, 8), nlist), dim3(TPB), md, sys_e, sel, (int)nlist,
+              diag, x, xs, y, ys, b, part, red);
+        return;
+    }
     const int S = mv_sys(v);
     const dim3 g((unsigned)matvec_partials_v(md, v), (nlist + S - 1) / S);
     const size_t smem = (v >= 4 && v < 8) ? (size_t)mv_tiled_smem(md, v, sizeof(cx<T>)) : 0;
@@ -2929,7 +3161,7 @@ template <class R, int M> struct Solver {
 
 template <class R, int M>
 int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vbk_stats* stats, cudaStream_t st) {
-    const DevModel& md = mdl->dm;
+    DevModel md = mdl->dm;  // own copy: the per-call buffers of q-dependent couplings are set below
     const int N = md.N, nsys = job.nsys, nE = job.nE;
     const bool mixed = sizeof(R) == 4;
     const int method = o.method;
@@ -2937,6 +3169,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     const int pspan = o.precond_span;
     const bool block = pspan > 0;
     Runner rn{mdl, st, o.timing != 0, {}, {}};
+    const bool sand = md.nsc > 0;  // q-dependent coupling (Sec. II.C)
 
     BlockPlan bp;
     DevPlanBuf pbuf;
@@ -2959,10 +3192,10 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             return rc;
         }
     }
-    const bool tune = o.autotune != 0;
+    const bool tune = o.autotune != 0 && !sand;
     // FP32 COCG with a point preconditioner and a system small enough for shared memory:
     // one CTA per system (k_cocg_resident)
-    bool resident = sizeof(R) == 4 && method == VBK_COCG && pspan <= 0 && resident_ok(md) && o.resident != 0;
+    bool resident = sizeof(R) == 4 && method == VBK_COCG && pspan <= 0 && !sand && resident_ok(md) && o.resident != 0;
     if (resident && prepare_resident<M>(md) != VBK_OK) {
         cudaGetLastError();
         resident = false;
@@ -2997,6 +3230,12 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     bytes += 3 * carve_size<int>(nsys) + carve_size<int>(nE) + carve_size<int>(4);
     bytes += 3 * carve_size<double2>((size_t)nsys * nslot);           // partial buffers
     if (block) bytes += carve_size<cx<R>>((size_t)nE * factor_entries(bp, NN));
+    const size_t n_g = sand ? (size_t)nE * md.npair * md.Nnu : 1, n_w = sand ? (size_t)nsys * md.nsc * md.Nnu : 1;
+    if (sand) {  // pair tables, sandwich diagonal, inner-pass vectors w (FP64 size, shared by the FP32 pass)
+        bytes += carve_size<double2>(n_g) + carve_size<float2>(mixed ? n_g : 1);
+        bytes += carve_size<double2>((size_t)nE * NN) + carve_size<float2>(mixed ? (size_t)nE * NN : 1);
+        bytes += carve_size<double2>(n_w);
+    }
     if (method == VBK_COCG) {
         bytes += 5 * carve_size<cx<R>>((size_t)nsys * NN);            // x r p q z
     } else {
@@ -3048,6 +3287,15 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     double2* partB = carve<double2>(p, (size_t)nsys * nslot);
     double2* partC = carve<double2>(p, (size_t)nsys * nslot);
     cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * factor_entries(bp, NN)) : nullptr;
+    if (sand) {
+        md.sg64 = carve<double2>(p, n_g);
+        md.sg32 = carve<float2>(p, mixed ? n_g : 1);
+        md.sfd64 = carve<double2>(p, (size_t)nE * NN);
+        md.sfd32 = carve<float2>(p, mixed ? (size_t)nE * NN : 1);
+        md.sw64 = carve<double2>(p, n_w);
+        md.sw32 = reinterpret_cast<float2*>(md.sw64);  // the FP32 and FP64 passes never overlap
+        if (!mixed) md.sg32 = nullptr, md.sfd32 = nullptr;
+    }
     cx<R>*x = nullptr, *r = nullptr, *pv = nullptr, *q = nullptr, *z = nullptr, *V = nullptr, *w = nullptr;
     double2 *H = nullptr, *g = nullptr, *h1 = nullptr, *h2 = nullptr, *yv = nullptr, *sn = nullptr;
     double *cs = nullptr, *invh = nullptr;
@@ -3109,7 +3357,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             fail(vbk_cuda_fail(cudaGetLastError(), "solver set-up copies"));
             break;
         }
-        // energy tables (FP64 + inner-precision copy)
+        // energy tables (FP64 + inner-precision copy); pair transforms of q-dependent couplings first
+        if (sand) rn.go("sandwich_table", k_sand_table, dim3(cdiv_u(md.Nnu, TPB), nE), dim3(TPB), md, nE, (const double*)dE);
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE,
               dfr ? (double2*)nullptr : diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR, dsp);
         if (block) factor_blocks<R, M>(rn, md, pbuf, nE, (const cx<R>*)diagR, F, pfail);
@@ -3253,7 +3502,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 };
                 const int K = std::max(1, o.check_every);
                 int k = 0;
-                if (!block) {
+                if (!block && !sand) {
                     // persistent iterations: static grids over the device-side lists (A = ilist with
                     // count cnt[0], B = ilist2 with count cnt[1]); K (even) iterations per CUDA graph,
                     // captured once per solve and relaunched until list A is empty.  With timing on,
@@ -3609,6 +3858,8 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     BlockPlan bp;
     DevPlanBuf pbuf;
     const bool block = op == 1 && span > 0;
+    DevModel md = m->dm;  // own copy: the per-call buffers of q-dependent couplings are set below
+    const bool sand = md.nsc > 0;
     if (block) {
         int rc = vbk_make_block_plan(m, span, &bp);
         if (rc) return rc;
@@ -3629,6 +3880,10 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     size_t bytes = carve_size<double2>((size_t)nE * N) + carve_size<float2>(mixed ? (size_t)nE * N : 1) +
                    2 * carve_size<cx<R>>(mixed ? (size_t)nsys * N : 1) + carve_size<int>(nsys) + carve_size<double>(nE) +
                    carve_size<int>(nE) + (block ? carve_size<cx<R>>((size_t)nE * factor_entries(bp, N)) : 0);
+    const size_t n_g = sand ? (size_t)nE * md.npair * md.Nnu : 1, n_w = sand ? (size_t)nsys * md.nsc * md.Nnu : 1;
+    if (sand)
+        bytes += carve_size<double2>(n_g) + carve_size<float2>(n_g) + carve_size<double2>((size_t)nE * N) +
+                 carve_size<float2>((size_t)nE * N) + carve_size<double2>(n_w);
     char* base = nullptr;
     if (vbk_alloc(m, (void**)&base, bytes, st) != cudaSuccess) {
         if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
@@ -3645,6 +3900,14 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     double* dE = carve<double>(p, nE);
     int* pfail = carve<int>(p, nE);
     cx<R>* F = block ? carve<cx<R>>(p, (size_t)nE * factor_entries(bp, N)) : nullptr;
+    if (sand) {
+        md.sg64 = carve<double2>(p, n_g);
+        md.sg32 = mixed ? carve<float2>(p, n_g) : nullptr;
+        md.sfd64 = carve<double2>(p, (size_t)nE * N);
+        md.sfd32 = mixed ? carve<float2>(p, (size_t)nE * N) : nullptr;
+        md.sw64 = carve<double2>(p, n_w);
+        md.sw32 = reinterpret_cast<float2*>(md.sw64);
+    }
     if (!mixed) {
         xr = reinterpret_cast<cx<R>*>(const_cast<double2*>(x));
         yr = reinterpret_cast<cx<R>*>(y);
@@ -3660,16 +3923,17 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
         cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess) {
         rc = vbk_cuda_fail(cudaGetLastError(), "operator set-up");
     } else {
-        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), m->dm, nE, (const double*)dE, d64,
+        if (sand) rn.go("sandwich_table", k_sand_table, dim3(cdiv_u(md.Nnu, TPB), nE), dim3(TPB), md, nE, (const double*)dE);
+        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE, d64,
               mixed ? d32 : (float2*)nullptr, (float2*)nullptr, (float4*)nullptr);
         const dim3 ge(cdiv_u(N, TPB), (unsigned)nsys);
         if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
         if (op == 0) {
-            launch_matvec<R, M>(rn, "matvec", m->dm, (const int*)se, none, (unsigned)nsys, diagR, (const cx<R>*)xr, (long long)N,
+            launch_matvec<R, M>(rn, "matvec", md, (const int*)se, none, (unsigned)nsys, diagR, (const cx<R>*)xr, (long long)N,
                                 yr, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0,
                                 variant >= 0 ? variant : m->mv_variant[sizeof(R) == 4 ? 0 : 1]);
         } else if (block) {
-            factor_blocks<R, M>(rn, m->dm, pbuf, nE, diagR, F, pfail);
+            factor_blocks<R, M>(rn, md, pbuf, nE, diagR, F, pfail);
             block_precond<R>(rn, pbuf, N, none, (unsigned)nsys, (const int*)se, (const cx<R>*)F, (const SysState*)nullptr, 0,
                              nullptr, xr, (long long)N, nullptr, nullptr, yr, (long long)N, nullptr, nullptr);
         } else {
@@ -3827,6 +4091,10 @@ extern "C" int vbk_matvec_noalloc(vbk_model* m, int n_E, const double* E, int n_
             vbk_set_error("energies must be finite");
             return VBK_ERR_INVALID_ARG;
         }
+    if (m->dm.nsc) {
+        vbk_set_error("noalloc: q-dependent continuum couplings need per-call tables beyond the scratch array; use vbk_matvec");
+        return VBK_ERR_UNSUPPORTED;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const double2* x = (const double2*)x_dev;
     double2* y = (double2*)y_dev;

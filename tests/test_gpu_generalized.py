@@ -1,0 +1,302 @@
+"""The generalized model of Sec. II.C (Table II) on the GPU, against the oracle.
+
+Its continuum coupling depends on q, so the level shift is the non-local sandwich operator of
+Eq. FE; the library applies it as a two-pass stencil (k_sand_w, k_matvec_sw) with the pair
+transforms F[f_j f_j'] tabulated per energy.  Checked against the oracle in complex128:
+
+* the operator A x and the point preconditioner r / diag(A) (the diagonal includes that of the
+  sandwich operator) at several energies, FP64 and mixed, on a ragged basis;
+* Phi, psi and the true residual of every Krylov method and precision, cross sections from the
+  polynomial-weighted T of Eq. crs2, an adjoint gradient in the U parameters;
+* every block preconditioner z = B^-1 r, whose blocks now hold sandwich entries;
+* a 40 x 40 basis batched over 64 incident energies on (0, 5] eV (the paper's energy range);
+* the paper's statements on this model (Sec. III.C): M^g is the most efficient preconditioner,
+  M^{du} and M^u coincide, and point-preconditioned (M^{gu}) COCG is slower than plain COCG;
+* the requests this build does not serve for such models return VBK_ERR_UNSUPPORTED, and
+  malformed coupling descriptions VBK_ERR_INVALID_ARG.
+"""
+
+import copy
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as w  # noqa: E402
+from oracle import vibronic as o  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vbk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2307_13483_gb300 as lib
+
+    return lib
+
+
+def rand_vectors(rng, shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_generalized_matvec_parity(vbk, precision):
+    desc = w.gen_ecd_model(9, 11)  # N = 198: several tiles of nothing, a ragged one
+    model = vbk.Model(desc)
+    rng = np.random.default_rng(3)
+    E = np.array([0.6, 2.5, 4.1])
+    x = rand_vectors(rng, (E.size, 3, model.N))
+    y = vbk.vbk_matvec(model, E, torch.tensor(x, device="cuda"), precision=0 if precision == "fp64" else 1)
+    y = y.cpu().numpy()
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    for e in range(E.size):
+        A = o.a_matrix(desc, E[e])
+        for k in range(3):
+            ref = A @ x[e, k]
+            assert np.linalg.norm(y[e, k] - ref) <= tol * np.linalg.norm(ref), (e, k)
+
+
+def test_generalized_matvec_larger_basis_several_tiles(vbk):
+    desc = w.gen_ecd_model(37, 29)  # N = 2146: 5 tiles of 256 levels per state, ragged last
+    model = vbk.Model(desc)
+    rng = np.random.default_rng(4)
+    E = np.array([3.3])
+    x = rand_vectors(rng, (1, 2, model.N))
+    y = vbk.vbk_matvec(model, E, torch.tensor(x, device="cuda")).cpu().numpy()
+    A = o.a_matrix(desc, E[0])
+    for k in range(2):
+        ref = A @ x[0, k]
+        assert np.linalg.norm(y[0, k] - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_generalized_point_preconditioner_uses_the_full_diagonal(vbk):
+    desc = w.gen_ecd_model(8, 7)
+    model = vbk.Model(desc)
+    rng = np.random.default_rng(5)
+    E = np.array([1.9, 3.6])
+    r = rand_vectors(rng, (E.size, 2, model.N))
+    z = vbk.vbk_precond_apply(model, E, torch.tensor(r, device="cuda"), 0).cpu().numpy()
+    for e in range(E.size):
+        dA = o.a_matrix(desc, E[e]).diagonal()
+        np.testing.assert_allclose(z[e], r[e] / dA[None, :], rtol=1e-13)
+
+
+SPANS = {"none": -1, "Mdg": 0x4, "Mgu": 0x1, "Mdu": 0x2, "Md": 0x6, "Mg": 0x5, "Mu": 0x3}
+
+
+@pytest.mark.parametrize("span", [0x5, 0x3, 0x2, 0x6, 0x4, 0x1, 0x7])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_generalized_block_preconditioner_parity(vbk, span, precision):
+    """z = B^-1 r with B the block-diagonal section of A, which now holds entries of the
+    sandwich operator (Sec. III.B; Eq. FE), against the oracle's sparse direct solve."""
+    desc = w.gen_ecd_model(9, 13)
+    model = vbk.Model(desc)
+    rng = np.random.default_rng(6)
+    E = np.array([1.1, 3.4, 4.8])
+    r = rand_vectors(rng, (E.size, 3, model.N))
+    z = vbk.vbk_precond_apply(model, E, torch.tensor(r, device="cuda"), span,
+                              precision=0 if precision == "fp64" else 1).cpu().numpy()
+    tol = 1e-11 if precision == "fp64" else 5e-5
+    for e in range(E.size):
+        for k in range(3):
+            ref = o.precond_apply(desc, E[e], span, r[e, k])
+            assert np.linalg.norm(z[e, k] - ref) <= tol * np.linalg.norm(ref), (span, e, k)
+
+
+@pytest.mark.parametrize("method,precision,span", [("cocg", "mixed", 0), ("cocg", "fp64", 0), ("gmres", "mixed", 0),
+                                                   ("gmres", "fp64", 0), ("cocg", "mixed", 0x5), ("gmres", "fp64", 0x5),
+                                                   ("cocg", "fp64", -1)])
+def test_generalized_solve_parity(vbk, method, precision, span):
+    desc = w.gen_ecd_model(12, 14)
+    model = vbk.Model(desc)
+    eps = np.array([0.5, 2.0, 3.7, 4.6])
+    vi = [[0, 0], [1, 0]]
+    opts = vbk.vbk_default_opts(method=method, precision=precision, precond_span=span, tol=1e-10, restart=48,
+                                max_iter=20000, max_refine=200)
+    psi, stats = vbk.vbk_solve(model, eps, vi, opts)
+    psi = psi.cpu().numpy()
+    for e, ei in enumerate(eps):
+        for i, v in enumerate(vi):
+            E = o.total_energy(desc, ei, v)
+            A = o.a_matrix(desc, E)
+            for mu in range(model.n_mu):
+                st = stats[(e * len(vi) + i) * model.n_mu + mu]
+                assert st["status"] == "converged", st
+                rhs = o.phi(desc, E, v, mu)
+                res = np.linalg.norm(rhs - A @ psi[e, i, mu]) / np.linalg.norm(rhs)
+                assert res <= 1e-10 * 1.05, (e, i, mu, res)
+                ref = o.solve(desc, E, rhs)
+                assert np.linalg.norm(psi[e, i, mu] - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_generalized_cross_sections_and_flux(vbk):
+    desc = w.gen_ecd_model(10, 12)
+    model = vbk.Model(desc)
+    eps = np.array([0.7, 2.4, 3.9])
+    vi = [[0, 0]]
+    opts = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=0, tol=1e-12, max_refine=200)
+    psi, stats = vbk.vbk_solve(model, eps, vi, opts)
+    assert all(s["status"] == "converged" for s in stats)
+    vf = w.lowest_levels(desc, 12)
+    sig, T = vbk.vbk_cross_sections(model, eps, vi, psi, vf, want_t=True)
+    sig, T = sig.cpu().numpy(), T.cpu().numpy()
+    ref, _ = o.cross_sections(desc, eps, vi, vf)
+    big = ref > 1e-9 * ref.max()
+    np.testing.assert_allclose(sig[big], ref[big], rtol=1e-8)
+    # flux: sum over open final levels and waves of |T|^2 = -Im T_ii / pi (GPU amplitudes)
+    ph = psi.cpu().numpy()
+    for e, ei in enumerate(eps):
+        E = o.total_energy(desc, ei, vi[0])
+        opn = o.open_levels(desc, E)
+        _, Tall = vbk.vbk_cross_sections(model, eps[e:e + 1], vi, torch.tensor(ph[e:e + 1], device="cuda"), opn,
+                                          want_t=True)
+        Tall = Tall.cpu().numpy()[0, 0]  # [mu_i][f][mu_f]
+        i0 = opn.index([0, 0])
+        for mi in range(model.n_mu):
+            total = np.sum(np.abs(Tall[mi]) ** 2)
+            assert total == pytest.approx(-Tall[mi, i0, mi].imag / np.pi, rel=1e-9)
+
+
+def test_generalized_batched_full_basis(vbk):
+    """40 x 40 oscillator functions (N = 3200), 64 incident energies on (0, 5] eV, FP64 COCG
+    without preconditioner to 1e-8 (up to ~1,700 iterations near 5 eV); the oracle checks every
+    fourth energy.  (Complex-FP32 COCG stagnates on this model above ~2 eV.)"""
+    desc = w.gen_ecd_model(40, 40)
+    model = vbk.Model(desc)
+    eps = w.eps_grid(5.0, 64)
+    vi = [[0, 0]]
+    opts = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=-1, tol=1e-8, max_iter=20000,
+                                max_refine=100)
+    psi, stats = vbk.vbk_solve(model, eps, vi, opts)
+    assert all(s["status"] == "converged" for s in stats), [s for s in stats if s["status"] != "converged"][:3]
+    psi = psi.cpu().numpy()
+    for e in range(0, eps.size, 4):
+        E = o.total_energy(desc, eps[e], vi[0])
+        A = o.a_matrix(desc, E)
+        for mu in range(2):
+            rhs = o.phi(desc, E, vi[0], mu)
+            res = np.linalg.norm(rhs - A @ psi[e, 0, mu]) / np.linalg.norm(rhs)
+            assert res <= 1e-8 * 1.05, (e, mu, res)
+
+
+def test_generalized_cocg_point_preconditioner_is_slower_than_none(vbk):
+    """Sec. III.C, generalized-model paragraph: with COCG every preconditioner except M^{dg} and
+    M^{gu} beats direct iterations.  M^{gu} (blocks spanning d only) is the diagonal of A for this
+    model (every inter-state entry changes n_u), i.e. the point preconditioner: above ~3 eV it
+    needs several times the iterations of unpreconditioned COCG."""
+    desc = w.gen_ecd_model(40, 40)
+    model = vbk.Model(desc)
+    eps = np.array([3.5, 4.5])
+    its = {}
+    for name, span in (("none", -1), ("Mgu", 0)):
+        opts = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=span, tol=1e-6, max_iter=30000,
+                                    max_refine=100)
+        _, st = vbk.vbk_solve(model, eps, [[0, 0]], opts)
+        assert all(s["status"] == "converged" for s in st)
+        its[name] = np.array(st.iterations)
+    assert (its["Mgu"] > 2 * its["none"]).all(), its
+
+
+@pytest.fixture(scope="module")
+def gen_study(vbk):
+    """GMRES (restart 256) and COCG over 50 incident energies on (0, 5] eV, basis 30 x 60, v_i = 0,
+    both partial waves, the paper's stopping rule ||r|| < 1e-6 ||b||, FP64, at most 6,000
+    iterations (the point-preconditioned runs do not all converge within that)."""
+    model = vbk.Model(w.gen_ecd_model(30, 60))
+    eps = w.eps_grid(5.0, 50)
+    out = {}
+    for method, names in (("gmres", list(SPANS)), ("cocg", ["none", "Mgu", "Mdu", "Mu", "Mg"])):
+        for name in names:
+            opts = vbk.vbk_default_opts(method=method, precision="fp64", precond_span=SPANS[name], tol=1e-6, restart=256,
+                                        max_iter=6000, max_refine=400)
+            _, st = vbk.vbk_solve(model, eps, [[0, 0]], opts, check=False)
+            out[method, name] = (np.array(st.iterations).reshape(eps.size, 2), np.array(st.status).reshape(eps.size, 2))
+    return eps, out
+
+
+@pytest.mark.parametrize("method", ["gmres", "cocg"])
+def test_generalized_mg_is_the_most_efficient(gen_study, method):
+    """Sec. III.C, generalized-model paragraph: M^g is again the most efficient preconditioner."""
+    eps, out = gen_study
+    mg, st = out[method, "Mg"]
+    assert (st == 0).all()
+    others = {n: it for (m, n), (it, _) in out.items() if m == method and n != "Mg"}
+    worse = {n: int(np.sum(mg > it)) for n, it in others.items()}
+    assert all(v == 0 for v in worse.values()), (worse, mg.tolist())
+
+
+def test_generalized_mdu_and_mu_coincide(gen_study):
+    """Sec. III.C: for the generalized model M^{du} and M^u give the same convergence (their
+    blocks differ only by zero entries), while other pairs that coincide for ECD86 now differ."""
+    _, out = gen_study
+    it = {n: out["gmres", n][0] for n in SPANS}
+    # identical GMRES runs, system by system (above ~2.5 eV both stop at the iteration cap together)
+    assert (np.abs(it["Mdu"] - it["Mu"]) <= 1).all(), (it["Mdu"].tolist(), it["Mu"].tolist())
+    assert (out["gmres", "Mdu"][1] == out["gmres", "Mu"][1]).all()
+    assert (out["gmres", "Md"][1] == 0).all()
+    assert np.abs(it["Mdu"] - it["Md"]).max() > 1
+
+
+def test_generalized_adjoint_in_u_parameters(vbk):
+    desc = w.gen_ecd_model(6, 6)
+    model = vbk.Model(desc)
+    eps = np.array([1.3, 3.2])
+    vi = [[0, 0]]
+    vf = [[0, 0], [1, 0], [0, 1]]
+    opts = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=0, tol=1e-12, max_refine=200)
+    psi, st = vbk.vbk_solve(model, eps, vi, opts)
+    sig = vbk.vbk_cross_sections(model, eps, vi, psi, vf)
+    target = np.full((eps.size, len(vf)), 0.05)
+    tgt = torch.tensor(target[:, None, :], device="cuda")
+    thetas = [0, 1, 2, 3, 4]  # E_1, E_2, kappa_1, kappa_2, lambda (Table I)
+    g, stats = vbk.vbk_solve_adjoint(model, eps, vi, psi, vf, 2.0 * (sig - tgt), thetas, opts)
+    assert all(s["status"] in ("converged", "zero_rhs") for s in stats)
+    g_ref = o.loss_gradient_adjoint(desc, eps, vi[0], vf, target, thetas)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-7, atol=1e-10 * np.abs(g_ref).max())
+
+
+def test_generalized_requests_not_served_are_rejected(vbk):
+    desc = w.gen_ecd_model(6, 6)
+    model = vbk.Model(desc)
+    r = torch.zeros((1, 1, model.N), dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(r)
+    with pytest.raises(vbk.VbkError) as ei:
+        vbk.vbk_matvec_noalloc(model, [2.0], r, y)
+    assert ei.value.code == 5
+    opts = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=0, tol=1e-10)
+    psi, _ = vbk.vbk_solve(model, [1.0], [[0, 0]], opts)
+    sig = vbk.vbk_cross_sections(model, [1.0], [[0, 0]], psi, [[0, 0]])
+    nt = len(desc["terms"])
+    with pytest.raises(vbk.VbkError) as ei:
+        vbk.vbk_solve_adjoint(model, [1.0], [[0, 0]], psi, [[0, 0]], sig, [nt], opts)
+    assert ei.value.code == 5
+
+
+def test_malformed_couplings_are_rejected(vbk):
+    bad_l = w.gen_ecd_model(4, 4)
+    bad_l["channels"][1]["l"] = 1  # the e wave's two channels no longer share l
+    with pytest.raises(vbk.VbkError) as ei:
+        vbk.Model(bad_l)
+    assert ei.value.code == 1
+    twice = w.ci2d_model(4)
+    twice["channels"].append(copy.deepcopy(twice["channels"][0]))  # state 0 coupled twice to wave 0
+    with pytest.raises(vbk.VbkError) as ei:
+        vbk.Model(twice)
+    assert ei.value.code == 1
+    # one wave coupled to two states without polynomials is a q-dependent (non-local) wave too
+    two = w.ci2d_model(5)
+    two["channels"][1]["mu"] = 0
+    model = vbk.Model(two)
+    assert model.n_mu == 1
+    rng = np.random.default_rng(8)
+    x = rand_vectors(rng, (1, 2, model.N))
+    y = vbk.vbk_matvec(model, [2.2], torch.tensor(x, device="cuda")).cpu().numpy()
+    A = o.a_matrix(two, 2.2)
+    for k in range(2):
+        assert np.linalg.norm(y[0, k] - A @ x[0, k]) <= 1e-13 * np.linalg.norm(A @ x[0, k])
