@@ -214,8 +214,11 @@ int vbk_eels(vbk_model* model, int n_eps, int n_vi, const int* vi, int n_vf, con
  *   dL/dtheta = Re sum [ sum_f w_f dPhi_f^T psi + lambda^T dPhi_i - lambda^T (dA/dtheta) psi ],
  *   w_f = dL/dsigma * 2 pi^3/eps_i * 2 conj(T_f).
  * theta_ids (host [n_theta]): k < n_terms is the coefficient of term k; n_terms + 2c and
- * n_terms + 2c + 1 are a and b of channel c (VBK_ERR_UNSUPPORTED for a channel of a
- * q-dependent partial wave, whose a and b enter the non-local level shift).
+ * n_terms + 2c + 1 are a and b of channel c; n_terms + 2 n_channels + t is the coefficient of
+ * coupling term t (vbk_cterm, in the order given; Sec. II.C).  For q-dependent partial waves
+ * the derivatives run through the non-local level shift of Eq. FE (pair transforms
+ * F[f_c f_c'] depend on a_c through sqrt(a_c a_c') and on b_c through (b_c + b_c') / 2) and
+ * through Phi = f_c P_c |v>.
  *   grad      : host double [n_theta], written.
  *   stats     : host [n_eps * n_vi * n_mu] adjoint solve outcomes, or NULL.
  * Synchronises `stream`. */

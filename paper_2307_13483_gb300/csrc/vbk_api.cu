@@ -706,9 +706,11 @@ __global__ void k_adjoint_rhs(DevModel md, int n_eps, int n_vi, int n_vf, const 
 }
 
 // Gradient parameter descriptor: kind 0 = term coefficient (points [pb, pe) of the point list),
-// kind 1 = channel a, kind 2 = channel b (channel index c).
+// kind 1 = channel a, kind 2 = channel b (channel index c), kind 3 = coefficient of a coupling-
+// polynomial term of channel c (its unit-coefficient points [pb, pe)).  j = sandwich index of
+// channel c (q-dependent coupling, Sec. II.C), -1 for a diagonal channel or a U term.
 struct GradParam {
-    int kind, c, pb, pe;
+    int kind, c, pb, pe, j;
 };
 
 template <int M> __device__ __forceinline__ void decode_nu(const DevModel& md, int nu, int (&n)[MAXM]) {
@@ -778,7 +780,7 @@ __global__ void __launch_bounds__(TPB) k_adjoint_contract(DevModel md, int nsys,
                 // -lambda^T (dA) psi with dA = -(unit-coefficient term matrix)
                 const double2 t = cmul<double>(li, acc);
                 v = t.x;
-            } else if (md.ch_d[g.c] == d) {
+            } else if (g.j < 0 && md.ch_d[g.c] == d) {
                 const int c = g.c;
                 const double eps = E - en;
                 if (g.kind == 1) {  // dA/da = -F/a
@@ -810,7 +812,8 @@ __global__ void k_adjoint_rhs_terms(DevModel md, int n_eps, int n_vi, int n_vf, 
                                     const double* __restrict__ E_vi, const int* __restrict__ vf_flat,
                                     const double* __restrict__ E_vf, const double2* __restrict__ W,
                                     const double2* __restrict__ lam, const double2* __restrict__ psi, int ntheta,
-                                    const GradParam* __restrict__ gp, double* __restrict__ out) {
+                                    const GradParam* __restrict__ gp, const DevEntry* __restrict__ pts,
+                                    double* __restrict__ out) {
     const int nmu = md.nmu;
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= (long long)n_eps * n_vi * nmu) return;
@@ -821,7 +824,64 @@ __global__ void k_adjoint_rhs_terms(DevModel md, int n_eps, int n_vi, int n_vf, 
     for (int th = 0; th < ntheta; ++th) {
         const GradParam g = gp[th];
         double acc = 0.0;
-        if (g.kind != 0) {
+        if (g.j >= 0) {
+            // q-dependent channel: Phi^{v mu} carries f_c(eps) P_c |v>, so dPhi = df P_c |v> (kinds 1, 2)
+            // or f Q_t |v> (kind 3, Q_t the unit-coefficient term); both sums use (X y_(d_c))(v)
+            // for the symmetric operator X = P_c or Q_t
+            const int c = g.c, mu = md.ch_mu[c], d = md.ch_d[c], j = g.j;
+            const double a = md.ch_a[c], b = md.ch_b[c];
+            const int l = md.ch_l[c];
+            auto apply = [&](const double2* y, int v) -> double2 {
+                double2 t = make_double2(0.0, 0.0);
+                const double2* yd = y + (long long)d * md.Nnu;
+                if (g.kind == 3) {
+                    int n[MAXM];
+                    int rem = v;
+                    for (int m = md.M - 1; m >= 0; --m) {
+                        n[m] = rem % md.nb[m];
+                        rem /= md.nb[m];
+                    }
+                    for (int k = g.pb; k < g.pe; ++k) {
+                        const DevEntry pt = pts[k];
+                        double cf = 1.0;
+                        bool ok = true;
+                        for (int m = 0; m < md.M; ++m)
+                            if (pt.col[m] >= 0) {
+                                const int nn = n[m] + pt.delta[m];
+                                ok = ok && nn >= 0 && nn < md.nb[m];
+                                cf *= md.tab64[pt.col[m] + n[m]];
+                            }
+                        if (ok) {
+                            const double2 x = yd[v + pt.lin];
+                            t.x += cf * x.x;
+                            t.y += cf * x.y;
+                        }
+                    }
+                } else {
+                    for (int k = md.sc_pbeg[j]; k < md.sc_pbeg[j + 1]; ++k) {
+                        const double cf = md.spc64[(long long)k * md.Nnu + v];
+                        if (cf == 0.0) continue;
+                        const double2 x = yd[v + md.sp_lin[k]];
+                        t.x += cf * x.x;
+                        t.y += cf * x.y;
+                    }
+                }
+                return t;
+            };
+            auto dfac = [&](double ep) {  // df/da, df/db, or f itself (kind 3)
+                const double f = vbk_amplitude(ep, a, b, l);
+                return g.kind == 1 ? (a > 0 ? f / (2.0 * a) : 0.0) : g.kind == 2 ? -0.5 * ep * f : f;
+            };
+            if (mi == mu) {  // lambda^T dPhi_i
+                const double ei = E - E_vi[i];
+                acc += dfac(ei) * apply(ls, vi_flat[i]).x;
+            }
+            for (int f = 0; f < n_vf; ++f) {  // sum_f w_f dPhi_f^T psi
+                const double ef = E - E_vf[f];
+                const double2 w = W[(s * n_vf + f) * nmu + mu];
+                acc += dfac(ef) * cmul<double>(w, apply(ps, vf_flat[f])).x;
+            }
+        } else if (g.kind != 0) {
             const int c = g.c, mu = md.ch_mu[c], d = md.ch_d[c];
             const double a = md.ch_a[c], b = md.ch_b[c];
             const int l = md.ch_l[c];
@@ -844,14 +904,122 @@ __global__ void k_adjoint_rhs_terms(DevModel md, int n_eps, int n_vi, int n_vf, 
     }
 }
 
-// grad[theta] = sum_s sum_blk part[s][blk][theta] + sum_s rhs_terms[s][theta] (fixed order)
-__global__ void k_grad_reduce(int nsys, int nblk, int ntheta, const double* __restrict__ part,
-                              const double* __restrict__ rhs_terms, double* __restrict__ grad) {
+// Contractions -lambda^T (dA/dtheta) psi = lambda^T (dF/dtheta) psi for the parameters of
+// q-dependent channels (Eq. FE, F = sum_mu P_j g_(j,j') P_j'), per level kappa of the vibrational
+// basis, with u^x_j = (P_j x_(d_j))(kappa) and g_(j,j') = F[f_j f_j'](E - E_kappa):
+//   a_j : sum_j' g_(j,j') / (2 a_j) (u^lam_j u^psi_j' + u^lam_j' u^psi_j)  (dg_(j,j)/da_j = g_(j,j)/a_j)
+//   b_j : sum_j' h_(j,j') / 2 (u^lam_j u^psi_j' + u^lam_j' u^psi_j),  h = dg/db = -F^(l+1)
+//   c_t of P_j : (Q_t lam_(d_j)) W^psi_j + (Q_t psi_(d_j)) W^lam_j,  W^x_j = sum_j' g_(j,j') u^x_j'
+// (Q_t the unit-coefficient term, symmetric).  part[s][blk][theta]; zero for other parameters.
+template <int M>
+__global__ void __launch_bounds__(TPB) k_adjoint_sand(DevModel md, const double* __restrict__ Etot,
+                                                     const double2* __restrict__ lam, const double2* __restrict__ psi,
+                                                     int ntheta, const GradParam* __restrict__ gp,
+                                                     const DevEntry* __restrict__ pts, double* __restrict__ part) {
+    __shared__ double red[TPB / 32];
+    const int s = blockIdx.y, Nnu = md.Nnu;
+    const int kap = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = kap < Nnu;
+    const double2* ls = lam + (long long)s * md.N;
+    const double2* ps = psi + (long long)s * md.N;
+    double2 ul[MAXCH], up[MAXCH];
+    double eps = 0.0;
+    int n[MAXM];
+    if (on) {
+        eps = Etot[s / md.nmu] - md.enu[kap];
+        decode_nu<M>(md, kap, n);
+        for (int j = 0; j < md.nsc; ++j) {
+            double2 a = make_double2(0.0, 0.0), b = a;
+            const long long od = (long long)md.sc_d[j] * Nnu;
+            for (int k = md.sc_pbeg[j]; k < md.sc_pbeg[j + 1]; ++k) {
+                const double cf = md.spc64[(long long)k * Nnu + kap];
+                if (cf == 0.0) continue;
+                const double2 xl = ls[od + kap + md.sp_lin[k]], xp = ps[od + kap + md.sp_lin[k]];
+                a.x += cf * xl.x;
+                a.y += cf * xl.y;
+                b.x += cf * xp.x;
+                b.y += cf * xp.y;
+            }
+            ul[j] = a;
+            up[j] = b;
+        }
+    }
+    auto pair_shift = [&](int p, int dl) {
+        return vbk_level_shift_core(eps, md.pr_a[p], md.pr_b[p], md.pr_sb[p], md.pr_isb[p], md.pr_ib[p], md.pr_l[p] + dl);
+    };
+    for (int th = 0; th < ntheta; ++th) {
+        const GradParam g = gp[th];
+        double v = 0.0;
+        if (on && g.j >= 0) {
+            const int j = g.j;
+            if (g.kind == 1 || g.kind == 2) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int j2 = 0; j2 < md.nsc; ++j2) {
+                    const int p = md.sc_pair[j][j2];
+                    if (p < 0) continue;
+                    double2 G = g.kind == 1 ? pair_shift(p, 0) : pair_shift(p, 1);
+                    const double sc = g.kind == 1 ? 0.5 / md.ch_a[g.c] : -0.5;
+                    G = make_double2(sc * G.x, sc * G.y);
+                    const double2 t = cadd<double>(cmul<double>(ul[j], up[j2]), cmul<double>(ul[j2], up[j]));
+                    acc = cfma<double>(G, t, acc);
+                }
+                v = acc.x;
+            } else if (g.kind == 3) {
+                double2 wl = make_double2(0.0, 0.0), wp = wl;
+                for (int j2 = 0; j2 < md.nsc; ++j2) {
+                    const int p = md.sc_pair[j][j2];
+                    if (p < 0) continue;
+                    const double2 G = pair_shift(p, 0);
+                    wl = cfma<double>(G, ul[j2], wl);
+                    wp = cfma<double>(G, up[j2], wp);
+                }
+                double2 ql = make_double2(0.0, 0.0), qp = ql;
+                const long long od = (long long)md.sc_d[j] * Nnu;
+                for (int k = g.pb; k < g.pe; ++k) {
+                    const DevEntry pt = pts[k];
+                    double cf = 1.0;
+                    bool ok = true;
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (pt.col[m] >= 0) {
+                            const int nn = n[m] + pt.delta[m];
+                            ok = ok && nn >= 0 && nn < md.nb[m];
+                            cf *= md.tab64[pt.col[m] + n[m]];
+                        }
+                    if (ok) {
+                        const double2 xl = ls[od + kap + pt.lin], xp = ps[od + kap + pt.lin];
+                        ql.x += cf * xl.x;
+                        ql.y += cf * xl.y;
+                        qp.x += cf * xp.x;
+                        qp.y += cf * xp.y;
+                    }
+                }
+                v = cadd<double>(cmul<double>(ql, wp), cmul<double>(qp, wl)).x;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < TPB / 32; ++w) t += red[w];
+            part[((long long)s * gridDim.x + blockIdx.x) * ntheta + th] = t;
+        }
+    }
+}
+
+// grad[theta] = sum_s sum_blk part[s][blk][theta] + sum_s sum_blk2 part2[s][blk2][theta]
+//             + sum_s rhs_terms[s][theta]  (fixed order)
+__global__ void k_grad_reduce(int nsys, int nblk, int nblk2, int ntheta, const double* __restrict__ part,
+                              const double* __restrict__ part2, const double* __restrict__ rhs_terms,
+                              double* __restrict__ grad) {
     const int th = blockIdx.x * blockDim.x + threadIdx.x;
     if (th >= ntheta) return;
     double acc = 0.0;
     for (int s = 0; s < nsys; ++s) {
         for (int b = 0; b < nblk; ++b) acc += part[((long long)s * nblk + b) * ntheta + th];
+        for (int b = 0; b < nblk2; ++b) acc += part2[((long long)s * nblk2 + b) * ntheta + th];
         acc += rhs_terms[(long long)s * ntheta + th];
     }
     grad[th] = acc;
@@ -1110,10 +1278,55 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
     std::vector<GradParam> gps(n_theta);
     std::vector<DevEntry> pts;
     std::vector<int> ptd;
+    const int nch = (int)m->chans.size(), nct = (int)m->cterms.size();
+    auto sand_index = [&](int c) {
+        for (int j = 0; j < m->dm.nsc; ++j)
+            if (m->dm.sc_ch[j] == c) return j;
+        return -1;
+    };
     for (int k = 0; k < n_theta; ++k) {
         const int id = theta_ids[k];
-        if (id < 0 || id >= nterm + 2 * (int)m->chans.size()) return invalid("theta id out of range");
-        GradParam g{0, 0, 0, 0};
+        if (id < 0 || id >= nterm + 2 * nch + nct) return invalid("theta id out of range");
+        GradParam g{0, 0, 0, 0, -1};
+        if (id >= nterm + 2 * nch) {
+            // coefficient of coupling term t: the unit-coefficient points of its polynomial term
+            const vbk_cterm& t = m->cterms[id - nterm - 2 * nch];
+            g.kind = 3;
+            g.c = t.channel;
+            g.j = sand_index(t.channel);
+            g.pb = (int)pts.size();
+            int cnt[MAXM], o[MAXM];
+            long long ncomb = 1;
+            for (int q = 0; q < m->M; ++q) {
+                cnt[q] = t.pow[q] + 1;
+                ncomb *= cnt[q];
+            }
+            for (long long cb = 0; cb < ncomb; ++cb) {
+                long long rem = cb;
+                for (int q = m->M - 1; q >= 0; --q) {
+                    o[q] = (int)(rem % cnt[q]);
+                    rem /= cnt[q];
+                }
+                DevEntry e{};
+                e.coef = 1.0;
+                e.dp = m->chans[t.channel].d;
+                for (int q = 0; q < MAXM; ++q) {
+                    e.col[q] = -1;
+                    e.delta[q] = 0;
+                }
+                for (int q = 0; q < m->M; ++q) {
+                    if (!t.pow[q]) continue;
+                    e.delta[q] = -t.pow[q] + 2 * o[q];
+                    e.col[q] = m->colbase[q][t.pow[q]] + o[q] * m->nb[q];
+                    e.lin += e.delta[q] * m->stride[q];
+                }
+                pts.push_back(e);
+                ptd.push_back(-1);  // not a U point: never matched by the element-wise contraction
+            }
+            g.pe = (int)pts.size();
+            gps[k] = g;
+            continue;
+        }
         if (id < nterm) {
             g.kind = 0;
             g.pb = (int)pts.size();
@@ -1130,10 +1343,7 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
             g.kind = 1 + (id - nterm) % 2;
             g.c = (id - nterm) / 2;
             if (g.kind == 1 && !(m->chans[g.c].a > 0.0)) return invalid("gradient in a needs a > 0");
-            if (m->dm.ch_sw[g.c]) {
-                g_last_error = "adjoint: gradients in a and b of a q-dependent channel are not available";
-                return VBK_ERR_UNSUPPORTED;
-            }
+            g.j = m->dm.ch_sw[g.c] ? sand_index(g.c) : -1;
         }
         gps[k] = g;
     }
@@ -1144,10 +1354,11 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
     const size_t N = m->N;
     const long long nsys = job.nsys;
     const int nblk = (int)cdiv_u(N, TPB);
+    const int nblk2 = m->dm.nsc ? (int)cdiv_u(m->Nnu, TPB) : 0;  // sandwich contractions per level
     const int nmu = m->nmu;
     const size_t nT = (size_t)n_eps * n_vi * nmu * n_vf * nmu;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t off[16];
+    size_t off[17];
     size_t tot = 0;
     size_t sizes[] = {al(nsys * N * sizeof(double2)),                      // 0 g (adjoint rhs)
                       al(nsys * N * sizeof(double2)),                      // 1 lambda
@@ -1160,8 +1371,9 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
                       al(pts.size() * sizeof(DevEntry)), al(ptd.size() * 4),  // 11, 12
                       al(nsys * (size_t)nblk * n_theta * 8),               // 13 partials
                       al(nsys * (size_t)n_theta * 8),                      // 14 rhs terms
-                      al((size_t)n_theta * 8)};                            // 15 grad (device)
-    for (int k = 0; k < 16; ++k) {
+                      al((size_t)n_theta * 8),                             // 15 grad (device)
+                      al(nsys * (size_t)nblk2 * n_theta * 8 + 8)};         // 16 sandwich partials
+    for (int k = 0; k < 17; ++k) {
         off[k] = tot;
         tot += sizes[k];
     }
@@ -1198,7 +1410,7 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
     job.x64 = (double2*)P(1);
     int rc = vbk_solve_job(m, job, *opts, stats, st);
     if (rc != VBK_OK && rc != VBK_ERR_NOT_CONVERGED) return rc;
-    const long long extra_launches = 5;
+    const long long extra_launches = nblk2 ? 6 : 5;
     // contractions
     const dim3 gc(nblk, (unsigned)nsys);
     switch (m->M) {
@@ -1207,13 +1419,22 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
         case 3: k_adjoint_contract<3><<<gc, TPB, 0, st>>>(m->dm, (int)nsys, n_vi, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const int*)P(12), (const DevEntry*)P(11), (double*)P(13)); break;
         default: k_adjoint_contract<4><<<gc, TPB, 0, st>>>(m->dm, (int)nsys, n_vi, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const int*)P(12), (const DevEntry*)P(11), (double*)P(13)); break;
     }
+    if (nblk2) {
+        const dim3 gs(nblk2, (unsigned)nsys);
+        switch (m->M) {
+            case 1: k_adjoint_sand<1><<<gs, TPB, 0, st>>>(m->dm, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const DevEntry*)P(11), (double*)P(16)); break;
+            case 2: k_adjoint_sand<2><<<gs, TPB, 0, st>>>(m->dm, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const DevEntry*)P(11), (double*)P(16)); break;
+            case 3: k_adjoint_sand<3><<<gs, TPB, 0, st>>>(m->dm, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const DevEntry*)P(11), (double*)P(16)); break;
+            default: k_adjoint_sand<4><<<gs, TPB, 0, st>>>(m->dm, (const double*)P(5), (const double2*)P(1), (const double2*)psi_dev, n_theta, (const GradParam*)P(10), (const DevEntry*)P(11), (double*)P(16)); break;
+        }
+    }
     k_adjoint_rhs_terms<<<cdiv_u(nsys, 128), 128, 0, st>>>(m->dm, n_eps, n_vi, n_vf, (const double*)P(4), (const double*)P(5),
                                                            (const int*)P(8), (const double*)P(9), (const int*)P(6),
                                                            (const double*)P(7), (const double2*)P(3), (const double2*)P(1),
                                                            (const double2*)psi_dev, n_theta, (const GradParam*)P(10),
-                                                           (double*)P(14));
-    k_grad_reduce<<<cdiv_u(n_theta, 64), 64, 0, st>>>((int)nsys, nblk, n_theta, (const double*)P(13), (const double*)P(14),
-                                                      (double*)P(15));
+                                                           (const DevEntry*)P(11), (double*)P(14));
+    k_grad_reduce<<<cdiv_u(n_theta, 64), 64, 0, st>>>((int)nsys, nblk, nblk2, n_theta, (const double*)P(13),
+                                                      (const double*)P(16), (const double*)P(14), (double*)P(15));
     VBK_CUDA(cudaGetLastError());
     VBK_CUDA(cudaMemcpyAsync(grad, P(15), n_theta * 8, cudaMemcpyDeviceToHost, st));
     VBK_CUDA(cudaStreamSynchronize(st));

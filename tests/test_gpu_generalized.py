@@ -7,7 +7,7 @@ transforms F[f_j f_j'] tabulated per energy.  Checked against the oracle in comp
 * the operator A x and the point preconditioner r / diag(A) (the diagonal includes that of the
   sandwich operator) at several energies, FP64 and mixed, on a ragged basis;
 * Phi, psi and the true residual of every Krylov method and precision, cross sections from the
-  polynomial-weighted T of Eq. crs2, an adjoint gradient in the U parameters;
+  polynomial-weighted T of Eq. crs2, adjoint gradients in U and in the coupling parameters;
 * every block preconditioner z = B^-1 r, whose blocks now hold sandwich entries;
 * a 40 x 40 basis batched over 64 incident energies on (0, 5] eV (the paper's energy range);
 * the paper's statements on this model (Sec. III.C): M^g is the most efficient preconditioner,
@@ -261,6 +261,31 @@ def test_generalized_adjoint_in_u_parameters(vbk):
     np.testing.assert_allclose(g, g_ref, rtol=1e-7, atol=1e-10 * np.abs(g_ref).max())
 
 
+def test_generalized_adjoint_in_coupling_parameters(vbk):
+    """Gradients in the parameters of the q-dependent coupling (Sec. II.C): a and b of channels
+    whose pair transforms enter the non-local level shift, and the coefficients of the coupling
+    polynomials (lambda_1, lambda_2, the constant and the q_u terms), against the oracle's
+    dense-LU adjoint; the U parameter lambda rides along."""
+    desc = w.gen_ecd_model(7, 6)
+    model = vbk.Model(desc)
+    eps = np.array([0.9, 2.6, 4.2])
+    vi = [[0, 0]]
+    vf = [[0, 0], [1, 0], [0, 1], [1, 1]]
+    opts = vbk.vbk_default_opts(method="gmres", precision="fp64", precond_span=0x5, tol=1e-12, restart=64,
+                                max_refine=200)
+    psi, _ = vbk.vbk_solve(model, eps, vi, opts)
+    sig = vbk.vbk_cross_sections(model, eps, vi, psi, vf)
+    target = np.full((eps.size, len(vf)), 0.02)
+    tgt = torch.tensor(target[:, None, :], device="cuda")
+    nt, nc = len(desc["terms"]), len(desc["channels"])
+    pt = nt + 2 * nc  # first coupling-polynomial coefficient
+    thetas = [4, nt + 0, nt + 1, nt + 3, nt + 6, nt + 7, pt + 0, pt + 1, pt + 2, pt + 3, pt + 5]
+    g, stats = vbk.vbk_solve_adjoint(model, eps, vi, psi, vf, 2.0 * (sig - tgt), thetas, opts)
+    assert all(s["status"] in ("converged", "zero_rhs") for s in stats)
+    g_ref = o.loss_gradient_adjoint(desc, eps, vi[0], vf, target, thetas)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-6, atol=1e-9 * np.abs(g_ref).max())
+
+
 def test_generalized_requests_not_served_are_rejected(vbk):
     desc = w.gen_ecd_model(6, 6)
     model = vbk.Model(desc)
@@ -272,10 +297,10 @@ def test_generalized_requests_not_served_are_rejected(vbk):
     opts = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=0, tol=1e-10)
     psi, _ = vbk.vbk_solve(model, [1.0], [[0, 0]], opts)
     sig = vbk.vbk_cross_sections(model, [1.0], [[0, 0]], psi, [[0, 0]])
-    nt = len(desc["terms"])
-    with pytest.raises(vbk.VbkError) as ei:
-        vbk.vbk_solve_adjoint(model, [1.0], [[0, 0]], psi, [[0, 0]], sig, [nt], opts)
-    assert ei.value.code == 5
+    nt, nc, nct = len(desc["terms"]), len(desc["channels"]), sum(len(c["terms"]) for c in desc["channels"])
+    with pytest.raises(vbk.VbkError) as ei:  # one past the last coupling term
+        vbk.vbk_solve_adjoint(model, [1.0], [[0, 0]], psi, [[0, 0]], sig, [nt + 2 * nc + nct], opts)
+    assert ei.value.code == 1
 
 
 def test_malformed_couplings_are_rejected(vbk):

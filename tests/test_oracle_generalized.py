@@ -226,8 +226,12 @@ def test_generalized_adjoint_gradient_matches_finite_differences():
     vf = [[0, 0], [1, 0], [0, 1]]
     target = np.full((len(eps), len(vf)), 0.05)
     nt, nc = len(m["terms"]), len(m["channels"])
-    thetas = [0, 4, nt + 0, nt + 3, nt + 2 * nc + 1, nt + 2 * nc + 5]  # E_1, lambda, a, b, lambda_1, lambda_2
-    assert o.get_parameter(m, thetas[4]) == 0.2 and o.get_parameter(m, thetas[5]) == 0.1
+    # E_1, lambda, a, b, lambda_1, the q_u coefficient of (d=2, e) alone, lambda_2
+    thetas = [0, 4, nt + 0, nt + 3, nt + 2 * nc + 1, nt + 2 * nc + 2, nt + 2 * nc + 5]
+    assert o.get_parameter(m, thetas[4]) == 0.2 and o.get_parameter(m, thetas[6]) == 0.1
+    # each coefficient is a parameter of its own channel (no term shared between channels)
+    m2 = o.with_parameter(m, thetas[5], 1.5)
+    assert m2["channels"][1]["terms"][0]["coef"] == 1.5 and m2["channels"][2]["terms"][0]["coef"] == 1.0
     g_adj = o.loss_gradient_adjoint(m, eps, vi, vf, target, thetas)
     g_fd = o.loss_gradient_fd(m, eps, vi, vf, target, thetas, h=1e-6)
     np.testing.assert_allclose(g_adj, g_fd, rtol=2e-6, atol=1e-9 * np.abs(g_fd).max())

@@ -181,13 +181,14 @@ def gen_ecd_model(n_g: int, n_u: int) -> dict:
     """
     m = ecd86_model(n_g, n_u)
     lam1, lam2 = 0.2, 0.1
+    # every channel gets its own term list (its coefficients are parameters of their own)
     one_plus = lambda lam: [{"coef": 1.0, "pow": [0, 0]}, {"coef": lam, "pow": [1, 0]}]  # noqa: E731
-    q_u = [{"coef": 1.0, "pow": [0, 1]}]
+    q_u = lambda: [{"coef": 1.0, "pow": [0, 1]}]  # noqa: E731
     m["name"] = f"gen-ecd-{n_g}x{n_u}"
     m["channels"] = [
         {"d": 0, "mu": 0, "a": 0.07, "b": 0.25, "l": 0, "terms": one_plus(lam1)},
-        {"d": 1, "mu": 0, "a": 0.1, "b": 0.5, "l": 0, "terms": q_u},
-        {"d": 0, "mu": 1, "a": 0.186, "b": 0.375, "l": 1, "terms": q_u},
+        {"d": 1, "mu": 0, "a": 0.1, "b": 0.5, "l": 0, "terms": q_u()},
+        {"d": 0, "mu": 1, "a": 0.186, "b": 0.375, "l": 1, "terms": q_u()},
         {"d": 1, "mu": 1, "a": 0.15, "b": 0.8, "l": 1, "terms": one_plus(lam2)},
     ]
     return m
