@@ -147,10 +147,14 @@ typedef struct {
     int resident;      /* 1: FP32 COCG with a point preconditioner runs each inner solve of a
                           system in one thread block (vectors p, q in shared memory) when
                           2 N * 8 bytes + tables fit; 0: grid-wide kernels                   */
+    int inner_max_iter; /* VBK_MIXED COCG: iterations of one FP32 inner solve before it ends
+                          and the FP64 residual restarts it (complex-FP32 COCG can stagnate
+                          short of inner_tol on hard systems); 0 = no cap                    */
 } vbk_opts;
 
 /* Fills `o` with defaults: GMRES, VBK_MIXED, Jacobi, restart 64, max_iter 20000,
- * max_refine 40, tol 1e-8, inner_tol 1e-5, check_every 8, timing 0, autotune 1, resident 1. */
+ * max_refine 40, tol 1e-8, inner_tol 1e-5, check_every 8, timing 0, autotune 1, resident 1,
+ * inner_max_iter 2000. */
 void vbk_default_opts(vbk_opts* o);
 
 typedef struct {

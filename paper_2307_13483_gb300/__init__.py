@@ -69,6 +69,7 @@ class vbk_opts(C.Structure):
         ("timing", C.c_int),
         ("autotune", C.c_int),
         ("resident", C.c_int),
+        ("inner_max_iter", C.c_int),
     ]
 
 

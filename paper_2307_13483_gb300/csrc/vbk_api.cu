@@ -556,8 +556,10 @@ struct DevBuf {
 // Phi^{v mu} of a q-dependent wave (Sec. II.C, II.D): sum over its channels j of
 // f_j(eps) (P_j |v>) in state d_j, i.e. w * f_j * (P_j)_{v + lin_k, v} at v + lin_k for every point
 // k of P_j (P_j symmetric), added to the vector g of one system.  The targets are distinct: the
-// offsets of one channel differ and the channels of one wave sit in different states.
-__device__ void sand_scatter(const DevModel& md, int mu, double eps, int v, double2 w, double2* __restrict__ g) {
+// offsets of one channel differ and the channels of one wave sit in different states.  Returns
+// the sum of (f_j (P_j)_{v + lin_k, v})^2, the squared norm of Phi for w = 1.
+__device__ double sand_scatter(const DevModel& md, int mu, double eps, int v, double2 w, double2* __restrict__ g) {
+    double nrm = 0.0;
     for (int j = 0; j < md.nsc; ++j) {
         if (md.sc_mu[j] != mu) continue;
         const int c = md.sc_ch[j];
@@ -570,8 +572,10 @@ __device__ void sand_scatter(const DevModel& md, int mu, double eps, int v, doub
             double2& t = gd[v + md.sp_lin[k]];
             t.x += w.x * f * cf;
             t.y += w.y * f * cf;
+            nrm += (f * cf) * (f * cf);
         }
     }
+    return nrm;
 }
 
 // <Phi^{v mu} | psi> of a q-dependent wave: sum_j f_j(eps) (P_j psi_(d_j))(v)  (Eq. crs2, real Phi).
@@ -598,23 +602,27 @@ __device__ double2 sand_project(const DevModel& md, int mu, double eps, int v, c
 }
 
 // Dense right-hand sides Phi^{v_i mu} (Sec. II.D): f_{d(mu)}(E - E_vi) on entry (d(mu), v_i), or
-// the polynomial columns of a q-dependent wave (Sec. II.C).  b is zero on entry.
+// the polynomial columns of a q-dependent wave (Sec. II.C).  b is zero on entry.  bn2[s] receives
+// ||Phi||^2 (the sum of the squared entries written), so the solver need not read b for it.
 __global__ void k_build_rhs(DevModel md, int nsys, int n_vi, const double* __restrict__ eps, const int* __restrict__ vflat,
-                            double2* __restrict__ b) {
+                            double2* __restrict__ b, double* __restrict__ bn2) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     const int mu = s % md.nmu, i = (s / md.nmu) % n_vi, e = s / (md.nmu * n_vi);
     if (md.mu_sw[mu]) {
-        sand_scatter(md, mu, eps[e], vflat[i], make_double2(1.0, 0.0), b + (long long)s * md.N);
+        bn2[s] = sand_scatter(md, mu, eps[e], vflat[i], make_double2(1.0, 0.0), b + (long long)s * md.N);
         return;
     }
     const int d = md.mu_d[mu];
-    if (d < 0) return;
-    for (int c = 0; c < md.nchan; ++c)
-        if (md.ch_mu[c] == mu) {
-            const double f = vbk_amplitude(eps[e], md.ch_a[c], md.ch_b[c], md.ch_l[c]);
-            b[(long long)s * md.N + (long long)d * md.Nnu + vflat[i]] = make_double2(f, 0.0);
-        }
+    double nrm = 0.0;
+    if (d >= 0)
+        for (int c = 0; c < md.nchan; ++c)
+            if (md.ch_mu[c] == mu) {  // one channel per wave here
+                const double f = vbk_amplitude(eps[e], md.ch_a[c], md.ch_b[c], md.ch_l[c]);
+                b[(long long)s * md.N + (long long)d * md.Nnu + vflat[i]] = make_double2(f, 0.0);
+                nrm = f * f;
+            }
+    bn2[s] = nrm;
 }
 
 __device__ __forceinline__ int chan_of_mu(const DevModel& md, int mu) {
@@ -1044,6 +1052,7 @@ void vbk_default_opts(vbk_opts* o) {
     o->timing = 0;
     o->autotune = 1;
     o->resident = 1;
+    o->inner_max_iter = 2000;
 }
 
 int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
@@ -1111,6 +1120,7 @@ static int check_opts(const vbk_opts* o) {
     if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0)) return invalid("inner_tol must be in (0, 1)");
     if (o->check_every < 1) return invalid("check_every must be >= 1");
     if (o->precond_span < -1) return invalid("precond_span must be -1 or a span mask");
+    if (o->inner_max_iter < 0) return invalid("inner_max_iter must be >= 0");
     return VBK_OK;
 }
 
@@ -1166,17 +1176,21 @@ int vbk_solve(vbk_model* m, int n_eps, const double* eps_i, int n_vi, const int*
     DevBuf b;
     b.st = st;
     const size_t bbytes = (size_t)job.nsys * N * sizeof(double2);
-    const size_t extra = (size_t)n_eps * sizeof(double) + (size_t)n_vi * sizeof(int) + 512;
+    const size_t o_vf = (((size_t)n_eps * sizeof(double) + 255) & ~size_t(255));
+    const size_t o_bn = o_vf + (((size_t)n_vi * sizeof(int) + 255) & ~size_t(255));
+    const size_t extra = o_bn + (size_t)job.nsys * sizeof(double);
     VBK_CUDA(vbk_alloc(m, &b.p, bbytes + extra, st));
     double2* b64 = (double2*)b.p;
     double* deps = (double*)((char*)b.p + bbytes);
-    int* dvf = (int*)((char*)deps + (((size_t)n_eps * sizeof(double) + 255) & ~size_t(255)));
+    int* dvf = (int*)((char*)deps + o_vf);
+    double* bn2 = (double*)((char*)deps + o_bn);
     VBK_CUDA(cudaMemsetAsync(b64, 0, bbytes, st));
     VBK_CUDA(cudaMemcpyAsync(deps, eps_i, n_eps * sizeof(double), cudaMemcpyHostToDevice, st));
     VBK_CUDA(cudaMemcpyAsync(dvf, vflat.data(), n_vi * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_build_rhs<<<cdiv_u(job.nsys, 128), 128, 0, st>>>(m->dm, job.nsys, n_vi, deps, dvf, b64);
+    k_build_rhs<<<cdiv_u(job.nsys, 128), 128, 0, st>>>(m->dm, job.nsys, n_vi, deps, dvf, b64, bn2);
     VBK_CUDA(cudaGetLastError());
     job.b64 = b64;
+    job.bnorm2 = bn2;
     job.x64 = (double2*)psi_dev;
     int rc = vbk_solve_job(m, job, *opts, stats, st);
     m->launches += 1;  // k_build_rhs

@@ -422,6 +422,7 @@ struct SysState {
     int j;           // GMRES: steps in the current cycle
     int cycle_iters; // iterations in the current inner solve
     int last_cycle;  // iterations of the previous inner solve (orders the next launch)
+    int icap;        // iteration count at which the current inner solve stops (<= max_iter)
 };
 
 // Internal solve over an explicit list of systems with dense FP64 right-hand sides.
@@ -432,6 +433,7 @@ struct SolveJob {
     std::vector<int> sys_e;     // energy index of each system
     const double2* b64 = nullptr;  // device [nsys][N]
     double2* x64 = nullptr;        // device [nsys][N] (output)
+    const double* bnorm2 = nullptr;  // device [nsys] ||b||^2 when the caller built b, else computed from b
 };
 int vbk_solve_job(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stats* st, cudaStream_t stream);
 

@@ -1337,15 +1337,19 @@ __global__ void __launch_bounds__(TPB) k_rhs_norm(int N, const double2* __restri
 
 // Outer convergence test on the FP64 residual (stopping rule of Sec. III, true residual).
 __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restrict__ outer, int* __restrict__ inner,
-                              const double2* __restrict__ part, int nb, int first, double tol, double inner_tol,
-                              int max_refine, int max_iter, int* __restrict__ count, int* __restrict__ olist,
-                              int* __restrict__ ilist) {
+                              const double2* __restrict__ part, int nb, const double* __restrict__ bn2, int first,
+                              double tol, double inner_tol, int max_refine, int max_iter, int inner_cap,
+                              int* __restrict__ count, int* __restrict__ olist, int* __restrict__ ilist) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     inner[s] = 0;
     if (!outer[s]) return;
     double rr = 0.0;
-    for (int k = 0; k < nb; ++k) rr += part[(long long)s * nb + k].x;
+    if (bn2) {  // first check with ||b||^2 known from the right-hand-side builder
+        rr = bn2[s];
+    } else {
+        for (int k = 0; k < nb; ++k) rr += part[(long long)s * nb + k].x;
+    }
     const double rn = sqrt(rr);
     SysState& S = st[s];
     if (first) {
@@ -1382,6 +1386,9 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
     S.j = 0;
     S.last_cycle = S.cycle_iters;
     S.cycle_iters = 0;
+    // the inner solve ends at max_iter, or after inner_cap iterations (the FP64 residual then
+    // restarts it: a cure for FP32 Krylov stagnation)
+    S.icap = inner_cap > 0 ? (int)min((long long)max_iter, (long long)S.iters + inner_cap) : max_iter;
     S.inres = 1.0;
     inner[s] = 1;
     const int pos = atomicAdd(count, 1);
@@ -1560,7 +1567,7 @@ __global__ void k_cocg_beta(int nsys, SysState* __restrict__ st, int* __restrict
         act[s] = 0;  // the outer FP64 residual decides (a NaN there ends the system)
         return;
     }
-    if (rn <= S.target || S.iters >= max_iter) {
+    if (rn <= S.target || S.iters >= S.icap) {
         act[s] = 0;
         return;
     }
@@ -1847,7 +1854,7 @@ __global__ void __launch_bounds__(TPB) k_pupdate(int N, const int* __restrict__ 
                 const double rn = sqrt(rr);
                 Sx.inres = rn;
                 const double den = Sx.rho.x * Sx.rho.x + Sx.rho.y * Sx.rho.y;
-                if (!isfinite(rn) || !isfinite(rz.x) || !isfinite(rz.y) || rn <= Sx.target || Sx.iters >= max_iter) {
+                if (!isfinite(rn) || !isfinite(rz.x) || !isfinite(rz.y) || rn <= Sx.target || Sx.iters >= Sx.icap) {
                     act[s] = 0;  // the FP64 residual decides
                 } else if (!(rz.x * rz.x + rz.y * rz.y > 0.0) || !(den > 0.0)) {
                     Sx.status = VBK_SYS_BREAKDOWN;
@@ -2038,12 +2045,16 @@ __device__ __forceinline__ double f2d_exact(float f) {
     return __longlong_as_double((long long)bits);
 }
 
-// x64 = hi + lo of the double-float solution (every system); the sum is exact in FP64
+// x64 = hi + lo of the double-float solution (every system); the sum is exact in FP64.  Two
+// entries per thread (independent loads in flight), streamed: neither side is read again here.
 __global__ void __launch_bounds__(TPB) k_df_out(long long n, const float4* __restrict__ xs, double2* __restrict__ x64) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 2;
     if (i >= n) return;
-    const float4 v = xs[i];
-    x64[i] = make_double2(f2d_exact(v.x) + f2d_exact(v.z), f2d_exact(v.y) + f2d_exact(v.w));
+    const bool two = i + 1 < n;
+    const float4 v = __ldcs(xs + i);
+    const float4 u = two ? __ldcs(xs + i + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __stcs(x64 + i, make_double2(f2d_exact(v.x) + f2d_exact(v.z), f2d_exact(v.y) + f2d_exact(v.w)));
+    if (two) __stcs(x64 + i + 1, make_double2(f2d_exact(u.x) + f2d_exact(u.z), f2d_exact(u.y) + f2d_exact(u.w)));
 }
 
 constexpr int RTPB = 1024;
@@ -2097,6 +2108,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     // (fields read where they are needed: nothing of the state stays live across the loop)
     const float target2 = (float)(st[s].target * st[s].target);
     int iters = st[s].iters;
+    const int icap = min(max_iter, st[s].icap);
     float rr = 0.f;
     int status = -1;  // -1: stopped normally (the FP64 residual decides)
     __syncthreads();
@@ -2149,7 +2161,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
         rho = make_float2(t.y, t.z);
     }
     bool wrote_x = false;
-    const int budget = max(0, max_iter - iters);
+    const int budget = max(0, icap - iters);
     for (int it = 0; it < budget; ++it) {
         // q = A p and p^T q
         float pq_x = 0.f, pq_y = 0.f;
@@ -2211,7 +2223,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
         wrote_x = true;
         iters += 1;
         rr = sums.x;
-        if (!isfinite(sums.x) || !isfinite(sums.y) || !isfinite(sums.z) || sums.x <= target2 || iters >= max_iter) break;
+        if (!isfinite(sums.x) || !isfinite(sums.y) || !isfinite(sums.z) || sums.x <= target2 || iters >= icap) break;
         const float rden = rho.x * rho.x + rho.y * rho.y;
         if (!(sums.y * sums.y + sums.z * sums.z > 0.f) || !(rden > 0.f)) {
             status = VBK_SYS_BREAKDOWN;
@@ -3391,8 +3403,9 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             const Sel so{olist, outer};
             // the first residual is b itself (x = 0): only its norm is computed, and the first
             // inner solve reads b directly
-            if (it == 0)
-                rn.go("rhs_norm", k_rhs_norm, dim3(nsys), dim3(TPB), N, job.b64, partA);
+            if (it == 0) {
+                if (!job.bnorm2) rn.go("rhs_norm", k_rhs_norm, dim3(nsys), dim3(TPB), N, job.b64, partA);
+            }
             else if (dfr_res)
                 rn.go_smem("residual_df", k_residual_res<M>, dim3(n_out), dim3(RTPB), residual_res_smem(md), md,
                            (const int*)sys_e, (const int*)olist, (const float4*)dsp, (const float4*)xs, job.b64, rsp, partA);
@@ -3420,7 +3433,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
                   it == 0 || dfr_res ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
-                  it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter, cnt, olist, ilist);
+                  it == 0 ? job.bnorm2 : (const double*)nullptr, it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter,
+                  mixed && method == VBK_COCG ? o.inner_max_iter : 0, cnt, olist, ilist);
             if (resident && nsys <= ORDER_MAX)  // longest expected inner solve first (one CTA each)
                 rn.go("order_lists", k_order_lists, dim3(1), dim3(1024), nsys, (const SysState*)sst, (const int*)inner, olist,
                       ilist);
@@ -3764,7 +3778,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         if (rc) break;
         if (dfr)
-            rn.go("df_out", k_df_out, dim3(cdiv_u((long long)nsys * N, TPB)), dim3(TPB), (long long)nsys * N, (const float4*)xs,
+            rn.go("df_out", k_df_out, dim3(cdiv_u((long long)nsys * N, 2 * TPB)), dim3(TPB), (long long)nsys * N, (const float4*)xs,
                   job.x64);
         // results
         if (cudaMemcpyAsync(hst, sst, nsys * sizeof(SysState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

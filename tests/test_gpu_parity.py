@@ -287,6 +287,31 @@ def test_edge_cases(vbk):
     # maximum restart length and a single-iteration check interval
     psi, st = vbk.vbk_solve(model, [2.0], [[0, 0]], vbk.vbk_default_opts(restart=256, check_every=1, tol=1e-10))
     assert all(s["status"] == "converged" for s in st)
+    with pytest.raises(vbk.VbkError):
+        vbk.vbk_solve(model, [1.0], [[0, 0]], vbk.vbk_default_opts(inner_max_iter=-1))
+
+
+@pytest.mark.parametrize("resident", [1, 0])
+def test_inner_solves_capped_and_restarted_still_converge(vbk, resident):
+    """Mixed COCG whose FP32 inner solves stop after a quarter of the iterations an uncapped
+    inner solve takes: each FP64 residual restarts the inner solve (the cure for FP32
+    stagnation), the refinement takes more steps and still reaches the tolerance."""
+    desc = w.ci2d_model(16)
+    model = vbk.Model(desc)
+    eps = np.array([0.8, 2.9])
+    base = dict(method="cocg", precision="mixed", precond_span=0, tol=1e-9, max_refine=400, resident=resident)
+    _, st0 = vbk.vbk_solve(model, eps, [[0, 0]], vbk.vbk_default_opts(inner_max_iter=0, **base))
+    cap = max(4, max(s["iterations"] for s in st0) // 4)
+    psi, st = vbk.vbk_solve(model, eps, [[0, 0]], vbk.vbk_default_opts(inner_max_iter=cap, **base))
+    assert all(s["status"] == "converged" for s in st)
+    assert max(s["refinements"] for s in st) > max(s["refinements"] for s in st0)
+    assert all(s["iterations"] <= cap * (s["refinements"] + 1) for s in st)
+    psi = psi.cpu().numpy()
+    for e, ei in enumerate(eps):
+        E = o.total_energy(desc, ei, [0, 0])
+        for mu in range(2):
+            rhs = o.phi(desc, E, [0, 0], mu)
+            assert o.relative_residual(desc, E, psi[e, 0, mu], rhs) <= 1e-9 * 1.05
 
 
 def test_uneven_batch_with_several_initial_states(vbk):
