@@ -186,7 +186,10 @@ int vbk_model_size(const vbk_model* model, int* n_unknowns, int* n_partial_waves
  *   psi_dev : device complex128 [n_eps][n_vi][n_mu][N], written.
  *   stats   : host [n_eps * n_vi * n_mu] in the same order, or NULL.
  * Returns VBK_ERR_NOT_CONVERGED if any system ended with a status other than CONVERGED or
- * ZERO_RHS (psi then holds the last iterate).  Synchronises `stream`. */
+ * ZERO_RHS (psi then holds the last iterate).  With VBK_MIXED COCG, a system whose FP32 inner
+ * iterations stop helping (a refinement step lowers the FP64 residual by less than 10%, or a
+ * non-finite value or a breakdown appears) is solved again in FP64 from psi = 0, and its stats
+ * add both runs.  Synchronises `stream`. */
 int vbk_solve(vbk_model* model, int n_eps, const double* eps_i, int n_vi, const int* vi,
               const vbk_opts* opts, void* psi_dev, vbk_stats* stats, void* stream);
 

@@ -1033,6 +1033,90 @@ __global__ void k_grad_reduce(int nsys, int nblk, int nblk2, int ntheta, const d
     grad[th] = acc;
 }
 
+// rows idx[k] of src into row k of dst (gather) or row k of src into rows idx[k] of dst (scatter)
+__global__ void k_move_rows(int n, int N, const int* __restrict__ idx, const double2* __restrict__ src,
+                            double2* __restrict__ dst, int scatter) {
+    const int k = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || i >= N) return;
+    const long long a = (long long)idx[k] * N + i, c = (long long)k * N + i;
+    if (scatter)
+        dst[a] = src[c];
+    else
+        dst[c] = src[a];
+}
+
+// A VBK_MIXED COCG solve whose FP32 inner iterations stop helping a system (the FP64 residual of a
+// refinement step falls by less than 10%, or a non-finite value or a breakdown appears) solves
+// that system again in FP64 from x = 0; its statistics then add both runs.
+int solve_job_with_fallback(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stats* stats, cudaStream_t st) {
+    std::vector<vbk_stats> own;
+    vbk_stats* sv = stats;
+    if (!sv) {
+        own.resize(job.nsys);
+        sv = own.data();
+    }
+    int rc = vbk_solve_job(m, job, o, sv, st);
+    if (o.precision != VBK_MIXED || o.method != VBK_COCG || rc != VBK_ERR_NOT_CONVERGED) return rc;
+    std::vector<int> redo;
+    for (int s = 0; s < job.nsys; ++s)
+        if (sv[s].status == VBK_SYS_STALLED || sv[s].status == VBK_SYS_NAN || sv[s].status == VBK_SYS_BREAKDOWN)
+            redo.push_back(s);
+    if (redo.empty()) return rc;
+    const std::vector<KTimer> timers = m->timers;
+    const long long launches = m->launches;
+    const int nf = (int)redo.size(), N = m->N;
+    const size_t rows = (size_t)nf * N * sizeof(double2), ib = ((size_t)nf * sizeof(int) + 255) & ~size_t(255);
+    DevBuf buf;
+    buf.st = st;
+    VBK_CUDA(vbk_alloc(m, &buf.p, 2 * rows + ib, st));
+    double2* bsub = (double2*)buf.p;
+    double2* xsub = (double2*)((char*)buf.p + rows);
+    int* didx = (int*)((char*)buf.p + 2 * rows);
+    VBK_CUDA(cudaMemcpyAsync(didx, redo.data(), nf * sizeof(int), cudaMemcpyHostToDevice, st));
+    const dim3 g(cdiv_u(N, TPB), (unsigned)nf);
+    k_move_rows<<<g, TPB, 0, st>>>(nf, N, didx, job.b64, bsub, 0);
+    VBK_CUDA(cudaGetLastError());
+    SolveJob sub;
+    sub.nsys = nf;
+    sub.nE = job.nE;
+    sub.E = job.E;
+    for (int s : redo) sub.sys_e.push_back(job.sys_e[s]);
+    sub.b64 = bsub;
+    sub.x64 = xsub;
+    vbk_opts o64 = o;
+    o64.precision = VBK_FP64;
+    std::vector<vbk_stats> s2(nf);
+    const int rc2 = vbk_solve_job(m, sub, o64, s2.data(), st);
+    if (rc2 != VBK_OK && rc2 != VBK_ERR_NOT_CONVERGED) return rc2;
+    k_move_rows<<<g, TPB, 0, st>>>(nf, N, didx, xsub, job.x64, 1);
+    VBK_CUDA(cudaGetLastError());
+    VBK_CUDA(cudaStreamSynchronize(st));  // `redo` must outlive its copy
+    bool ok = true;
+    for (int k = 0; k < nf; ++k) {
+        vbk_stats& S = sv[redo[k]];
+        S.status = s2[k].status;
+        S.iterations += s2[k].iterations;
+        S.refinements += s2[k].refinements;
+        S.rel_residual = s2[k].rel_residual;
+    }
+    for (int s = 0; s < job.nsys; ++s) ok = ok && (sv[s].status == VBK_SYS_CONVERGED || sv[s].status == VBK_SYS_ZERO_RHS);
+    // kernel bookkeeping of both runs
+    std::vector<KTimer> merged = timers;
+    for (const KTimer& t : m->timers) {
+        bool found = false;
+        for (KTimer& u : merged)
+            if (u.name == t.name) {
+                u.launches += t.launches;
+                u.ms += t.ms;
+                found = true;
+            }
+        if (!found) merged.push_back(t);
+    }
+    m->timers = merged;
+    m->launches += launches + 2;
+    return ok ? VBK_OK : VBK_ERR_NOT_CONVERGED;
+}
+
 }  // namespace
 
 // =============================================================================== C ABI
@@ -1192,7 +1276,7 @@ int vbk_solve(vbk_model* m, int n_eps, const double* eps_i, int n_vi, const int*
     job.b64 = b64;
     job.bnorm2 = bn2;
     job.x64 = (double2*)psi_dev;
-    int rc = vbk_solve_job(m, job, *opts, stats, st);
+    int rc = solve_job_with_fallback(m, job, *opts, stats, st);
     m->launches += 1;  // k_build_rhs
     return rc;
 }
@@ -1422,7 +1506,7 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
     // lambda = A^-1 g  (A = A^T: the forward operator serves as its own transpose)
     job.b64 = (const double2*)P(0);
     job.x64 = (double2*)P(1);
-    int rc = vbk_solve_job(m, job, *opts, stats, st);
+    int rc = solve_job_with_fallback(m, job, *opts, stats, st);
     if (rc != VBK_OK && rc != VBK_ERR_NOT_CONVERGED) return rc;
     const long long extra_launches = nblk2 ? 6 : 5;
     // contractions

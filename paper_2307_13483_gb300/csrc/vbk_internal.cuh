@@ -425,6 +425,10 @@ struct SysState {
     int icap;        // iteration count at which the current inner solve stops (<= max_iter)
 };
 
+// Internal per-system status (never returned to callers): a VBK_MIXED refinement step that
+// lowered the FP64 residual by less than 10%; such systems are solved again in FP64.
+#define VBK_SYS_STALLED 6
+
 // Internal solve over an explicit list of systems with dense FP64 right-hand sides.
 struct SolveJob {
     int nsys = 0;

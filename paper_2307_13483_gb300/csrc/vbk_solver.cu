@@ -1339,7 +1339,8 @@ __global__ void __launch_bounds__(TPB) k_rhs_norm(int N, const double2* __restri
 __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restrict__ outer, int* __restrict__ inner,
                               const double2* __restrict__ part, int nb, const double* __restrict__ bn2, int first,
                               double tol, double inner_tol, int max_refine, int max_iter, int inner_cap,
-                              int* __restrict__ count, int* __restrict__ olist, int* __restrict__ ilist) {
+                              int stall_check, int* __restrict__ count, int* __restrict__ olist,
+                              int* __restrict__ ilist) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsys) return;
     inner[s] = 0;
@@ -1363,6 +1364,7 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
     } else {
         S.refines += 1;
     }
+    const double prev = S.rnorm;
     S.rnorm = rn;
     if (!isfinite(rn)) {
         S.status = VBK_SYS_NAN;
@@ -1371,6 +1373,11 @@ __global__ void k_outer_check(int nsys, SysState* __restrict__ st, int* __restri
     }
     if (rn <= tol * S.bnorm) {
         S.status = VBK_SYS_CONVERGED;
+        outer[s] = 0;
+        return;
+    }
+    if (stall_check && !first && !(rn <= 0.9 * prev)) {  // the inner FP32 solve no longer helps
+        S.status = VBK_SYS_STALLED;
         outer[s] = 0;
         return;
     }
@@ -3434,7 +3441,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
                   it == 0 || dfr_res ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
                   it == 0 ? job.bnorm2 : (const double*)nullptr, it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter,
-                  mixed && method == VBK_COCG ? o.inner_max_iter : 0, cnt, olist, ilist);
+                  mixed && method == VBK_COCG ? o.inner_max_iter : 0, mixed && method == VBK_COCG ? 1 : 0, cnt, olist,
+                  ilist);
             if (resident && nsys <= ORDER_MAX)  // longest expected inner solve first (one CTA each)
                 rn.go("order_lists", k_order_lists, dim3(1), dim3(1024), nsys, (const SysState*)sst, (const int*)inner, olist,
                       ilist);
