@@ -102,7 +102,8 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------- roofline model
 def kernel_bytes_per_unit(name, N, nmu, c, p_band):
-    """Algorithmic bytes one kernel moves per system-iteration (kernel table)."""
+    """Algorithmic bytes one kernel moves per system-iteration: the vectors and tables the method
+    must read and write once (c bytes per complex entry, N unknowns, n_mu waves per energy)."""
     if name == "matvec":
         return (2 * c + c / nmu) * N          # read x, write y, diagonal shared by the n_mu waves
     if name == "cocg_update":
