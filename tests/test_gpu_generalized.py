@@ -307,6 +307,39 @@ def test_generalized_adjoint_in_coupling_parameters(vbk):
     np.testing.assert_allclose(g, g_ref, rtol=1e-6, atol=1e-9 * np.abs(g_ref).max())
 
 
+def test_model_with_q_dependent_and_constant_waves(vbk):
+    """One partial wave couples through 1 + 0.15 q_g (a sandwich of its own), the other through a
+    constant: the first leaves the diagonal tables, the second stays in them.  Operator, solve,
+    cross sections and gradients in a and b of both channels against the oracle."""
+    desc = w.ci2d_model(9)
+    desc["channels"][0]["terms"] = [{"coef": 1.0, "pow": [0, 0]}, {"coef": 0.15, "pow": [1, 0]}]
+    model = vbk.Model(desc)
+    rng = np.random.default_rng(12)
+    E = np.array([2.3, 3.6])
+    x = rand_vectors(rng, (E.size, 2, model.N))
+    y = vbk.vbk_matvec(model, E, torch.tensor(x, device="cuda")).cpu().numpy()
+    for e in range(E.size):
+        A = o.a_matrix(desc, E[e])
+        for k in range(2):
+            assert np.linalg.norm(y[e, k] - A @ x[e, k]) <= 1e-13 * np.linalg.norm(A @ x[e, k])
+    eps = np.array([0.9, 2.2])
+    vi = [[0, 0]]
+    opts = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=0, tol=1e-12, max_refine=200)
+    psi, st = vbk.vbk_solve(model, eps, vi, opts)
+    assert all(s["status"] == "converged" for s in st)
+    vf = [[0, 0], [1, 0], [0, 1]]
+    sig = vbk.vbk_cross_sections(model, eps, vi, psi, vf)
+    ref, _ = o.cross_sections(desc, eps, vi, vf)
+    np.testing.assert_allclose(sig.cpu().numpy(), ref, rtol=1e-8, atol=1e-12 * ref.max())
+    target = np.full((eps.size, len(vf)), 0.03)
+    tgt = torch.tensor(target[:, None, :], device="cuda")
+    nt = len(desc["terms"])
+    thetas = [nt + 0, nt + 1, nt + 2, nt + 3, nt + 4 + 1]  # a, b of both channels; the q_g coefficient
+    g, _ = vbk.vbk_solve_adjoint(model, eps, vi, psi, vf, 2.0 * (sig - tgt), thetas, opts)
+    g_ref = o.loss_gradient_adjoint(desc, eps, vi[0], vf, target, thetas)
+    np.testing.assert_allclose(g, g_ref, rtol=1e-6, atol=1e-9 * np.abs(g_ref).max())
+
+
 def test_generalized_requests_not_served_are_rejected(vbk):
     desc = w.gen_ecd_model(6, 6)
     model = vbk.Model(desc)
