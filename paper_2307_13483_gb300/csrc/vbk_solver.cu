@@ -2084,7 +2084,9 @@ template <int M> __device__ __forceinline__ int nsel(const int (&n)[MAXM], int m
     return r;
 }
 
-template <int M>
+// SEC: some stencil point involves a second mode (its factor from the oscillator tables); the
+// instantiation without it drops that test from the point loop.
+template <int M, bool SEC>
 __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const int* __restrict__ sys_e,
                                                           const int* __restrict__ list, int pmode,
                                                           const float2* __restrict__ diag, const float2* __restrict__ dinv,
@@ -2169,13 +2171,34 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
     }
     bool wrote_x = false;
     const int budget = max(0, icap - iters);
+    // mixed-radix digits of this thread's first element and of the stride RTPB
+    int d0, n0[MAXM], inc[MAXM], incd;
+    {
+        d0 = (int)fdiv((unsigned)tid, md.fd_nnu);
+        decode<M>(md, tid - d0 * md.Nnu, n0);
+        incd = (int)fdiv((unsigned)RTPB, md.fd_nnu);
+        decode<M>(md, RTPB - incd * md.Nnu, inc);
+    }
     for (int it = 0; it < budget; ++it) {
         // q = A p and p^T q
         float pq_x = 0.f, pq_y = 0.f;
+        // (d, n) of element i, advanced by RTPB in the mixed radix (d, n_0, ..., n_{M-1}) with
+        // one carry per digit instead of a division per digit
+        int d = d0;
+        int n[MAXM];
+#pragma unroll
+        for (int m = 0; m < MAXM; ++m) n[m] = n0[m];
         for (int i = tid; i < N; i += RTPB) {
-            const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * md.Nnu;
-            int n[MAXM];
-            decode<M>(md, nu, n);
+            if (i != tid) {
+                int c = 0;
+#pragma unroll
+                for (int m = M - 1; m >= 0; --m) {
+                    int v = n[m] + inc[m] + c;
+                    c = v >= md.nb[m];
+                    n[m] = c ? v - md.nb[m] : v;
+                }
+                d += incd + c;
+            }
             const float2 pi = P[i];
             float2 acc = cmul<float>(dg[i], pi);
             const char* Pi = reinterpret_cast<const char*>(P + i);
@@ -2188,10 +2211,12 @@ __global__ void __launch_bounds__(RTPB, 1) k_cocg_resident(DevModel md, const in
                 for (; k < kend; ++k) {
                     const int4 q = sdesc[k];
                     float2 cc = *reinterpret_cast<const float2*>(row + q.x);  // (-c, -c)
-                    if (q.z >= 0) {
-                        const float t = md.tab32[q.z + nsel<M>(n, q.w)];
-                        cc.x *= t;
-                        cc.y *= t;
+                    if constexpr (SEC) {
+                        if (q.z >= 0) {
+                            const float t = md.tab32[q.z + nsel<M>(n, q.w)];
+                            cc.x *= t;
+                            cc.y *= t;
+                        }
                     }
                     // neighbours outside [0, N) read the zero halo
                     acc = ffma2(cc, *reinterpret_cast<const float2*>(Pi + q.y), acc);
@@ -2469,7 +2494,10 @@ inline bool resident_ok(const DevModel& md) {
 }
 template <int M> int prepare_resident(const DevModel& md) {
     const cudaError_t ce =
-        cudaFuncSetAttribute(k_cocg_resident<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)resident_smem(md));
+        md.rsec ? cudaFuncSetAttribute(k_cocg_resident<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)resident_smem(md))
+                : cudaFuncSetAttribute(k_cocg_resident<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)resident_smem(md));
     return ce == cudaSuccess ? VBK_OK : vbk_cuda_fail(ce, "resident COCG shared-memory opt-in");
 }
 
@@ -3468,11 +3496,17 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             if (method == VBK_COCG && resident && !block) {
                 // one CTA per system runs the whole inner solve: scaled double-float residual in,
                 // double-float correction out (list = ilist from the outer check)
-                rn.go_smem("cocg_resident", k_cocg_resident<M>, dim3(n_in), dim3(RTPB), resident_smem(md), md,
-                           (const int*)sys_e, (const int*)ilist, pmode, reinterpret_cast<const float2*>(diagR),
-                           (const float2*)dinvR, reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r),
-                           it == 0 ? job.b64 : (const double2*)nullptr, (const float4*)rsp, xs, sst, inner, outer,
-                           o.max_iter);
+                auto res_go = [&](auto kern) {
+                    rn.go_smem("cocg_resident", kern, dim3(n_in), dim3(RTPB), resident_smem(md), md,
+                               (const int*)sys_e, (const int*)ilist, pmode, reinterpret_cast<const float2*>(diagR),
+                               (const float2*)dinvR, reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r),
+                               it == 0 ? job.b64 : (const double2*)nullptr, (const float4*)rsp, xs, sst, inner, outer,
+                               o.max_iter);
+                };
+                if (md.rsec)
+                    res_go(k_cocg_resident<M, true>);
+                else
+                    res_go(k_cocg_resident<M, false>);
             } else if (method == VBK_COCG) {
                 // r = rhs, x = 0, z = B^-1 r, p = z, rho = r^T z.  With a block preconditioner the
                 // search direction carries over from the previous inner solve (k_cocg_start):
