@@ -2,8 +2,10 @@
 entry points behave as documented (no GPU needed).
 
 The host level shift is pinned against the oracle's closed form (which is itself pinned
-against quadrature), so the library's own Dawson (Rybicki's method) and erfcx code paths
-are checked on both sides of threshold.
+against quadrature), so the library's own Dawson and erfcx code paths (series near zero,
+piecewise polynomials, asymptotic expansions) are checked on both sides of threshold.  The
+ctypes structures of the binding are checked field by field against the C header compiled by
+the host compiler.
 """
 
 import os
@@ -73,8 +75,36 @@ def test_default_options(lib):
     o = lib.vbk_default_opts()
     assert (o.method, o.precision, o.precond_span, o.restart) == (lib.VBK_GMRES, lib.VBK_MIXED, 0, 64)
     assert o.tol == 1e-8 and o.inner_tol == 1e-5 and o.check_every == 8 and o.timing == 0 and o.autotune == 1 and o.resident == 1
+    assert o.inner_max_iter == 2000 and o.max_iter == 20000 and o.max_refine == 40
     o2 = lib.vbk_default_opts(method="cocg", precision="fp64", tol=1e-10)
     assert (o2.method, o2.precision, o2.tol) == (lib.VBK_COCG, lib.VBK_FP64, 1e-10)
+
+
+def test_binding_structs_match_the_header(lib, tmp_path):
+    """sizeof and every field offset of the ABI structs, from the header compiled by gcc, equal
+    those of the binding's ctypes classes (a field added on one side only would shift them)."""
+    import ctypes
+
+    structs = {"vbk_term": lib.vbk_term, "vbk_channel": lib.vbk_channel, "vbk_cterm": lib.vbk_cterm,
+               "vbk_model_desc": lib.vbk_model_desc, "vbk_opts": lib.vbk_opts, "vbk_stats": lib.vbk_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[name, field] = int(value)
+    for name, cls in structs.items():
+        assert got[name, "sizeof"] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[name, fname] == getattr(cls, fname).offset, (name, fname)
 
 
 def test_status_strings(lib):
