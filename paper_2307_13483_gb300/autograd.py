@@ -4,7 +4,9 @@ Forward: build the model with the given parameter values, solve every (eps_i, v_
 system (Eq. Ax=b) and form sigma (Eq. crs).  The solutions psi are kept (one checkpoint
 per energy) for the backward pass, which calls the library's adjoint solve with the same
 complex-symmetric operator.  Parameter ids follow ``vbk_solve_adjoint``: k < n_terms is the
-coefficient of term k, n_terms + 2c / n_terms + 2c + 1 are a / b of channel c.
+coefficient of term k, n_terms + 2c / n_terms + 2c + 1 are a / b of channel c, and
+n_terms + 2 n_channels + t is the coefficient of coupling-polynomial term t, counted channel by
+channel in listed order (the order in which the binding passes them to the library).
 """
 
 from __future__ import annotations
@@ -16,14 +18,17 @@ import torch
 
 def _with_values(desc: dict, theta_ids, values) -> dict:
     m = copy.deepcopy(desc)
-    nt = len(m["terms"])
+    nt, nc = len(m["terms"]), len(m["channels"])
+    cterms = [t for c in m["channels"] for t in (c.get("terms") or [])]
     for tid, v in zip(theta_ids, values):
         tid = int(tid)
         if tid < nt:
             m["terms"][tid]["coef"] = float(v)
-        else:
+        elif tid < nt + 2 * nc:
             c, which = divmod(tid - nt, 2)
             m["channels"][c]["ab"[which]] = float(v)
+        else:
+            cterms[tid - nt - 2 * nc]["coef"] = float(v)
     return m
 
 

@@ -124,3 +124,17 @@ def test_build_without_device_reports_no_device(lib):
     with pytest.raises(lib.VbkError) as ei:
         lib.Model(workloads.ci2d_model(4))
     assert ei.value.code == 6
+
+
+def test_autograd_parameter_ids_match_the_oracle(lib):
+    """The autograd wrapper maps parameter ids to model values exactly as the oracle does: U terms,
+    a / b of channels, then coupling-polynomial coefficients channel by channel (Table II model)."""
+    import workloads
+    from oracle import vibronic as o
+    from paper_2307_13483_gb300.autograd import _with_values
+
+    desc = workloads.gen_ecd_model(3, 3)
+    n = len(desc["terms"]) + 2 * len(desc["channels"]) + sum(len(c["terms"]) for c in desc["channels"])
+    for tid in range(n):
+        value = 0.5 + 0.01 * tid
+        assert _with_values(desc, [tid], [value]) == o.with_parameter(desc, tid, value), tid
