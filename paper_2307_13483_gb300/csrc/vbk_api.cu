@@ -62,6 +62,63 @@ std::vector<std::vector<double>> q_power_band(int n, int k) {
     return cur;
 }
 
+// The conditions on a model description that need no device, checked before the device is
+// touched (so that a malformed description is reported as such on any machine); build() relies
+// on them and repeats them where it derives its tables.
+int validate_desc(const vbk_model_desc* d) {
+    if (!d) return invalid("model description is NULL");
+    if (d->n_states < 1 || d->n_states > VBK_MAX_STATES) return invalid("n_states out of range");
+    if (d->n_modes < 1 || d->n_modes > VBK_MAX_MODES) return invalid("n_modes out of range");
+    long long nnu = 1;
+    for (int k = 0; k < d->n_modes; ++k) {
+        if (d->n_basis[k] < 1 || d->n_basis[k] > 100000) return invalid("n_basis out of range");
+        if (!(d->omega[k] > 0.0) || !std::isfinite(d->omega[k])) return invalid("omega must be positive and finite");
+        nnu *= d->n_basis[k];
+        if (nnu * d->n_states > (1LL << 30)) return invalid("basis too large");
+    }
+    if (d->n_terms < 0 || (d->n_terms > 0 && !d->terms)) return invalid("terms missing");
+    if (d->n_channels < 1 || d->n_channels > VBK_MAX_CHANNELS || !d->channels) return invalid("n_channels out of range");
+    if (d->n_cterms < 0 || d->n_cterms > VBK_MAX_CTERMS || (d->n_cterms > 0 && !d->cterms))
+        return invalid("n_cterms out of range (0..VBK_MAX_CTERMS) or cterms missing");
+    for (int k = 0; k < d->n_terms; ++k) {
+        const vbk_term& t = d->terms[k];
+        if (t.d < 0 || t.dp < 0 || t.d >= d->n_states || t.dp >= d->n_states || t.d > t.dp)
+            return invalid("term state indices must satisfy 0 <= d <= dp < n_states");
+        if (!std::isfinite(t.coef)) return invalid("term coefficient not finite");
+        for (int q = 0; q < VBK_MAX_MODES; ++q)
+            if (q < d->n_modes ? (t.pow[q] < 0 || t.pow[q] > 8) : t.pow[q] != 0)
+                return invalid("term power out of range (0..8, zero beyond n_modes)");
+    }
+    bool seen[MAXS][VBK_MAX_CHANNELS] = {};
+    int cnt[VBK_MAX_CHANNELS] = {0}, q_dep[VBK_MAX_CHANNELS] = {0};
+    for (int k = 0; k < d->n_channels; ++k) {
+        const vbk_channel& c = d->channels[k];
+        if (c.d < 0 || c.d >= d->n_states) return invalid("channel state index out of range");
+        if (c.mu < 0 || c.mu >= VBK_MAX_CHANNELS) return invalid("partial-wave index out of range");
+        if (!(c.a >= 0.0) || !std::isfinite(c.a) || !(c.b > 0.0) || !std::isfinite(c.b) || c.l < 0 || c.l > 20)
+            return invalid("channel parameters out of range (a >= 0, b > 0, 0 <= l <= 20)");
+        if (seen[c.d][c.mu]) return invalid("a state couples to a partial wave at most once");
+        seen[c.d][c.mu] = true;
+        if (++cnt[c.mu] > 1) q_dep[c.mu] = 1;
+    }
+    for (int k = 0; k < d->n_cterms; ++k) {
+        const vbk_cterm& t = d->cterms[k];
+        if (t.channel < 0 || t.channel >= d->n_channels) return invalid("coupling term names no channel");
+        if (!std::isfinite(t.coef)) return invalid("coupling term coefficient not finite");
+        for (int q = 0; q < VBK_MAX_MODES; ++q)
+            if (q < d->n_modes ? (t.pow[q] < 0 || t.pow[q] > 8) : t.pow[q] != 0)
+                return invalid("coupling term power out of range (0..8, zero beyond n_modes)");
+        q_dep[d->channels[t.channel].mu] = 1;
+    }
+    for (int a = 0; a < d->n_channels; ++a)
+        for (int b = 0; b < d->n_channels; ++b) {
+            const vbk_channel &ca = d->channels[a], &cb = d->channels[b];
+            if (ca.mu == cb.mu && q_dep[ca.mu] && ca.l != cb.l)
+                return invalid("the channels of a q-dependent partial wave must share l");
+        }
+    return VBK_OK;
+}
+
 int build(const vbk_model_desc* d, vbk_model* m) {
     if (!d) return invalid("model description is NULL");
     if (d->n_states < 1 || d->n_states > VBK_MAX_STATES) return invalid("n_states out of range");
@@ -1143,6 +1200,7 @@ int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
     g_last_error.clear();
     if (!out) return invalid("output handle pointer is NULL");
     *out = nullptr;
+    if (int rc = validate_desc(desc)) return rc;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
         cudaGetLastError();

@@ -138,3 +138,61 @@ def test_autograd_parameter_ids_match_the_oracle(lib):
     for tid in range(n):
         value = 0.5 + 0.01 * tid
         assert _with_values(desc, [tid], [value]) == o.with_parameter(desc, tid, value), tid
+
+
+def test_malformed_models_are_rejected_before_any_device_work(lib):
+    """vbk_build_model checks the description before it touches a device: each malformed model
+    returns VBK_ERR_INVALID_ARG (1) on any machine, with or without a GPU."""
+    import copy
+    import ctypes
+
+    import workloads
+
+    base = workloads.ci2d_model(4)
+    cases = {}
+    m = copy.deepcopy(base)
+    m["n_states"] = 0
+    cases["no states"] = m
+    m = copy.deepcopy(base)
+    m["modes"][1]["omega"] = 0.0
+    cases["omega 0"] = m
+    m = copy.deepcopy(base)
+    m["modes"][0]["n"] = 0
+    cases["empty basis"] = m
+    m = copy.deepcopy(base)
+    m["terms"][0]["pow"] = [9, 0]
+    cases["power 9"] = m
+    m = copy.deepcopy(base)
+    m["terms"].append({"d": 1, "dp": 0, "coef": 0.1, "pow": [0, 1]})
+    cases["d > dp"] = m
+    m = copy.deepcopy(base)
+    m["terms"][0]["coef"] = float("nan")
+    cases["nan coefficient"] = m
+    m = copy.deepcopy(base)
+    m["channels"][0]["b"] = 0.0
+    cases["b 0"] = m
+    m = copy.deepcopy(base)
+    m["channels"].append(copy.deepcopy(m["channels"][0]))
+    cases["state twice on one wave"] = m
+    m = workloads.gen_ecd_model(3, 3)
+    m["channels"][1]["l"] = 1
+    cases["q-dependent wave with two l"] = m
+    m = workloads.gen_ecd_model(3, 3)
+    m["channels"][0]["terms"][1]["pow"] = [0, 0, 1]
+    cases["coupling power beyond n_modes"] = m
+    for name, desc in cases.items():
+        with pytest.raises(lib.VbkError) as ei:
+            lib.Model(desc)
+        assert ei.value.code == 1, name
+    # a coupling term that names no channel (built directly: the dictionaries cannot express it)
+    d = lib.vbk_model_desc()
+    d.n_states, d.n_modes = 1, 1
+    d.n_basis[0], d.omega[0] = 4, 0.2
+    ch = (lib.vbk_channel * 1)()
+    ch[0].d, ch[0].mu, ch[0].a, ch[0].b, ch[0].l = 0, 0, 0.1, 1.0, 0
+    ct = (lib.vbk_cterm * 1)()
+    ct[0].channel, ct[0].coef = 3, 1.0
+    d.n_terms, d.n_channels, d.channels, d.n_cterms, d.cterms = 0, 1, ch, 1, ct
+    h = ctypes.c_void_p()
+    assert lib._lib.vbk_build_model(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert "no channel" in lib.vbk_last_error()
