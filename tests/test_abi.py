@@ -196,3 +196,27 @@ def test_malformed_models_are_rejected_before_any_device_work(lib):
     h = ctypes.c_void_p()
     assert lib._lib.vbk_build_model(ctypes.byref(d), ctypes.byref(h)) == 1
     assert "no channel" in lib.vbk_last_error()
+
+
+def test_every_workload_model_passes_validation(lib):
+    """Without a GPU the build stops at the device check, after the description checks: every
+    model the workloads define (q-independent and q-dependent couplings, 1 to 4 modes, up to
+    4 states) gets that far, i.e. reports VBK_ERR_NO_DEVICE rather than an invalid argument."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    import workloads
+
+    models = [workloads.ci2d_model(5), workloads.ci2d_model(5, extra_terms=True), workloads.ecd86_model(4, 6),
+              workloads.gen_ecd_model(5, 4), workloads.co2_like_model(basis=(3, 3, 3, 2))]
+    one_mode = {"n_states": 1, "modes": [{"name": "x", "omega": 0.2, "n": 7}], "terms": [],
+                "channels": [{"d": 0, "mu": 0, "a": 0.1, "b": 1.0, "l": 0,
+                              "terms": [{"coef": 1.0, "pow": [0]}, {"coef": 0.3, "pow": [2]}]}]}
+    four_states = workloads.ci2d_model(3)
+    four_states["n_states"] = 4
+    four_states["channels"] += [{"d": 2, "mu": 0, "a": 0.1, "b": 1.0, "l": 0}, {"d": 3, "mu": 1, "a": 0.1, "b": 1.0, "l": 0}]
+    for desc in models + [one_mode, four_states]:
+        with pytest.raises(lib.VbkError) as ei:
+            lib.Model(desc)
+        assert ei.value.code == 6, (desc.get("name"), lib.vbk_last_error())
