@@ -16,7 +16,14 @@ sign, index or factor, a transposed Kronecker product) would fail it:
 * without q-dependent terms the solution is the closed form Phi / diagonal;
 * a model without q_u terms decouples into 1D problems at shifted energies,
   each solved by a separately built dense 1D matrix;
-* the EELS sum integrates to the sum of the cross sections (unit-area Gaussian).
+* the EELS sum integrates to the sum of the cross sections (unit-area Gaussian);
+* one EELS line has its peak at the energy loss E_vf - E_vi, the peak height of a unit-area
+  Gaussian of 10 meV FWHM, and half that height 5 meV either side (a FWHM used as the
+  standard deviation, or a line on the wrong side of the elastic peak, fails);
+* at the energy where the real part of a one-channel diagonal A vanishes, T = -i/pi and the
+  cross section is the s-wave unitarity limit 4 pi / k^2 (in bohr^2, eps_i = k^2 / 2 hartree):
+  this pins the prefactor of the cross section (a slip to pi^2, or eps_i in the wrong unit,
+  fails), and |1 - 2 pi i T| = 1 holds at every energy of that model (elastic unitarity).
 """
 
 import json
@@ -26,6 +33,7 @@ import os
 import numpy as np
 import pytest
 import scipy.integrate as si
+import scipy.optimize as so
 
 from oracle import vibronic as o
 import workloads as w
@@ -233,6 +241,59 @@ def test_eels_integrates_to_sum_of_cross_sections():
     de = np.arange(-0.2, 3.0, 0.0005)
     S = o.eels(m, [1.0, 1.2, 1.5], [0, 0], vf, sig, de)
     np.testing.assert_allclose(S.sum(axis=1) * 0.0005, sig.sum(axis=1), rtol=1e-6)
+
+
+def test_eels_single_line_width_and_position():
+    """Eq. 2Dsp with a Gaussian of 10 meV FWHM: a single line of unit cross section sits at the
+    energy loss E_vf - E_vi, peaks at 2 sqrt(ln 2 / pi) / FWHM (unit area) and falls to half of
+    that 5 meV either side."""
+    m = w.ci2d_model(5)
+    wg = m["modes"][0]["omega"]
+    fwhm = 0.010
+    peak = 2.0 * math.sqrt(math.log(2.0) / math.pi) / fwhm
+    for vf, loss in (([0, 0], 0.0), ([1, 0], wg)):
+        de = np.array([loss - 0.005, loss, loss + 0.005, loss - 0.02])
+        S = o.eels(m, [1.0], [0, 0], [vf], np.ones((1, 1)), de)[0]
+        assert S[1] == pytest.approx(peak, rel=1e-12)
+        assert S[0] == pytest.approx(0.5 * peak, rel=1e-12)
+        assert S[2] == pytest.approx(0.5 * peak, rel=1e-12)
+        assert S[3] == pytest.approx(peak * 2.0 ** (-16), rel=1e-9)  # 2 FWHM away: 2^-(2*2)^2
+
+
+HARTREE_EV = 27.211386245988  # CODATA 2018
+
+
+def _one_channel_model(e_d, a, b, l):
+    """One discrete state, one vibrational function, one partial wave: A is the 1 x 1 matrix
+    E - E_0 - e_d - F(E - E_0)."""
+    return {"n_states": 1, "modes": [{"name": "x", "omega": 0.2, "n": 1}],
+            "terms": [{"d": 0, "dp": 0, "coef": e_d, "pow": [0]}],
+            "channels": [{"d": 0, "mu": 0, "a": a, "b": b, "l": l}]}
+
+
+@pytest.mark.parametrize("e_d,a,b", [(1.0, 0.1, 0.5), (2.45, 0.186, 0.833)])
+def test_cross_section_at_resonance_is_the_unitarity_limit(e_d, a, b):
+    m = _one_channel_model(e_d, a, b, 0)
+    re_a = lambda e: e - e_d - o.level_shift(np.array([e]), a, b, 0)[0].real
+    eps_r = so.brentq(re_a, 0.05, 6.0, xtol=1e-15, rtol=1e-15)
+    E = o.total_energy(m, eps_r, [0])
+    psi = o.solve(m, E, o.phi(m, E, [0], 0))
+    t = o.t_amplitude(m, E, [0], 0, psi)
+    assert abs(t - (-1j / math.pi)) <= 1e-12
+    sig, _ = o.cross_sections(m, [eps_r], [[0]], [[0]])
+    k2 = 2.0 * eps_r / HARTREE_EV          # eps_i = k^2 / 2 in hartree
+    sigma_bohr2 = sig[0, 0, 0] * HARTREE_EV  # the raw value takes eps_i in eV
+    assert sigma_bohr2 == pytest.approx(4.0 * math.pi / k2, rel=1e-12)
+
+
+def test_one_channel_amplitude_is_unitary_at_every_energy():
+    m = _one_channel_model(1.0, 0.1, 0.5, 0)
+    for eps_i in (0.05, 0.4, 0.99, 1.7, 3.5):
+        E = o.total_energy(m, eps_i, [0])
+        t = o.t_amplitude(m, E, [0], 0, o.solve(m, E, o.phi(m, E, [0], 0)))
+        assert abs(1.0 - 2j * math.pi * t) == pytest.approx(1.0, abs=1e-13)
+        sig, _ = o.cross_sections(m, [eps_i], [[0]], [[0]])
+        assert sig[0, 0, 0] * HARTREE_EV <= 4.0 * math.pi / (2.0 * eps_i / HARTREE_EV) * (1 + 1e-12)
 
 
 # ---------------------------------------------------------------------- gradient
