@@ -47,7 +47,7 @@ extern "C" {
 #define VBK_ERR_NO_DEVICE 6     /* no CUDA device is visible                            */
 
 /* Per-system outcome (vbk_stats.status). */
-#define VBK_SYS_CONVERGED 0 /* ||Phi - A psi|| / ||Phi|| <= tol in FP64                        */
+#define VBK_SYS_CONVERGED 0 /* ||Phi - A psi|| / ||Phi|| <= tol (refinement residual, VBK_MIXED) */
 #define VBK_SYS_MAX_ITER 1  /* iteration or refinement cap reached                             */
 #define VBK_SYS_BREAKDOWN 2 /* COCG bilinear form p^T A p or r^T z vanished (Sec. III.A)       */
 #define VBK_SYS_NAN 3       /* a non-finite value appeared                                     */
@@ -113,9 +113,17 @@ typedef struct vbk_model vbk_model;
 
 /* Arithmetic of the Krylov iterations. */
 #define VBK_FP64 0  /* complex FP64 throughout                                                  */
-#define VBK_MIXED 1 /* complex FP32 Krylov iterations inside FP64 iterative refinement: the
-                       residual b - A x, the update of x and the GMRES Hessenberg least-squares
-                       problem stay in FP64                                                      */
+#define VBK_MIXED 1 /* complex FP32 Krylov iterations inside iterative refinement.  The
+                       refinement residual b - A x and the solution x are kept in FP64, except
+                       on the resident path (VBK_COCG with the point preconditioner and
+                       opts.resident = 1, when a system fits one SM's shared memory): there
+                       x, the diagonal of A and the residual are double-float numbers
+                       (unevaluated sums hi + lo of two FP32 values: ~48-bit significands,
+                       FP32 exponent range) formed on the FP32 pipes, and ||r||^2 is summed
+                       in FP32 within a warp and in FP64 across warps (relative error
+                       ~1e-7 of the norm, i.e. of the stopping threshold, not of r).  psi is
+                       returned in FP64 (hi + lo, exact).  The GMRES Hessenberg least-squares
+                       problem is FP64 in every case.                                         */
 
 /* Block-diagonal preconditioner (Sec. III.B), given by the indices its blocks SPAN:
  * bit 0 = the discrete-state index d, bit (1 + m) = mode m.  The paper names preconditioners
@@ -135,7 +143,7 @@ typedef struct {
     int precond_span;  /* see above                                                        */
     int restart;       /* GMRES restart length m (1..256); one restart cycle per refinement */
     int max_iter;      /* cap on Krylov iterations per system, summed over refinements     */
-    int max_refine;    /* cap on FP64 refinement steps per system                          */
+    int max_refine;    /* cap on refinement steps per system                               */
     double tol;        /* stop when ||Phi - A psi||_2 / ||Phi||_2 <= tol (true residual)    */
     double inner_tol;  /* relative tolerance of each inner solve (COCG; GMRES stops a cycle
                           early when its residual estimate reaches it)                      */
@@ -148,7 +156,7 @@ typedef struct {
                           system in one thread block (vectors p, q in shared memory) when
                           2 N * 8 bytes + tables fit; 0: grid-wide kernels                   */
     int inner_max_iter; /* VBK_MIXED COCG: iterations of one FP32 inner solve before it ends
-                          and the FP64 residual restarts it (complex-FP32 COCG can stagnate
+                          and the refinement residual restarts it (complex-FP32 COCG can stagnate
                           short of inner_tol on hard systems); 0 = no cap                    */
 } vbk_opts;
 
@@ -160,8 +168,9 @@ void vbk_default_opts(vbk_opts* o);
 typedef struct {
     int status;          /* VBK_SYS_*                                                    */
     int iterations;      /* Krylov iterations (matrix-vector products in the inner loop) */
-    int refinements;     /* FP64 residual evaluations after the first                    */
-    double rel_residual; /* final ||Phi - A psi|| / ||Phi|| computed in FP64             */
+    int refinements;     /* refinement residual evaluations after the first              */
+    double rel_residual; /* final ||Phi - A psi|| / ||Phi|| of the refinement residual: FP64,
+                            or double-float on the resident VBK_MIXED path (see VBK_MIXED)  */
 } vbk_stats;
 
 /* Builds a model from the description (Sec. II; tables of Sec. III: oscillator matrix
@@ -187,7 +196,7 @@ int vbk_model_size(const vbk_model* model, int* n_unknowns, int* n_partial_waves
  *   stats   : host [n_eps * n_vi * n_mu] in the same order, or NULL.
  * Returns VBK_ERR_NOT_CONVERGED if any system ended with a status other than CONVERGED or
  * ZERO_RHS (psi then holds the last iterate).  With VBK_MIXED COCG, a system whose FP32 inner
- * iterations stop helping (a refinement step lowers the FP64 residual by less than 10%, or a
+ * iterations stop helping (a refinement step lowers the refinement residual by less than 10%, or a
  * non-finite value or a breakdown appears) is solved again in FP64 from psi = 0, and its stats
  * add both runs.  Synchronises `stream`. */
 int vbk_solve(vbk_model* model, int n_eps, const double* eps_i, int n_vi, const int* vi,
@@ -226,7 +235,9 @@ int vbk_eels(vbk_model* model, int n_eps, int n_vi, const int* vi, int n_vf, con
  * the derivatives run through the non-local level shift of Eq. FE (pair transforms
  * F[f_c f_c'] depend on a_c through sqrt(a_c a_c') and on b_c through (b_c + b_c') / 2) and
  * through Phi = f_c P_c |v>.
- *   grad      : host double [n_theta], written.
+ *   grad      : host double [n_theta], written (a host buffer: the ~20 numbers are reduced
+ *               on the device and copied back, since callers use them on the host, e.g. in
+ *               an optimiser or a torch.autograd backward that builds a CPU tensor).
  *   stats     : host [n_eps * n_vi * n_mu] adjoint solve outcomes, or NULL.
  * Synchronises `stream`. */
 int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi, const int* vi,

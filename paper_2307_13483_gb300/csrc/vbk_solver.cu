@@ -130,7 +130,8 @@ __device__ __forceinline__ bool point_coef(const DevEntry& en, const int (&n)[MA
 // FP32 copy for the inner iterations.
 template <int M>
 __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, double2* __restrict__ d64,
-                             float2* __restrict__ d32, float2* __restrict__ dinv32, float4* __restrict__ dsp) {
+                             float2* __restrict__ d32, float2* __restrict__ dinv32, float4* __restrict__ dsp,
+                             int* __restrict__ zpiv) {
     const int e = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;  // grid: elements x energies
     if (i >= md.N) return;
     const long long t = (long long)e * md.N + i;
@@ -167,6 +168,9 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
         if (md.sfd32) md.sfd32[t] = make_float2((float)fr, (float)fi);
     }
     if (d64) d64[t] = make_double2(re, im);
+    // a zero diagonal entry is a zero pivot of the point (Jacobi) preconditioner, in FP64 or in
+    // the FP32 copy the inner iterations use
+    if (zpiv && ((re == 0.0 && im == 0.0) || (d32 && (float)re == 0.f && (float)im == 0.f))) zpiv[e] = 1;
     if (dsp) {  // double-float pair (hi, lo) of the FP64 value for the double-float residual
         const float hr = (float)re, hi = (float)im;
         dsp[t] = make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
@@ -1935,14 +1939,14 @@ __device__ __forceinline__ float2 df_norm(float h, float l) {
 // are (re hi, im hi, re lo, im lo) quadruples, b is FP64 (split where nonzero); the energy-independent stencil
 // coefficients come as (hi, lo) pairs.  Register blocking as in k_matvec3 (S systems x EPT
 // consecutive elements per thread, coefficients loaded once for the S systems); one
-// ||r||^2 partial (of the hi parts, FP32) per thread block and system.
+// ||r||^2 partial (of the hi parts: FP32 within a warp, FP64 across warps) per thread block and system.
 template <int S, int EPT>
 __global__ void __launch_bounds__(TPB) k_residual_df(DevModel md, const int* __restrict__ sys_e, Sel sel, int nlist,
                                                     const float4* __restrict__ dsp, const float4* __restrict__ xs,
                                                     const double2* __restrict__ b64, float4* __restrict__ rs,
                                                     double2* __restrict__ part) {
     __shared__ int offs[MV_MAXPTS];
-    __shared__ float redsh[TPB / 32][S];
+    __shared__ double redsh[TPB / 32][S];
     constexpr int T = TPB * EPT;
     const int Nnu = md.Nnu, N = md.N;
     const int nchunk = (Nnu + T - 1) / T;
@@ -2029,13 +2033,13 @@ __global__ void __launch_bounds__(TPB) k_residual_df(DevModel md, const int* __r
         float v = loc[t];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) redsh[w][t] = v;
+        if (lane == 0) redsh[w][t] = (double)v;  // FP32 within a warp, FP64 across warps
     }
     __syncthreads();
     if (threadIdx.x < S && sy[threadIdx.x] >= 0) {
-        float tot = 0.f;
+        double tot = 0.0;
         for (int q = 0; q < TPB / 32; ++q) tot += redsh[q][threadIdx.x];
-        part[(long long)sy[threadIdx.x] * gridDim.x + blockIdx.x] = make_double2((double)tot, 0.0);
+        part[(long long)sy[threadIdx.x] * gridDim.x + blockIdx.x] = make_double2(tot, 0.0);
     }
 }
 constexpr int DF_S = 2, DF_EPT = 4;
@@ -2314,7 +2318,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_residual_res(DevModel md, const int
     float4* X = reinterpret_cast<float4*>(smraw) + H;
     float2* rows = reinterpret_cast<float2*>(X + N + H);
     __shared__ int4 sdesc[MAXS * 64];
-    __shared__ float red[RTPB / 32];
+    __shared__ double red[RTPB / 32];
     const int s = list[blockIdx.x];
     if (s < 0) return;
     const int tid = threadIdx.x;
@@ -2363,13 +2367,13 @@ __global__ void __launch_bounds__(RTPB, 1) k_residual_res(DevModel md, const int
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
-    if ((tid & 31) == 0) red[tid >> 5] = nrm;
+    if ((tid & 31) == 0) red[tid >> 5] = (double)nrm;  // FP32 within a warp, FP64 across warps
     __syncthreads();
     if (tid < 32) {
-        float t = red[tid];
+        double t = red[tid];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (tid == 0) part[s] = make_double2((double)t, 0.0);
+        if (tid == 0) part[s] = make_double2(t, 0.0);
     }
 }
 inline size_t residual_res_smem(const DevModel& md) {
@@ -3407,7 +3411,8 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         // energy tables (FP64 + inner-precision copy); pair transforms of q-dependent couplings first
         if (sand) rn.go("sandwich_table", k_sand_table, dim3(cdiv_u(md.Nnu, TPB), nE), dim3(TPB), md, nE, (const double*)dE);
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE,
-              dfr ? (double2*)nullptr : diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR, dsp);
+              dfr ? (double2*)nullptr : diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR, dsp,
+              pspan == 0 ? pfail : (int*)nullptr);
         if (block) factor_blocks<R, M>(rn, md, pbuf, nE, (const cx<R>*)diagR, F, pfail);
         if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) {
             fail(vbk_cuda_fail(ce, "set-up kernels"));
@@ -3830,7 +3835,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         rn.flush();
         std::vector<int> hfail(nE, 0);
-        if (block) {
+        if (block || pspan == 0) {  // zero pivots of the block factors or of the point preconditioner
             cudaMemcpy(hfail.data(), pfail, nE * sizeof(int), cudaMemcpyDeviceToHost);
         }
         bool all_ok = true;
@@ -3981,7 +3986,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     } else {
         if (sand) rn.go("sandwich_table", k_sand_table, dim3(cdiv_u(md.Nnu, TPB), nE), dim3(TPB), md, nE, (const double*)dE);
         rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE, d64,
-              mixed ? d32 : (float2*)nullptr, (float2*)nullptr, (float4*)nullptr);
+              mixed ? d32 : (float2*)nullptr, (float2*)nullptr, (float4*)nullptr, (int*)nullptr);
         const dim3 ge(cdiv_u(N, TPB), (unsigned)nsys);
         if (mixed) rn.go("narrow", k_inner_rhs_plain, dim3(cdiv_u(nsys * N, TPB)), dim3(TPB), nsys * N, x, reinterpret_cast<float2*>(xr));
         if (op == 0) {
@@ -4063,6 +4068,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[VBK_NOALLOC_SCR
 namespace {
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
+constexpr int NOALLOC_MAX_VECS = 4096;  // vectors (n_E * n_vec) per call
 void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
 
 // Device address of the scratch array for the current device, looked up once per device with
@@ -4090,11 +4096,17 @@ template <int M>
 int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* x, double2* y, cudaStream_t st) {
     const int N = m->N;
     const long long nsys = (long long)nE * nvec;
+    // the host-side system map below holds at most NOALLOC_MAX_VECS entries
+    if (nsys > NOALLOC_MAX_VECS) {
+        vbk_set_error("noalloc: n_E * n_vec = " + std::to_string(nsys) + " vectors exceed the limit of " +
+                      std::to_string(NOALLOC_MAX_VECS) + " per call; use vbk_matvec or split the batch");
+        return VBK_ERR_INVALID_ARG;
+    }
     // scratch layout: E [nE] | sys_e [nsys] | diag [nE][N]
     const size_t off_se = ((size_t)nE * sizeof(double) + 255) & ~size_t(255);
     const size_t off_dg = (off_se + (size_t)nsys * sizeof(int) + 255) & ~size_t(255);
     const size_t need = off_dg + (size_t)nE * N * sizeof(double2);
-    if (need > VBK_NOALLOC_SCRATCH_BYTES || nsys > 65535) {
+    if (need > VBK_NOALLOC_SCRATCH_BYTES) {
         vbk_set_error("noalloc: n_E * N complex entries (plus energies and the system map) exceed the " +
                       std::to_string(VBK_NOALLOC_SCRATCH_BYTES) + "-byte scratch array (need " + std::to_string(need) +
                       " bytes); use vbk_matvec or fewer energies per call");
@@ -4106,11 +4118,7 @@ int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* 
     double* dE = (double*)sb;
     int* se = (int*)(sb + off_se);
     double2* d64 = (double2*)(sb + off_dg);
-    if (nsys > 4096) {
-        vbk_set_error("noalloc: at most 4096 vectors per call");
-        return VBK_ERR_INVALID_ARG;
-    }
-    int hse[4096];
+    int hse[NOALLOC_MAX_VECS];
     for (long long s = 0; s < nsys; ++s) hse[s] = (int)(s / nvec);
     cudaError_t ce;
     if ((ce = cudaMemcpyAsync(dE, E, nE * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -4118,7 +4126,7 @@ int noalloc_run(vbk_model* m, int nE, const double* E, int nvec, const double2* 
         return vbk_cuda_fail(ce, "noalloc: copies into scratch");
     Runner rn{m, st, false, {}, {}};
     rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), m->dm, nE, (const double*)dE, d64,
-          (float2*)nullptr, (float2*)nullptr, (float4*)nullptr);
+          (float2*)nullptr, (float2*)nullptr, (float4*)nullptr, (int*)nullptr);
     const Sel none{nullptr, nullptr};
     launch_matvec_v<double>(rn, 9, "matvec_fp64", m->dm, (const int*)se, none, (unsigned)nsys, (const double2*)d64, x,
                             (long long)N, y, (long long)N, (const double2*)nullptr, (double2*)nullptr, 0);

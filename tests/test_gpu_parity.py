@@ -291,6 +291,46 @@ def test_edge_cases(vbk):
         vbk.vbk_solve(model, [1.0], [[0, 0]], vbk.vbk_default_opts(inner_max_iter=-1))
 
 
+def _zero_pivot_model():
+    """Two states, binary-fraction parameters, no continuum on state 1: at eps_i = 1 eV from
+    v_i = (0, 0) the diagonal entry of A at (d = 1, nu = (0, 0)) is E - E_nu - E_1 = 0 exactly
+    (E = 1.1875, E_nu = 0.1875, E_1 = 1), a zero pivot of the point preconditioner and of the
+    span-d blocks (lambda q_u couples the states only across n_u, so those blocks are diagonal)."""
+    return {"n_states": 2, "modes": [{"name": "g", "omega": 0.25, "n": 4}, {"name": "u", "omega": 0.125, "n": 4}],
+            "terms": [{"d": 0, "dp": 0, "coef": 1.5, "pow": [0, 0]}, {"d": 1, "dp": 1, "coef": 1.0, "pow": [0, 0]},
+                      {"d": 0, "dp": 1, "coef": 0.1, "pow": [0, 1]}],
+            "channels": [{"d": 0, "mu": 0, "a": 0.1, "b": 0.5, "l": 0}]}
+
+
+@pytest.mark.parametrize("method,precision,span", [("cocg", "mixed", 0), ("cocg", "fp64", 0), ("gmres", "fp64", 0),
+                                                   ("gmres", "mixed", 0), ("cocg", "fp64", 0x1),
+                                                   ("gmres", "mixed", 0x1)])
+def test_zero_pivot_is_reported(vbk, method, precision, span):
+    model = vbk.Model(_zero_pivot_model())
+    opts = vbk.vbk_default_opts(method=method, precision=precision, precond_span=span, tol=1e-10, max_iter=200,
+                                max_refine=5)
+    with pytest.raises(vbk.VbkError) as err:
+        vbk.vbk_solve(model, [1.0], [[0, 0]], opts)
+    assert err.value.code == vbk.VBK_ERR_NOT_CONVERGED
+    _, st = vbk.vbk_solve(model, [1.0], [[0, 0]], opts, check=False)
+    assert [s["status"] for s in st] == ["pivot"]
+    # away from the zero pivot the same model converges
+    _, st = vbk.vbk_solve(model, [1.03], [[0, 0]], opts)
+    assert [s["status"] for s in st] == ["converged"]
+
+
+def test_non_finite_energies_are_rejected(vbk):
+    model = vbk.Model(w.ci2d_model(4))
+    for bad in (float("nan"), float("inf")):
+        with pytest.raises(vbk.VbkError) as err:
+            vbk.vbk_solve(model, [1.0, bad], [[0, 0]])
+        assert err.value.code == 1
+        x = torch.zeros((1, 1, model.N), dtype=torch.complex128, device="cuda")
+        with pytest.raises(vbk.VbkError) as err:
+            vbk.vbk_matvec(model, [bad], x)
+        assert err.value.code == 1
+
+
 @pytest.mark.parametrize("resident", [1, 0])
 def test_inner_solves_capped_and_restarted_still_converge(vbk, resident):
     """Mixed COCG whose FP32 inner solves stop after a quarter of the iterations an uncapped

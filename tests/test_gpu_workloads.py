@@ -147,3 +147,40 @@ def test_adjoint_full_size_matches_finite_differences(vbk):
         lm = loss_and_sig(o.with_parameter(desc, thetas[k], p0 - h))[0]
         fd = (lp - lm) / (2 * h)
         assert abs(g[k] - fd) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(g).max()), (k, g[k], fd)
+
+
+def test_resident_mixed_cocg_at_tol_1e12_near_resonances(vbk):
+    """How far the resident path's double-float refinement carries: FP32 COCG inside double-float
+    residuals (resident = 1) at tol 1e-12 on the 80 x 80 model, at the two energies where the
+    oracle's |psi| / |Phi| peaks on a 0.02 eV scan of 2.3..2.9 eV (one per partial wave: the
+    resonances, where A is closest to singular), near threshold and at 3 eV.  The oracle's
+    complex128 residual of the returned psi must meet the tolerance and sigma must match LU."""
+    desc = w.ci2d_model(80)
+    vi = [[0, 0]]
+    scan = np.arange(2.30, 2.9001, 0.02)
+    amp = np.zeros((scan.size, 2))
+    for k, e in enumerate(scan):
+        E = o.total_energy(desc, e, vi[0])
+        rhs = [o.phi(desc, E, vi[0], mu) for mu in range(2)]
+        ps = o.solve_many(desc, E, rhs)
+        amp[k] = [np.linalg.norm(ps[:, mu]) / np.linalg.norm(rhs[mu]) for mu in range(2)]
+    peaks = sorted({float(scan[np.argmax(amp[:, mu])]) for mu in range(2)})
+    eps = np.array([0.05] + peaks + [3.0])
+    model = vbk.Model(desc)
+    tol = 1e-12
+    opts = vbk.vbk_default_opts(method="cocg", precision="mixed", precond_span=0, tol=tol, resident=1, max_refine=100)
+    psi, stats = vbk.vbk_solve(model, eps, vi, opts)
+    assert all(s["status"] == "converged" for s in stats), [s for s in stats]
+    psi_h = psi.cpu().numpy()
+    vf = o.open_levels(desc, o.total_energy(desc, float(eps[-1]), vi[0]))
+    sig = vbk.vbk_cross_sections(model, eps, vi, psi, vf).cpu().numpy()
+    ref, _ = o.cross_sections(desc, eps, vi, vf)
+    for e, ei in enumerate(eps):
+        E = o.total_energy(desc, ei, vi[0])
+        A = o.a_matrix(desc, E)
+        for mu in range(2):
+            rhs = o.phi(desc, E, vi[0], mu)
+            res = np.linalg.norm(rhs - A @ psi_h[e, 0, mu]) / np.linalg.norm(rhs)
+            assert res <= 1.05 * tol, (ei, mu, res)
+    big = ref > 1e-6 * ref.max()
+    np.testing.assert_allclose(sig[big], ref[big], rtol=1e-8)
