@@ -152,9 +152,13 @@ typedef struct {
                           the Krylov loop then launches kernels directly instead of as graphs */
     int autotune;      /* 1: on the first solve of a model, time the matvec kernel variants on
                           the batch and keep the fastest (per precision) for later calls       */
-    int resident;      /* 1: FP32 COCG with a point preconditioner runs each inner solve of a
-                          system in one thread block (vectors p, q in shared memory) when
-                          2 N * 8 bytes + tables fit; 0: grid-wide kernels                   */
+    int resident;      /* FP32 COCG with the point preconditioner (or none): 1 = the whole
+                          refinement of each system in one cluster of n_states thread blocks
+                          (one block per discrete state, every vector of the FP32 iterations
+                          on chip) when N / n_states * 32 bytes + tables fit one block's shared
+                          memory, else as 2; 2 = each inner solve of a system in one thread
+                          block (p, q in shared memory) when 2 N * 8 bytes + tables fit, the
+                          refinement between launches; 0 = grid-wide kernels                */
     int inner_max_iter; /* VBK_MIXED COCG: iterations of one FP32 inner solve before it ends
                           and the refinement residual restarts it (complex-FP32 COCG can stagnate
                           short of inner_tol on hard systems); 0 = no cap                    */
@@ -257,8 +261,10 @@ int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi
  *   kernel with (systems, elements) per thread (1,4), (2,4), (4,2), (2,2); 4..7 = shared-
  *   memory-windowed kernel with (1,4), (2,4), (4,2), (8,1); 8, 9 = direct kernel with 1 or 4
  *   systems per thread; 10, 11 = one or two systems per thread block with x in shared memory
- *   (VBK_MIXED only).  VBK_ERR_INVALID_ARG if the variant does not fit this model and
- *   precision.  Asynchronous on `stream`. */
+ *   (VBK_MIXED only); 12..15 = every state of a tile per thread block, x windows staged
+ *   asynchronously, coefficients from shared memory, (systems per block, elements per thread)
+ *   = (2,4), (2,2), (4,2), (1,4).  VBK_ERR_INVALID_ARG if the variant does not fit this model
+ *   and precision.  Asynchronous on `stream`. */
 int vbk_matvec(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,
                void* y_dev, int precision, int variant, void* stream);
 
@@ -292,6 +298,12 @@ int vbk_precond_apply(vbk_model* model, int n_E, const double* E, int n_vec, int
  * the launch stream).  Returns the number of entries available. */
 int vbk_kernel_timings(const vbk_model* model, int cap, const char** names, int* launches,
                        double* total_ms);
+
+/* on = 1: each later vbk_matvec / vbk_precond_apply call on this model records per-kernel
+ * CUDA-event timings of its own launches (replacing those of the previous call or solve; read
+ * them with vbk_kernel_timings) and synchronises `stream`; on = 0 (the default) turns it off.
+ * The paper has no counterpart: this serves measurement of the operator kernels alone. */
+int vbk_set_op_timing(vbk_model* model, int on);
 
 /* Matvec kernel variant the autotuner chose for this model in `precision` (VBK_MIXED: the FP32
  * Krylov operator, VBK_FP64: the FP64 residual), or -1 if it has not run yet. */

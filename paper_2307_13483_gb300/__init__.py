@@ -112,7 +112,7 @@ EXPORTED = [
     "vbk_default_opts", "vbk_build_model", "vbk_free_model", "vbk_model_size", "vbk_solve",
     "vbk_cross_sections", "vbk_eels", "vbk_solve_adjoint", "vbk_matvec", "vbk_precond_apply",
     "vbk_kernel_timings", "vbk_last_launch_count", "vbk_level_shift", "vbk_status_str",
-    "vbk_sys_status_str", "vbk_last_error", "vbk_matvec_noalloc", "vbk_matvec_variant",
+    "vbk_sys_status_str", "vbk_last_error", "vbk_matvec_noalloc", "vbk_matvec_variant", "vbk_set_op_timing",
 ]
 
 
@@ -137,6 +137,7 @@ def _load():
         "vbk_kernel_timings": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), ip, dp]),
         "vbk_last_launch_count": (C.c_longlong, [vp]),
         "vbk_matvec_variant": (C.c_int, [vp, C.c_int]),
+        "vbk_set_op_timing": (C.c_int, [vp, C.c_int]),
         "vbk_level_shift": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]),
         "vbk_status_str": (C.c_char_p, [C.c_int]),
         "vbk_sys_status_str": (C.c_char_p, [C.c_int]),
@@ -363,6 +364,12 @@ def vbk_kernel_timings(model: Model):
     ms = (C.c_double * cap)()
     n = _lib.vbk_kernel_timings(model.handle, cap, names, launches, ms)
     return {names[k].decode(): (launches[k], ms[k]) for k in range(min(n, cap))}
+
+
+def vbk_set_op_timing(model: Model, on: bool = True):
+    """Per-kernel CUDA-event timings of later vbk_matvec / vbk_precond_apply calls (see
+    vbk_kernel_timings); those calls then synchronise their stream."""
+    _check(_lib.vbk_set_op_timing(model.handle, 1 if on else 0), "vbk_set_op_timing")
 
 
 def vbk_matvec_variant(model: Model, precision=VBK_MIXED) -> int:

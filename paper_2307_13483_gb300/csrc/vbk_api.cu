@@ -425,7 +425,9 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     // descriptors and primary-mode coefficient rows of the one-block-per-system kernel, the
     // points of each state grouped by primary mode
     std::vector<int4> rdesc;
+    std::vector<int4> wdesc;        // the same points for the windowed matvec: (row offset, lin, col2, m2 | dp << 8)
     std::vector<float2> rct, rctd;  // (-c, -c) and the double-float pair (hi, lo) of +c
+    std::vector<double> rct64;      // -c in FP64
     int rsec = 0;
     int rhalo = 0, rok = 1;
     for (int d = 0; d < m->ns; ++d) {
@@ -456,11 +458,13 @@ int build(const vbk_model_desc* d, vbk_model* m) {
                         c = (nn >= 0 && nn < m->nb[m1]) ? c * m->tab[e.col[m1] + n] : 0.0;
                     }
                     rct.push_back(make_float2((float)-c, (float)-c));
+                    rct64.push_back(-c);
                     const float ch = (float)c;
                     rctd.push_back(make_float2(ch, (float)(c - (double)ch)));
                 }
                 const int poff = (e.dp - d) * m->Nnu + e.lin;
                 rdesc.push_back(make_int4(off * 8, poff * 8, col2, m2));
+                wdesc.push_back(make_int4(off * 8, e.lin, col2, m2 | (e.dp << 8)));
                 if (col2 >= 0) rsec = 1;
                 dm.rcnt[d][mg] += 1;
                 rhalo = std::max(rhalo, std::max(-(d * m->Nnu + poff), (d + 1) * m->Nnu - 1 + poff - (m->N - 1)));
@@ -469,7 +473,9 @@ int build(const vbk_model_desc* d, vbk_model* m) {
     }
     dm.rbeg[m->ns] = (int)rdesc.size();
     if (rdesc.empty()) rdesc.push_back(make_int4(0, 0, -1, 0));
+    if (wdesc.empty()) wdesc.push_back(make_int4(0, 0, -1, 0));
     if (rct.empty()) rct.push_back(make_float2(0.f, 0.f));
+    if (rct64.empty()) rct64.push_back(0.0);
     if (rctd.empty()) rctd.push_back(make_float2(0.f, 0.f));
     dm.rsec = rsec;
     if (rdesc.size() > (size_t)MAXS * 64) rok = 0;
@@ -503,9 +509,11 @@ int build(const vbk_model_desc* d, vbk_model* m) {
                  b4 = al(nt * sizeof(float)), b5 = al(npc * sizeof(double)), b6 = al(npc * sizeof(float)),
                  b7 = al(rdesc.size() * sizeof(int4)), b8 = al(rct.size() * sizeof(float2)),
                  b9 = al(npc * sizeof(float2)), b10 = al(rctd.size() * sizeof(float2)),
-                 b11 = al(enu.size() * sizeof(double)), b12 = al(u0.size() * sizeof(double));
+                 b11 = al(enu.size() * sizeof(double)), b12 = al(u0.size() * sizeof(double)),
+                 b13 = al(wdesc.size() * sizeof(int4)), b14 = al(rct64.size() * sizeof(double));
     char* mem = nullptr;
-    cudaError_t err = cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8 + b9 + b10 + b11 + b12);
+    cudaError_t err =
+        cudaMalloc((void**)&mem, b1 + b2 + b3 + b4 + b5 + b6 + b7 + b8 + b9 + b10 + b11 + b12 + b13 + b14);
     if (err != cudaSuccess) return vbk_cuda_fail(err, "model tables");
     m->dev_mem = mem;
     std::vector<DevEntry> he(ne), hd(nd);
@@ -553,6 +561,13 @@ int build(const vbk_model_desc* d, vbk_model* m) {
             return vbk_cuda_fail(err, "model diagonal upload");
         dm.enu = (const double*)b2base;
         dm.u0 = (const double*)(b2base + b11);
+        char* b3base = b2base + b11 + b12;
+        if ((err = cudaMemcpy(b3base, wdesc.data(), wdesc.size() * sizeof(int4), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(b3base + b13, rct64.data(), rct64.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+            return vbk_cuda_fail(err, "model descriptor upload");
+        dm.wdesc = (const int4*)b3base;
+        dm.rct64 = (const double*)(b3base + b13);
     }
     if (!spc.empty()) {
         const size_t bs = (spc.size() * sizeof(double) + 255) & ~size_t(255);
@@ -1263,6 +1278,7 @@ static int check_opts(const vbk_opts* o) {
     if (o->check_every < 1) return invalid("check_every must be >= 1");
     if (o->precond_span < -1) return invalid("precond_span must be -1 or a span mask");
     if (o->inner_max_iter < 0) return invalid("inner_max_iter must be >= 0");
+    if (o->resident < 0 || o->resident > 2) return invalid("resident must be 0, 1 or 2");
     return VBK_OK;
 }
 
@@ -1622,6 +1638,13 @@ int vbk_precond_apply(vbk_model* m, int n_E, const double* E, int n_vec, int pre
         if (!std::isfinite(E[k])) return invalid("energies must be finite");
     return vbk_operator_run(m, 1, n_E, E, n_vec, precond_span, (const double2*)r_dev, (double2*)z_dev, precision,
                             (cudaStream_t)stream);
+}
+
+int vbk_set_op_timing(vbk_model* m, int on) {
+    g_last_error.clear();
+    if (int rc = check_model(m)) return rc;
+    m->op_timing = on ? 1 : 0;
+    return VBK_OK;
 }
 
 int vbk_kernel_timings(const vbk_model* m, int cap, const char** names, int* launches, double* total_ms) {

@@ -140,6 +140,11 @@ struct DevModel {
     const int4* rdesc;
     const float2* rct;
     const float2* rctd;  // the same rows as double-float pairs (hi, lo) of +coef (q^k)_{n, n + delta}
+    const double* rct64;  // the same rows in FP64, -coef (q^k)_{n, n + delta} (one value per n)
+    // the same points for the windowed matvec (in rdesc order): x = byte offset of the point's
+    // row in rct, y = in-plane offset lin, z = tab32 column of a secondary mode or -1,
+    // w = secondary mode | (neighbour state dp << 8)
+    const int4* wdesc;
     int rsec;            // 1 if some point involves a secondary mode
     int nrct;
     int rbeg[MAXS + 1];
@@ -212,6 +217,7 @@ struct vbk_model {
     int device = 0;
     cudaStream_t cap_stream = nullptr;  // library-owned stream used only to capture CUDA graphs
     int mv_variant[2] = {-1, -1};       // autotuned matvec variant per precision (FP32, FP64); -1: untuned
+    int op_timing = 0;                  // 1: vbk_matvec / vbk_precond_apply record per-kernel timings
     cudaMemPool_t pool = nullptr;       // library-owned stream-ordered pool (keeps its memory between calls)
     void* hpin = nullptr;               // library-owned pinned host staging buffer (grown on demand)
     size_t hpin_bytes = 0;
@@ -428,6 +434,27 @@ struct SysState {
 // Internal per-system status (never returned to callers): a VBK_MIXED refinement step that
 // lowered the FP64 residual by less than 10%; such systems are solved again in FP64.
 #define VBK_SYS_STALLED 6
+
+// Fused mixed-precision solve on thread-block clusters (vbk_cluster.cu): one cluster of n_s CTAs
+// per system runs the whole refinement (FP32 COCG with the point preconditioner or none, the
+// double-float residual, the checks) and writes psi in FP64.
+struct ClArgs {
+    int nsys = 0, pmode = 0, max_refine = 0, max_iter = 0, inner_cap = 0, stall_check = 0;
+    int halo = 0, nrow = 0, npt = 0;  // set by vbk_cluster_plan
+    double tol = 0.0, inner_tol = 0.0;
+    int* counter = nullptr;             // zero before the launch
+    const int* sys_e = nullptr;         // energy index of each system
+    const float2* diag32 = nullptr;     // [energy][N] FP32 diagonal of A
+    const float4* diagdf = nullptr;     // [energy][N] double-float diagonal of A
+    const double2* b64 = nullptr;       // [system][N]
+    const double* bn2 = nullptr;        // ||b||^2 per system, or null
+    float4* xs = nullptr;               // [system][N] double-float solution, zero before the launch
+    double2* psi = nullptr;             // [system][N] FP64 solution (written)
+    SysState* st = nullptr;             // per-system record (written)
+};
+bool vbk_cluster_plan(const DevModel& md, ClArgs* a, size_t* smem);
+int vbk_cluster_prepare(const DevModel& md, const ClArgs& a, size_t smem, int* max_clusters);
+cudaError_t vbk_cluster_launch(const DevModel& md, const ClArgs& a, size_t smem, int nclusters, cudaStream_t st);
 
 // Internal solve over an explicit list of systems with dense FP64 right-hand sides.
 struct SolveJob {

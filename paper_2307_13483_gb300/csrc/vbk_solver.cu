@@ -10,8 +10,10 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "vbk_internal.cuh"
+#include "vbk_device.cuh"
 
 namespace {
 
@@ -55,6 +57,7 @@ __device__ __forceinline__ double2 block_sum2(double2 v, double2* sh) {
     return r;
 }
 
+
 // Systems a launch covers: blockIdx.y indexes `list` (compacted active systems) when given,
 // else the system itself; `act` masks systems that retired after the list was built.
 struct Sel {
@@ -92,17 +95,6 @@ template <class R> __device__ __forceinline__ const R* tabp(const DevModel& md);
 template <> __device__ __forceinline__ const float* tabp<float>(const DevModel& md) { return md.tab32; }
 template <> __device__ __forceinline__ const double* tabp<double>(const DevModel& md) { return md.tab64; }
 
-template <int M> __device__ __forceinline__ void decode(const DevModel& md, int nu, int (&n)[MAXM]) {
-    unsigned rem = (unsigned)nu;
-#pragma unroll
-    for (int m = M - 1; m >= 0; --m) {
-        const unsigned q = fdiv(rem, md.fd_nb[m]);
-        n[m] = (int)(rem - q * (unsigned)md.nb[m]);
-        rem = q;
-    }
-#pragma unroll
-    for (int m = M; m < MAXM; ++m) n[m] = 0;
-}
 
 // Coefficient of one stencil point at oscillator coordinates n; false if the neighbour lies
 // outside the truncated basis (the table holds zero there as well).
@@ -708,6 +700,168 @@ __global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, int W_alloc, 
 }
 
 // ---------------------------------------------------------------- block preconditioner
+
+// Windowed batched matvec with every state of a tile in one CTA.  A CTA owns T = TPB * EPT
+// consecutive vibrational indices nu of all n_s states for S systems: it stages, per system and
+// state, the window [nu0 + lo, nu0 + T + hi) of x that the stencil reaches (lo, hi: smallest and
+// largest in-plane offset of any point) into shared memory with cp.async (zero-filled outside
+// the basis), so every entry of x leaves L2/HBM about (T + hi - lo) / T times and every staged
+// window serves all the states that read it.  Coefficients come from the primary-mode rows of
+// the stencil (rct: -coef (q^k)_{n, n + delta}, energy-independent) held in shared memory, times
+// the oscillator table of a secondary mode where a point has one; nothing is streamed per system
+// but x, y and the diagonal table (read once for the systems of the CTA that share an energy).
+// Same contract as k_matvec2 (y = A x or b - A x, optional partials per system and CTA).
+template <class R> __device__ __forceinline__ const R* wrows(const DevModel& md);
+template <> __device__ __forceinline__ const float* wrows<float>(const DevModel& md) {
+    return reinterpret_cast<const float*>(md.rct);  // packed pairs (-c, -c)
+}
+template <> __device__ __forceinline__ const double* wrows<double>(const DevModel& md) { return md.rct64; }
+
+template <class R> __device__ __forceinline__ void cp_async_cx(unsigned dst, const void* src, bool ok) {
+    const int n = ok ? (int)sizeof(cx<R>) : 0;  // 0 source bytes: the destination is zero-filled
+    if constexpr (sizeof(cx<R>) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+
+// acc += c * v for a real coefficient c (float: the packed pair (c, c) from the row)
+__device__ __forceinline__ float2 wfma(float2 c, float2 v, float2 acc) { return ffma2(c, v, acc); }
+__device__ __forceinline__ double2 wfma(double c, double2 v, double2 acc) {
+    return make_double2(fma(c, v.x, acc.x), fma(c, v.y, acc.y));
+}
+
+template <class R, int S, int EPT, int M>
+__global__ void __launch_bounds__(TPB) k_matvec_win(DevModel md, int lo, int Wst, const int* __restrict__ sys_e, Sel sel,
+                                                   int nlist, const cx<R>* __restrict__ diag, const cx<R>* __restrict__ x,
+                                                   long long xs, cx<R>* __restrict__ y, long long ys,
+                                                   const double2* __restrict__ b, double2* __restrict__ part, int red) {
+    using C = cx<R>;
+    using CR = typename std::conditional<sizeof(R) == 4, float2, double>::type;  // row entry type
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ C redsh[TPB / 32][S];
+    constexpr int T = TPB * EPT;
+    const int Nnu = md.Nnu, N = md.N, ns = md.ns, tid = threadIdx.x;
+    const int nu0 = blockIdx.x * T, base = nu0 + lo;
+    const size_t wbytes = (((size_t)S * ns * Wst * sizeof(C)) + 15) & ~size_t(15);
+    const size_t rbytes = (((size_t)md.nrct * 8) + 15) & ~size_t(15);
+    const CR* rows = reinterpret_cast<const CR*>(smraw + wbytes);
+    int4* sdesc = reinterpret_cast<int4*>(smraw + wbytes + rbytes);
+    int sy[S], se[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const int li = blockIdx.y * S + t;
+        int s = -1;
+        if (li < nlist) {
+            s = sel.list ? sel.list[li] : li;
+            if (s >= 0 && sel.act && !sel.act[s]) s = -1;
+        }
+        sy[t] = s;
+        se[t] = s < 0 ? -1 : sys_e[s];
+    }
+    // stage the windows (asynchronous copies), the coefficient rows and the point descriptors
+    const unsigned wsh = (unsigned)__cvta_generic_to_shared(smraw);
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+        for (int dp = 0; dp < ns; ++dp) {
+            const C* src = x + (long long)(sy[t] < 0 ? 0 : sy[t]) * xs + (long long)dp * Nnu;
+            const unsigned dst = wsh + (unsigned)(((t * ns + dp) * Wst) * sizeof(C));
+            for (int q = tid; q < Wst; q += TPB) {
+                const int g = base + q;
+                const bool ok = sy[t] >= 0 && g >= 0 && g < Nnu;
+                cp_async_cx<R>(dst + (unsigned)(q * sizeof(C)), ok ? (const void*)(src + g) : (const void*)x, ok);
+            }
+        }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    {
+        const CR* grow = reinterpret_cast<const CR*>(wrows<R>(md));
+        CR* srow = const_cast<CR*>(rows);
+        for (int k = tid; k < md.nrct; k += TPB) srow[k] = grow[k];
+        for (int k = tid; k < md.rbeg[ns]; k += TPB) {
+            const int4 w = md.wdesc[k];
+            sdesc[k] = make_int4(w.x, (int)sizeof(C) * ((w.w >> 8) * Wst + w.y), w.z, w.w & 0xff);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const R* tab = tabp<R>(md);
+    const unsigned char* win = smraw;
+    const size_t tstride = (size_t)ns * Wst * sizeof(C);  // bytes between the windows of two systems
+    C loc[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) loc[t] = mkc<R>(0, 0);
+    for (int d = 0; d < ns; ++d) {
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int nu = nu0 + e * TPB + tid;
+            if (nu >= Nnu) break;
+            const int i = d * Nnu + nu;
+            int n[MAXM];
+            decode<M>(md, nu, n);
+            // window slot of nu in the state-0 window of system 0; state dp's slot lies dp * Wst
+            // entries further (the descriptors' byte offsets q.y include dp * Wst + lin)
+            const unsigned char* wc = win + (size_t)(nu - base) * sizeof(C);
+            const size_t dself = (size_t)d * Wst * sizeof(C);
+            C acc[S], xi[S];
+            const C dg0 = se[0] >= 0 ? diag[(long long)se[0] * N + i] : mkc<R>(0, 0);
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                xi[t] = *reinterpret_cast<const C*>(wc + t * tstride + dself);
+                const C dg = (t == 0 || se[t] == se[0]) ? dg0 : diag[(long long)(se[t] < 0 ? 0 : se[t]) * N + i];
+                acc[t] = cmul<R>(dg, xi[t]);
+            }
+            int k = md.rbeg[d];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const int kend = k + md.rcnt[d][m];
+                const unsigned char* row = reinterpret_cast<const unsigned char*>(rows) + (size_t)n[m] * 8;
+#pragma unroll 4
+                for (; k < kend; ++k) {
+                    const int4 q = sdesc[k];
+                    CR c = *reinterpret_cast<const CR*>(row + q.x);
+                    if (q.z >= 0) {  // a second mode's factor (bilinear terms)
+                        const R f = tab[q.z + nsel<M>(n, q.w)];
+                        if constexpr (sizeof(R) == 4) c = make_float2(c.x * f, c.y * f);
+                        else c *= f;
+                    }
+#pragma unroll
+                    for (int t = 0; t < S; ++t)  // neighbours outside the basis read zero-filled slots
+                        acc[t] = wfma(c, *reinterpret_cast<const C*>(wc + t * tstride + q.y), acc[t]);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                if (sy[t] < 0) continue;
+                C out = acc[t];
+                if (b) {
+                    const double2 bb = b[(long long)sy[t] * N + i];
+                    out = mkc<R>((R)bb.x - out.x, (R)bb.y - out.y);
+                }
+                y[(long long)sy[t] * ys + i] = out;
+                if (red == 1) loc[t] = cfma<R>(xi[t], out, loc[t]);
+                else if (red == 2) {
+                    const float ox = (float)out.x, oy = (float)out.y;  // norm for the stopping test: FP32 suffices
+                    loc[t].x += (R)(ox * ox + oy * oy);
+                }
+            }
+        }
+    }
+    if (red) {
+        const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            const C v = warp_sum_c<R>(loc[t]);
+            if (lane == 0) redsh[w][t] = v;
+        }
+        __syncthreads();
+        if (tid < S && sy[tid] >= 0) {
+            C tot = mkc<R>(0, 0);
+            for (int q = 0; q < TPB / 32; ++q) tot = cadd<R>(tot, redsh[q][tid]);
+            part[(long long)sy[tid] * gridDim.x + blockIdx.x] = cvt_to_d<R>(tot);
+        }
+    }
+}
+
 struct PlanDev {
     int L, nblk, p, span;
     const int* chain_off;   // [L]   element offset of chain position c (relative)
@@ -1910,30 +2064,6 @@ __global__ void __launch_bounds__(TPB) k_pp(int N, DList L, const SysState* __re
 // (L2-resident for the systems in flight), and the scalars come from block reductions.  No
 // grid-wide synchronisation is needed because the systems are independent; a converged system
 // frees its SM for the next one.  The iteration count is bounded by max_iter.
-// ------------------------------------------------------------------ double-float arithmetic
-// Unevaluated sums hi + lo of two floats (Dekker 1971 products with a fused multiply-add;
-// Knuth's TwoSum): the residual b - A x of the FP32 refinement path is formed with ~48-bit
-// significands on the FP32 pipes, which GB300 runs ~64x faster than its FP64 pipe.
-__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    const float z = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
-}
-// (sh, sl) += (ah + al) (xh + xl), the al xl term (~2^-48 relative) dropped
-__device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al, float xh, float xl) {
-    const float p = __fmul_rn(ah, xh);
-    float e = __fmaf_rn(ah, xh, -p);
-    e = __fmaf_rn(ah, xl, __fmaf_rn(al, xh, e));
-    float sum, t;
-    df_two_sum(sh, p, sum, t);
-    sh = sum;
-    sl = __fadd_rn(sl, __fadd_rn(t, e));
-}
-// renormalised pair (s, l) with s = fl(h + l)
-__device__ __forceinline__ float2 df_norm(float h, float l) {
-    const float sum = __fadd_rn(h, l);
-    return make_float2(sum, __fsub_rn(l, __fsub_rn(sum, h)));
-}
 
 // r = b - A x for the FP32 refinement path in double-float arithmetic.  x, r and the diagonal
 // are (re hi, im hi, re lo, im lo) quadruples, b is FP64 (split where nonzero); the energy-independent stencil
@@ -2045,16 +2175,6 @@ __global__ void __launch_bounds__(TPB) k_residual_df(DevModel md, const int* __r
 constexpr int DF_S = 2, DF_EPT = 4;
 inline int df_partials(const DevModel& md) { return md.ns * ((md.Nnu + TPB * DF_EPT - 1) / (TPB * DF_EPT)); }
 
-// float -> double, exact, by moving the bit fields (integer pipes; GB300's FP64 pipe is the
-// scarce one); zeros, subnormals, infinities and NaNs take the conversion instruction
-__device__ __forceinline__ double f2d_exact(float f) {
-    const unsigned u = __float_as_uint(f), ex = (u >> 23) & 0xffu;
-    if (ex == 0u || ex == 0xffu) return (double)f;
-    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                    ((unsigned long long)(ex + (1023u - 127u)) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
-}
 
 // x64 = hi + lo of the double-float solution (every system); the sum is exact in FP64.  Two
 // entries per thread (independent loads in flight), streamed: neither side is read again here.
@@ -2070,23 +2190,6 @@ __global__ void __launch_bounds__(TPB) k_df_out(long long n, const float4* __res
 
 constexpr int RTPB = 1024;
 
-// a * b + c on both halves of a float pair with one packed FP32x2 instruction
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;"
-        : "=l"(r)
-        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
-          "l"(*reinterpret_cast<unsigned long long*>(&c)));
-    return *reinterpret_cast<float2*>(&r);
-}
-
-// n[m] for a runtime mode index m without dynamic register indexing
-template <int M> __device__ __forceinline__ int nsel(const int (&n)[MAXM], int m) {
-    int r = n[0];
-#pragma unroll
-    for (int k = 1; k < M; ++k) r = (m == k) ? n[k] : r;
-    return r;
-}
 
 // SEC: some stencil point involves a second mode (its factor from the oscillator tables); the
 // instantiation without it drops that test from the point loop.
@@ -2815,6 +2918,24 @@ struct Runner {
             pend.push_back(pd);
         }
     }
+    // a launch made by `launch()` (returning its cudaError_t), timed like the others
+    template <class F> void go_custom(const char* name, F launch) {
+        Pend pd{0, nullptr, nullptr};
+        if (timing) {
+            pd.id = id(name);
+            pd.a = ev();
+            pd.b = ev();
+            cudaEventRecord(pd.a, st);
+        }
+        const cudaError_t ce = launch();
+        m->launches += 1;
+        if (ce != cudaSuccess) note_error(ce, name);
+        if (timing) {
+            cudaEventRecord(pd.b, st);
+            m->timers[pd.id].launches += 1;
+            pend.push_back(pd);
+        }
+    }
     cudaError_t first_error = cudaSuccess;
     void note_error(cudaError_t e, const char* where) {
         if (first_error == cudaSuccess) {
@@ -2991,14 +3112,33 @@ inline int block_partials(const DevPlanBuf& pb) {
 //   4..7  windowed k_matvec_tiled with (S, EPT) = (1, 4), (2, 4), (4, 2), (8, 1)
 //   8..9  direct k_matvec2 with S = 1, 4
 //   10..11 one / two systems per CTA with x in shared memory (k_matvec_sys, FP32)
-constexpr int MV_NVAR = 12;
+//   12..15 every state of a tile per CTA, windows staged by cp.async, coefficients from rows in
+//          shared memory (k_matvec_win) with (S, EPT) = (2, 4), (2, 2), (4, 2), (1, 4)
+constexpr int MV_NVAR = 16;
 inline int mv_ept(int v) {
-    static const int e[MV_NVAR] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1, 1, 1};
+    static const int e[MV_NVAR] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1, 1, 1, 4, 2, 2, 4};
     return e[v];
 }
 inline int mv_sys(int v) {
-    static const int sv[MV_NVAR] = {1, 2, 4, 2, 1, 2, 4, 8, 1, 4, 1, 2};
+    static const int sv[MV_NVAR] = {1, 2, 4, 2, 1, 2, 4, 8, 1, 4, 1, 2, 2, 2, 4, 1};
     return sv[v];
+}
+// window geometry of k_matvec_win: smallest in-plane offset and window length per state
+inline void mv_win_geom(const DevModel& md, int v, int* lo, int* wst) {
+    int l = 0, h = 0;
+    for (int d = 0; d < md.ns; ++d) {
+        l = std::min(l, md.lmin[d]);
+        h = std::max(h, md.lmax[d]);
+    }
+    *lo = l;
+    *wst = TPB * mv_ept(v) + h - l;
+}
+inline long long mv_win_smem(const DevModel& md, int v, size_t c) {
+    int lo, wst;
+    mv_win_geom(md, v, &lo, &wst);
+    const long long wb = ((long long)mv_sys(v) * md.ns * wst * (long long)c + 15) & ~15LL;
+    const long long rb = ((long long)md.nrct * 8 + 15) & ~15LL;
+    return wb + rb + (long long)md.rbeg[md.ns] * 16;
 }
 inline int mv_window(const DevModel& md, int v) {
     int lr = 0;
@@ -3014,12 +3154,14 @@ inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
 }
 inline bool mv_valid(const DevModel& md, int v, size_t c) {
     if (md.nsc) return v == 8;  // sandwich channels: k_sand_w + k_matvec_sw, launched in place of variant 8
+    if (v >= 12) return md.rok && mv_win_smem(md, v, c) <= 110 * 1024;
     if (v >= 10) return c == 8 && md.rok && matvec_sys_smem(md, v - 9) <= 220 * 1024;
     if (c == 16 && (mv_sys(v) * mv_ept(v) > 8 || v == 7)) return false;  // FP64: register budget
     return mv_tiled_smem(md, v, c) >= 0;
 }
 inline int matvec_partials_v(const DevModel& md, int v) {
     if (md.nsc) v = 8;
+    if (v >= 12) return (md.Nnu + TPB * mv_ept(v) - 1) / (TPB * mv_ept(v));  // one CTA per tile of all states
     if (v >= 10) return 1;
     const int T = TPB * mv_ept(v);
     return md.ns * ((md.Nnu + T - 1) / T);
@@ -3057,6 +3199,31 @@ void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, co
     const int S = mv_sys(v);
     const dim3 g((unsigned)matvec_partials_v(md, v), (nlist + S - 1) / S);
     const size_t smem = (v >= 4 && v < 8) ? (size_t)mv_tiled_smem(md, v, sizeof(cx<T>)) : 0;
+    if (v >= 12) {
+        int lo, wst;
+        mv_win_geom(md, v, &lo, &wst);
+        const size_t sm = (size_t)mv_win_smem(md, v, sizeof(cx<T>));
+        auto go = [&](auto kern) { rn.go_smem(name, kern, g, dim3(TPB), sm, md, lo, wst, sys_e, sel, (int)nlist, diag, x, xs, y, ys, b, part, red); };
+        switch (v * 4 + md.M - 1) {
+            case 48: go(k_matvec_win<T, 2, 4, 1>); break;
+            case 49: go(k_matvec_win<T, 2, 4, 2>); break;
+            case 50: go(k_matvec_win<T, 2, 4, 3>); break;
+            case 51: go(k_matvec_win<T, 2, 4, 4>); break;
+            case 52: go(k_matvec_win<T, 2, 2, 1>); break;
+            case 53: go(k_matvec_win<T, 2, 2, 2>); break;
+            case 54: go(k_matvec_win<T, 2, 2, 3>); break;
+            case 55: go(k_matvec_win<T, 2, 2, 4>); break;
+            case 56: go(k_matvec_win<T, 4, 2, 1>); break;
+            case 57: go(k_matvec_win<T, 4, 2, 2>); break;
+            case 58: go(k_matvec_win<T, 4, 2, 3>); break;
+            case 59: go(k_matvec_win<T, 4, 2, 4>); break;
+            case 60: go(k_matvec_win<T, 1, 4, 1>); break;
+            case 61: go(k_matvec_win<T, 1, 4, 2>); break;
+            case 62: go(k_matvec_win<T, 1, 4, 3>); break;
+            default: go(k_matvec_win<T, 1, 4, 4>); break;
+        }
+        return;
+    }
     if (v >= 10) {
         if constexpr (sizeof(T) == 4) {
             const int Sv = v - 9;
@@ -3102,10 +3269,29 @@ cudaError_t tiled_optin(const DevModel& md, int need) {
         default: return cudaFuncSetAttribute(k_matvec_tiled<T, S, EPT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
     }
 }
+template <class T, int S, int EPT>
+cudaError_t win_optin(const DevModel& md, int need) {
+    switch (md.M) {
+        case 1: return cudaFuncSetAttribute(k_matvec_win<T, S, EPT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        case 2: return cudaFuncSetAttribute(k_matvec_win<T, S, EPT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        case 3: return cudaFuncSetAttribute(k_matvec_win<T, S, EPT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        default: return cudaFuncSetAttribute(k_matvec_win<T, S, EPT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+    }
+}
 template <class T> int prepare_matvec(const DevModel& md) {
     const int need[4] = {mv_tiled_smem(md, 4, sizeof(cx<T>)), mv_tiled_smem(md, 5, sizeof(cx<T>)),
                          mv_tiled_smem(md, 6, sizeof(cx<T>)), mv_tiled_smem(md, 7, sizeof(cx<T>))};
     cudaError_t ce = cudaSuccess;
+    for (int v = 12; v < 16 && ce == cudaSuccess; ++v) {
+        if (!mv_valid(md, v, sizeof(cx<T>))) continue;
+        const int sm = (int)mv_win_smem(md, v, sizeof(cx<T>));
+        switch (v) {
+            case 12: ce = win_optin<T, 2, 4>(md, sm); break;
+            case 13: ce = win_optin<T, 2, 2>(md, sm); break;
+            case 14: ce = win_optin<T, 4, 2>(md, sm); break;
+            default: ce = win_optin<T, 1, 4>(md, sm); break;
+        }
+    }
     if (need[0] > 0) ce = tiled_optin<T, 1, 4>(md, need[0]);
     if (need[1] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 2, 4>(md, need[1]);
     if (need[2] > 0 && ce == cudaSuccess) ce = tiled_optin<T, 4, 2>(md, need[2]);
@@ -3258,6 +3444,16 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     // the double-float residual with one CTA per system when the split solution fits shared memory
     const bool dfr_res = dfr && prepare_residual_res<M>(md);
     const bool spec = dfr_res && o.timing == 0;  // refinement rounds enqueued ahead of the host check
+    // resident = 1: the whole refinement of every system in one launch of thread-block clusters
+    // (one cluster of n_s CTAs per system, vbk_cluster.cu) when the model fits it
+    ClArgs cla;
+    size_t cl_smem = 0;
+    int cl_n = 0;
+    bool cluster = resident && o.resident == 1 && vbk_cluster_plan(md, &cla, &cl_smem);
+    if (cluster && (vbk_cluster_prepare(md, cla, cl_smem, &cl_n) != VBK_OK || cl_n < 1)) {
+        cudaGetLastError();
+        cluster = false;
+    }
 
     // ---- workspace
     const size_t NN = (size_t)N;
@@ -3438,7 +3634,35 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         };
         const int nb_rz = block ? nb_b : nb_e;
 
-        for (int it = 0; it <= o.max_refine + 1; ++it) {
+        if (cluster) {
+            cla.nsys = nsys;
+            cla.pmode = pmode;
+            cla.max_refine = o.max_refine;
+            cla.max_iter = o.max_iter;
+            cla.inner_cap = o.inner_max_iter;
+            cla.stall_check = 1;
+            cla.tol = o.tol;
+            cla.inner_tol = o.inner_tol;
+            cla.counter = cnt;
+            cla.sys_e = sys_e;
+            cla.diag32 = reinterpret_cast<const float2*>(diagR);
+            cla.diagdf = dsp;
+            cla.b64 = job.b64;
+            cla.bn2 = job.bnorm2;
+            cla.xs = xs;
+            cla.psi = job.x64;
+            cla.st = sst;
+            if (cudaMemsetAsync(cnt, 0, sizeof(int), st) != cudaSuccess) {
+                fail(vbk_cuda_fail(cudaGetLastError(), "cluster solve set-up"));
+                break;
+            }
+            rn.go_custom("solve_cluster", [&] { return vbk_cluster_launch(md, cla, cl_smem, std::min(cl_n, nsys), st); });
+            if (rn.first_error != cudaSuccess) {
+                fail(VBK_ERR_CUDA);
+                break;
+            }
+        }
+        for (int it = 0; !cluster && it <= o.max_refine + 1; ++it) {
             // FP64 residual r = b - A x
             const Sel so{olist, outer};
             // the first residual is b itself (x = 0): only its norm is computed, and the first
@@ -3824,7 +4048,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             }
         }
         if (rc) break;
-        if (dfr)
+        if (dfr && !cluster)
             rn.go("df_out", k_df_out, dim3(cdiv_u((long long)nsys * N, 2 * TPB)), dim3(TPB), (long long)nsys * N, (const float4*)xs,
                   job.x64);
         // results
@@ -3977,7 +4201,7 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     std::vector<int> hse(nsys);
     for (long long s = 0; s < nsys; ++s) hse[s] = (int)(s / nvec);
     int rc = VBK_OK;
-    Runner rn{m, st, false, {}, {}};
+    Runner rn{m, st, m->op_timing != 0, {}, {}};
     const Sel none{nullptr, nullptr};
     if (cudaMemcpyAsync(se, hse.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(dE, E, nE * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -4018,6 +4242,10 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
             }
         }
     }
+    if (rn.timing) {  // per-kernel timings of this call (vbk_set_op_timing)
+        if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = vbk_cuda_fail(cudaGetLastError(), "operator timing");
+        rn.flush();
+    }
     cudaFreeAsync(base, st);
     if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
     return rc;
@@ -4047,6 +4275,10 @@ int vbk_solve_job(vbk_model* m, const SolveJob& job, const vbk_opts& o, vbk_stat
 
 int vbk_operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int span, const double2* x, double2* y,
                      int precision, cudaStream_t st, int variant) {
+    if (m->op_timing) {
+        m->timers.clear();
+        m->launches = 0;
+    }
     if (precision == VBK_MIXED) return operator_dispatch<float>(m, op, nE, E, nvec, span, x, y, st, variant);
     return operator_dispatch<double>(m, op, nE, E, nvec, span, x, y, st, variant);
 }

@@ -56,7 +56,7 @@ MODELS = {
 
 @pytest.mark.parametrize("name", list(MODELS))
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("variant", list(range(12)))
+@pytest.mark.parametrize("variant", list(range(16)))
 def test_matvec_parity(vbk, name, precision, variant):
     """Every matvec kernel variant (direct / shared-memory-windowed, 1..8 systems per thread)."""
     desc = MODELS[name]()
@@ -137,6 +137,34 @@ SOLVERS = [
     ("cocg", "mixed", 0x5),
     ("cocg", "fp64", 0x1),
 ]
+
+
+@pytest.mark.parametrize("name", ["ci2d_x", "ecd86", "co2_small", "one_mode", "frozen_mode"])
+@pytest.mark.parametrize("span,resident", [(0, 1), (-1, 1), (0, 2)])
+def test_resident_paths_on_every_model_shape(vbk, name, span, resident):
+    """The fused cluster solve (resident = 1: one cluster of n_s thread blocks per system, 1 to 3
+    states, 1 to 4 modes, bilinear points with a second mode, a frozen mode) and the one-block
+    inner solves (resident = 2), Jacobi or no preconditioner: true residuals by the oracle."""
+    desc = MODELS[name]()
+    model = vbk.Model(desc)
+    eps = np.array([0.3, 1.1, 2.4, 3.3])
+    vi = [[0] * len(desc["modes"])]
+    opts = vbk.vbk_default_opts(method="cocg", precision="mixed", precond_span=span, tol=1e-10, resident=resident,
+                                max_iter=40000, max_refine=400)
+    psi, stats = vbk.vbk_solve(model, eps, vi, opts)
+    psi = psi.cpu().numpy()
+    for e, ei in enumerate(eps):
+        E = o.total_energy(desc, ei, vi[0])
+        A = o.a_matrix(desc, E)
+        for mu in range(model.n_mu):
+            st = stats[e * model.n_mu + mu]
+            rhs = o.phi(desc, E, vi[0], mu)
+            if not np.any(rhs):
+                assert st["status"] == "zero_rhs"
+                continue
+            assert st["status"] == "converged", (e, mu, st)
+            res = np.linalg.norm(rhs - A @ psi[e, 0, mu]) / np.linalg.norm(rhs)
+            assert res <= 1e-10 * 1.05, (e, mu, res, st)
 
 
 @pytest.mark.parametrize("method,precision,span", SOLVERS)
@@ -292,10 +320,12 @@ def test_edge_cases(vbk):
 
 
 def _zero_pivot_model():
-    """Two states, binary-fraction parameters, no continuum on state 1: at eps_i = 1 eV from
-    v_i = (0, 0) the diagonal entry of A at (d = 1, nu = (0, 0)) is E - E_nu - E_1 = 0 exactly
-    (E = 1.1875, E_nu = 0.1875, E_1 = 1), a zero pivot of the point preconditioner and of the
-    span-d blocks (lambda q_u couples the states only across n_u, so those blocks are diagonal)."""
+    """Two states, binary-fraction parameters, no continuum on state 1: at eps_i = 1.125 eV from
+    v_i = (0, 0) the diagonal entry of A at (d = 1, nu = (0, 1)) is E - E_nu - E_1 = 0 exactly
+    (E = 1.3125, E_nu = 0.3125, E_1 = 1), a zero pivot of the point preconditioner and of the
+    span-d blocks (lambda q_u couples the states only across n_u, so those blocks are diagonal).
+    The entry lies in the symmetry sector of Phi ((0, even n_u) with (1, odd n_u)), so the
+    Krylov iterates reach it."""
     return {"n_states": 2, "modes": [{"name": "g", "omega": 0.25, "n": 4}, {"name": "u", "omega": 0.125, "n": 4}],
             "terms": [{"d": 0, "dp": 0, "coef": 1.5, "pow": [0, 0]}, {"d": 1, "dp": 1, "coef": 1.0, "pow": [0, 0]},
                       {"d": 0, "dp": 1, "coef": 0.1, "pow": [0, 1]}],
@@ -310,12 +340,12 @@ def test_zero_pivot_is_reported(vbk, method, precision, span):
     opts = vbk.vbk_default_opts(method=method, precision=precision, precond_span=span, tol=1e-10, max_iter=200,
                                 max_refine=5)
     with pytest.raises(vbk.VbkError) as err:
-        vbk.vbk_solve(model, [1.0], [[0, 0]], opts)
+        vbk.vbk_solve(model, [1.125], [[0, 0]], opts)
     assert err.value.code == vbk.VBK_ERR_NOT_CONVERGED
-    _, st = vbk.vbk_solve(model, [1.0], [[0, 0]], opts, check=False)
+    _, st = vbk.vbk_solve(model, [1.125], [[0, 0]], opts, check=False)
     assert [s["status"] for s in st] == ["pivot"]
     # away from the zero pivot the same model converges
-    _, st = vbk.vbk_solve(model, [1.03], [[0, 0]], opts)
+    _, st = vbk.vbk_solve(model, [1.16], [[0, 0]], opts)
     assert [s["status"] for s in st] == ["converged"]
 
 
@@ -331,7 +361,7 @@ def test_non_finite_energies_are_rejected(vbk):
         assert err.value.code == 1
 
 
-@pytest.mark.parametrize("resident", [1, 0])
+@pytest.mark.parametrize("resident", [1, 2, 0])
 def test_inner_solves_capped_and_restarted_still_converge(vbk, resident):
     """Mixed COCG whose FP32 inner solves stop after a quarter of the iterations an uncapped
     inner solve takes: each FP64 residual restarts the inner solve (the cure for FP32
@@ -372,7 +402,7 @@ def test_uneven_batch_with_several_initial_states(vbk):
                 assert res <= 1e-9 * 1.05
 
 
-@pytest.mark.parametrize("span,resident", [(0, 1), (0, 0), (0x5, 1)])
+@pytest.mark.parametrize("span,resident", [(0, 1), (0, 2), (0, 0), (0x5, 1)])
 def test_full_size_batched_sampled(vbk, span, resident):
     """The 80 x 80 basis (N = 12,800) over 256 energies in (0, 3] eV, in the launch configurations
     of the benchmark (Jacobi: one thread block per system, or grid-wide kernels; M^g): every
