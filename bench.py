@@ -118,7 +118,7 @@ def kernel_bytes_per_unit(name, N, nmu, c, p_band):
         return (2 * c + (p_band + 1) * c / nmu) * N  # r in, z out, L D L^T factor shared by the waves
     if name == "point_precond":
         return (2 * c + c / nmu) * N
-    if name == "cocg_resident":
+    if name in ("cocg_resident", "solve_cluster"):
         # one COCG iteration (matvec x in / y out, updates of x, r, p, q, z: (2 + 7) c N) plus the
         # diagonal and reciprocal tables shared by the n_mu waves; p and q stay in shared memory
         # and x, r in L2 across iterations, so DRAM traffic is far below this algorithmic figure
@@ -181,26 +181,49 @@ def job_rate(t_step_ms, units_per_rank, world, dist=None, device="cpu"):
 
 
 # ------------------------------------------------------------------------------ oracle
-_ORACLE_DESC = None
+_ORACLE_DESC = {}
 
 
 def _oracle_init():
-    """Worker set-up: one BLAS/OpenMP thread per process (the energies are the parallel axis) and
-    the workload's model description built once."""
-    global _ORACLE_DESC
+    """Worker set-up: one BLAS/OpenMP thread per process (the energies are the parallel axis)."""
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[k] = "1"
-    _ORACLE_DESC = workload()[0]
+
+
+def _oracle_model(name):
+    """The workload's model description, built once per worker process."""
+    import workloads as w
+
+    if name not in _ORACLE_DESC:
+        _ORACLE_DESC[name] = w.WORKLOADS[name]["model"]()
+    return _ORACLE_DESC[name]
 
 
 def _oracle_energy(args):
-    """One incident energy of the workload: A(E) by the oracle, sparse LU, both partial waves."""
+    """One (incident energy, initial level) of a workload: A(E) by the oracle, sparse LU, every
+    partial wave."""
     from oracle import vibronic as o
 
-    eps_i, vi = args
-    desc = _ORACLE_DESC
+    eps_i, vi, name = args if len(args) == 3 else (*args, "ci2d_batched")
+    desc = _oracle_model(name)
     E = o.total_energy(desc, float(eps_i), vi)
     o.solve_many(desc, E, [o.phi(desc, E, vi, mu) for mu in range(o.n_partial_waves(desc))])
+    return 0
+
+
+def _oracle_gradient(args):
+    """Adjoint-workload loss gradient contribution of one incident energy (the oracle's dense-LU
+    adjoint)."""
+    from oracle import vibronic as o
+
+    eps_i, vi, vf, target, thetas = args
+    desc = _oracle_model("ci2d_adjoint")
+    return o.loss_gradient_adjoint(desc, [eps_i], vi, vf, target[None, :], thetas)
+
+
+def _oracle_init_probe(_):
+    from oracle import vibronic  # noqa: F401  (imports numpy / scipy in the worker)
+
     return 0
 
 
@@ -213,18 +236,34 @@ class OraclePool:
         import multiprocessing as mp
 
         self.cores = cores or os.cpu_count() or 1
-        self.ex = cf.ProcessPoolExecutor(max_workers=self.cores, mp_context=mp.get_context("spawn"),
-                                         initializer=_oracle_init)
-        list(self.ex.map(_oracle_energy, [(1.0, [0, 0])] * self.cores))  # start-up outside the timing
+        # one BLAS thread per worker, in the environment the spawned workers start with (before
+        # their numpy import); the parent's own setting is restored
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})
+        try:
+            self.ex = cf.ProcessPoolExecutor(max_workers=self.cores, mp_context=mp.get_context("spawn"),
+                                             initializer=_oracle_init)
+            list(self.ex.map(_oracle_init_probe, range(self.cores)))  # start-up outside the timing
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
 
-    def rate(self, eps, vi, n_sample):
-        """Oracle energies/s on a bounded, evenly spaced sample of the energy grid (all of it when
-        n_sample >= its size)."""
+    def rate(self, eps, vi, n_sample, name="ci2d_batched"):
+        """Oracle (energy, initial level) points/s on a bounded, evenly spaced sample of the energy
+        grid (all of it when n_sample >= its size), for every initial level in vi."""
         idx = np.linspace(0, eps.size - 1, min(n_sample, eps.size)).round().astype(int)
+        tasks = [(float(eps[k]), list(v), name) for k in idx for v in vi]
         t0 = time.perf_counter()
-        list(self.ex.map(_oracle_energy, [(float(eps[k]), list(vi[0])) for k in idx]))
+        list(self.ex.map(_oracle_energy, tasks))
         dt = time.perf_counter() - t0
-        return idx.size / dt, dt, idx.size
+        return len(tasks) / dt, dt, len(tasks)
+
+    def map(self, fn, tasks):
+        return list(self.ex.map(fn, tasks))
 
     def close(self):
         self.ex.shutdown()
@@ -258,6 +297,184 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------- the other configurations
+def _timed(fn, reps=1):
+    """Device time of fn() (CUDA events on the current stream), best of reps, after one warm-up."""
+    import torch
+
+    out = fn()
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        out = fn()
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return best, out
+
+
+def _top_kernels(vbk, model, k=5):
+    t = vbk.vbk_kernel_timings(model)
+    tot = sum(v[1] for v in t.values()) or 1.0
+    return {nm: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 3)}
+            for nm, v in sorted(t.items(), key=lambda kv: -kv[1][1])[:k]}
+
+
+SPAN_STATES_BEND = 0x1 | 0x4 | 0x8  # d, bend x, bend y of the CO2-like model
+
+
+def config_extras(vbk, pool, peaks):
+    """Configurations 1, 3, 4 and 5 of the workload list, each timed on the GPU (CUDA events) with
+    its dominant kernels (a run with per-kernel timing) and the oracle timed beside it."""
+    import torch
+    import scipy.linalg as sla
+    import workloads as w
+    from oracle import vibronic as o
+
+    out = {}
+    peak = (peaks or {}).get("hbm_gbs") or 6800.0
+    # ---- 1: one energy, 40 x 40 (N = 3200), FP64 GMRES(64) + Jacobi to 1e-10
+    spec = w.WORKLOADS["ci2d_single"]
+    desc, eps, vi = spec["model"](), spec["eps"], spec["vi"]
+    m = vbk.Model(desc)
+    o1 = vbk.vbk_default_opts(method="gmres", precision="fp64", precond_span=0, tol=1e-10, restart=64, max_refine=400)
+    ms, (_, st) = _timed(lambda: vbk.vbk_solve(m, eps, vi, o1), reps=5)
+    vbk.vbk_solve(m, eps, vi, vbk.vbk_default_opts(method="gmres", precision="fp64", precond_span=0, tol=1e-10,
+                                                   restart=64, max_refine=400, timing=1))
+    E = o.total_energy(desc, float(eps[0]), vi[0])
+    A = o.a_matrix(desc, E).toarray()
+    rhs = np.stack([o.phi(desc, E, vi[0], mu) for mu in range(o.n_partial_waves(desc))], axis=1)
+    t0 = time.perf_counter()
+    sla.lu_solve(sla.lu_factor(A), rhs)
+    t_lu = time.perf_counter() - t0
+    out["config1_single_energy"] = {
+        "value": 1.0 / (ms * 1e-3), "unit": UNIT, "ms_per_solve": round(ms, 3),
+        "workload": "2 states x 40 x 40 (N=3200), eps_i = 1 eV, v_i = 0, both waves; FP64 GMRES(64) + Jacobi, tol 1e-10",
+        "converged": all(x["status"] == "converged" for x in st), "iterations": [int(x) for x in st.iterations],
+        "kernel_ms": _top_kernels(vbk, m),
+        "bound": "latency: one system whose vectors (51 KB) stay in L2; every Arnoldi step is a chain of dependent "
+                 "launches",
+        "cpu_baseline": {"value": 1.0 / t_lu, "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(),
+                         "blas_threads": "library default", "sample": f"dense LU of A (3200 x 3200), {t_lu:.2f} s"}}
+    m.close()
+    # ---- 4: uneven batch, 80 x 80, 128 eps_i on (0, 4] x the 4 lowest levels x 2 waves = 1024
+    # systems, mixed COCG to 1e-8, then cross sections and the 1 meV EELS spectrum
+    spec = w.WORKLOADS["ci2d_uneven"]
+    desc, eps = spec["model"](), spec["eps"]
+    vi = w.lowest_levels(desc, 4)
+    m = vbk.Model(desc)
+    o4 = vbk.vbk_default_opts(method="cocg", precision="mixed", precond_span=0, tol=1e-8)
+    vf = w.lowest_levels(desc, 24)
+    de = np.arange(0.0, 4.0, 0.001)
+    psi4 = torch.empty((eps.size, len(vi), m.n_mu, m.N), dtype=torch.complex128, device="cuda")
+
+    def step4():
+        p, st_ = vbk.vbk_solve(m, eps, vi, o4, psi=psi4)
+        sg = vbk.vbk_cross_sections(m, eps, vi, p, vf)
+        return vbk.vbk_eels(m, vi, vf, sg, de), st_
+
+    ms, (_, st) = _timed(step4, reps=3)
+    vbk.vbk_solve(m, eps, vi, vbk.vbk_default_opts(method="cocg", precision="mixed", precond_span=0, tol=1e-8, timing=1),
+                  psi=psi4)
+    rate, dt, nd = pool.rate(eps, vi, 16, "ci2d_uneven")
+    out["config4_uneven_batch"] = {
+        "value": eps.size * len(vi) / (ms * 1e-3), "unit": UNIT, "ms_per_step": round(ms, 3),
+        "workload": "2 x 80 x 80 (N=12800), 128 eps_i on (0,4] eV x 4 lowest levels x 2 waves = 1024 systems, mixed "
+                    "COCG tol 1e-8, then cross sections to 24 final levels and the EELS spectrum on a 1 meV grid",
+        "converged": all(x["status"] == "converged" for x in st),
+        "iterations": {"min": int(st.iterations.min()), "max": int(st.iterations.max())},
+        "kernel_ms": _top_kernels(vbk, m),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "kind": "oracle", "cores": pool.cores, "blas_threads": 1,
+                         "sample": f"{nd} (eps_i, v_i) points (16 energies x 4 levels), sparse LU, {dt:.1f} s"}}
+    m.close()
+    del psi4
+    # ---- 5: adjoint gradient, 40 x 40 with the extra couplings, 256 eps_i, 10 final levels, 19 parameters
+    spec = w.WORKLOADS["ci2d_adjoint"]
+    desc, eps, vi = spec["model"](), spec["eps"], spec["vi"]
+    vf = w.lowest_levels(desc, 10)
+    nt = len(desc["terms"])
+    thetas = list(range(nt)) + list(range(nt, nt + 2 * len(desc["channels"])))
+    target = np.random.default_rng(2307134831).uniform(0.0, 1.0, (eps.size, len(vf)))
+    tgt = torch.tensor(target[:, None, :], device="cuda")
+    m = vbk.Model(desc)
+    o5 = vbk.vbk_default_opts(method="cocg", precision="mixed", tol=1e-10, max_refine=100)
+
+    def step5():
+        p, _ = vbk.vbk_solve(m, eps, vi, o5)
+        sg = vbk.vbk_cross_sections(m, eps, vi, p, vf)
+        g, st_ = vbk.vbk_solve_adjoint(m, eps, vi, p, vf, 2.0 * (sg - tgt), thetas, o5)
+        return g, st_
+
+    ms, (g5, st) = _timed(step5, reps=3)
+    sample = np.linspace(0, eps.size - 1, 16).round().astype(int)
+    t0 = time.perf_counter()
+    pool.map(_oracle_gradient, [(float(eps[k]), vi[0], vf, target[k], thetas) for k in sample])
+    dt = time.perf_counter() - t0
+    out["config5_adjoint"] = {
+        "value": eps.size / (ms * 1e-3), "unit": UNIT, "ms_per_gradient": round(ms, 3),
+        "workload": "2 x 40 x 40 with cubic / bilinear couplings (N=3200), 256 eps_i on (0,3] eV, 10 final levels, "
+                    "L = sum (sigma - target)^2, gradient in 19 parameters: forward solves, cross sections, adjoint "
+                    "solves and contractions (mixed COCG, tol 1e-10)",
+        "adjoint_converged": all(x["status"] in ("converged", "zero_rhs") for x in st), "n_theta": len(thetas),
+        "cpu_baseline": {"value": sample.size / dt, "unit": UNIT, "kind": "oracle", "cores": pool.cores,
+                         "blas_threads": 1,
+                         "sample": f"{sample.size} energies, dense-LU adjoint gradient per energy, {dt:.1f} s"}}
+    m.close()
+    # ---- 3: CO2-like, 3 states x 30 x 20 x 20 x 12 (N = 432,000), eps_i = 3 eV, three waves,
+    # states x bend blocks: FP64 COCG, and mixed GMRES(256) (FP32 Arnoldi inside FP64 refinement)
+    spec = w.WORKLOADS["co2_like"]
+    desc, eps, vi = spec["model"](), spec["eps"], spec["vi"]
+    m = vbk.Model(desc)
+    res3 = {}
+    for key, kw in (("fp64_cocg", dict(method="cocg", precision="fp64")),
+                    ("mixed_gmres256", dict(method="gmres", precision="mixed", restart=256))):
+        oc = vbk.vbk_default_opts(precond_span=SPAN_STATES_BEND, tol=1e-8, max_iter=20000, max_refine=100, **kw)
+        ms, (_, st) = _timed(lambda: vbk.vbk_solve(m, eps, vi, oc, check=False), reps=1)
+        res3[key] = {"seconds": round(ms * 1e-3, 3), "converged": all(x["status"] == "converged" for x in st),
+                     "iterations": [int(x) for x in st.iterations],
+                     "rel_residual_max": float(st.rel_residual.max())}
+    ot = vbk.vbk_default_opts(method="cocg", precision="fp64", precond_span=SPAN_STATES_BEND, tol=1e-8, max_iter=20000,
+                              max_refine=100, timing=1)
+    _, stt = vbk.vbk_solve(m, eps, vi, ot, check=False)
+    kt = vbk.vbk_kernel_timings(m)
+    iters = int(stt.iterations.max())
+    la = kt.get("block_apply_wide")
+    roof3 = None
+    if la and la[0] > 0:
+        # level-blocked L D L^T apply: r in, z out per system, the factor levels once per energy
+        # (shared by the 3 waves): 5 S x S blocks per level, K = L / S levels per block
+        nb, L_blk, p_half = 30 * 12, 3 * 20 * 20, 120
+        S_lv = 4 * ((p_half + 7) // 8)
+        K = (L_blk + S_lv - 1) // S_lv
+        factor_bytes = nb * K * 5 * S_lv * S_lv * 16
+        per_launch = 3 * 2 * 16 * m.N + factor_bytes
+        ach = per_launch * la[0] / (la[1] * 1e-3) / 1e9
+        roof3 = {"kernel": "block_apply_wide", "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                 "frac": round(ach / peak, 4), "bytes_per_launch": int(per_launch), "launches": la[0],
+                 "avg_launch_us": round(la[1] * 1e3 / la[0], 1)}
+    # the oracle on a reduced basis (sparse LU at 12 x 8 x 8 x 6, N = 13,824)
+    rdesc = w.co2_like_model(basis=(12, 8, 8, 6))
+    E = o.total_energy(rdesc, 3.0, [0, 0, 0, 0])
+    t0 = time.perf_counter()
+    o.solve_many(rdesc, E, [o.phi(rdesc, E, [0, 0, 0, 0], mu) for mu in range(3)])
+    t_red = time.perf_counter() - t0
+    best = min(res3.values(), key=lambda r: r["seconds"])
+    out["config3_co2_like"] = {
+        "value": 1.0 / best["seconds"], "unit": UNIT,
+        "workload": "CO2-like: 3 states x 30 x 20 x 20 x 12 (N=432,000), eps_i = 3 eV, v_i = 0, 3 waves, blocks over "
+                    "states x 2D bend (1200 unknowns, half bandwidth 120), tol 1e-8",
+        "solves": res3, "per_iteration_ms": round(sum(v[1] for v in kt.values()) / max(1, iters), 3),
+        "kernel_ms": _top_kernels(vbk, m, 8), "roofline": roof3,
+        "cpu_baseline": {"value": 1.0 / t_red, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"reduced basis 12 x 8 x 8 x 6 (N=13,824), sparse LU, 3 waves, {t_red:.1f} s "
+                                   "(the full 4D LU does not fit the host)"}}
+    m.close()
+    return out
+
+
 # ------------------------------------------------------------------------------- ours
 def main():
     ap = argparse.ArgumentParser()
@@ -270,6 +487,7 @@ def main():
     ap.add_argument("--restart", type=int, default=64)
     ap.add_argument("--inner-tol", type=float, default=1e-5)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparisons and the CPU baseline")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workload configurations")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -471,6 +689,8 @@ def main():
         # CPU oracle over all host cores on the whole energy grid of the workload
         pool = OraclePool()
         rate, dt, n_done = pool.rate(eps, vi, eps.size)
+        if not args.no_configs:
+            extras["configs"] = config_extras(vbk, pool, load_json("MEASURED_PEAKS.json"))
         pool.close()
         extras["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": pool.cores, "blas_threads": 1, "kind": "oracle",
                                   "sample": f"{n_done} of 256 energies, sparse LU per energy (both waves), one energy per "

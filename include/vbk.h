@@ -55,14 +55,23 @@ extern "C" {
 #define VBK_SYS_ZERO_RHS 5  /* Phi = 0 (closed incident channel); psi = 0 is returned          */
 
 /* One polynomial term of the direct vibronic coupling U (Sec. II.A, Eq. H_d; Eq. U):
- * coef * prod_m q_m^pow[m] in the block (d, dp) of U.  Only d <= dp is given; a term with
- * d < dp also stands in block (dp, d) (U is real symmetric).  State energies E_d are terms
- * with all powers zero.  q_m is the dimensionless normal coordinate with
- * <n|q|n+1> = sqrt((n+1)/2) (Sec. III); powers are products of the truncated matrices. */
+ * coef * T in the block (d, dp) of U with T = prod_m O_m, where O_m = q_m^pow[m], or, for a
+ * mode with raise[m] or lower[m] nonzero (then pow[m] = 0), the ladder monomial
+ * (a_m^+)^raise[m] a_m^lower[m] (normal order).  q_m is the dimensionless normal coordinate with
+ * <n|q|n+1> = sqrt((n+1)/2) (Sec. III), a_m|n> = sqrt(n)|n-1>; powers and monomials are products
+ * of the truncated matrices.  Only d <= dp is given: a term with d < dp adds coef T^T to block
+ * (dp, d), and one with d = dp adds the symmetric part coef (T + T^T)/2 (T itself when every
+ * O_m is a power of q), so U is real symmetric.  State energies E_d are terms with all powers
+ * zero.  Ladder monomials serve a two-dimensional mode written in circular oscillator quanta
+ * n_+-, the polar eigenfunctions |v, l> of the 2D isotropic oscillator with v = n_+ + n_-,
+ * l = n_+ - n_- (Sec. III.C, CO2 model): there q_x +- i q_y = a_-+ + a_+-^+ have real matrix
+ * elements.  raise[m], lower[m], pow[m] are each 0..8. */
 typedef struct {
     int d, dp;
     double coef;
     int pow[VBK_MAX_MODES];
+    int raise[VBK_MAX_MODES];
+    int lower[VBK_MAX_MODES];
 } vbk_term;
 
 /* Coupling of discrete state d to partial wave mu (Sec. II.B): width
@@ -152,13 +161,14 @@ typedef struct {
                           the Krylov loop then launches kernels directly instead of as graphs */
     int autotune;      /* 1: on the first solve of a model, time the matvec kernel variants on
                           the batch and keep the fastest (per precision) for later calls       */
-    int resident;      /* FP32 COCG with the point preconditioner (or none): 1 = the whole
-                          refinement of each system in one cluster of n_states thread blocks
-                          (one block per discrete state, every vector of the FP32 iterations
-                          on chip) when N / n_states * 32 bytes + tables fit one block's shared
-                          memory, else as 2; 2 = each inner solve of a system in one thread
-                          block (p, q in shared memory) when 2 N * 8 bytes + tables fit, the
-                          refinement between launches; 0 = grid-wide kernels                */
+    int resident;      /* FP32 COCG with the point preconditioner (or none), when a system's
+                          p and q (2 N * 8 bytes + tables) fit one thread block's shared memory:
+                          1 = the whole refinement of each system (double-float residual, checks,
+                          inner solves, FP64 output) in one thread block, all systems in one
+                          launch; 2 = each inner solve in one thread block, the refinement steps
+                          between launches; 3 = as 1 but one cluster of n_states thread blocks
+                          per system (one block per discrete state, every FP32 vector on chip;
+                          falls back to 2 where it does not fit); 0 = grid-wide kernels     */
     int inner_max_iter; /* VBK_MIXED COCG: iterations of one FP32 inner solve before it ends
                           and the refinement residual restarts it (complex-FP32 COCG can stagnate
                           short of inner_tol on hard systems); 0 = no cap                    */

@@ -141,21 +141,53 @@ def _kron_all(mats):
     return out
 
 
-def term_matrix(model: dict, pows) -> sp.csr_matrix:
-    """prod_m q_m^(pow_m) on the vibrational product basis (Kronecker product)."""
-    return _kron_all([q_power(m["n"], int(k)) for m, k in zip(model["modes"], pows)])
+def lowering_matrix(n: int) -> np.ndarray:
+    """Truncated annihilation operator of one oscillator: a|k> = sqrt(k)|k-1>."""
+    a = np.zeros((n, n))
+    k = np.arange(1, n)
+    a[k - 1, k] = np.sqrt(k)
+    return a
+
+
+def ladder_matrix(n: int, j: int, k: int) -> np.ndarray:
+    """(a^+)^j a^k as the product of truncated matrices (normal order: a^k acts first)."""
+    a = lowering_matrix(n)
+    return np.linalg.matrix_power(a.T, j) @ np.linalg.matrix_power(a, k)
+
+
+def term_matrix(model: dict, pows, raises=None, lowers=None) -> sp.csr_matrix:
+    """prod_m O_m on the vibrational product basis (Kronecker product), with O_m = q_m^(pow_m), or
+    the ladder monomial (a_m^+)^raise_m a_m^lower_m when the term gives one for mode m."""
+    mats = []
+    for i, (m, k) in enumerate(zip(model["modes"], pows)):
+        j = int(raises[i]) if raises else 0
+        l = int(lowers[i]) if lowers else 0
+        mats.append(ladder_matrix(m["n"], j, l) if (j or l) else q_power(m["n"], int(k)))
+    return _kron_all(mats)
+
+
+def term_operator(model: dict, t: dict) -> sp.csr_matrix:
+    """The operator T of one term of U (coefficient excluded)."""
+    return term_matrix(model, t["pow"], t.get("raise"), t.get("lower"))
 
 
 def coupling_matrix(model: dict) -> sp.csr_matrix:
-    """U (Eq. H_d / Eq. U) as a real symmetric sparse matrix over (d, nu)."""
+    """U (Eq. H_d / Eq. U) as a real symmetric sparse matrix over (d, nu).
+
+    A term adds coef T to block (d, dp) and coef T^T to block (dp, d); on a diagonal block it
+    adds the symmetric part coef (T + T^T) / 2 (T itself for powers of q, which are symmetric).
+    Ladder monomials make T non-symmetric: they serve couplings written in circular (polar)
+    oscillator quanta, where q_x +- i q_y = a_-+ + a_+-^+ have real matrix elements."""
     ns = model["n_states"]
     nv = int(np.prod(basis_shape(model)))
     blocks = [[sp.csr_matrix((nv, nv)) for _ in range(ns)] for _ in range(ns)]
     for t in model["terms"]:
-        m = t["coef"] * term_matrix(model, t["pow"])
-        blocks[t["d"]][t["dp"]] = blocks[t["d"]][t["dp"]] + m
+        m = t["coef"] * term_operator(model, t)
         if t["d"] != t["dp"]:
-            blocks[t["dp"]][t["d"]] = blocks[t["dp"]][t["d"]] + m
+            blocks[t["d"]][t["dp"]] = blocks[t["d"]][t["dp"]] + m
+            blocks[t["dp"]][t["d"]] = blocks[t["dp"]][t["d"]] + m.T
+        else:
+            blocks[t["d"]][t["d"]] = blocks[t["d"]][t["d"]] + 0.5 * (m + m.T)
     return sp.bmat(blocks, format="csr")
 
 

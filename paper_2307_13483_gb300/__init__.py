@@ -29,7 +29,8 @@ SYS_STATUS = {0: "converged", 1: "max_iter", 2: "breakdown", 3: "nan", 4: "pivot
 
 
 class vbk_term(C.Structure):
-    _fields_ = [("d", C.c_int), ("dp", C.c_int), ("coef", C.c_double), ("pow", C.c_int * VBK_MAX_MODES)]
+    _fields_ = [("d", C.c_int), ("dp", C.c_int), ("coef", C.c_double), ("pow", C.c_int * VBK_MAX_MODES),
+                ("raise", C.c_int * VBK_MAX_MODES), ("lower", C.c_int * VBK_MAX_MODES)]
 
 
 class vbk_channel(C.Structure):
@@ -203,6 +204,10 @@ class Model:
             terms[k].d, terms[k].dp, terms[k].coef = int(t["d"]), int(t["dp"]), float(t["coef"])
             for j, pw in enumerate(t["pow"]):
                 terms[k].pow[j] = int(pw)
+            for j, v in enumerate(t.get("raise") or []):
+                getattr(terms[k], "raise")[j] = int(v)  # (a Python keyword as a field name)
+            for j, v in enumerate(t.get("lower") or []):
+                terms[k].lower[j] = int(v)
         chans = (vbk_channel * max(1, len(desc["channels"])))()
         for k, c in enumerate(desc["channels"]):
             chans[k].d, chans[k].mu, chans[k].a, chans[k].b, chans[k].l = (

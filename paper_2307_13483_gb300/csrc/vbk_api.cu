@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 
 #include "vbk_internal.cuh"
@@ -85,9 +86,15 @@ int validate_desc(const vbk_model_desc* d) {
         if (t.d < 0 || t.dp < 0 || t.d >= d->n_states || t.dp >= d->n_states || t.d > t.dp)
             return invalid("term state indices must satisfy 0 <= d <= dp < n_states");
         if (!std::isfinite(t.coef)) return invalid("term coefficient not finite");
-        for (int q = 0; q < VBK_MAX_MODES; ++q)
+        for (int q = 0; q < VBK_MAX_MODES; ++q) {
             if (q < d->n_modes ? (t.pow[q] < 0 || t.pow[q] > 8) : t.pow[q] != 0)
                 return invalid("term power out of range (0..8, zero beyond n_modes)");
+            if (q < d->n_modes ? (t.raise[q] < 0 || t.raise[q] > 8 || t.lower[q] < 0 || t.lower[q] > 8)
+                               : (t.raise[q] != 0 || t.lower[q] != 0))
+                return invalid("ladder powers out of range (0..8, zero beyond n_modes)");
+            if ((t.raise[q] || t.lower[q]) && t.pow[q])
+                return invalid("a mode of a term carries a power of q or a ladder monomial, not both");
+        }
     }
     bool seen[MAXS][VBK_MAX_CHANNELS] = {};
     int cnt[VBK_MAX_CHANNELS] = {0}, q_dep[VBK_MAX_CHANNELS] = {0};
@@ -189,10 +196,13 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         if (!std::isfinite(t.coef)) return invalid("term coefficient not finite");
         for (int k = 0; k < m->M; ++k) {
             if (t.pow[k] < 0 || t.pow[k] > 8) return invalid("term power out of range (0..8)");
+            if (t.raise[k] < 0 || t.raise[k] > 8 || t.lower[k] < 0 || t.lower[k] > 8)
+                return invalid("ladder powers out of range (0..8)");
+            if ((t.raise[k] || t.lower[k]) && t.pow[k]) return invalid("a mode of a term carries a power of q or a ladder monomial, not both");
             kmax[k] = std::max(kmax[k], t.pow[k]);
         }
         for (int k = m->M; k < VBK_MAX_MODES; ++k)
-            if (t.pow[k] != 0) return invalid("power given for a mode beyond n_modes");
+            if (t.pow[k] != 0 || t.raise[k] != 0 || t.lower[k] != 0) return invalid("power given for a mode beyond n_modes");
     }
     // tables: for every mode and power k = 1..kmax[m], columns o = 0..k of length n_m
     m->tab.clear();
@@ -208,11 +218,94 @@ int build(const vbk_model_desc* d, vbk_model* m) {
             }
         }
     }
+    // ladder monomials (a^+)^j a^k of one mode: per (mode, j, k) two columns of length n_m, the
+    // entries a point reads at output level n: T_{n, n + k - j} (the term) and T_{n + j - k, n}
+    // (its transpose), with <c - k + j|T|c> = sqrt(c! / (c - k)!) sqrt((c - k + j)! / (c - k)!)
+    // for c >= k and c - k + j < n_m (products of truncated matrices), zero otherwise
+    std::map<std::tuple<int, int, int>, int> ladder_col;
+    auto ladder_entry = [&](int nm, int j, int k, int c) {  // <c - k + j|T|c>
+        const int r = c - k + j;
+        if (c < k || c >= nm || r < 0 || r >= nm) return 0.0;
+        double v = 1.0;
+        for (int i = 0; i < k; ++i) v *= std::sqrt((double)(c - i));
+        for (int i = 1; i <= j; ++i) v *= std::sqrt((double)(c - k + i));
+        return v;
+    };
+    for (const auto& t : m->terms)
+        for (int mm = 0; mm < m->M; ++mm) {
+            const int j = t.raise[mm], k = t.lower[mm];
+            if (!j && !k) continue;
+            const auto key = std::make_tuple(mm, j, k);
+            if (ladder_col.count(key)) continue;
+            ladder_col[key] = (int)m->tab.size();
+            for (int n = 0; n < m->nb[mm]; ++n) m->tab.push_back(ladder_entry(m->nb[mm], j, k, n + k - j));  // T
+            for (int n = 0; n < m->nb[mm]; ++n) m->tab.push_back(ladder_entry(m->nb[mm], j, k, n));          // T^T
+        }
     if (m->tab.empty()) m->tab.push_back(0.0);
     // stencil points
     std::vector<HostEntry> offd, diagp;
     for (int ti = 0; ti < (int)m->terms.size(); ++ti) {
         const auto& t = m->terms[ti];
+        bool ladder = false;
+        for (int mm = 0; mm < m->M; ++mm) ladder = ladder || t.raise[mm] || t.lower[mm];
+        if (ladder) {
+            // points of T (and of T^T): every combination of the q-power offsets, the single
+            // offset of each ladder monomial
+            int cnt[MAXM], o[MAXM];
+            long long ncomb = 1;
+            for (int k = 0; k < m->M; ++k) {
+                cnt[k] = t.pow[k] + 1;
+                ncomb *= cnt[k];
+            }
+            for (int tr = 0; tr < 2; ++tr)
+                for (long long c = 0; c < ncomb; ++c) {
+                    long long rem = c;
+                    for (int k = m->M - 1; k >= 0; --k) {
+                        o[k] = (int)(rem % cnt[k]);
+                        rem /= cnt[k];
+                    }
+                    DevEntry e{};
+                    e.lin = 0;
+                    bool zero = true;
+                    for (int k = 0; k < MAXM; ++k) {
+                        e.col[k] = -1;
+                        e.delta[k] = 0;
+                    }
+                    for (int k = 0; k < m->M; ++k) {
+                        const int j = t.raise[k], l = t.lower[k];
+                        if (j || l) {
+                            e.delta[k] = tr == 0 ? l - j : j - l;
+                            e.col[k] = ladder_col[std::make_tuple(k, j, l)] + tr * m->nb[k];
+                        } else if (t.pow[k]) {
+                            e.delta[k] = -t.pow[k] + 2 * o[k];
+                            e.col[k] = m->colbase[k][t.pow[k]] + o[k] * m->nb[k];
+                        } else {
+                            continue;
+                        }
+                        e.lin += e.delta[k] * m->stride[k];
+                        if (e.delta[k] != 0) zero = false;
+                    }
+                    HostEntry h{};
+                    h.term = ti;
+                    if (t.d == t.dp) {  // the symmetric part: T / 2 and T^T / 2 on state d
+                        h.d = t.d;
+                        h.mirror = tr;
+                        h.w = 0.5;
+                        e.dp = t.d;
+                        e.coef = 0.5 * t.coef;
+                        h.e = e;
+                        (zero ? diagp : offd).push_back(h);
+                    } else {  // T in block (d, dp), T^T in block (dp, d)
+                        h.d = tr == 0 ? t.d : t.dp;
+                        h.mirror = tr;
+                        e.dp = tr == 0 ? t.dp : t.d;
+                        e.coef = t.coef;
+                        h.e = e;
+                        offd.push_back(h);
+                    }
+                }
+            continue;
+        }
         int cnt[MAXM], o[MAXM];
         long long ncomb = 1;
         for (int k = 0; k < m->M; ++k) {
@@ -1278,7 +1371,7 @@ static int check_opts(const vbk_opts* o) {
     if (o->check_every < 1) return invalid("check_every must be >= 1");
     if (o->precond_span < -1) return invalid("precond_span must be -1 or a span mask");
     if (o->inner_max_iter < 0) return invalid("inner_max_iter must be >= 0");
-    if (o->resident < 0 || o->resident > 2) return invalid("resident must be 0, 1 or 2");
+    if (o->resident < 0 || o->resident > 3) return invalid("resident must be 0, 1, 2 or 3");
     return VBK_OK;
 }
 
@@ -1506,7 +1599,7 @@ int vbk_solve_adjoint(vbk_model* m, int n_eps, const double* eps_i, int n_vi, co
                 for (const auto& he : *lst)
                     if (he.term == id) {
                         DevEntry e = he.e;
-                        e.coef = 1.0;  // derivative of coef * (term matrix)
+                        e.coef = he.w;  // derivative of the point's coefficient in the term's
                         pts.push_back(e);
                         ptd.push_back(he.d);
                     }

@@ -36,15 +36,17 @@ __device__ __forceinline__ unsigned cl_map(unsigned local_addr, unsigned rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
     return r;
 }
+// Loads from another CTA's shared memory.  Volatile keeps them in order with the cluster
+// barriers (also volatile asm); without a memory clobber the compiler still schedules the
+// ordinary shared-memory loads around them.
 __device__ __forceinline__ float2 dsm_f2(unsigned a) {
     float2 v;
-    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
     return v;
 }
 __device__ __forceinline__ float4 dsm_f4(unsigned a) {
     float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
-                 : "memory");
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
     return v;
 }
 __device__ __forceinline__ double dsm_d(unsigned a) {

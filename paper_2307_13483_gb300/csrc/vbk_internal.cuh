@@ -188,6 +188,7 @@ struct HostEntry {
     int term;    // index of the generating term (for gradients)
     int mirror;  // 1 if this point comes from the transposed block of an off-diagonal term
     DevEntry e;
+    double w = 1.0;  // d(point coefficient) / d(term coefficient): 1/2 for the halves of (T + T^T)/2
 };
 
 struct KTimer {

@@ -699,8 +699,6 @@ __global__ void __launch_bounds__(TPB) k_matvec_tiled(DevModel md, int W_alloc, 
     }
 }
 
-// ---------------------------------------------------------------- block preconditioner
-
 // Windowed batched matvec with every state of a tile in one CTA.  A CTA owns T = TPB * EPT
 // consecutive vibrational indices nu of all n_s states for S systems: it stages, per system and
 // state, the window [nu0 + lo, nu0 + T + hi) of x that the stencil reaches (lo, hi: smallest and
@@ -862,6 +860,8 @@ __global__ void __launch_bounds__(TPB) k_matvec_win(DevModel md, int lo, int Wst
     }
 }
 
+
+// ---------------------------------------------------------------- block preconditioner
 struct PlanDev {
     int L, nblk, p, span;
     const int* chain_off;   // [L]   element offset of chain position c (relative)
@@ -2482,6 +2482,377 @@ __global__ void __launch_bounds__(RTPB, 1) k_residual_res(DevModel md, const int
 inline size_t residual_res_smem(const DevModel& md) {
     return (size_t)(md.N + 2 * md.rhalo) * sizeof(float4) + (size_t)md.nrct * sizeof(float2) + 16;
 }
+// Fused mixed-precision solve, one 1024-thread CTA per system and every refinement step in the
+// same launch.  A persistent grid (one CTA per SM: the CTA holds p, q and the coefficient rows in
+// shared memory) takes systems from a counter, highest index first (the higher energies of an
+// ascending grid open more channels and take longer), and for each runs
+//   r = b - A x in double-float arithmetic (x staged in shared memory, b and the diagonal from
+//   global), ||r|| (FP32 within a warp, FP64 across warps), the stopping / stall / cap checks of
+//   the refinement, the FP32 COCG inner solve of the resident kernel on r / ||r||, and
+//   x += ||r|| d in double-float,
+// then writes psi = hi + lo in FP64.  This replaces, for such systems, the host loop of separate
+// residual, check, ordering and output launches.
+template <int M, bool SEC>
+__global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs a, float2* __restrict__ xw,
+                                                           float2* __restrict__ rw, const float2* __restrict__ dinv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int N = md.N, H = md.rhalo, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float2* P = reinterpret_cast<float2*>(smraw) + H;  // p with H zero entries on either side
+    float2* Q = P + N + H;
+    float4* XS = reinterpret_cast<float4*>(smraw) + H;  // the split solution during the residual
+    const size_t rows_off = std::max((size_t)(2 * N + 2 * H) * 8, (size_t)(N + 2 * H) * 16);
+    float2* rows = reinterpret_cast<float2*>(smraw + rows_off);  // rct (FP32 pass) or rctd (residual)
+    __shared__ int4 sdesc[MAXS * 64];
+    __shared__ float redA[RTPB / 32][3], redB[RTPB / 32][3];
+    __shared__ double redD[RTPB / 32];
+    __shared__ int snext;
+    // per-round scalars decided by thread 0 (FP64 arithmetic once per CTA, not per thread):
+    // status (-1: go on), inner scale 1 / ||r|| (FP32), inner threshold^2, the FP64 scale split
+    // into hi + lo floats, the inner iteration cap
+    __shared__ int s_status, s_icap;
+    __shared__ float s_inv, s_target2, s_sh, s_sl;
+    static_assert(RTPB == 1024, "one partial per lane in the final warp sums");
+    for (int k = tid; k < md.rbeg[md.ns]; k += RTPB) sdesc[k] = md.rdesc[k];
+    auto all_sum3 = [&](float (*buf)[3], float a0, float a1, float a2) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            buf[wid][0] = a0;
+            buf[wid][1] = a1;
+            buf[wid][2] = a2;
+        }
+        __syncthreads();
+        float3 t = make_float3(buf[lane][0], buf[lane][1], buf[lane][2]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+            t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+            t.z += __shfl_xor_sync(0xffffffffu, t.z, o);
+        }
+        return t;
+    };
+    // mixed-radix digits (d, n_0 .. n_{M-1}) of this thread's first element and of the stride RTPB
+    int d0, n0[MAXM], inc[MAXM], incd;
+    d0 = (int)fdiv((unsigned)tid, md.fd_nnu);
+    decode<M>(md, tid - d0 * md.Nnu, n0);
+    incd = (int)fdiv((unsigned)RTPB, md.fd_nnu);
+    decode<M>(md, RTPB - incd * md.Nnu, inc);
+    auto advance = [&](int& d, int (&n)[MAXM]) {
+        int c = 0;
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m) {
+            const int v = n[m] + inc[m] + c;
+            c = v >= md.nb[m];
+            n[m] = c ? v - md.nb[m] : v;
+        }
+        d += incd + c;
+    };
+    for (;;) {
+        __syncthreads();  // the previous system's shared data is no longer read
+        if (tid == 0) {
+            const int q = atomicAdd(a.counter, 1);
+            snext = q < a.nsys ? a.nsys - 1 - q : -1;
+        }
+        __syncthreads();
+        const int s = snext;
+        if (s < 0) break;
+        const long long so = (long long)s * N;
+        const int e = a.sys_e[s];
+        const float2* dg = a.diag32 + (long long)e * N;
+        const float2* di = dinv + (long long)e * N;
+        const float4* dgdf = a.diagdf + (long long)e * N;
+        float4* xs = a.xs + so;
+        float2* x = xw + so;
+        float2* r = rw + so;
+        int iters = 0, refines = 0, status = -1;
+        double bnorm = 0.0, rn = 0.0, prev = 0.0;  // meaningful in thread 0
+        float inres = 1.f;
+        for (int k = 0;; ++k) {
+            // ---- r = b - A x in double-float (x = 0 in the first round); its FP32 hi part to r
+            if (k > 0) {
+                for (int i = tid; i < N; i += RTPB) XS[i] = xs[i];
+                for (int i = tid; i < H; i += RTPB) XS[-1 - i] = XS[N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = tid; i < md.nrct; i += RTPB) rows[i] = md.rctd[i];
+                __syncthreads();
+            }
+            float nrm = 0.f;
+            {
+                int d = d0, n[MAXM];
+#pragma unroll
+                for (int m = 0; m < MAXM; ++m) n[m] = n0[m];
+                for (int i = tid; i < N; i += RTPB) {
+                    if (i != tid) advance(d, n);
+                    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+                    const double2 bb = a.b64[so + i];
+                    if ((__double_as_longlong(bb.x) | __double_as_longlong(bb.y)) != 0) {  // b is mostly zero
+                        rh = (float)bb.x;
+                        ih = (float)bb.y;
+                        rl = (float)(bb.x - (double)rh);
+                        il = (float)(bb.y - (double)ih);
+                    }
+                    if (k > 0) {
+                        const float4 xv = XS[i], g = dgdf[i];
+                        df_fma(rh, rl, -g.x, -g.z, xv.x, xv.z);
+                        df_fma(rh, rl, g.y, g.w, xv.y, xv.w);
+                        df_fma(ih, il, -g.x, -g.z, xv.y, xv.w);
+                        df_fma(ih, il, -g.y, -g.w, xv.x, xv.z);
+                        int kk = md.rbeg[d];
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            const int kend = kk + md.rcnt[d][m];
+                            const float2* row = rows + n[m];
+#pragma unroll 4
+                            for (; kk < kend; ++kk) {
+                                const int4 q = sdesc[kk];
+                                float2 c = row[q.x >> 3];
+                                if constexpr (SEC) {
+                                    if (q.z >= 0) {  // a second mode's factor t (FP64 table, split hi + lo)
+                                        const double tv = md.tab64[q.z + nsel<M>(n, q.w)];
+                                        const float th = (float)tv, tl = (float)(tv - (double)th);
+                                        const float ph = c.x * th;
+                                        c = make_float2(ph, fmaf(c.x, th, -ph) + fmaf(c.x, tl, c.y * th));
+                                    }
+                                }
+                                const float4 v = XS[i + (q.y >> 3)];  // neighbours outside [0, N) read the zero halo
+                                df_fma(rh, rl, c.x, c.y, v.x, v.z);
+                                df_fma(ih, il, c.x, c.y, v.y, v.w);
+                            }
+                        }
+                    }
+                    const float2 re = df_norm(rh, rl), im = df_norm(ih, il);
+                    r[i] = make_float2(re.x, im.x);
+                    nrm = fmaf(re.x, re.x, fmaf(im.x, im.x, nrm));
+                }
+            }
+            // ||r||^2: FP32 within a warp, FP64 across warps (warp 0); the refinement checks in
+            // thread 0, the outcome broadcast through shared memory
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+            if (lane == 0) redD[wid] = (double)nrm;
+            __syncthreads();
+            if (wid == 0) {
+                double t = redD[lane];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) {
+                    int st_ = -1;
+                    rn = sqrt(t);
+                    if (k == 0) {
+                        bnorm = a.bn2 ? sqrt(a.bn2[s]) : rn;
+                        if (bnorm == 0.0) {
+                            st_ = VBK_SYS_ZERO_RHS;
+                            rn = 0.0;
+                        }
+                    } else {
+                        refines += 1;
+                    }
+                    if (st_ < 0) {
+                        if (!isfinite(rn)) st_ = VBK_SYS_NAN;
+                        else if (rn <= a.tol * bnorm) st_ = VBK_SYS_CONVERGED;
+                        else if (a.stall_check && k > 0 && !(rn <= 0.9 * prev)) st_ = VBK_SYS_STALLED;  // FP32 inner solve no longer helps
+                        else if (refines >= a.max_refine || iters >= a.max_iter) st_ = VBK_SYS_MAX_ITER;
+                    }
+                    s_status = st_;
+                    if (st_ < 0) {
+                        prev = rn;
+                        s_inv = (float)(1.0 / rn);
+                        const float tg = (float)fmax(a.inner_tol, 0.3 * a.tol * bnorm / rn);
+                        s_target2 = tg * tg;
+                        s_sh = (float)rn;
+                        s_sl = (float)(rn - (double)s_sh);
+                        s_icap = a.inner_cap > 0 ? (int)min((long long)a.max_iter, (long long)iters + a.inner_cap) : a.max_iter;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_status >= 0) {
+                status = s_status;
+                break;
+            }
+            const float inv = s_inv, target2 = s_target2;
+            const int icap = s_icap;
+            // ---- inner FP32 COCG on r / ||r|| (x = 0, z = B^-1 r, p = z, rho = r^T z)
+            for (int i = tid; i < md.nrct; i += RTPB) rows[i] = md.rct[i];
+            for (int i = tid; i < H; i += RTPB) P[-1 - i] = P[N + i] = make_float2(0.f, 0.f);
+            __syncthreads();  // XS (which overlays P) fully read
+            float2 rho, beta = make_float2(0.f, 0.f);
+            {
+                float rz_x = 0.f, rz_y = 0.f;
+                for (int i = tid; i < N; i += RTPB) {
+                    const float2 rv = r[i];
+                    const float2 rn2 = make_float2(rv.x * inv, rv.y * inv);
+                    r[i] = rn2;
+                    const float2 zi = a.pmode == 0 ? cmul<float>(rn2, di[i]) : rn2;
+                    P[i] = zi;
+                    rz_x += rn2.x * zi.x - rn2.y * zi.y;
+                    rz_y += rn2.x * zi.y + rn2.y * zi.x;
+                }
+                const float3 t = all_sum3(redB, 0.f, rz_x, rz_y);
+                rho = make_float2(t.y, t.z);
+            }
+            bool wrote_x = false;
+            float rr = 0.f;
+            const int budget = max(0, icap - iters);
+            for (int it = 0; it < budget; ++it) {
+                float pq_x = 0.f, pq_y = 0.f;
+                int d = d0, n[MAXM];
+#pragma unroll
+                for (int m = 0; m < MAXM; ++m) n[m] = n0[m];
+                // the diagonal of RC consecutive elements of this thread is loaded ahead (L2 latency)
+                constexpr int RC = 4;
+                for (int i0 = tid; i0 < N; i0 += RC * RTPB) {
+                    float2 dgv[RC];
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) {
+                        const int ic = i0 + c * RTPB;
+                        dgv[c] = ic < N ? dg[ic] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) {
+                    const int i = i0 + c * RTPB;
+                    if (i >= N) break;
+                    if (i != tid) advance(d, n);
+                    const float2 pi = P[i];
+                    float2 acc = cmul<float>(dgv[c], pi);
+                    const char* Pi = reinterpret_cast<const char*>(P + i);
+                    int kk = md.rbeg[d];
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int kend = kk + md.rcnt[d][m];
+                        const char* row = reinterpret_cast<const char*>(rows) + n[m] * 8;
+#pragma unroll 4
+                        for (; kk < kend; ++kk) {
+                            const int4 q = sdesc[kk];
+                            float2 cc = *reinterpret_cast<const float2*>(row + q.x);  // (-c, -c)
+                            if constexpr (SEC) {
+                                if (q.z >= 0) {
+                                    const float t = md.tab32[q.z + nsel<M>(n, q.w)];
+                                    cc.x *= t;
+                                    cc.y *= t;
+                                }
+                            }
+                            acc = ffma2(cc, *reinterpret_cast<const float2*>(Pi + q.y), acc);  // zero halo outside
+                        }
+                    }
+                    Q[i] = acc;
+                    pq_x += pi.x * acc.x - pi.y * acc.y;
+                    pq_y += pi.x * acc.y + pi.y * acc.x;
+                    }
+                }
+                const float3 pq = all_sum3(redA, pq_x, pq_y, 0.f);
+                const float den = pq.x * pq.x + pq.y * pq.y;
+                if (!(den > 0.f) || !isfinite(den)) {
+                    status = isfinite(den) ? VBK_SYS_BREAKDOWN : VBK_SYS_NAN;
+                    break;
+                }
+                const float2 al = make_float2((rho.x * pq.x + rho.y * pq.y) / den, (rho.y * pq.x - rho.x * pq.y) / den);
+                float rr_l = 0.f, rz_x = 0.f, rz_y = 0.f;
+                // x, r and 1/diag of UC elements of this thread are loaded ahead (L2 latency)
+                constexpr int UC = 2;
+                for (int i0 = tid; i0 < N; i0 += UC * RTPB) {
+                    float2 xl[UC], rl[UC], dl[UC];
+#pragma unroll
+                    for (int c = 0; c < UC; ++c) {
+                        const int ic = i0 + c * RTPB;
+                        const bool ok = ic < N;
+                        xl[c] = ok && it > 0 ? x[ic] : make_float2(0.f, 0.f);
+                        rl[c] = ok ? r[ic] : make_float2(0.f, 0.f);
+                        dl[c] = ok && a.pmode == 0 ? di[ic] : make_float2(1.f, 0.f);
+                    }
+#pragma unroll
+                    for (int c = 0; c < UC; ++c) {
+                        const int i = i0 + c * RTPB;
+                        if (i >= N) break;
+                        const float2 pi = P[i], qi = Q[i];
+                        float2 xv = xl[c];
+                        xv.x += al.x * pi.x - al.y * pi.y;
+                        xv.y += al.x * pi.y + al.y * pi.x;
+                        x[i] = xv;
+                        float2 rv = rl[c];
+                        rv.x -= al.x * qi.x - al.y * qi.y;
+                        rv.y -= al.x * qi.y + al.y * qi.x;
+                        r[i] = rv;
+                        const float2 zi = a.pmode == 0 ? cmul<float>(rv, dl[c]) : rv;
+                        Q[i] = zi;
+                        rr_l += rv.x * rv.x + rv.y * rv.y;
+                        rz_x += rv.x * zi.x - rv.y * zi.y;
+                        rz_y += rv.x * zi.y + rv.y * zi.x;
+                    }
+                }
+                const float3 sums = all_sum3(redB, rr_l, rz_x, rz_y);
+                wrote_x = true;
+                iters += 1;
+                rr = sums.x;
+                if (!isfinite(sums.x) || !isfinite(sums.y) || !isfinite(sums.z) || sums.x <= target2 || iters >= icap) break;
+                const float rden = rho.x * rho.x + rho.y * rho.y;
+                if (!(sums.y * sums.y + sums.z * sums.z > 0.f) || !(rden > 0.f)) {
+                    status = VBK_SYS_BREAKDOWN;
+                    break;
+                }
+                beta = make_float2((sums.y * rho.x + sums.z * rho.y) / rden, (sums.z * rho.x - sums.y * rho.y) / rden);
+                rho = make_float2(sums.y, sums.z);
+                for (int i = tid; i < N; i += RTPB) {
+                    const float2 pi = P[i], zi = Q[i];
+                    P[i] = make_float2(zi.x + beta.x * pi.x - beta.y * pi.y, zi.y + beta.x * pi.y + beta.y * pi.x);
+                }
+                __syncthreads();
+            }
+            inres = sqrtf(rr);
+            // ---- x += scale d in double-float (each thread its own elements)
+            if (wrote_x) {
+                const float sh = s_sh, sl = s_sl;
+                for (int i = tid; i < N; i += RTPB) {
+                    const float2 dv = x[i];
+                    float4 X = xs[i];
+                    df_fma(X.x, X.z, sh, sl, dv.x, 0.f);
+                    df_fma(X.y, X.w, sh, sl, dv.y, 0.f);
+                    const float2 re = df_norm(X.x, X.z), im = df_norm(X.y, X.w);
+                    xs[i] = make_float4(re.x, im.x, re.y, im.y);
+                }
+            }
+            if (status >= 0) break;
+            __syncthreads();  // P, Q fully read before the next residual stages XS over them
+        }
+        // ---- psi = hi + lo in FP64, and the system's record
+        double2* psi = a.psi + so;
+        for (int i = tid; i < N; i += RTPB) {
+            const float4 v = xs[i];
+            psi[i] = make_double2(f2d_exact(v.x) + f2d_exact(v.z), f2d_exact(v.y) + f2d_exact(v.w));
+        }
+        if (tid == 0) {
+            SysState& S = a.st[s];
+            S.status = status < 0 ? VBK_SYS_MAX_ITER : status;
+            S.iters = iters;
+            S.refines = refines;
+            S.rnorm = rn;
+            S.bnorm = bnorm;
+            S.inres = (double)inres;
+        }
+    }
+}
+inline bool resident_ok(const DevModel& md);
+inline size_t solve_resident_smem(const DevModel& md) {
+    const size_t pq = (size_t)(2 * md.N + 2 * md.rhalo) * 8, xsb = (size_t)(md.N + 2 * md.rhalo) * 16;
+    return std::max(pq, xsb) + (size_t)md.nrct * 8 + 16;
+}
+template <int M> bool prepare_solve_resident(const DevModel& md) {
+    if (!resident_ok(md) || solve_resident_smem(md) > 220 * 1024) return false;
+    const cudaError_t ce =
+        md.rsec ? cudaFuncSetAttribute(k_solve_resident<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)solve_resident_smem(md))
+                : cudaFuncSetAttribute(k_solve_resident<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)solve_resident_smem(md));
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 template <int M> bool prepare_residual_res(const DevModel& md) {
     if (md.rsec || residual_res_smem(md) > 220 * 1024) return false;
     if (cudaFuncSetAttribute(k_residual_res<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)residual_res_smem(md)) !=
@@ -3444,16 +3815,20 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     // the double-float residual with one CTA per system when the split solution fits shared memory
     const bool dfr_res = dfr && prepare_residual_res<M>(md);
     const bool spec = dfr_res && o.timing == 0;  // refinement rounds enqueued ahead of the host check
-    // resident = 1: the whole refinement of every system in one launch of thread-block clusters
-    // (one cluster of n_s CTAs per system, vbk_cluster.cu) when the model fits it
+    // The whole refinement of every system in one launch: resident = 1, one CTA per system
+    // (k_solve_resident); resident = 3, one cluster of n_s CTAs per system (vbk_cluster.cu)
     ClArgs cla;
     size_t cl_smem = 0;
     int cl_n = 0;
-    bool cluster = resident && o.resident == 1 && vbk_cluster_plan(md, &cla, &cl_smem);
-    if (cluster && (vbk_cluster_prepare(md, cla, cl_smem, &cl_n) != VBK_OK || cl_n < 1)) {
-        cudaGetLastError();
-        cluster = false;
+    int fused = 0;
+    if (resident && o.resident == 1 && prepare_solve_resident<M>(md)) fused = 1;
+    if (resident && o.resident == 3 && vbk_cluster_plan(md, &cla, &cl_smem)) {
+        if (vbk_cluster_prepare(md, cla, cl_smem, &cl_n) == VBK_OK && cl_n >= 1)
+            fused = 2;
+        else
+            cudaGetLastError();
     }
+    const bool cluster = fused != 0;
 
     // ---- workspace
     const size_t NN = (size_t)N;
@@ -3656,7 +4031,16 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 fail(vbk_cuda_fail(cudaGetLastError(), "cluster solve set-up"));
                 break;
             }
-            rn.go_custom("solve_cluster", [&] { return vbk_cluster_launch(md, cla, cl_smem, std::min(cl_n, nsys), st); });
+            if (fused == 1) {
+                static int nsm = 0;
+                if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) nsm = 148;
+                const dim3 g((unsigned)std::min(nsys, nsm));
+                auto kern = md.rsec ? k_solve_resident<M, true> : k_solve_resident<M, false>;
+                rn.go_smem("solve_resident", kern, g, dim3(RTPB), solve_resident_smem(md), md, cla,
+                           reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), (const float2*)dinvR);
+            } else {
+                rn.go_custom("solve_cluster", [&] { return vbk_cluster_launch(md, cla, cl_smem, std::min(cl_n, nsys), st); });
+            }
             if (rn.first_error != cudaSuccess) {
                 fail(VBK_ERR_CUDA);
                 break;

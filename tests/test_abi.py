@@ -177,6 +177,12 @@ def test_malformed_models_are_rejected_before_any_device_work(lib):
     m = workloads.gen_ecd_model(3, 3)
     m["channels"][1]["l"] = 1
     cases["q-dependent wave with two l"] = m
+    m = workloads.co2_polar_model(basis=(2, 3, 3, 2))
+    m["terms"].append({"d": 0, "dp": 0, "coef": 0.1, "pow": [0, 1, 0, 0], "raise": [0, 1, 0, 0], "lower": [0, 0, 0, 0]})
+    cases["power of q and ladder monomial on one mode"] = m
+    m = workloads.co2_polar_model(basis=(2, 3, 3, 2))
+    m["terms"].append({"d": 0, "dp": 1, "coef": 0.1, "pow": [0, 0, 0, 0], "raise": [0, 9, 0, 0], "lower": [0, 0, 0, 0]})
+    cases["ladder power 9"] = m
     m = workloads.gen_ecd_model(3, 3)
     m["channels"][0]["terms"][1]["pow"] = [0, 0, 1]
     cases["coupling power beyond n_modes"] = m

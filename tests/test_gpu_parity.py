@@ -140,7 +140,7 @@ SOLVERS = [
 
 
 @pytest.mark.parametrize("name", ["ci2d_x", "ecd86", "co2_small", "one_mode", "frozen_mode"])
-@pytest.mark.parametrize("span,resident", [(0, 1), (-1, 1), (0, 2)])
+@pytest.mark.parametrize("span,resident", [(0, 1), (-1, 1), (0, 2), (0, 3), (-1, 3)])
 def test_resident_paths_on_every_model_shape(vbk, name, span, resident):
     """The fused cluster solve (resident = 1: one cluster of n_s thread blocks per system, 1 to 3
     states, 1 to 4 modes, bilinear points with a second mode, a frozen mode) and the one-block
@@ -361,7 +361,7 @@ def test_non_finite_energies_are_rejected(vbk):
         assert err.value.code == 1
 
 
-@pytest.mark.parametrize("resident", [1, 2, 0])
+@pytest.mark.parametrize("resident", [1, 2, 3, 0])
 def test_inner_solves_capped_and_restarted_still_converge(vbk, resident):
     """Mixed COCG whose FP32 inner solves stop after a quarter of the iterations an uncapped
     inner solve takes: each FP64 residual restarts the inner solve (the cure for FP32
@@ -402,7 +402,7 @@ def test_uneven_batch_with_several_initial_states(vbk):
                 assert res <= 1e-9 * 1.05
 
 
-@pytest.mark.parametrize("span,resident", [(0, 1), (0, 2), (0, 0), (0x5, 1)])
+@pytest.mark.parametrize("span,resident", [(0, 1), (0, 2), (0, 3), (0, 0), (0x5, 1)])
 def test_full_size_batched_sampled(vbk, span, resident):
     """The 80 x 80 basis (N = 12,800) over 256 energies in (0, 3] eV, in the launch configurations
     of the benchmark (Jacobi: one thread block per system, or grid-wide kernels; M^g): every

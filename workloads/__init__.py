@@ -145,6 +145,63 @@ def co2_like_model(basis=(30, 20, 20, 12), seed: int = CO2_SEED) -> dict:
     }
 
 
+def co2_polar_model(basis=(30, 20, 20, 12), seed: int = CO2_SEED) -> dict:
+    """The CO2-like model with its bend in polar form (Sec. III.C, CO2 paragraph: the 2D bend in
+    eigenfunctions of the 2D isotropic oscillator in polar coordinates, couplings up to fourth
+    order).  The bend basis is the product of the circular quanta n_+, n_- (modes 1 and 2, both
+    of frequency omega_b: the polar states with v = n_+ + n_-, l = n_+ - n_-), truncated at
+    n_+-  < basis[1]; the electronic states are Sigma (d=0) and Pi_+, Pi_- (d=1, 2:
+    (Pi_x +- i Pi_y)/sqrt 2), so every coupling has real ladder-operator coefficients.
+
+    Recipe (seeded like ``co2_like_model``, couplings ~ U(-0.2, 0.2) eV): stretch linear and
+    quadratic terms on each state; isotropic bend terms gamma rho^2 with
+    rho^2 = a_+ a_- + a_+^+ a_-^+ + n_+ + n_- + 1; fourth-order isotropic bend terms
+    c1 n_+ n_- + c2 ((a_+ a_-)^2 + h.c.) + c3 (a_+^+2 a_+^2 + a_-^+2 a_-^2) with c ~ U(-0.004, 0.004);
+    the Renner-Teller coupling <Pi_+|H|Pi_-> = c (a_+ + a_-^+)^2; Sigma-Pi couplings
+    <Sigma|H|Pi_+-> = lambda (a_-+ + a_+-^+) / sqrt 2.  All of them conserve K = Lambda + l."""
+    rng = np.random.default_rng(seed + 7)
+    om = [0.172, 0.083, 0.083, 0.291]
+    modes = [{"name": nm, "omega": w, "n": int(n)} for nm, w, n in zip(("s1", "b+", "b-", "s3"), om, basis)]
+    terms = []
+
+    def t(d, dp, c, p=(0, 0, 0, 0), r=(0, 0, 0, 0), lo=(0, 0, 0, 0)):
+        terms.append({"d": d, "dp": dp, "coef": float(c), "pow": list(p), "raise": list(r), "lower": list(lo)})
+
+    def rho2(d, c):
+        t(d, d, 2 * c, lo=(0, 1, 1, 0))          # a_+ a_- + h.c. (a diagonal block keeps the symmetric part)
+        t(d, d, c, r=(0, 1, 0, 0), lo=(0, 1, 0, 0))
+        t(d, d, c, r=(0, 0, 1, 0), lo=(0, 0, 1, 0))
+        t(d, d, c)
+
+    e_sig, e_pi = _u(rng, 1.0, 2.0), _u(rng, 3.0, 4.0)
+    for d in range(3):
+        t(d, d, e_sig if d == 0 else e_pi)
+        t(d, d, _u(rng, -0.2, 0.2), p=(1, 0, 0, 0))
+        t(d, d, max(_u(rng, -0.2, 0.2), -0.4 * om[0]), p=(2, 0, 0, 0))
+        t(d, d, max(_u(rng, -0.2, 0.2), -0.4 * om[3]), p=(0, 0, 0, 2))
+        rho2(d, max(_u(rng, -0.2, 0.2), -0.3 * om[1]))
+        t(d, d, _u(rng, -0.004, 0.004), r=(0, 1, 1, 0), lo=(0, 1, 1, 0))
+        t(d, d, 2 * _u(rng, -0.004, 0.004), lo=(0, 2, 2, 0))
+        c3 = _u(rng, -0.004, 0.004)
+        t(d, d, c3, r=(0, 2, 0, 0), lo=(0, 2, 0, 0))
+        t(d, d, c3, r=(0, 0, 2, 0), lo=(0, 0, 2, 0))
+    c_rt = float(np.clip(_u(rng, -0.2, 0.2), -0.1 * om[1], 0.1 * om[1]))
+    t(1, 2, c_rt, lo=(0, 2, 0, 0))
+    t(1, 2, 2 * c_rt, r=(0, 0, 1, 0), lo=(0, 1, 0, 0))
+    t(1, 2, c_rt, r=(0, 0, 2, 0))
+    lam = _u(rng, -0.2, 0.2) / np.sqrt(2.0)
+    t(0, 1, lam, lo=(0, 0, 1, 0))
+    t(0, 1, lam, r=(0, 1, 0, 0))
+    t(0, 2, lam, lo=(0, 1, 0, 0))
+    t(0, 2, lam, r=(0, 0, 1, 0))
+    a_pi, b_pi = _u(rng, 0.05, 0.2), 1.0 / _u(rng, 1.0, 4.0)
+    channels = [{"d": 0, "mu": 0, "a": _u(rng, 0.05, 0.2), "b": 1.0 / _u(rng, 1.0, 4.0), "l": 0},
+                {"d": 1, "mu": 1, "a": a_pi, "b": b_pi, "l": 1},
+                {"d": 2, "mu": 2, "a": a_pi, "b": b_pi, "l": 1}]
+    return {"name": "co2polar-" + "x".join(str(n) for n in basis), "seed": seed + 7, "n_states": 3, "modes": modes,
+            "terms": terms, "channels": channels}
+
+
 def ecd86_model(n_g: int, n_u: int) -> dict:
     """The ECD86 pseudo-Jahn-Teller model with the parameter values of Table I.
 
@@ -219,6 +276,7 @@ WORKLOADS = {
     "ci2d_single": dict(model=lambda: ci2d_model(40), eps=np.array([1.0]), vi=[[0, 0]]),
     "ci2d_batched": dict(model=lambda: ci2d_model(80), eps=eps_grid(3.0, 256), vi=[[0, 0]]),
     "co2_like": dict(model=lambda: co2_like_model(), eps=np.array([3.0]), vi=[[0, 0, 0, 0]]),
+    "co2_polar": dict(model=lambda: co2_polar_model(), eps=np.array([3.0]), vi=[[0, 0, 0, 0]]),
     "ci2d_uneven": dict(model=lambda: ci2d_model(80), eps=eps_grid(4.0, 128), vi=None),
     "ci2d_adjoint": dict(model=lambda: ci2d_model(40, extra_terms=True), eps=eps_grid(3.0, 256), vi=[[0, 0]]),
 }
