@@ -118,10 +118,11 @@ def kernel_bytes_per_unit(name, N, nmu, c, p_band):
         return (2 * c + (p_band + 1) * c / nmu) * N  # r in, z out, L D L^T factor shared by the waves
     if name == "point_precond":
         return (2 * c + c / nmu) * N
-    if name in ("cocg_resident", "solve_cluster"):
+    if name in ("cocg_resident", "solve_resident", "solve_cluster"):
         # one COCG iteration (matvec x in / y out, updates of x, r, p, q, z: (2 + 7) c N) plus the
         # diagonal and reciprocal tables shared by the n_mu waves; p and q stay in shared memory
-        # and x, r in L2 across iterations, so DRAM traffic is far below this algorithmic figure
+        # and x, r in L2 across iterations, so DRAM traffic is far below this algorithmic figure.
+        # The fused kernels also form the refinement residuals, which this figure leaves out.
         return (9 * c + 2 * c / nmu) * N
     return None
 
@@ -486,6 +487,8 @@ def main():
     ap.add_argument("--precond", type=int, default=0, help="span mask (0 = Jacobi, 0x5 = M^g, -1 = none)")
     ap.add_argument("--restart", type=int, default=64)
     ap.add_argument("--inner-tol", type=float, default=1e-5)
+    ap.add_argument("--resident", type=int, default=1,
+                    help="1: fused one-CTA solve, 2: one-CTA inner solves between host checks, 3: clusters, 0: grid-wide")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 comparisons and the CPU baseline")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workload configurations")
     args = ap.parse_args()
@@ -513,7 +516,7 @@ def main():
     model = vbk.Model(desc)
     N, nmu = model.N, model.n_mu
     opts = vbk.vbk_default_opts(method=args.method, precision="mixed", precond_span=args.precond, tol=1e-8,
-                                restart=args.restart, inner_tol=args.inner_tol, max_refine=100)
+                                restart=args.restart, inner_tol=args.inner_tol, max_refine=100, resident=args.resident)
     psi = torch.empty((eps.size, len(vi), nmu, N), dtype=torch.complex128, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
@@ -553,7 +556,8 @@ def main():
     # per-kernel CUDA-event timings: the same solves once more with an event pair around every
     # launch (direct launches instead of graphs), for the roofline of the dominant kernel
     timing_opts = vbk.vbk_default_opts(method=args.method, precision="mixed", precond_span=args.precond, tol=1e-8,
-                                       restart=args.restart, inner_tol=args.inner_tol, max_refine=100, timing=1)
+                                       restart=args.restart, inner_tol=args.inner_tol, max_refine=100, timing=1,
+                                       resident=args.resident)
     timings = {}
     prof_stats = []
     prof_ms = 0.0
@@ -702,6 +706,7 @@ def main():
             "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 Krylov + double-float (2 x f32) refinement residual and solution; f64 output", "data": "synthetic (seeded model, no dataset)",
             "config": {"workload": WORKLOAD_NAME, "method": args.method, "precond_span": args.precond,
+                       "resident": args.resident,
                        "inner_tol": args.inner_tol, "restart": args.restart,
                        "l2": "256 MB buffer written between timed steps (outside the step events)",
                        "parallelism": f"replicas x{world}"},
