@@ -45,6 +45,15 @@ def workload():
     return spec["model"](), spec["eps"], spec["vi"]
 
 
+def rank_energies(eps_max, n_per_rank, rank, world):
+    """The incident energies rank `rank` of `world` solves: every world-th point, from `rank`, of
+    the grid eps_k = eps_max k / (n_per_rank world), k = 1..n_per_rank world.  Each rank gets
+    n_per_rank distinct energies spread over the whole range (the same mix of easy and hard
+    systems), the ranks together the full grid; at world = 1 it is the workload's own grid."""
+    k = np.arange(1, n_per_rank * world + 1, dtype=np.float64)
+    return (eps_max * k / (n_per_rank * world))[rank::world].copy()
+
+
 REFERENCE_ENERGIES_PER_STEP = 128  # half of the grid, evenly spaced, per reference step
 
 WORKLOAD_NAME = ("ci2d_batched: 2 states x 80 x 80 oscillator functions (N=12800), 256 incident energies "
@@ -513,6 +522,8 @@ def main():
     from oracle import vibronic as o
 
     desc, eps, vi = workload()
+    if world > 1:  # distinct energies per rank (weak scaling: 256 per rank), no data-path collective
+        eps = rank_energies(3.0, eps.size, rank, world)
     model = vbk.Model(desc)
     N, nmu = model.N, model.n_mu
     opts = vbk.vbk_default_opts(method=args.method, precision="mixed", precond_span=args.precond, tol=1e-8,
@@ -709,7 +720,7 @@ def main():
                        "resident": args.resident,
                        "inner_tol": args.inner_tol, "restart": args.restart,
                        "l2": "256 MB buffer written between timed steps (outside the step events)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"energies split over {world} rank(s), 256 each" if world > 1 else "1 GPU"},
             "roofline": roof,
             "matvec_hbm_gbs": matvec_gbs,
             "gpu_launches": launches,

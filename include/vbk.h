@@ -327,6 +327,12 @@ long long vbk_last_launch_count(const vbk_model* model);
  * closed form the device tables use.  Writes Re F and Im F = -Gamma/2.  Needs no GPU. */
 int vbk_level_shift(double eps, double a, double b, int l, double* re, double* im);
 
+/* The same level-shift factor evaluated in double-float arithmetic (unevaluated sums of two
+ * floats, ~2^-47 relative per operation), the way the FP32 refinement path builds its energy
+ * tables on the GPU (GB300 runs FP32 far faster than FP64); host evaluation of the identical
+ * code, for checking it against vbk_level_shift.  Needs no GPU. */
+int vbk_level_shift_df(double eps, double a, double b, int l, double* re, double* im);
+
 /* Human-readable text of a return code (VBK_OK, VBK_ERR_*). */
 const char* vbk_status_str(int code);
 

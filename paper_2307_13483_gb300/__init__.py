@@ -114,6 +114,7 @@ EXPORTED = [
     "vbk_cross_sections", "vbk_eels", "vbk_solve_adjoint", "vbk_matvec", "vbk_precond_apply",
     "vbk_kernel_timings", "vbk_last_launch_count", "vbk_level_shift", "vbk_status_str",
     "vbk_sys_status_str", "vbk_last_error", "vbk_matvec_noalloc", "vbk_matvec_variant", "vbk_set_op_timing",
+    "vbk_level_shift_df",
 ]
 
 
@@ -140,6 +141,7 @@ def _load():
         "vbk_matvec_variant": (C.c_int, [vp, C.c_int]),
         "vbk_set_op_timing": (C.c_int, [vp, C.c_int]),
         "vbk_level_shift": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]),
+        "vbk_level_shift_df": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]),
         "vbk_status_str": (C.c_char_p, [C.c_int]),
         "vbk_sys_status_str": (C.c_char_p, [C.c_int]),
         "vbk_last_error": (C.c_char_p, []),
@@ -388,6 +390,14 @@ def vbk_last_launch_count(model: Model) -> int:
 def vbk_level_shift(eps: float, a: float, b: float, l: int) -> complex:
     re, im = C.c_double(), C.c_double()
     _check(_lib.vbk_level_shift(float(eps), float(a), float(b), int(l), C.byref(re), C.byref(im)), "vbk_level_shift")
+    return complex(re.value, im.value)
+
+
+def vbk_level_shift_df(eps: float, a: float, b: float, l: int) -> complex:
+    """The level shift in double-float arithmetic (the FP32 refinement path's table code), on the host."""
+    re, im = C.c_double(), C.c_double()
+    _check(_lib.vbk_level_shift_df(float(eps), float(a), float(b), int(l), C.byref(re), C.byref(im)),
+           "vbk_level_shift_df")
     return complex(re.value, im.value)
 
 

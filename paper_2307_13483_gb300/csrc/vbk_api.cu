@@ -404,6 +404,11 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         dm.ch_sb[c] = std::sqrt(m->chans[c].b);
         dm.ch_isb[c] = 1.0 / dm.ch_sb[c];
         dm.ch_ib[c] = 1.0 / m->chans[c].b;
+        const double cv[5] = {dm.ch_a[c], dm.ch_b[c], dm.ch_sb[c], dm.ch_isb[c], dm.ch_ib[c]};
+        for (int q = 0; q < 5; ++q) {
+            const dflt v = dd_from(cv[q]);
+            dm.ch_df[c][q] = make_float2(v.h, v.l);
+        }
     }
     for (int k = 0; k < MAXCH; ++k) dm.mu_d[k] = mu_d[k];
     // sandwich channels: points of the coupling polynomials (merged by offset), pair transforms
@@ -543,6 +548,11 @@ int build(const vbk_model_desc* d, vbk_model* m) {
                 }
                 if ((m1 < 0 ? 0 : m1) != mg) continue;
                 if (nmodes > 2) rok = 0;
+                if (rct.size() & 1) {  // rows start on 16 bytes: four consecutive entries load as two float4
+                    rct.push_back(make_float2(0.f, 0.f));
+                    rct64.push_back(0.0);
+                    rctd.push_back(make_float2(0.f, 0.f));
+                }
                 const int off = (int)rct.size();
                 for (int n = 0; n < m->nb[mg]; ++n) {
                     double c = e.coef;
@@ -661,6 +671,29 @@ int build(const vbk_model_desc* d, vbk_model* m) {
             return vbk_cuda_fail(err, "model descriptor upload");
         dm.wdesc = (const int4*)b3base;
         dm.rct64 = (const double*)(b3base + b13);
+    }
+    {  // double-float tables of the energy diagonal: Dawson, erfcx, Taylor, u0 per element
+        std::vector<float2> dws, erx, tay, u0d(m->N);
+        vbk_df_tables(&dws, &erx, &tay);
+        for (int i = 0; i < m->N; ++i) {
+            const dflt v = dd_from(u0[i]);
+            u0d[i] = make_float2(v.h, v.l);
+        }
+        const size_t c1 = al(dws.size() * sizeof(float2)), c2 = al(erx.size() * sizeof(float2)),
+                     c3 = al(tay.size() * sizeof(float2)), c4 = al(u0d.size() * sizeof(float2));
+        char* mem3 = nullptr;
+        if ((err = cudaMalloc((void**)&mem3, c1 + c2 + c3 + c4)) != cudaSuccess) return vbk_cuda_fail(err, "double-float tables");
+        m->dev_mem3 = mem3;
+        if ((err = cudaMemcpy(mem3, dws.data(), dws.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(mem3 + c1, erx.data(), erx.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(mem3 + c1 + c2, tay.data(), tay.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (err = cudaMemcpy(mem3 + c1 + c2 + c3, u0d.data(), u0d.size() * sizeof(float2), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+            return vbk_cuda_fail(err, "double-float table upload");
+        dm.dawson_df = (const float2*)mem3;
+        dm.erfcx_df = (const float2*)(mem3 + c1);
+        dm.taylor_df = (const float2*)(mem3 + c1 + c2);
+        dm.u0df = (const float2*)(mem3 + c1 + c2 + c3);
     }
     if (!spc.empty()) {
         const size_t bs = (spc.size() * sizeof(double) + 255) & ~size_t(255);
@@ -1344,6 +1377,7 @@ void vbk_free_model(vbk_model* m) {
     if (!m) return;
     if (m->dev_mem) cudaFree(m->dev_mem);
     if (m->dev_mem2) cudaFree(m->dev_mem2);
+    if (m->dev_mem3) cudaFree(m->dev_mem3);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     if (m->pool) {
         cudaDeviceSynchronize();  // outstanding frees of this model's calls complete before the pool goes
@@ -1731,6 +1765,28 @@ int vbk_precond_apply(vbk_model* m, int n_E, const double* E, int n_vec, int pre
         if (!std::isfinite(E[k])) return invalid("energies must be finite");
     return vbk_operator_run(m, 1, n_E, E, n_vec, precond_span, (const double2*)r_dev, (double2*)z_dev, precision,
                             (cudaStream_t)stream);
+}
+
+int vbk_level_shift_df(double eps, double a, double b, int l, double* re, double* im) {
+    g_last_error.clear();
+    if (!re || !im) return invalid("level shift: output pointers must be given");
+    if (!std::isfinite(eps) || !(a >= 0.0) || !std::isfinite(a) || !(b > 0.0) || !std::isfinite(b) || l < 0 || l > 20)
+        return invalid("level shift: eps finite, a >= 0, b > 0, 0 <= l <= 20");
+    static std::vector<float2> dws, erx, tay;
+    static std::once_flag once;
+    std::call_once(once, [] { vbk_df_tables(&dws, &erx, &tay); });
+    const DfLevelShift T{dws.data(), erx.data(), tay.data(), VBK_ERFCX_NINT};
+    const double cv[5] = {a, b, std::sqrt(b), 1.0 / std::sqrt(b), 1.0 / b};
+    float2 c[5];
+    for (int q = 0; q < 5; ++q) {
+        const dflt v = dd_from(cv[q]);
+        c[q] = make_float2(v.h, v.l);
+    }
+    dflt fr, fi;
+    dd_level_shift(dd_from(eps), c, l, T, &fr, &fi);
+    *re = dd_to_double(fr);
+    *im = dd_to_double(fi);
+    return VBK_OK;
 }
 
 int vbk_set_op_timing(vbk_model* m, int on) {

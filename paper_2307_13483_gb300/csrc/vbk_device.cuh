@@ -27,6 +27,29 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return *reinterpret_cast<float2*>(&r);
 }
 
+// a + b, a - b, a * b on both halves of a float pair (packed FP32x2, round to nearest)
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&r);
+}
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&r);
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&r);
+}
+
 // n[m] for a runtime mode index m without dynamic register indexing
 template <int M> __device__ __forceinline__ int nsel(const int (&n)[MAXM], int m) {
     int r = n[0];
@@ -53,6 +76,21 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ah, float al,
     df_two_sum(sh, p, sum, t);
     sh = sum;
     sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+// df_fma on both halves of float pairs at once (packed FP32x2): (sh, sl) += (a + al) (x + xl)
+// lane by lane, with na = -a supplied by the caller (the packed instructions take no negated
+// operand).  The same operations in the same order as df_fma, so each lane's result is
+// bit-identical to it: p = fl(a x) is formed as -fl((-a) x), the product error a x - p by one
+// fused multiply-add, and TwoSum(sh, p) is written with -p.
+__device__ __forceinline__ void df_fma2(float2& sh, float2& sl, float2 a, float2 al, float2 na, float2 x, float2 xl) {
+    const float2 pn = fmul2(na, x);                  // -p
+    float2 e = ffma2(a, x, pn);                      // a x - p, exact
+    e = ffma2(a, xl, ffma2(al, x, e));
+    const float2 s = fsub2(sh, pn);                  // fl(sh + p)
+    const float2 z = fsub2(s, sh);
+    const float2 t = fsub2(fsub2(sh, fsub2(s, z)), fadd2(pn, z));  // (sh - (s - z)) + (p - z)
+    sh = s;
+    sl = fadd2(sl, fadd2(t, e));
 }
 // renormalised pair (s, l) with s = fl(h + l)
 __device__ __forceinline__ float2 df_norm(float h, float l) {

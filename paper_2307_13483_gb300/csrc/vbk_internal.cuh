@@ -16,6 +16,7 @@
 
 #include "../../include/vbk.h"
 #include "vbk_erfcx_table.h"
+#include "vbk_dfmath.cuh"
 
 #define MAXM VBK_MAX_MODES
 #define MAXS VBK_MAX_STATES
@@ -151,6 +152,15 @@ struct DevModel {
     int rcnt[MAXS][MAXM];
     int rhalo;   // largest distance a neighbour index falls outside [0, N)
     int rok;     // 1 if no point involves more than two modes and no state more than 64 points
+    // double-float forms for the FP32 refinement path's energy tables (vbk_dfmath.cuh): the
+    // interpolants of Dawson's integral and erfcx, the Taylor coefficients of Dawson's
+    // integral, the delta = 0 part of U_dd per element, and per channel (a, b, sqrt b,
+    // 1 / sqrt b, 1 / b)
+    const float2* dawson_df;
+    const float2* erfcx_df;
+    const float2* taylor_df;
+    const float2* u0df;
+    float2 ch_df[MAXCH][5];
     int ch_d[MAXCH], ch_mu[MAXCH], ch_l[MAXCH];
     double ch_a[MAXCH], ch_b[MAXCH], ch_sb[MAXCH];  // ch_sb = sqrt(b)
     double ch_isb[MAXCH], ch_ib[MAXCH];            // 1 / sqrt(b), 1 / b
@@ -203,6 +213,7 @@ struct vbk_model {
     std::vector<vbk_channel> chans;
     std::vector<vbk_cterm> cterms;
     void* dev_mem2 = nullptr;  // coefficient columns of the coupling polynomials (q-dependent channels)
+    void* dev_mem3 = nullptr;  // double-float tables of the energy diagonal (vbk_dfmath.cuh)
     std::vector<std::vector<int>> sp_delta;  // per polynomial point of a sandwich channel: offset per mode
     int M = 0, ns = 0, Nnu = 0, N = 0, nmu = 0;
     int nb[MAXM] = {0}, stride[MAXM] = {0};
@@ -388,6 +399,30 @@ __host__ __device__ inline double2 vbk_level_shift_eval_sb(double eps, double a,
     return vbk_level_shift_core(eps, a, b, sb, 1.0 / sb, 1.0 / b, l);
 }
 
+// The double-float tables of the level shift built on the host from the FP64 ones: Dawson
+// interpolants, erfcx interpolants (VBK_ERFCX_NINT x 13 pairs each) and Dawson's Taylor
+// coefficients (14 pairs).
+inline void vbk_df_tables(std::vector<float2>* dawson, std::vector<float2>* erfcx, std::vector<float2>* taylor) {
+    const int n = VBK_ERFCX_NINT * (VBK_ERFCX_DEG + 1);
+    dawson->resize(n);
+    erfcx->resize(n);
+    for (int k = 0; k < n; ++k) {
+        const dflt a = dd_from(vbk_dawson_c_host[k]), b = dd_from(vbk_erfcx_c_host[k]);
+        (*dawson)[k] = make_float2(a.h, a.l);
+        (*erfcx)[k] = make_float2(b.h, b.l);
+    }
+    taylor->resize(14);
+    double c = 1.0, dfact = 1.0;  // (-2)^k / (2k + 1)!!
+    for (int k = 0; k < 14; ++k) {
+        if (k > 0) {
+            c *= -2.0;
+            dfact *= (double)(2 * k + 1);
+        }
+        const dflt t = dd_from(c / dfact);
+        (*taylor)[k] = make_float2(t.h, t.l);
+    }
+}
+
 // f(eps) = sqrt(Gamma(eps) / 2 pi), zero for eps <= 0 (reading: closed channels do not couple)
 __host__ __device__ inline double vbk_amplitude(double eps, double a, double b, int l) {
     if (!(eps > 0.0)) return 0.0;
@@ -452,6 +487,11 @@ struct ClArgs {
     float4* xs = nullptr;               // [system][N] double-float solution, zero before the launch
     double2* psi = nullptr;             // [system][N] FP64 solution (written)
     SysState* st = nullptr;             // per-system record (written)
+    // quad loops of the one-CTA solve: fast divisors by the digit radices (n_s, nb_0 .. nb_{M-3},
+    // nb_{M-2} / 4, nb_{M-1}) of a quad index (entries M.. unused) and the digits of the thread
+    // stride, set on the host (kernel parameters: no registers held)
+    FastDiv qfd[MAXM] = {};
+    int qinc[MAXM] = {}, qincd = 0;
 };
 bool vbk_cluster_plan(const DevModel& md, ClArgs* a, size_t* smem);
 int vbk_cluster_prepare(const DevModel& md, const ClArgs& a, size_t smem, int* max_clusters);

@@ -177,6 +177,41 @@ __global__ void k_diag_table(DevModel md, int nE, const double* __restrict__ E, 
     }
 }
 
+// Energy tables of the FP32 refinement path, in double-float arithmetic on the FP32 pipes
+// (vbk_dfmath.cuh): diag[e][d, nu] = E_e - E_nu - U_dd^(delta=0)(nu) - sum_ch F[Gamma/2pi](E_e - E_nu)
+// as the split (re hi, im hi, re lo, im lo), its FP32 rounding and the FP32 reciprocal.  The
+// only FP64 arithmetic per element is E_e - E_nu and its split (models with q-dependent
+// couplings take the FP64 kernel above).  Grid: elements x energies.
+__global__ void __launch_bounds__(TPB) k_diag_table_df(DevModel md, int nE, const double* __restrict__ E,
+                                                      float2* __restrict__ d32, float2* __restrict__ dinv32,
+                                                      float4* __restrict__ dsp, int* __restrict__ zpiv) {
+    const int e = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= md.N) return;
+    const long long t = (long long)e * md.N + i;
+    const int d = (int)fdiv((unsigned)i, md.fd_nnu), nu = i - d * md.Nnu;
+    const double epsd = E[e] - md.enu[nu];
+    const float eh = (float)epsd;
+    const dflt eps = dfv(eh, (float)(epsd - (double)eh));
+    const float2 u0 = md.u0df[i];
+    dflt re = dd_sub(eps, dfv(u0.x, u0.y)), im = dfv(0.f);
+    const DfLevelShift T{md.dawson_df, md.erfcx_df, md.taylor_df, VBK_ERFCX_NINT};
+    for (int c = 0; c < md.nchan; ++c) {
+        if (md.ch_d[c] != d) continue;
+        dflt fr, fi;
+        dd_level_shift(eps, md.ch_df[c], md.ch_l[c], T, &fr, &fi);
+        re = dd_sub(re, fr);
+        im = dd_sub(im, fi);
+    }
+    dsp[t] = make_float4(re.h, im.h, re.l, im.l);
+    const float2 f = make_float2(re.h, im.h);
+    d32[t] = f;
+    if (dinv32) {
+        const float den = f.x * f.x + f.y * f.y;
+        dinv32[t] = make_float2(f.x / den, -f.y / den);
+    }
+    if (zpiv && f.x == 0.f && f.y == 0.f) zpiv[e] = 1;  // a zero pivot of the point preconditioner
+}
+
 // Batched matvec y = A x (or y = b - A x): one thread owns one element of one state and applies
 // its stencil to S systems.  The off-diagonal part of A is energy-independent, so the coefficient
 // of every stencil point is read once per element (precomputed column, L2-resident) and reused
@@ -2492,7 +2527,13 @@ inline size_t residual_res_smem(const DevModel& md) {
 //   x += ||r|| d in double-float,
 // then writes psi = hi + lo in FP64.  This replaces, for such systems, the host loop of separate
 // residual, check, ordering and output launches.
-template <int M, bool SEC>
+// QD (models whose points involve one mode and whose second-fastest mode has a multiple of 4
+// functions): the two stencil loops (the FP32 product and the double-float residual) take quads
+// of elements, i0 + c S for c = 0..3 with S = nb[M-1] -- the same state and quanta but for
+// n[M-2] = 4 b + c -- so that each point's descriptor and (fastest-mode) coefficient are read
+// once for four elements; the residual runs on both halves of (re, im) pairs at once (packed
+// FP32x2 double-float steps, bit-identical to the scalar ones).
+template <int M, bool SEC, bool QD>
 __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs a, float2* __restrict__ xw,
                                                            float2* __restrict__ rw, const float2* __restrict__ dinv) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -2502,6 +2543,10 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
     float4* XS = reinterpret_cast<float4*>(smraw) + H;  // the split solution during the residual
     const size_t rows_off = std::max((size_t)(2 * N + 2 * H) * 8, (size_t)(N + 2 * H) * 16);
     float2* rows = reinterpret_cast<float2*>(smraw + rows_off);  // rct (FP32 pass) or rctd (residual)
+    // one bit per element: b_i != 0 (set in the first pass, which reads b whole; b is a few
+    // entries of an entry channel, so the later passes load only those)
+    unsigned* bmask = reinterpret_cast<unsigned*>(smraw + rows_off + (((size_t)md.nrct * 8 + 15) & ~(size_t)15));
+    const int NW = (N + 31) >> 5;
     __shared__ int4 sdesc[MAXS * 64];
     __shared__ float redA[RTPB / 32][3], redB[RTPB / 32][3];
     __shared__ double redD[RTPB / 32];
@@ -2511,6 +2556,9 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
     // into hi + lo floats, the inner iteration cap
     __shared__ int s_status, s_icap;
     __shared__ float s_inv, s_target2, s_sh, s_sl;
+    // the system's FP64 norms and refinement count, kept by thread 0 (no registers in the others)
+    __shared__ double s_bn, s_rn, s_prev;
+    __shared__ int s_ref;
     static_assert(RTPB == 1024, "one partial per lane in the final warp sums");
     for (int k = tid; k < md.rbeg[md.ns]; k += RTPB) sdesc[k] = md.rdesc[k];
     auto all_sum3 = [&](float (*buf)[3], float a0, float a1, float a2) {
@@ -2551,11 +2599,40 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
         }
         d += incd + c;
     };
+    // quad digits (d, n_0 .. n_{M-3}, b, n_{M-1}), radices (n_s, nb_0 .. nb_{M-3}, nb_{M-2} / 4,
+    // nb_{M-1}): those of this thread's first quad (u = tid), then steps of RTPB quads
+    const int S = md.nb[M - 1], NQ = N >> 2;
+    const int S8 = S * (int)sizeof(float2);
+    auto qstart = [&](int& d, int (&n)[MAXM]) {
+        unsigned rem = (unsigned)tid;
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m) {
+            const unsigned q = fdiv(rem, a.qfd[m]);
+            n[m] = (int)(rem - q * (unsigned)a.qfd[m].d);
+            rem = q;
+        }
+#pragma unroll
+        for (int m = M; m < MAXM; ++m) n[m] = 0;
+        d = (int)rem;
+    };
+    auto qadvance = [&](int& d, int (&n)[MAXM]) {
+        int c = 0;
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m) {
+            const int v = n[m] + a.qinc[m] + c;
+            c = v >= a.qfd[m].d;
+            n[m] = c ? v - a.qfd[m].d : v;
+        }
+        d += a.qincd + c;
+    };
     for (;;) {
         __syncthreads();  // the previous system's shared data is no longer read
+        for (int w = tid; w < NW; w += RTPB) bmask[w] = 0u;
         if (tid == 0) {
             const int q = atomicAdd(a.counter, 1);
             snext = q < a.nsys ? a.nsys - 1 - q : -1;
+            s_bn = s_rn = s_prev = 0.0;
+            s_ref = 0;
         }
         __syncthreads();
         const int s = snext;
@@ -2568,13 +2645,15 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
         float4* xs = a.xs + so;
         float2* x = xw + so;
         float2* r = rw + so;
-        int iters = 0, refines = 0, status = -1;
-        double bnorm = 0.0, rn = 0.0, prev = 0.0;  // meaningful in thread 0
+        int iters = 0, status = -1;
         float inres = 1.f;
+        // the split solution: written to xs by the first x update (never read before it: no zero
+        // fill needed) and to XS in shared memory by every x update, where the next residual
+        // reads it; xs_smem: XS holds it (not yet overwritten by an inner solve's p and q)
+        bool xs_set = false, xs_smem = false;
         for (int k = 0;; ++k) {
             // ---- r = b - A x in double-float (x = 0 in the first round); its FP32 hi part to r
             if (k > 0) {
-                for (int i = tid; i < N; i += RTPB) XS[i] = xs[i];
                 for (int i = tid; i < H; i += RTPB) XS[-1 - i] = XS[N + i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int i = tid; i < md.nrct; i += RTPB) rows[i] = md.rctd[i];
                 __syncthreads();
@@ -2584,22 +2663,28 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
                 int d = d0, n[MAXM];
 #pragma unroll
                 for (int m = 0; m < MAXM; ++m) n[m] = n0[m];
+                float4 gn = k > 0 && tid < N ? dgdf[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int i = tid; i < N; i += RTPB) {
                     if (i != tid) advance(d, n);
-                    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-                    const double2 bb = a.b64[so + i];
-                    if ((__double_as_longlong(bb.x) | __double_as_longlong(bb.y)) != 0) {  // b is mostly zero
-                        rh = (float)bb.x;
-                        ih = (float)bb.y;
-                        rl = (float)(bb.x - (double)rh);
-                        il = (float)(bb.y - (double)ih);
+                    const float4 g = gn;  // the diagonal of this element; the next one's load issued now
+                    if (k > 0 && i + RTPB < N) gn = dgdf[i + RTPB];
+                    // the (re, im) pair as one packed double-float accumulator (hi parts, lo parts)
+                    float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
+                    if (k == 0 || ((bmask[i >> 5] >> (i & 31)) & 1u)) {
+                        const double2 bb = a.b64[so + i];
+                        if ((__double_as_longlong(bb.x) | __double_as_longlong(bb.y)) != 0) {
+                            sh = make_float2((float)bb.x, (float)bb.y);
+                            sl = make_float2((float)(bb.x - (double)sh.x), (float)(bb.y - (double)sh.y));
+                            if (k == 0) atomicOr(&bmask[i >> 5], 1u << (i & 31));
+                        }
                     }
                     if (k > 0) {
-                        const float4 xv = XS[i], g = dgdf[i];
-                        df_fma(rh, rl, -g.x, -g.z, xv.x, xv.z);
-                        df_fma(rh, rl, g.y, g.w, xv.y, xv.w);
-                        df_fma(ih, il, -g.x, -g.z, xv.y, xv.w);
-                        df_fma(ih, il, -g.y, -g.w, xv.x, xv.z);
+                        // - diag x: (re, im) += (-g_re)(x_re, x_im) + (g_im, -g_im)(x_im, x_re)
+                        const float4 xv = XS[i];
+                        df_fma2(sh, sl, make_float2(-g.x, -g.x), make_float2(-g.z, -g.z), make_float2(g.x, g.x),
+                                make_float2(xv.x, xv.y), make_float2(xv.z, xv.w));
+                        df_fma2(sh, sl, make_float2(g.y, -g.y), make_float2(g.w, -g.w), make_float2(-g.y, g.y),
+                                make_float2(xv.y, xv.x), make_float2(xv.w, xv.z));
                         int kk = md.rbeg[d];
 #pragma unroll
                         for (int m = 0; m < M; ++m) {
@@ -2618,14 +2703,14 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
                                     }
                                 }
                                 const float4 v = XS[i + (q.y >> 3)];  // neighbours outside [0, N) read the zero halo
-                                df_fma(rh, rl, c.x, c.y, v.x, v.z);
-                                df_fma(ih, il, c.x, c.y, v.y, v.w);
+                                df_fma2(sh, sl, make_float2(c.x, c.x), make_float2(c.y, c.y), make_float2(-c.x, -c.x),
+                                        make_float2(v.x, v.y), make_float2(v.z, v.w));
                             }
                         }
                     }
-                    const float2 re = df_norm(rh, rl), im = df_norm(ih, il);
-                    r[i] = make_float2(re.x, im.x);
-                    nrm = fmaf(re.x, re.x, fmaf(im.x, im.x, nrm));
+                    const float2 hi = fadd2(sh, sl);  // the FP32 part of the renormalised pair
+                    r[i] = hi;
+                    nrm = fmaf(hi.x, hi.x, fmaf(hi.y, hi.y, nrm));
                 }
             }
             // ||r||^2: FP32 within a warp, FP64 across warps (warp 0); the refinement checks in
@@ -2640,30 +2725,30 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
                 for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
                 if (lane == 0) {
                     int st_ = -1;
-                    rn = sqrt(t);
+                    s_rn = sqrt(t);
                     if (k == 0) {
-                        bnorm = a.bn2 ? sqrt(a.bn2[s]) : rn;
-                        if (bnorm == 0.0) {
+                        s_bn = a.bn2 ? sqrt(a.bn2[s]) : s_rn;
+                        if (s_bn == 0.0) {
                             st_ = VBK_SYS_ZERO_RHS;
-                            rn = 0.0;
+                            s_rn = 0.0;
                         }
                     } else {
-                        refines += 1;
+                        s_ref += 1;
                     }
                     if (st_ < 0) {
-                        if (!isfinite(rn)) st_ = VBK_SYS_NAN;
-                        else if (rn <= a.tol * bnorm) st_ = VBK_SYS_CONVERGED;
-                        else if (a.stall_check && k > 0 && !(rn <= 0.9 * prev)) st_ = VBK_SYS_STALLED;  // FP32 inner solve no longer helps
-                        else if (refines >= a.max_refine || iters >= a.max_iter) st_ = VBK_SYS_MAX_ITER;
+                        if (!isfinite(s_rn)) st_ = VBK_SYS_NAN;
+                        else if (s_rn <= a.tol * s_bn) st_ = VBK_SYS_CONVERGED;
+                        else if (a.stall_check && k > 0 && !(s_rn <= 0.9 * s_prev)) st_ = VBK_SYS_STALLED;  // FP32 inner solve no longer helps
+                        else if (s_ref >= a.max_refine || iters >= a.max_iter) st_ = VBK_SYS_MAX_ITER;
                     }
                     s_status = st_;
                     if (st_ < 0) {
-                        prev = rn;
-                        s_inv = (float)(1.0 / rn);
-                        const float tg = (float)fmax(a.inner_tol, 0.3 * a.tol * bnorm / rn);
+                        s_prev = s_rn;
+                        s_inv = (float)(1.0 / s_rn);
+                        const float tg = (float)fmax(a.inner_tol, 0.3 * a.tol * s_bn / s_rn);
                         s_target2 = tg * tg;
-                        s_sh = (float)rn;
-                        s_sl = (float)(rn - (double)s_sh);
+                        s_sh = (float)s_rn;
+                        s_sl = (float)(s_rn - (double)s_sh);
                         s_icap = a.inner_cap > 0 ? (int)min((long long)a.max_iter, (long long)iters + a.inner_cap) : a.max_iter;
                     }
                 }
@@ -2676,6 +2761,7 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
             const float inv = s_inv, target2 = s_target2;
             const int icap = s_icap;
             // ---- inner FP32 COCG on r / ||r|| (x = 0, z = B^-1 r, p = z, rho = r^T z)
+            xs_smem = false;
             for (int i = tid; i < md.nrct; i += RTPB) rows[i] = md.rct[i];
             for (int i = tid; i < H; i += RTPB) P[-1 - i] = P[N + i] = make_float2(0.f, 0.f);
             __syncthreads();  // XS (which overlays P) fully read
@@ -2699,48 +2785,102 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
             const int budget = max(0, icap - iters);
             for (int it = 0; it < budget; ++it) {
                 float pq_x = 0.f, pq_y = 0.f;
-                int d = d0, n[MAXM];
+                if constexpr (QD) {
+                    // quads: q = diag p - sum_points c p[nu + delta] for four elements per step
+                    int d, n[MAXM];
+                    qstart(d, n);
+                    for (int u = tid; u < NQ; u += RTPB) {
+                        if (u != tid) qadvance(d, n);
+                        const int w = (int)fdiv((unsigned)u, md.fd_nb[M - 1]);
+                        const int i0 = 4 * S * w + (u - w * S);
+                        float2 acc[4];
 #pragma unroll
-                for (int m = 0; m < MAXM; ++m) n[m] = n0[m];
-                // the diagonal of RC consecutive elements of this thread is loaded ahead (L2 latency)
-                constexpr int RC = 4;
-                for (int i0 = tid; i0 < N; i0 += RC * RTPB) {
-                    float2 dgv[RC];
+                        for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.f, 0.f);
+                        const char* Pq = reinterpret_cast<const char*>(P + i0);
+                        int kk = md.rbeg[d];
 #pragma unroll
-                    for (int c = 0; c < RC; ++c) {
-                        const int ic = i0 + c * RTPB;
-                        dgv[c] = ic < N ? dg[ic] : make_float2(0.f, 0.f);
-                    }
+                        for (int m = 0; m < M; ++m) {
+                            const int kend = kk + md.rcnt[d][m];
+                            if (m == M - 2) {  // four consecutive (-c, -c) pairs, two float4 loads
+                                const char* row = reinterpret_cast<const char*>(rows) + n[m] * 32;
+#pragma unroll 1
+                                for (; kk < kend; ++kk) {
+                                    const int4 q = sdesc[kk];
+                                    const float4 c01 = *reinterpret_cast<const float4*>(row + q.x);
+                                    const float4 c23 = *reinterpret_cast<const float4*>(row + q.x + 16);
+                                    const char* ap = Pq + q.y;  // zero halo outside [0, N)
+                                    acc[0] = ffma2(make_float2(c01.x, c01.y), *reinterpret_cast<const float2*>(ap), acc[0]);
+                                    acc[1] = ffma2(make_float2(c01.z, c01.w), *reinterpret_cast<const float2*>(ap + S8), acc[1]);
+                                    acc[2] = ffma2(make_float2(c23.x, c23.y), *reinterpret_cast<const float2*>(ap + 2 * S8), acc[2]);
+                                    acc[3] = ffma2(make_float2(c23.z, c23.w), *reinterpret_cast<const float2*>(ap + 3 * S8), acc[3]);
+                                }
+                            } else {  // one (-c, -c) pair for the four
+                                const char* row = reinterpret_cast<const char*>(rows) + n[m] * 8;
+#pragma unroll 1
+                                for (; kk < kend; ++kk) {
+                                    const int4 q = sdesc[kk];
+                                    const float2 cc = *reinterpret_cast<const float2*>(row + q.x);
+                                    const char* ap = Pq + q.y;
 #pragma unroll
-                    for (int c = 0; c < RC; ++c) {
-                    const int i = i0 + c * RTPB;
-                    if (i >= N) break;
-                    if (i != tid) advance(d, n);
-                    const float2 pi = P[i];
-                    float2 acc = cmul<float>(dgv[c], pi);
-                    const char* Pi = reinterpret_cast<const char*>(P + i);
-                    int kk = md.rbeg[d];
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const int kend = kk + md.rcnt[d][m];
-                        const char* row = reinterpret_cast<const char*>(rows) + n[m] * 8;
-#pragma unroll 4
-                        for (; kk < kend; ++kk) {
-                            const int4 q = sdesc[kk];
-                            float2 cc = *reinterpret_cast<const float2*>(row + q.x);  // (-c, -c)
-                            if constexpr (SEC) {
-                                if (q.z >= 0) {
-                                    const float t = md.tab32[q.z + nsel<M>(n, q.w)];
-                                    cc.x *= t;
-                                    cc.y *= t;
+                                    for (int c = 0; c < 4; ++c)
+                                        acc[c] = ffma2(cc, *reinterpret_cast<const float2*>(ap + c * S8), acc[c]);
                                 }
                             }
-                            acc = ffma2(cc, *reinterpret_cast<const float2*>(Pi + q.y), acc);  // zero halo outside
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float2 pi = P[i0 + c * S], g = dg[i0 + c * S];
+                            const float2 v = make_float2(acc[c].x + g.x * pi.x - g.y * pi.y,
+                                                         acc[c].y + g.x * pi.y + g.y * pi.x);
+                            Q[i0 + c * S] = v;
+                            pq_x += pi.x * v.x - pi.y * v.y;
+                            pq_y += pi.x * v.y + pi.y * v.x;
                         }
                     }
-                    Q[i] = acc;
-                    pq_x += pi.x * acc.x - pi.y * acc.y;
-                    pq_y += pi.x * acc.y + pi.y * acc.x;
+                } else {
+                    int d = d0, n[MAXM];
+#pragma unroll
+                    for (int m = 0; m < MAXM; ++m) n[m] = n0[m];
+                    // the diagonal of RC consecutive elements of this thread is loaded ahead (L2 latency)
+                    constexpr int RC = 4;
+                    for (int i0 = tid; i0 < N; i0 += RC * RTPB) {
+                        float2 dgv[RC];
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) {
+                            const int ic = i0 + c * RTPB;
+                            dgv[c] = ic < N ? dg[ic] : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int c = 0; c < RC; ++c) {
+                        const int i = i0 + c * RTPB;
+                        if (i >= N) break;
+                        if (i != tid) advance(d, n);
+                        const float2 pi = P[i];
+                        float2 acc = cmul<float>(dgv[c], pi);
+                        const char* Pi = reinterpret_cast<const char*>(P + i);
+                        int kk = md.rbeg[d];
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            const int kend = kk + md.rcnt[d][m];
+                            const char* row = reinterpret_cast<const char*>(rows) + n[m] * 8;
+#pragma unroll 4
+                            for (; kk < kend; ++kk) {
+                                const int4 q = sdesc[kk];
+                                float2 cc = *reinterpret_cast<const float2*>(row + q.x);  // (-c, -c)
+                                if constexpr (SEC) {
+                                    if (q.z >= 0) {
+                                        const float t = md.tab32[q.z + nsel<M>(n, q.w)];
+                                        cc.x *= t;
+                                        cc.y *= t;
+                                    }
+                                }
+                                acc = ffma2(cc, *reinterpret_cast<const float2*>(Pi + q.y), acc);  // zero halo outside
+                            }
+                        }
+                        Q[i] = acc;
+                        pq_x += pi.x * acc.x - pi.y * acc.y;
+                        pq_y += pi.x * acc.y + pi.y * acc.x;
+                        }
                     }
                 }
                 const float3 pq = all_sum3(redA, pq_x, pq_y, 0.f);
@@ -2803,33 +2943,45 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
             }
             inres = sqrtf(rr);
             // ---- x += scale d in double-float (each thread its own elements)
-            if (wrote_x) {
+            if (wrote_x) {  // P and Q are dead: XS (over them) receives the new solution as well
                 const float sh = s_sh, sl = s_sl;
                 for (int i = tid; i < N; i += RTPB) {
                     const float2 dv = x[i];
-                    float4 X = xs[i];
+                    float4 X = xs_set ? xs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                     df_fma(X.x, X.z, sh, sl, dv.x, 0.f);
                     df_fma(X.y, X.w, sh, sl, dv.y, 0.f);
                     const float2 re = df_norm(X.x, X.z), im = df_norm(X.y, X.w);
-                    xs[i] = make_float4(re.x, im.x, re.y, im.y);
+                    X = make_float4(re.x, im.x, re.y, im.y);
+                    xs[i] = X;
+                    XS[i] = X;
                 }
+                xs_set = true;
+            } else {  // no new solution, but the inner solve wrote over XS: restore it
+                for (int i = tid; i < N; i += RTPB) XS[i] = xs_set ? xs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            xs_smem = true;
             if (status >= 0) break;
             __syncthreads();  // P, Q fully read before the next residual stages XS over them
         }
-        // ---- psi = hi + lo in FP64, and the system's record
+        // ---- psi = hi + lo in FP64 (from XS after a final residual, else from xs; zero if no
+        // solution was ever formed), and the system's record
         double2* psi = a.psi + so;
+        if (!xs_smem) {
+            __syncthreads();  // an inner solve may still be reading P / Q over XS
+            for (int i = tid; i < N; i += RTPB) XS[i] = xs_set ? xs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+        }
         for (int i = tid; i < N; i += RTPB) {
-            const float4 v = xs[i];
+            const float4 v = XS[i];
             psi[i] = make_double2(f2d_exact(v.x) + f2d_exact(v.z), f2d_exact(v.y) + f2d_exact(v.w));
         }
         if (tid == 0) {
             SysState& S = a.st[s];
             S.status = status < 0 ? VBK_SYS_MAX_ITER : status;
             S.iters = iters;
-            S.refines = refines;
-            S.rnorm = rn;
-            S.bnorm = bnorm;
+            S.refines = s_ref;
+            S.rnorm = s_rn;
+            S.bnorm = s_bn;
             S.inres = (double)inres;
         }
     }
@@ -2837,15 +2989,39 @@ __global__ void __launch_bounds__(RTPB, 1) k_solve_resident(DevModel md, ClArgs 
 inline bool resident_ok(const DevModel& md);
 inline size_t solve_resident_smem(const DevModel& md) {
     const size_t pq = (size_t)(2 * md.N + 2 * md.rhalo) * 8, xsb = (size_t)(md.N + 2 * md.rhalo) * 16;
-    return std::max(pq, xsb) + (size_t)md.nrct * 8 + 16;
+    return std::max(pq, xsb) + (((size_t)md.nrct * 8 + 15) & ~(size_t)15) + (size_t)((md.N + 31) / 32) * 4 + 16;
+}
+// the instance for a model: a second mode's factor per point (SEC), else quads when n_{M-2} runs
+// over a multiple of 4 functions, else one element per step
+using SolveResidentFn = void (*)(DevModel, ClArgs, float2*, float2*, const float2*);
+template <int M> SolveResidentFn solve_resident_fn(const DevModel& md) {
+    if (md.rsec) return k_solve_resident<M, true, false>;
+    if constexpr (M >= 2) {
+        if (md.nb[M - 2] % 4 == 0) return k_solve_resident<M, false, true>;
+    }
+    return k_solve_resident<M, false, false>;
+}
+// the quad digit radices and the digits of the stride RTPB (quad loops of k_solve_resident)
+inline void set_quad_args(const DevModel& md, int M, ClArgs& a) {
+    for (int m = 0; m < MAXM; ++m) {
+        a.qfd[m] = make_fastdiv(1);
+        a.qinc[m] = 0;
+    }
+    a.qincd = 0;
+    if (M < 2 || md.nb[M - 2] % 4 != 0) return;
+    int rem = RTPB;
+    for (int m = M - 1; m >= 0; --m) {
+        const int rad = m == M - 2 ? md.nb[m] / 4 : md.nb[m];
+        a.qfd[m] = make_fastdiv(rad);
+        a.qinc[m] = rem % rad;
+        rem /= rad;
+    }
+    a.qincd = rem;
 }
 template <int M> bool prepare_solve_resident(const DevModel& md) {
     if (!resident_ok(md) || solve_resident_smem(md) > 220 * 1024) return false;
-    const cudaError_t ce =
-        md.rsec ? cudaFuncSetAttribute(k_solve_resident<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)solve_resident_smem(md))
-                : cudaFuncSetAttribute(k_solve_resident<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)solve_resident_smem(md));
+    const cudaError_t ce = cudaFuncSetAttribute(solve_resident_fn<M>(md), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)solve_resident_smem(md));
     if (ce != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -3973,7 +4149,9 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         if (cudaMemcpyAsync(smallp, hp + o_stage, small_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemsetAsync(sst, 0, nsys * sizeof(SysState), st) != cudaSuccess ||
-            cudaMemsetAsync(dfr ? (void*)xs : (void*)job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) != cudaSuccess ||
+            // (the one-CTA fused solve writes its split solution before reading it)
+            (fused != 1 && cudaMemsetAsync(dfr ? (void*)xs : (void*)job.x64, 0, (size_t)nsys * NN * sizeof(double2), st) !=
+                               cudaSuccess) ||
             cudaMemsetAsync(pfail, 0, nE * sizeof(int), st) != cudaSuccess ||
             cudaMemsetAsync(done, 0, nsys * sizeof(int), st) != cudaSuccess) {
             fail(vbk_cuda_fail(cudaGetLastError(), "solver set-up copies"));
@@ -3981,9 +4159,13 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
         }
         // energy tables (FP64 + inner-precision copy); pair transforms of q-dependent couplings first
         if (sand) rn.go("sandwich_table", k_sand_table, dim3(cdiv_u(md.Nnu, TPB), nE), dim3(TPB), md, nE, (const double*)dE);
-        rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE,
-              dfr ? (double2*)nullptr : diag64, mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR, dsp,
-              pspan == 0 ? pfail : (int*)nullptr);
+        if (dfr)  // the resident FP32 paths: double-float tables on the FP32 pipes
+            rn.go("diag_table", k_diag_table_df, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE,
+                  reinterpret_cast<float2*>(diagR), dinvR, dsp, pspan == 0 ? pfail : (int*)nullptr);
+        else
+            rn.go("diag_table", k_diag_table<M>, dim3(cdiv_u(N, TPB), nE), dim3(TPB), md, nE, (const double*)dE, diag64,
+                  mixed ? reinterpret_cast<float2*>(diagR) : (float2*)nullptr, dinvR, (float4*)nullptr,
+                  pspan == 0 ? pfail : (int*)nullptr);
         if (block) factor_blocks<R, M>(rn, md, pbuf, nE, (const cx<R>*)diagR, F, pfail);
         if (cudaError_t ce = cudaGetLastError(); ce != cudaSuccess) {
             fail(vbk_cuda_fail(ce, "set-up kernels"));
@@ -4027,6 +4209,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cla.xs = xs;
             cla.psi = job.x64;
             cla.st = sst;
+            set_quad_args(md, M, cla);
             if (cudaMemsetAsync(cnt, 0, sizeof(int), st) != cudaSuccess) {
                 fail(vbk_cuda_fail(cudaGetLastError(), "cluster solve set-up"));
                 break;
@@ -4035,7 +4218,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                 static int nsm = 0;
                 if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) nsm = 148;
                 const dim3 g((unsigned)std::min(nsys, nsm));
-                auto kern = md.rsec ? k_solve_resident<M, true> : k_solve_resident<M, false>;
+                const SolveResidentFn kern = solve_resident_fn<M>(md);
                 rn.go_smem("solve_resident", kern, g, dim3(RTPB), solve_resident_smem(md), md, cla,
                            reinterpret_cast<float2*>(x), reinterpret_cast<float2*>(r), (const float2*)dinvR);
             } else {

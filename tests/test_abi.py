@@ -64,6 +64,32 @@ def test_host_level_shift_matches_oracle(lib, l):
             assert abs(got - ref) <= 2e-13 * cond * max(1.0, abs(ref)), (eps, b, l, got, ref)
 
 
+@pytest.mark.parametrize("l", [0, 1, 2])
+def test_double_float_level_shift_matches_the_fp64_closed_form(lib, l):
+    """The double-float code the FP32 refinement path's energy tables run (evaluated on the
+    host) against the FP64 closed form and the oracle: every branch (Taylor, interpolants,
+    asymptotic series; open and closed channels; threshold), relative to the diagonal scale
+    (the level shift enters A beside E - E_nu, an eV-sized term)."""
+    from oracle import vibronic as o
+
+    for b in (0.25, 0.4, 0.833, 1.7):
+        # b eps = 300 reaches the asymptotic series; with l > 0 the upward recursion cancels there
+        # (as in FP64, with double-float's shorter significand), far beyond the energies of interest
+        far = [300.0 / b] if l == 0 else []
+        for eps in np.concatenate([np.linspace(-40, -0.01, 23), [-1e-6, 0.0, 1e-6], np.linspace(0.003, 40, 61),
+                                   [0.02, 0.6 / b, 3.0 / b], far]):
+            got = lib.vbk_level_shift_df(eps, 0.13, b, l)
+            ref = lib.vbk_level_shift(eps, 0.13, b, l)
+            orc = complex(o.level_shift(np.array([eps]), 0.13, b, l)[0])
+            cond = (1.0 + abs(eps)) ** (l + 0.5) if eps < 0 else 1.0
+            scale = max(1.0, abs(ref), abs(eps))  # F enters A beside E - E_nu, of size |eps|
+            assert abs(got - ref) <= 2e-14 * cond * scale, (eps, b, l, got, ref)
+            assert abs(got - orc) <= 2e-13 * cond * scale, (eps, b, l, got, orc)
+            if 0 < b * eps < 80:  # the width, where exp(-b eps) is representable in float
+                # exp(-b eps) inherits the absolute error of its argument, ~1e-14 b eps in double-float
+                assert abs(got.imag - ref.imag) <= 1.5e-14 * (1.0 + b * eps) * abs(ref.imag), (eps, b, l)
+
+
 def test_host_level_shift_rejects_bad_arguments(lib):
     with pytest.raises(lib.VbkError):
         lib.vbk_level_shift(1.0, 0.1, -1.0, 0)

@@ -142,9 +142,10 @@ SOLVERS = [
 @pytest.mark.parametrize("name", ["ci2d_x", "ecd86", "co2_small", "one_mode", "frozen_mode"])
 @pytest.mark.parametrize("span,resident", [(0, 1), (-1, 1), (0, 2), (0, 3), (-1, 3)])
 def test_resident_paths_on_every_model_shape(vbk, name, span, resident):
-    """The fused cluster solve (resident = 1: one cluster of n_s thread blocks per system, 1 to 3
-    states, 1 to 4 modes, bilinear points with a second mode, a frozen mode) and the one-block
-    inner solves (resident = 2), Jacobi or no preconditioner: true residuals by the oracle."""
+    """The fused solves -- resident = 1: the whole refinement of each system in one thread block;
+    resident = 3: one cluster of n_s thread blocks per system -- and the one-block inner solves
+    (resident = 2) on 1 to 3 states, 1 to 4 modes, bilinear points with a second mode and a frozen
+    mode, Jacobi or no preconditioner: true residuals by the oracle."""
     desc = MODELS[name]()
     model = vbk.Model(desc)
     eps = np.array([0.3, 1.1, 2.4, 3.3])
@@ -165,6 +166,46 @@ def test_resident_paths_on_every_model_shape(vbk, name, span, resident):
             assert st["status"] == "converged", (e, mu, st)
             res = np.linalg.norm(rhs - A @ psi[e, 0, mu]) / np.linalg.norm(rhs)
             assert res <= 1e-10 * 1.05, (e, mu, res, st)
+
+
+@pytest.mark.parametrize("nb", [(12, 12), (40, 40), (64, 64), (80, 80), (5, 4, 8, 3)])
+def test_fused_solve_quad_shapes(vbk, nb):
+    """The fused one-block solve on models whose second-fastest mode has a multiple of 4 functions
+    (its stencil loops take quads of elements): fewer quads than threads, a whole number of
+    passes (64 x 64), a ragged last pass (80 x 80, the batched workload's size) and four modes
+    with three states (the CO2-like model without its bilinear coupling).  True residuals and
+    cross sections by the oracle."""
+    if len(nb) == 2:
+        desc = w.ci2d_model(nb[0])
+        desc["modes"][1]["n"] = nb[1]
+    else:
+        desc = w.co2_like_model(basis=nb)
+        desc["terms"] = [t for t in desc["terms"] if sum(1 for p in t["pow"] if p) <= 1]
+    model = vbk.Model(desc)
+    assert model.N == desc["n_states"] * int(np.prod([m["n"] for m in desc["modes"]]))
+    eps = np.array([0.35, 1.6, 2.8])
+    vi = [[0] * len(desc["modes"])]
+    opts = vbk.vbk_default_opts(method="cocg", precision="mixed", precond_span=0, tol=1e-10, resident=1,
+                                max_iter=40000, max_refine=400)
+    psi, stats = vbk.vbk_solve(model, eps, vi, opts)
+    psi = psi.cpu().numpy()
+    for e, ei in enumerate(eps):
+        E = o.total_energy(desc, ei, vi[0])
+        A = o.a_matrix(desc, E)
+        for mu in range(model.n_mu):
+            st = stats[e * model.n_mu + mu]
+            rhs = o.phi(desc, E, vi[0], mu)
+            if not np.any(rhs):
+                assert st["status"] == "zero_rhs"
+                continue
+            assert st["status"] == "converged", (e, mu, st)
+            res = np.linalg.norm(rhs - A @ psi[e, 0, mu]) / np.linalg.norm(rhs)
+            assert res <= 1e-10 * 1.05, (e, mu, res, st)
+    vf = o.open_levels(desc, o.total_energy(desc, eps[-1], vi[0]))[:8]
+    sig = vbk.vbk_cross_sections(model, eps, vi, torch.tensor(psi, device="cuda"), vf).cpu().numpy()
+    sig_ref, _ = o.cross_sections(desc, eps, vi, vf)
+    big = np.abs(sig_ref) > 1e-6 * np.abs(sig_ref).max()
+    assert (np.abs(sig - sig_ref)[big] / np.abs(sig_ref)[big]).max() <= 1e-8
 
 
 @pytest.mark.parametrize("method,precision,span", SOLVERS)

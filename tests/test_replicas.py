@@ -44,6 +44,22 @@ def test_job_rate_takes_the_slowest_rank_over_two_gloo_ranks():
         assert v == pytest.approx(2 * 256 / 5e-3)
 
 
+def test_ranks_solve_distinct_energies_covering_the_grid():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import workloads as w
+
+    np.testing.assert_array_equal(bench.rank_energies(3.0, 256, 0, 1), w.WORKLOADS["ci2d_batched"]["eps"])
+    for world in (2, 4, 8):
+        parts = [bench.rank_energies(3.0, 256, r, world) for r in range(world)]
+        assert all(p.size == 256 for p in parts)
+        allp = np.sort(np.concatenate(parts))
+        np.testing.assert_allclose(allp, w.eps_grid(3.0, 256 * world), rtol=0, atol=0)
+        assert all(p.min() < 0.1 and p.max() > 2.9 for p in parts)  # each rank spans the range
+
+
 def test_job_rate_single_rank():
     sys.path.insert(0, ROOT)
     import bench
