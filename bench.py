@@ -607,7 +607,7 @@ def main():
         vbk.vbk_set_op_timing(model, True)
         for prec, c, name in ((vbk.VBK_MIXED, 8, "fp32"), (vbk.VBK_FP64, 16, "fp64")):
             per_var = {}
-            for v in range(16):
+            for v in range(vbk.VBK_MATVEC_NVARIANTS):
                 best = None
                 for _ in range(3):
                     try:

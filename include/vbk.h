@@ -259,6 +259,9 @@ int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi
                       const double* dL_dsigma_dev, int n_theta, const int* theta_ids,
                       double* grad, vbk_stats* stats, void* stream);
 
+/* Number of matvec kernel variants vbk_matvec accepts (0 .. VBK_MATVEC_NVARIANTS - 1). */
+#define VBK_MATVEC_NVARIANTS 20
+
 /* y = A(E_k) x for a batch: the matrix-free operator of Sec. III (diagonal energy and
  * level-shift factors plus the q-polynomial stencils; with q-dependent couplings also the
  * non-local level shift of Eq. FE, applied as two stencil passes through the coupling
@@ -273,8 +276,14 @@ int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi
  *   systems per thread; 10, 11 = one or two systems per thread block with x in shared memory
  *   (VBK_MIXED only); 12..15 = every state of a tile per thread block, x windows staged
  *   asynchronously, coefficients from shared memory, (systems per block, elements per thread)
- *   = (2,4), (2,2), (4,2), (1,4).  VBK_ERR_INVALID_ARG if the variant does not fit this model
- *   and precision.  Asynchronous on `stream`. */
+ *   = (2,4), (2,2), (4,2), (1,4); 16..19 = persistent streaming kernel: a producer warp per
+ *   thread block brings the x windows and diagonal rows of tiles of (systems, rows of the first
+ *   mode) into a ring of shared-memory stages by bulk asynchronous copies while the other warps
+ *   compute, (systems per tile, row groups, rows per tile, stages) = (4,4,8,2), (4,2,4,2),
+ *   (2,2,8,3), (2,4,16,2) (the last with the rows +-2 of a thread's own state in registers where
+ *   the model allows); offered when n_states * N_nu / n_basis[0] <= 640, every term involves at
+ *   most two modes and, in VBK_MIXED, N_nu / n_basis[0] is even.  VBK_ERR_INVALID_ARG if the
+ *   variant does not fit this model and precision.  Asynchronous on `stream`. */
 int vbk_matvec(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,
                void* y_dev, int precision, int variant, void* stream);
 

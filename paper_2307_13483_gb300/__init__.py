@@ -25,6 +25,7 @@ VBK_ERR_NOT_CONVERGED = 4
 VBK_GMRES, VBK_COCG = 0, 1
 VBK_FP64, VBK_MIXED = 0, 1
 VBK_PRECOND_NONE = -1
+VBK_MATVEC_NVARIANTS = 20
 SYS_STATUS = {0: "converged", 1: "max_iter", 2: "breakdown", 3: "nan", 4: "pivot", 5: "zero_rhs"}
 
 

@@ -3661,14 +3661,17 @@ inline int block_partials(const DevPlanBuf& pb) {
 //   10..11 one / two systems per CTA with x in shared memory (k_matvec_sys, FP32)
 //   12..15 every state of a tile per CTA, windows staged by cp.async, coefficients from rows in
 //          shared memory (k_matvec_win) with (S, EPT) = (2, 4), (2, 2), (4, 2), (1, 4)
-constexpr int MV_NVAR = 16;
+//   16..19 persistent streaming kernel, tiles of rows of mode 0 brought in by bulk asynchronous
+//          copies through a ring of shared-memory stages (k_matvec_stream, vbk_stream.cu)
+constexpr int MV_NWIN = 16;  // variants 0..15 launched from this file
+constexpr int MV_NVAR = 20;
 inline int mv_ept(int v) {
-    static const int e[MV_NVAR] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1, 1, 1, 4, 2, 2, 4};
-    return e[v];
+    static const int e[MV_NWIN] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1, 1, 1, 4, 2, 2, 4};
+    return v < MV_NWIN ? e[v] : 1;
 }
 inline int mv_sys(int v) {
-    static const int sv[MV_NVAR] = {1, 2, 4, 2, 1, 2, 4, 8, 1, 4, 1, 2, 2, 2, 4, 1};
-    return sv[v];
+    static const int sv[MV_NWIN] = {1, 2, 4, 2, 1, 2, 4, 8, 1, 4, 1, 2, 2, 2, 4, 1};
+    return v < MV_NWIN ? sv[v] : 1;
 }
 // window geometry of k_matvec_win: smallest in-plane offset and window length per state
 inline void mv_win_geom(const DevModel& md, int v, int* lo, int* wst) {
@@ -3701,6 +3704,10 @@ inline int mv_tiled_smem(const DevModel& md, int v, size_t c) {
 }
 inline bool mv_valid(const DevModel& md, int v, size_t c) {
     if (md.nsc) return v == 8;  // sandwich channels: k_sand_w + k_matvec_sw, launched in place of variant 8
+    if (v >= MV_NWIN) {
+        StreamPlan sp;
+        return vbk_stream_plan(md, v - MV_NWIN, c, &sp);
+    }
     if (v >= 12) return md.rok && mv_win_smem(md, v, c) <= 110 * 1024;
     if (v >= 10) return c == 8 && md.rok && matvec_sys_smem(md, v - 9) <= 220 * 1024;
     if (c == 16 && (mv_sys(v) * mv_ept(v) > 8 || v == 7)) return false;  // FP64: register budget
@@ -3708,6 +3715,11 @@ inline bool mv_valid(const DevModel& md, int v, size_t c) {
 }
 inline int matvec_partials_v(const DevModel& md, int v) {
     if (md.nsc) v = 8;
+    if (v >= MV_NWIN) {  // one partial per strip (the plan's strip count is the same in FP32 and FP64)
+        StreamPlan sp;
+        if (vbk_stream_plan(md, v - MV_NWIN, 16, &sp) || vbk_stream_plan(md, v - MV_NWIN, 8, &sp)) return sp.nstrip;
+        return 1;
+    }
     if (v >= 12) return (md.Nnu + TPB * mv_ept(v) - 1) / (TPB * mv_ept(v));  // one CTA per tile of all states
     if (v >= 10) return 1;
     const int T = TPB * mv_ept(v);
@@ -3741,6 +3753,18 @@ void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, co
         rn.go("sandwich_w", k_sand_w<T>, dim3(cdiv_u(md.Nnu, TPB), nlist), dim3(TPB), md, sys_e, sel, (int)nlist, x, xs);
         rn.go(name, k_matvec_sw<T>, dim3((unsigned)matvec_partials_v(md, 8), nlist), dim3(TPB), md, sys_e, sel, (int)nlist,
               diag, x, xs, y, ys, b, part, red);
+        return;
+    }
+    if (v >= MV_NWIN) {
+        StreamPlan sp;
+        if (!vbk_stream_plan(md, v - MV_NWIN, sizeof(cx<T>), &sp)) {
+            rn.note_error(cudaErrorInvalidConfiguration, name);
+            return;
+        }
+        rn.go_custom(name, [&] {
+            return vbk_stream_matvec(md, sp, sys_e, sel.list, sel.act, (int)nlist, diag, x, xs, y, ys, b, part, red,
+                                     sizeof(T) == 4, rn.st);
+        });
         return;
     }
     const int S = mv_sys(v);
@@ -3826,6 +3850,7 @@ cudaError_t win_optin(const DevModel& md, int need) {
     }
 }
 template <class T> int prepare_matvec(const DevModel& md) {
+    if (const int rc = vbk_stream_prepare(md, sizeof(T) == 4)) return rc;
     const int need[4] = {mv_tiled_smem(md, 4, sizeof(cx<T>)), mv_tiled_smem(md, 5, sizeof(cx<T>)),
                          mv_tiled_smem(md, 6, sizeof(cx<T>)), mv_tiled_smem(md, 7, sizeof(cx<T>))};
     cudaError_t ce = cudaSuccess;
@@ -4625,6 +4650,11 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             break;
         }
         rn.flush();
+        if (vbk_stream_fault_take()) {  // a streaming matvec stopped waiting for its copies: results not valid
+            vbk_set_error("streaming matvec: a wait for shared-memory copies ran past its limit");
+            fail(VBK_ERR_CUDA);
+            break;
+        }
         std::vector<int> hfail(nE, 0);
         if (block || pspan == 0) {  // zero pivots of the block factors or of the point preconditioner
             cudaMemcpy(hfail.data(), pfail, nE * sizeof(int), cudaMemcpyDeviceToHost);
@@ -4812,6 +4842,10 @@ int operator_run(vbk_model* m, int op, int nE, const double* E, int nvec, int sp
     if (rn.timing) {  // per-kernel timings of this call (vbk_set_op_timing)
         if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = vbk_cuda_fail(cudaGetLastError(), "operator timing");
         rn.flush();
+        if (vbk_stream_fault_take() && !rc) {
+            vbk_set_error("streaming matvec: a wait for shared-memory copies ran past its limit");
+            rc = VBK_ERR_CUDA;
+        }
     }
     cudaFreeAsync(base, st);
     if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);

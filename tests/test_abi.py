@@ -133,6 +133,16 @@ def test_binding_structs_match_the_header(lib, tmp_path):
             assert got[name, fname] == getattr(cls, fname).offset, (name, fname)
 
 
+def test_binding_constants_match_header(lib):
+    """Every #define of the header that the binding also names has the same value."""
+    text = open(HEADER).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(VBK_[A-Z_0-9]+)\s+(-?\d+)", text)}
+    shared = [k for k in defs if hasattr(lib, k)]
+    assert "VBK_MATVEC_NVARIANTS" in shared and "VBK_OK" in shared
+    for k in shared:
+        assert getattr(lib, k) == defs[k], k
+
+
 def test_status_strings(lib):
     assert lib.vbk_status_str(0) == "ok"
     assert lib.vbk_status_str(4) == "not converged"

@@ -56,7 +56,7 @@ MODELS = {
 
 @pytest.mark.parametrize("name", list(MODELS))
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("variant", list(range(16)))
+@pytest.mark.parametrize("variant", list(range(20)))  # VBK_MATVEC_NVARIANTS
 def test_matvec_parity(vbk, name, precision, variant):
     """Every matvec kernel variant (direct / shared-memory-windowed, 1..8 systems per thread)."""
     desc = MODELS[name]()

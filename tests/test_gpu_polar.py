@@ -41,7 +41,7 @@ def _small():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("variant", list(range(16)))
+@pytest.mark.parametrize("variant", list(range(20)))  # VBK_MATVEC_NVARIANTS
 def test_polar_matvec_parity(vbk, precision, variant):
     desc = _small()
     model = vbk.Model(desc)
