@@ -336,6 +336,55 @@ def _top_kernels(vbk, model, k=5):
 SPAN_STATES_BEND = 0x1 | 0x4 | 0x8  # d, bend x, bend y of the CO2-like model
 
 
+def level_energy(desc, v):
+    """Harmonic level energy E_v = sum_m omega_m (v_m + 1/2) of the neutral (the model's input)."""
+    return float(sum(m["omega"] * (k + 0.5) for m, k in zip(desc["modes"], v)))
+
+
+def open_final_levels(desc, E):
+    """Multi-indices v_f with E_vf < E (open final channels), last mode fastest."""
+    grids = np.meshgrid(*[np.arange(m["n"]) for m in desc["modes"]], indexing="ij")
+    en = sum(m["omega"] * (g + 0.5) for m, g in zip(desc["modes"], grids))
+    return [list(map(int, idx)) for idx in np.argwhere(en < E)]
+
+
+def stencil_points(desc):
+    """Largest number of off-diagonal stencil points of a discrete state: per term q^k the offsets
+    -k, -k+2, .. k of each mode (their product over modes), the zero offset of a diagonal block
+    folded into the diagonal, off-diagonal terms acting in both blocks."""
+    import itertools
+
+    count = [0] * desc["n_states"]
+    for t in desc["terms"]:
+        sets = [range(-k, k + 1, 2) for k in t.get("pow", [0] * len(desc["modes"]))]
+        n = sum(1 for off in itertools.product(*sets) if t["d"] != t["dp"] or any(off))
+        count[t["d"]] += n
+        if t["d"] != t["dp"]:
+            count[t["dp"]] += n
+    return max(count)
+
+
+def fp64_peak_tflops():
+    """FP64 arithmetic roof of this GPU, measured in this run: cuBLAS DGEMM (torch.mm in float64,
+    2048^3), CUDA events around 20 products after 3 untimed ones."""
+    import torch
+
+    n, reps = 2048, 20
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    a = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=gen)
+    b = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=gen)
+    for _ in range(3):
+        torch.mm(a, b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        torch.mm(a, b)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2.0 * n ** 3 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
 def config_extras(vbk, pool, peaks):
     """Configurations 1, 3, 4 and 5 of the workload list, each timed on the GPU (CUDA events) with
     its dominant kernels (a run with per-kernel timing) and the oracle timed beside it."""
@@ -462,9 +511,18 @@ def config_extras(vbk, pool, peaks):
         factor_bytes = nb * K * 5 * S_lv * S_lv * 16
         per_launch = 3 * 2 * 16 * m.N + factor_bytes
         ach = per_launch * la[0] / (la[1] * 1e-3) / 1e9
-        roof3 = {"kernel": "block_apply_wide", "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                 "frac": round(ach / peak, 4), "bytes_per_launch": int(per_launch), "launches": la[0],
-                 "avg_launch_us": round(la[1] * 1e3 / la[0], 1)}
+        # FP64 arithmetic of one apply: per system and block 5 K - 6 products of an S x S complex
+        # level block with a vector (K levels: D_k^-1, L_{k,k-1}, L_{k,k-2} forward, their
+        # transposes backward), 8 flops per complex multiply-add
+        flops = 3 * nb * (5 * K - 6) * S_lv * S_lv * 8
+        tf = flops * la[0] / (la[1] * 1e-3) / 1e12
+        fp64_peak = (peaks or {}).get("fp64_tflops_measured")
+        roof3 = {"kernel": "block_apply_wide", "bound": "fp64", "achieved": round(tf, 3), "peak": fp64_peak,
+                 "unit": "TFLOP/s", "frac": round(tf / fp64_peak, 4) if fp64_peak else None,
+                 "flops_per_launch": int(flops), "peak_source": "cuBLAS DGEMM timed in this run",
+                 "hbm": {"achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "bytes_per_launch": int(per_launch)},
+                 "launches": la[0], "avg_launch_us": round(la[1] * 1e3 / la[0], 1)}
     # the oracle on a reduced basis (sparse LU at 12 x 8 x 8 x 6, N = 13,824)
     rdesc = w.co2_like_model(basis=(12, 8, 8, 6))
     E = o.total_energy(rdesc, 3.0, [0, 0, 0, 0])
@@ -519,7 +577,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     import paper_2307_13483_gb300 as vbk
-    from oracle import vibronic as o
 
     desc, eps, vi = workload()
     if world > 1:  # distinct energies per rank (weak scaling: 256 per rank), no data-path collective
@@ -600,7 +657,7 @@ def main():
     if rank == 0:
         peak = (peaks or {}).get("hbm_gbs") or 6800.0
         nvec = 6
-        E_tot = np.array([o.total_energy(desc, float(e), vi[0]) for e in eps])
+        E_tot = np.array([float(e) + level_energy(desc, vi[0]) for e in eps])
         gen = torch.Generator(device="cuda").manual_seed(2307)
         xm = torch.complex(torch.randn((eps.size, nvec, N), device="cuda", dtype=torch.float64, generator=gen),
                            torch.randn((eps.size, nvec, N), device="cuda", dtype=torch.float64, generator=gen))
@@ -633,13 +690,25 @@ def main():
                                          f"{bpu * nsys_m / 1e6:.0f} MB of algorithmic traffic"}
         vbk.vbk_set_op_timing(model, False)
         del xm
+        # the FP64 operator against the FP64 arithmetic roof (GB300 runs FP64 far below FP32):
+        # per element and system 6 flops for the diagonal product and 4 per stencil point
+        fp64_peak = fp64_peak_tflops()
+        peaks = dict(peaks or {}, fp64_tflops_measured=fp64_peak)
+        if "kernel_us" in matvec_gbs.get("fp64", {}):
+            npts = stencil_points(desc)
+            flops = (6 + 4 * npts) * N * eps.size * nvec
+            tf = flops / (matvec_gbs["fp64"]["kernel_us"] * 1e-6) / 1e12
+            matvec_gbs["fp64"]["alu"] = {"bound": "fp64", "achieved": round(tf, 3), "peak": round(fp64_peak, 3),
+                                         "unit": "TFLOP/s", "frac": round(tf / fp64_peak, 4),
+                                         "flops_per_unit": f"6 + 4 x {npts} stencil points per element and system",
+                                         "peak_source": "cuBLAS DGEMM timed in this run"}
         matvec_gbs["bytes_per_unit"] = "(2c + c/6) N per system: x in, y out, the diagonal once per energy (6 vectors each)"
         matvec_gbs["peak_source"] = "measured" if (peaks or {}).get("hbm_gbs") else "fallback"
 
     extras = {}
     if not args.no_extras and rank == 0:
         # end to end through the public API: host energies in, cross sections back to the host
-        vf = o.open_levels(desc, o.total_energy(desc, float(eps[-1]), vi[0]))
+        vf = open_final_levels(desc, float(eps[-1]) + level_energy(desc, vi[0]))
         vf_h = np.asarray(vf, dtype=np.int32)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -705,7 +774,7 @@ def main():
         pool = OraclePool()
         rate, dt, n_done = pool.rate(eps, vi, eps.size)
         if not args.no_configs:
-            extras["configs"] = config_extras(vbk, pool, load_json("MEASURED_PEAKS.json"))
+            extras["configs"] = config_extras(vbk, pool, peaks)
         pool.close()
         extras["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": pool.cores, "blas_threads": 1, "kind": "oracle",
                                   "sample": f"{n_done} of 256 energies, sparse LU per energy (both waves), one energy per "

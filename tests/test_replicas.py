@@ -96,3 +96,18 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["cores"] == os.cpu_count()  # the oracle runs over every host core
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_bench_level_helpers_match_the_oracle():
+    """The bench's main leg forms total energies and open final levels without the oracle; its
+    host helpers agree with the oracle's definitions (Eq. Econserv, open channels E_vf < E)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads
+    from oracle import vibronic as o
+
+    for desc, vi in ((workloads.ci2d_model(12), [1, 2]), (workloads.co2_like_model(basis=(4, 3, 3, 2)), [1, 0, 2, 1])):
+        for eps in (0.05, 0.7, 2.9):
+            E = eps + bench.level_energy(desc, vi)
+            assert abs(E - o.total_energy(desc, eps, vi)) < 1e-12
+            assert bench.open_final_levels(desc, E) == [list(map(int, v)) for v in o.open_levels(desc, E)]
