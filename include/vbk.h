@@ -280,8 +280,7 @@ int vbk_solve_adjoint(vbk_model* model, int n_eps, const double* eps_i, int n_vi
  *   thread block brings the x windows and diagonal rows of tiles of (systems, rows of the first
  *   mode) into a ring of shared-memory stages by bulk asynchronous copies while the other warps
  *   compute, (systems per tile, row groups, rows per tile, stages) = (4,4,8,2), (4,2,4,2),
- *   (2,2,8,3), (2,4,16,2) (the last with the rows +-2 of a thread's own state in registers where
- *   the model allows); offered when n_states * N_nu / n_basis[0] <= 640, every term involves at
+ *   (2,2,8,3), (2,4,16,2); offered when n_states * N_nu / n_basis[0] <= 640, every term involves at
  *   most two modes and, in VBK_MIXED, N_nu / n_basis[0] is even.  VBK_ERR_INVALID_ARG if the
  *   variant does not fit this model and precision.  Asynchronous on `stream`. */
 int vbk_matvec(vbk_model* model, int n_E, const double* E, int n_vec, const void* x_dev,

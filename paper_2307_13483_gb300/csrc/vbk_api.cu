@@ -575,14 +575,6 @@ int build(const vbk_model_desc* d, vbk_model* m) {
         if ((int)rdesc.size() - dm.rbeg[d] > 64) rok = 0;
     }
     dm.rbeg[m->ns] = (int)rdesc.size();
-    for (int d = 0; d < m->ns; ++d) {  // points of the streaming matvec outside its register rows
-        int gen = 0;
-        for (int q = 0; q < dm.rbeg[d + 1] - dm.rbeg[d]; ++q) {
-            const int c = st_column(wdesc.data(), dm.rbeg[d], d, q, m->stride[0], 2);
-            if (c >= 4) gen = std::max(gen, c - 3);
-        }
-        dm.st_gen2[d] = gen;
-    }
     if (rdesc.empty()) rdesc.push_back(make_int4(0, 0, -1, 0));
     if (wdesc.empty()) wdesc.push_back(make_int4(0, 0, -1, 0));
     if (rct.empty()) rct.push_back(make_float2(0.f, 0.f));

@@ -152,8 +152,6 @@ struct DevModel {
     int rcnt[MAXS][MAXM];
     int rhalo;   // largest distance a neighbour index falls outside [0, N)
     int rok;     // 1 if no point involves more than two modes and no state more than 64 points
-    int st_gen2[MAXS];  // per state: points the streaming matvec reads from shared memory when rows
-                        // within +-2 of the own state are held in registers (st_column with HG = 2)
     // double-float forms for the FP32 refinement path's energy tables (vbk_dfmath.cuh): the
     // interpolants of Dawson's integral and erfcx, the Taylor coefficients of Dawson's
     // integral, the delta = 0 part of U_dd per element, and per channel (a, b, sqrt b,
@@ -499,31 +497,6 @@ bool vbk_cluster_plan(const DevModel& md, ClArgs* a, size_t* smem);
 int vbk_cluster_prepare(const DevModel& md, const ClArgs& a, size_t smem, int* max_clusters);
 cudaError_t vbk_cluster_launch(const DevModel& md, const ClArgs& a, size_t smem, int nclusters, cudaStream_t st);
 
-// Column of point q of state d (points kb .. of `wd`, the windowed-matvec descriptors) in the
-// streaming matvec's per-row tables when the rows within +-HG of the own state are held in
-// registers: slots 0 .. 2 HG - 1 for the first point of each own-state row offset -HG .. -1,
-// 1 .. HG (in-plane offset a multiple of the row length R), then the other points in order.
-__host__ __device__ inline int st_column(const int4* wd, int kb, int d, int q, int R, int HG) {
-    unsigned used = 0;
-    int ng = 0, col = 0;
-    for (int k = 0; k <= q; ++k) {
-        const int4 w = wd[kb + k];
-        const int dp = w.w >> 8, lin = w.y;
-        int slot = -1;
-        if (HG > 0 && dp == d && lin % R == 0) {
-            const int jr = lin / R;
-            if (jr != 0 && jr >= -HG && jr <= HG) slot = jr < 0 ? jr + HG : HG + jr - 1;
-        }
-        if (slot >= 0 && !((used >> slot) & 1u)) {
-            used |= 1u << slot;
-            col = slot;
-        } else {
-            col = 2 * HG + ng++;
-        }
-    }
-    return col;
-}
-
 // Streaming batched matvec (vbk_stream.cu): persistent CTAs over tiles of S systems x TR rows of
 // mode 0 (all states), the x windows and diagonal rows of each tile brought into a ring of nst
 // shared-memory stages by bulk asynchronous copies.  Offered for models with n_s N_nu / n_0 <= 640
@@ -533,7 +506,7 @@ struct StreamPlan {
     int S = 1, RG = 1, TR = 1, nst = 2;         // systems per tile, row groups, rows per tile, stages
     int ndg = 1;                                // diagonal buffers per stage (energies staged per tile)
     int R = 0, nstrip = 0, lo = 0, W = 0;  // row length, strips, window start offset and length
-    int HG = 0, npg = 0, np = 0;  // own-state rows held in registers each side; window points; table columns
+    int npg = 0, np = 0;  // stencil points per state (padded); table columns
     int threads = 0;
     unsigned stage_bytes = 0, win_bytes = 0;  // bytes of one stage; of which the x windows
     size_t smem = 0;                          // dynamic shared memory of a CTA

@@ -3713,12 +3713,12 @@ inline bool mv_valid(const DevModel& md, int v, size_t c) {
     if (c == 16 && (mv_sys(v) * mv_ept(v) > 8 || v == 7)) return false;  // FP64: register budget
     return mv_tiled_smem(md, v, c) >= 0;
 }
-inline int matvec_partials_v(const DevModel& md, int v) {
+// partial sums per system that variant v writes for entries of c bytes (8: FP32, 16: FP64)
+inline int matvec_partials_v(const DevModel& md, int v, size_t c) {
     if (md.nsc) v = 8;
-    if (v >= MV_NWIN) {  // one partial per strip (the plan's strip count is the same in FP32 and FP64)
+    if (v >= MV_NWIN) {  // one partial per strip of the plan of this precision
         StreamPlan sp;
-        if (vbk_stream_plan(md, v - MV_NWIN, 16, &sp) || vbk_stream_plan(md, v - MV_NWIN, 8, &sp)) return sp.nstrip;
-        return 1;
+        return vbk_stream_plan(md, v - MV_NWIN, c, &sp) ? sp.nstrip : 1;
     }
     if (v >= 12) return (md.Nnu + TPB * mv_ept(v) - 1) / (TPB * mv_ept(v));  // one CTA per tile of all states
     if (v >= 10) return 1;
@@ -3751,7 +3751,7 @@ void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, co
         // q-dependent coupling: the two passes of the sandwich product (whatever variant was asked)
         if (nlist == 0) return;
         rn.go("sandwich_w", k_sand_w<T>, dim3(cdiv_u(md.Nnu, TPB), nlist), dim3(TPB), md, sys_e, sel, (int)nlist, x, xs);
-        rn.go(name, k_matvec_sw<T>, dim3((unsigned)matvec_partials_v(md, 8), nlist), dim3(TPB), md, sys_e, sel, (int)nlist,
+        rn.go(name, k_matvec_sw<T>, dim3((unsigned)matvec_partials_v(md, 8, sizeof(cx<T>)), nlist), dim3(TPB), md, sys_e, sel, (int)nlist,
               diag, x, xs, y, ys, b, part, red);
         return;
     }
@@ -3768,7 +3768,7 @@ void launch_matvec_v(Runner& rn, int v, const char* name, const DevModel& md, co
         return;
     }
     const int S = mv_sys(v);
-    const dim3 g((unsigned)matvec_partials_v(md, v), (nlist + S - 1) / S);
+    const dim3 g((unsigned)matvec_partials_v(md, v, sizeof(cx<T>)), (nlist + S - 1) / S);
     const size_t smem = (v >= 4 && v < 8) ? (size_t)mv_tiled_smem(md, v, sizeof(cx<T>)) : 0;
     if (v >= 12) {
         int lo, wst;
@@ -3940,7 +3940,7 @@ void launch_matvec(Runner& rn, const char* name, const DevModel& md, const int* 
     launch_matvec_v<T>(rn, variant < 0 ? (sizeof(T) == 4 ? 1 : 3) : variant, name, md, sys_e, sel, nlist, diag, x, xs, y, ys, b,
                        part, red);
 }
-inline int matvec_partials(const DevModel& md, int variant) { return matvec_partials_v(md, variant); }
+inline int matvec_partials(const DevModel& md, int variant, size_t c) { return matvec_partials_v(md, variant, c); }
 
 // L D L^T factors of every block of every energy (Sec. III.B: computed once per energy and
 // stored): thread-per-block kernel for narrow bands, band assembly + one CTA per block for
@@ -4034,9 +4034,11 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
     // ---- workspace
     const size_t NN = (size_t)N;
     const int nb_e = (int)cdiv_u(N, TPB);       // element-wise kernels
-    int nb_mv = matvec_partials(md, mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0 ? 0 : mdl->mv_variant[sizeof(R) == 4 ? 0 : 1]);
+    int nb_mv = matvec_partials(md, mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] < 0 ? 0 : mdl->mv_variant[sizeof(R) == 4 ? 0 : 1],
+                                sizeof(cx<R>));
     int nb_mv_max = 0;  // the largest partial count of any variant
-    for (int v = 0; v < MV_NVAR; ++v) nb_mv_max = std::max(nb_mv_max, matvec_partials(md, v));
+    for (int v = 0; v < MV_NVAR; ++v)  // either precision: the FP64 residual shares the buffers
+        nb_mv_max = std::max(nb_mv_max, std::max(matvec_partials(md, v, 8), matvec_partials(md, v, 16)));
     const int nb_v = (int)cdiv_u(N, VCHUNK);    // basis-vector kernels
     const int nb_b = block ? block_partials(pbuf) : 0;
     const int nslot = std::max(std::max(nb_e, nb_mv_max), std::max(nb_b, nb_v * (mres + 1)));
@@ -4288,7 +4290,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             cudaMemsetAsync(olist, 0xff, nsys * sizeof(int), st);  // -1: no system
             cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
             rn.go("outer_check", k_outer_check, dim3(gs), dim3(128), nsys, sst, outer, inner, (const double2*)partA,
-                  it == 0 || dfr_res ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1]),
+                  it == 0 || dfr_res ? 1 : dfr ? df_partials(md) : matvec_partials(md, mdl->mv_variant[1] < 0 ? 3 : mdl->mv_variant[1], 16),
                   it == 0 ? job.bnorm2 : (const double*)nullptr, it == 0 ? 1 : 0, o.tol, mixed ? o.inner_tol : 0.0, o.max_refine, o.max_iter,
                   mixed && method == VBK_COCG ? o.inner_max_iter : 0, mixed && method == VBK_COCG ? 1 : 0, cnt, olist,
                   ilist);
@@ -4354,7 +4356,7 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     }
                 }
                 const int mvv = mdl->mv_variant[sizeof(R) == 4 ? 0 : 1];
-                nb_mv = matvec_partials(md, mvv < 0 ? (sizeof(R) == 4 ? 1 : 3) : mvv);
+                nb_mv = matvec_partials(md, mvv < 0 ? (sizeof(R) == 4 ? 1 : 3) : mvv, sizeof(cx<R>));
                 // one COCG iteration for the systems of the inner list
                 auto cocg_iter = [&](unsigned ny) {
                     const Sel sc{ilist, inner};

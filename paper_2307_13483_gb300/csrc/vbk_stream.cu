@@ -10,10 +10,11 @@
 //
 // Persistent CTAs walk tiles (S systems, a strip of TR rows of every state).  A tile needs, per
 // system and state plane, the contiguous window of x that its rows reach (the strip widened by
-// the smallest and largest in-plane offset) and the strip's rows of the diagonal table.  One
-// thread issues them as bulk asynchronous copies (cp.async.bulk, the TMA engine's untiled
-// form) into a ring of shared-memory stages, each stage with an mbarrier that counts the bytes
-// in; while the CTA computes tile i, the copies of tiles i+1 .. i+stages-1 are in flight.  Each
+// the smallest and largest in-plane offset) and the strip's rows of the diagonal table.  A
+// producer warp issues them as bulk asynchronous copies (cp.async.bulk, the TMA engine's untiled
+// form) into a ring of shared-memory stages, each stage with a "full" mbarrier that counts the
+// bytes in and an "empty" one the consumer warps arrive on when they are done with it; while
+// the consumers compute tile i, the copies of the next tiles are in flight.  Each consumer
 // thread owns one (state, in-row position) and TR / RG rows of a tile: its factors of the
 // in-row modes stay in registers for the whole launch, the factors of mode 0 come from a table
 // in shared memory (one broadcast load per point and row), and every neighbour is read from the
@@ -35,7 +36,7 @@ __device__ unsigned int g_vbk_stream_fault = 0;
 namespace {
 
 constexpr int ST_NPM = 16;                          // stencil points per state (padded with zero points)
-constexpr int ST_MAXT = 640;                        // consumer threads per CTA at most
+constexpr int ST_MAXT = 640;                        // consumer threads per CTA at most (and one producer warp)
 constexpr int ST_SMALLT = 352;                      // blocks of at most this many threads: two per SM
 constexpr size_t ST_SMEM_MAX = 220 * 1024;          // dynamic shared memory of a CTA at most
 constexpr unsigned long long ST_WAIT_NS = 2000000000ull;  // a stage barrier wait gives up after 2 s
@@ -128,6 +129,13 @@ __device__ __forceinline__ void st_wait(unsigned bar, unsigned par) {
 // barrier over the consumer warps only (named barrier 1; the producer warp is not part of it)
 __device__ __forceinline__ void st_cons_sync(int ncons) { asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory"); }
 
+// The S systems' entries of one window slot (the systems' windows lie `sysb` bytes apart).
+template <class R, int S>
+__device__ __forceinline__ void st_load_sys(const unsigned char* p, int sysb, cx<R> (&v)[S]) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) v[k] = *reinterpret_cast<const cx<R>*>(p + k * sysb);
+}
+
 // Systems of tile t: list entries [g S, g S + S) of strip si (-1: no system / retired).
 template <int S>
 __device__ __forceinline__ void st_tile(const StreamPlan& p, int t, int nlist, const int* list, const int* act, int (&sy)[S],
@@ -146,24 +154,21 @@ __device__ __forceinline__ void st_tile(const StreamPlan& p, int t, int nlist, c
     }
 }
 
-// HG: own-state rows held in registers on either side of a thread's row (0 or 2); NPG: points
-// read from the staged windows (padded with zero points); PLAIN: y = A x with no residual form
-// and no partial sums (b == null, red == 0)
-// MAXT: launch bound (consumer threads + 32); MINB: thread blocks per SM it is compiled for
-template <class R, int S, int HG, int NPG, bool PLAIN, int MAXT, int MINB>
+// NPG: stencil points per state (padded with zero points); PLAIN: y = A x with no residual form
+// and no partial sums (b == null, red == 0); MAXT, MINB: launch bounds.
+template <class R, int S, int NPG, bool PLAIN, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, StreamPlan p, const int* __restrict__ sys_e,
-                                                            const int* __restrict__ list, const int* __restrict__ act,
-                                                            int nlist, const cx<R>* __restrict__ diag,
-                                                            const cx<R>* __restrict__ x, long long xs,
-                                                            cx<R>* __restrict__ y, long long ys,
-                                                            const double2* __restrict__ b, double2* __restrict__ part,
-                                                            int red) {
+                                                             const int* __restrict__ list, const int* __restrict__ act,
+                                                             int nlist, const cx<R>* __restrict__ diag,
+                                                             const cx<R>* __restrict__ x, long long xs,
+                                                             cx<R>* __restrict__ y, long long ys,
+                                                             const double2* __restrict__ b, double2* __restrict__ part,
+                                                             int red) {
     using C = cx<R>;
     using CR = typename StCoef<R>::T;
     using CR2 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;  // two table entries
-    constexpr int NPS = 2 * HG;       // register-row points
-    constexpr int NPT = NPS + NPG;    // table columns per (state, row)
-    constexpr int NW = 2 * HG + 1;    // rows of a thread's register window
+    constexpr int NPT = NPG;    // table columns per (state, row)
+    constexpr int NPROD = 32;   // one producer warp
     static_assert(NPT % 2 == 0, "table rows are read in pairs");
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long fullb[ST_MAXSTAGE], emptyb[ST_MAXSTAGE];
@@ -171,17 +176,20 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
     __shared__ C redsh[32][S];
     const int tid = threadIdx.x, ns = md.ns, Nnu = md.Nnu, N = md.N, nb0 = md.nb[0];
     const int Rl = p.R, plane = ns * Rl;
-    const int ncons = (int)blockDim.x - 32;  // consumer threads: warps 1 ..
-    const int ct = tid - 32;
+    const int ncons = (int)blockDim.x - NPROD;  // consumer threads: the warps after the producers
+    const int ct = tid - NPROD;
     const bool live = ct >= 0 && ct < p.RG * plane;
     const int rg = live ? ct / plane : 0;
     const int rem = live ? ct - rg * plane : 0;
     const int d = rem / Rl, col = rem - d * Rl;
     CR* cgt = reinterpret_cast<CR*>(sm + (size_t)p.nst * p.stage_bytes);  // [ns][nb0][NPT] factors of mode 0
     const R* tab = st_tab<R>(md);
+    // bytes between one window slot and the next, and between two systems' windows
+    constexpr int slotb = (int)sizeof(C);
+    const int sysb = ns * p.W * (int)sizeof(C);
 
     // this thread's factors of the in-row modes (table column order) and the byte offsets of the
-    // window points within a window
+    // stencil points within the windows
     CR cu[NPT];
     int off[NPG];
 #pragma unroll
@@ -193,9 +201,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
 #pragma unroll
         for (int m = 0; m < MAXM; ++m) n[m] = (m >= 1 && m < md.M) ? (col / md.stride[m]) % md.nb[m] : 0;
         const int kb = md.rbeg[d], cnt = md.rbeg[d + 1] - kb;
-        for (int q = 0; q < cnt; ++q) {
-            const int c = st_column(md.wdesc, kb, d, q, Rl, HG);
-            if (c >= NPT) continue;  // not reached: the plan sizes NPG for every state
+        for (int q = 0; q < cnt && q < NPG; ++q) {
             const int m1 = st_primary(md, d, q);
             const int4 w = md.wdesc[kb + q];
             const int m2 = w.w & 0xff, dp = w.w >> 8;
@@ -203,26 +209,24 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
             if (m1 >= 1) v *= row_val<R>(md, w.x / 8 + st_sel(n, m1));
             if (w.z >= 0 && m2 >= 1) v *= tab[w.z + st_sel(n, m2)];
 #pragma unroll
-            for (int j = 0; j < NPT; ++j)
-                if (j == c) cu[j] = st_pack(v);
-#pragma unroll
             for (int j = 0; j < NPG; ++j)
-                if (j + NPS == c) off[j] = ((dp - d) * p.W + w.y) * (int)sizeof(C);
+                if (j == q) {
+                    cu[j] = st_pack(v);
+                    off[j] = ((dp - d) * p.W + w.y) * slotb;
+                }
         }
     }
-    // factors of mode 0 for every (state, row, table column)
+    // factors of mode 0 for every (state, row, point)
     for (int i = tid; i < ns * nb0 * NPT; i += blockDim.x) {
-        const int dd = i / (nb0 * NPT), r2 = i - dd * nb0 * NPT, g = r2 / NPT, c = r2 - g * NPT;
+        const int dd = i / (nb0 * NPT), r2 = i - dd * nb0 * NPT, g = r2 / NPT, q = r2 - g * NPT;
         const int kb = md.rbeg[dd], cnt = md.rbeg[dd + 1] - kb;
         R v = (R)0;
-        for (int q = 0; q < cnt; ++q) {
-            if (st_column(md.wdesc, kb, dd, q, Rl, HG) != c) continue;
+        if (q < cnt) {
             const int m1 = st_primary(md, dd, q);
             const int4 w = md.wdesc[kb + q];
             v = (R)1;
             if (m1 == 0) v *= row_val<R>(md, w.x / 8 + g);
             if (w.z >= 0 && (w.w & 0xff) == 0) v *= tab[w.z + g];
-            break;
         }
         cgt[i] = st_pack(v);
     }
@@ -241,9 +245,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
     }
     __syncthreads();  // the only block-wide barrier: the producer warp leaves the loop below early
 
-    if (tid < 32) {
+    if (tid < NPROD) {
         // ------------------------------------------------------------ producer warp
-        const int lane = tid;
+        const int lane = tid & 31;
         int it = 0;
         // the systems and energies of 32 tiles at a time, one tile per lane (their global loads
         // overlap instead of forming one dependent chain per tile)
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
                 se[k] = __shfl_sync(0xffffffffu, bse[k], it & 31);
             }
             si = __shfl_sync(0xffffffffu, bsi, it & 31);
-            // up to two energies of the tile get their diagonal rows staged (buffers 0 and 1)
+            // up to ndg energies of the tile get their diagonal rows staged
 #pragma unroll
             for (int k = 0; k < S; ++k) {
                 slot[k] = -1;
@@ -285,22 +289,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
             if (u > 0) st_wait(ebase + 8u * s, (unsigned)((u - 1) & 1));  // the consumers released the stage
             const int g0 = si * p.TR, tre = min(p.TR, nb0 - g0);
             const long long wst = (long long)g0 * Rl + p.lo;
-            const long long a0 = wst > 0 ? wst : 0, a1 = min(wst + p.W, (long long)Nnu);
             unsigned char* stg = sm + (size_t)s * p.stage_bytes;
-            if (wst < 0 || wst + p.W > Nnu) {
-                // window slots outside the basis: zero (their coefficients are zero; the slots
-                // must hold finite values)
-                const int f0 = (int)(a0 - wst), b0 = (int)(a1 - wst), nz = f0 + (p.W - b0);
-#pragma unroll
-                for (int k = 0; k < S; ++k) {
-                    if (sy[k] < 0) continue;
-                    for (int dp = 0; dp < ns; ++dp) {
-                        C* w = reinterpret_cast<C*>(stg) + (size_t)(k * ns + dp) * p.W;
-                        for (int j = lane; j < nz; j += 32) w[j < f0 ? j : b0 + (j - f0)] = mkc<R>(0, 0);
-                    }
-                }
-            }
-            if (lane == 0) {
+            const unsigned st0 = sbase + (unsigned)s * p.stage_bytes;
+            const unsigned bar = fbase + 8u * s;
+            if (tid == 0) {
 #pragma unroll
                 for (int k = 0; k < S; ++k) {
                     info[s][k] = sy[k];
@@ -309,33 +301,49 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
                 }
                 info[s][3 * S] = si;
             }
-            __syncwarp();
-            if (lane == 0) {
-                const unsigned wb = a1 > a0 ? (unsigned)((a1 - a0) * (long long)sizeof(C)) : 0u;
-                const unsigned db = (unsigned)(tre * Rl * (int)sizeof(C));
-                const unsigned total = (unsigned)nact * ns * wb + (ea >= 0 ? ns * db : 0u) + (eb >= 0 ? ns * db : 0u);
-                // generic-proxy accesses of this stage (the consumers' reads, the zero fill)
-                // come before the copy engine writes it
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const unsigned bar = fbase + 8u * s;
-                mbar_arrive_expect(bar, total);  // release: the zeros and info[s] are visible after the wait
-                const unsigned st0 = sbase + (unsigned)s * p.stage_bytes;
+            {
+                const long long a0 = wst > 0 ? wst : 0, a1 = min(wst + p.W, (long long)Nnu);
+                if (wst < 0 || wst + p.W > Nnu) {
+                    // window slots outside the basis: zero (their coefficients are zero; the
+                    // slots must hold finite values)
+                    const int f0 = (int)(a0 - wst), b0 = (int)(a1 - wst), nz = f0 + (p.W - b0);
 #pragma unroll
-                for (int k = 0; k < S; ++k) {
-                    if (sy[k] < 0 || wb == 0) continue;
-                    for (int dp = 0; dp < ns; ++dp) {
-                        const C* src = x + (long long)sy[k] * xs + (long long)dp * Nnu + a0;
-                        const unsigned dst =
-                            st0 + (unsigned)(((long long)(k * ns + dp) * p.W + (a0 - wst)) * (long long)sizeof(C));
-                        bulk_g2s(dst, src, wb, bar);
+                    for (int k = 0; k < S; ++k) {
+                        if (sy[k] < 0) continue;
+                        for (int dp = 0; dp < ns; ++dp) {
+                            C* w = reinterpret_cast<C*>(stg) + (size_t)(k * ns + dp) * p.W;
+                            for (int j = lane; j < nz; j += 32) w[j < f0 ? j : b0 + (j - f0)] = mkc<R>(0, 0);
+                        }
                     }
                 }
-                for (int j = 0; j < 2; ++j) {
-                    const int e = j == 0 ? ea : eb;
-                    if (e < 0) continue;
-                    for (int dp = 0; dp < ns; ++dp) {
-                        const C* src = diag + (long long)e * N + (long long)dp * Nnu + (long long)g0 * Rl;
-                        bulk_g2s(st0 + p.win_bytes + j * dbytes + (unsigned)(dp * p.TR * Rl * (int)sizeof(C)), src, db, bar);
+                __syncwarp();
+                if (lane == 0) {
+                    const unsigned wb = a1 > a0 ? (unsigned)((a1 - a0) * (long long)sizeof(C)) : 0u;
+                    const unsigned db = (unsigned)(tre * Rl * (int)sizeof(C));
+                    const unsigned total =
+                        (unsigned)nact * ns * wb + (ea >= 0 ? ns * db : 0u) + (eb >= 0 ? ns * db : 0u);
+                    // generic-proxy accesses of this stage (the consumers' reads, the zero fill)
+                    // come before the copy engine writes it
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive_expect(bar, total);  // release: the zeros and info[s] are visible after the wait
+#pragma unroll
+                    for (int k = 0; k < S; ++k) {
+                        if (sy[k] < 0 || wb == 0) continue;
+                        for (int dp = 0; dp < ns; ++dp) {
+                            const C* src = x + (long long)sy[k] * xs + (long long)dp * Nnu + a0;
+                            const unsigned dst =
+                                st0 + (unsigned)(((long long)(k * ns + dp) * p.W + (a0 - wst)) * (long long)sizeof(C));
+                            bulk_g2s(dst, src, wb, bar);
+                        }
+                    }
+                    for (int jd = 0; jd < 2; ++jd) {
+                        const int e = jd == 0 ? ea : eb;
+                        if (e < 0) continue;
+                        for (int dp = 0; dp < ns; ++dp) {
+                            const C* src = diag + (long long)e * N + (long long)dp * Nnu + (long long)g0 * Rl;
+                            bulk_g2s(st0 + p.win_bytes + jd * dbytes + (unsigned)(dp * p.TR * Rl * (int)sizeof(C)), src,
+                                     db, bar);
+                        }
                     }
                 }
             }
@@ -351,8 +359,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
 
     // ---------------------------------------------------------------- consumer warps
     const int cw = ct >> 5, clane = ct & 31;
-    const int trt = p.TR / p.RG;  // rows of a tile per thread (consecutive: the register window slides)
-    const int rowb = Rl * (int)sizeof(C);
+    const int trt = p.TR / p.RG;  // rows of a tile per thread
+    const int rowb = Rl * slotb;  // bytes between a slot and the same slot one row further
     for (int it = 0;; ++it) {
         const int t = blockIdx.x + it * G;
         if (t >= ntile) break;
@@ -374,37 +382,27 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
         const int r0 = rg * trt, r1 = min(r0 + trt, tre);
         if (live && r0 < r1) {
             const unsigned char* dgs = stg + p.win_bytes + (size_t)d * p.TR * Rl * sizeof(C);
-            const size_t sstride = (size_t)ns * p.W * sizeof(C);  // bytes between two systems' windows
-            const unsigned char* wself = stg + ((size_t)d * p.W + (size_t)(r0 * Rl + col - p.lo)) * sizeof(C);
-            C X[S][NW];  // own-state rows r - HG .. r + HG of this column
-#pragma unroll
-            for (int k = 0; k < S; ++k)
-#pragma unroll
-                for (int i = 0; i < NW; ++i) X[k][i] = *reinterpret_cast<const C*>(wself + k * sstride + (i - HG) * rowb);
+            const unsigned char* wself = stg + (size_t)(d * p.W + (r0 * Rl + col - p.lo)) * slotb;
             for (int r = r0; r < r1; ++r, wself += rowb) {
                 const int el = r * Rl + col;
                 const CR2* cg2 = reinterpret_cast<const CR2*>(cgt + ((size_t)d * nb0 + g0 + r) * NPT);
                 const long long gi = (long long)d * Nnu + (long long)g0 * Rl + el;
-                C acc[S];
+                C xi[S], acc[S];
+                st_load_sys<R, S>(wself, sysb, xi);
 #pragma unroll
                 for (int k = 0; k < S; ++k) {
                     C dg;
                     if (slot[k] >= 0) dg = *reinterpret_cast<const C*>(dgs + (size_t)slot[k] * dbytes + (size_t)el * sizeof(C));
                     else dg = se[k] >= 0 ? diag[(long long)se[k] * N + gi] : mkc<R>(0, 0);
-                    acc[k] = cmul<R>(dg, X[k][HG]);
+                    acc[k] = cmul<R>(dg, xi[k]);
                 }
-                // table column j: coefficient c_j = (mode-0 factor of the row) (in-row factor of the
-                // thread); register rows first, then the window points (zero points past a
-                // state's count add 0 * x(self))
-                auto apply = [&](int j, CR cj) {
-                    if (j < NPS) {
+                // point q: coefficient c_q = (mode-0 factor of the row) (in-row factor of the
+                // thread); zero points (past a state's count) add 0 * x(self)
+                auto apply = [&](int q, CR cq) {
+                    C v[S];
+                    st_load_sys<R, S>(wself + off[q], sysb, v);
 #pragma unroll
-                        for (int k = 0; k < S; ++k) acc[k] = st_fma(cj, X[k][j < HG ? j : j + 1], acc[k]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < S; ++k)
-                            acc[k] = st_fma(cj, *reinterpret_cast<const C*>(wself + k * sstride + off[j - NPS]), acc[k]);
-                    }
+                    for (int k = 0; k < S; ++k) acc[k] = st_fma(cq, v[k], acc[k]);
                 };
 #pragma unroll
                 for (int j = 0; j < NPT / 2; ++j) {
@@ -427,18 +425,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
                     }
                     y[(long long)sy[k] * ys + gi] = out;
                     if (PLAIN) continue;
-                    if (red == 1) loc[k] = cfma<R>(X[k][HG], out, loc[k]);
+                    if (red == 1) loc[k] = cfma<R>(xi[k], out, loc[k]);
                     else if (red == 2) {
                         const float ox = (float)out.x, oy = (float)out.y;  // norm for the stopping test: FP32 suffices
                         loc[k].x += (R)(ox * ox + oy * oy);
-                    }
-                }
-                if (r + 1 < r1) {  // slide the window one row down
-#pragma unroll
-                    for (int k = 0; k < S; ++k) {
-#pragma unroll
-                        for (int i = 0; i + 1 < NW; ++i) X[k][i] = X[k][i + 1];
-                        X[k][NW - 1] = *reinterpret_cast<const C*>(wself + k * sstride + (HG + 1) * rowb);
                     }
                 }
             }
@@ -464,17 +454,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
     }
 }
 
-// instantiated shapes: S = 2 with (HG, NPG) in {(0, 8), (0, 16), (2, 4), (2, 8)}; S = 4 with
-// (0, 8), (0, 16) (a register window of four systems would not fit the register budget)
-// and each of them for up to 672 threads (one block per SM) or up to 352 threads (two blocks)
-template <class R, int S, int HG, int NPG, int MAXT, int MINB> void* st_kptr_p(bool plain) {
-    return plain ? (void*)k_matvec_stream<R, S, HG, NPG, true, MAXT, MINB>
-                 : (void*)k_matvec_stream<R, S, HG, NPG, false, MAXT, MINB>;
+// instantiated shapes: S in {2, 4}, NPG in {8, 16}; each for up to 672 threads (one block per
+// SM) or up to 352 threads (two blocks per SM)
+template <class R, int S, int NPG, int MAXT, int MINB> void* st_kptr_p(bool plain) {
+    return plain ? (void*)k_matvec_stream<R, S, NPG, true, MAXT, MINB> : (void*)k_matvec_stream<R, S, NPG, false, MAXT, MINB>;
+}
+template <class R, int S, int MAXT, int MINB> void* st_kptr_n(const StreamPlan& p, bool plain) {
+    return p.npg == 8 ? st_kptr_p<R, S, 8, MAXT, MINB>(plain) : st_kptr_p<R, S, 16, MAXT, MINB>(plain);
 }
 template <class R, int MAXT, int MINB> void* st_kptr_t(const StreamPlan& p, bool plain) {
-    if (p.S == 4) return p.npg == 8 ? st_kptr_p<R, 4, 0, 8, MAXT, MINB>(plain) : st_kptr_p<R, 4, 0, 16, MAXT, MINB>(plain);
-    if (p.HG == 2) return p.npg == 4 ? st_kptr_p<R, 2, 2, 4, MAXT, MINB>(plain) : st_kptr_p<R, 2, 2, 8, MAXT, MINB>(plain);
-    return p.npg == 8 ? st_kptr_p<R, 2, 0, 8, MAXT, MINB>(plain) : st_kptr_p<R, 2, 0, 16, MAXT, MINB>(plain);
+    return p.S == 4 ? st_kptr_n<R, 4, MAXT, MINB>(p, plain) : st_kptr_n<R, 2, MAXT, MINB>(p, plain);
 }
 template <class R> void* st_kernel_ptr(const StreamPlan& p, bool plain) {
     return p.threads <= ST_SMALLT ? st_kptr_t<R, ST_SMALLT, 2>(p, plain) : st_kptr_t<R, ST_MAXT + 32, 1>(p, plain);
@@ -494,7 +483,7 @@ int st_num_sms() {
 constexpr int ST_NDEV = 16;
 int st_optin[ST_NDEV][64] = {};
 int st_kidx(bool fp32, const StreamPlan& p, bool plain) {
-    const int shape = p.HG == 2 ? (p.npg == 4 ? 2 : 3) : (p.npg == 8 ? 0 : 1);
+    const int shape = p.npg == 8 ? 0 : 1;
     return (p.threads <= ST_SMALLT ? 32 : 0) + (fp32 ? 0 : 16) + (p.S == 2 ? 0 : 8) + shape * 2 + (plain ? 1 : 0);
 }
 
@@ -513,8 +502,8 @@ cudaError_t st_ensure_optin(bool fp32, const StreamPlan& p, bool plain) {
 }  // namespace
 
 // Tile shapes offered to the autotuner: (systems per tile, row groups, rows per tile, stages,
-// own-state rows in registers where the model allows, diagonal buffers per stage).
-static const int ST_CFG[][6] = {{4, 4, 8, 2, 0, 2}, {4, 2, 4, 2, 0, 2}, {2, 2, 8, 3, 0, 1}, {2, 4, 16, 2, 1, 1}};
+// diagonal buffers per stage).
+static const int ST_CFG[][5] = {{4, 4, 8, 2, 2}, {4, 2, 4, 2, 2}, {2, 2, 8, 3, 1}, {2, 4, 16, 2, 1}};
 
 int vbk_stream_nconfig() { return (int)(sizeof(ST_CFG) / sizeof(ST_CFG[0])); }
 
@@ -527,32 +516,23 @@ bool vbk_stream_plan(const DevModel& md, int cfg, size_t c, StreamPlan* out) {
     p.R = md.Nnu / nb0;
     const int plane = md.ns * p.R;
     if (plane > ST_MAXT || p.R < 1) return false;
-    int np = 0, gen2 = 0, lo = 0, hi = 0;
+    int np = 0, lo = 0, hi = 0;
     for (int d = 0; d < md.ns; ++d) {
         np = std::max(np, md.rbeg[d + 1] - md.rbeg[d]);
-        gen2 = std::max(gen2, md.st_gen2[d]);
         lo = std::min(lo, md.lmin[d]);
         hi = std::max(hi, md.lmax[d]);
     }
-    // own-state rows +-2 in registers when the windows reach them and the other points fit
-    // (two systems per tile: four systems' windows would not fit the register budget)
-    if (ST_CFG[cfg][4] && p.S == 2 && lo <= -2 * p.R && hi >= 2 * p.R && gen2 <= 8) {
-        p.HG = 2;
-        p.npg = gen2 <= 4 ? 4 : 8;
-    } else {
-        if (np > ST_NPM) return false;
-        p.HG = 0;
-        p.npg = np <= 8 ? 8 : ST_NPM;
-    }
-    p.np = 2 * p.HG + p.npg;  // table columns per (state, row)
-    if (c == 8) {  // 16-byte copies of 8-byte entries: even offsets, sizes and row lengths
+    if (np > ST_NPM) return false;
+    p.npg = np <= 8 ? 8 : ST_NPM;
+    p.np = p.npg;  // table columns per (state, row)
+    if (c == 8) {  // 16-byte bulk copies of 8-byte entries: even offsets, sizes and row lengths
         if (p.R & 1) return false;
         lo = -((-lo + 1) & ~1);
         hi = (hi + 1) & ~1;
     }
     p.lo = lo;
     p.nst = ST_CFG[cfg][3];
-    p.ndg = ST_CFG[cfg][5];
+    p.ndg = ST_CFG[cfg][4];
     const int rg = std::max(1, std::min(ST_CFG[cfg][1], ST_MAXT / plane));
     int tr = std::max(1, std::min(ST_CFG[cfg][2], nb0));
     for (;;) {
@@ -567,7 +547,7 @@ bool vbk_stream_plan(const DevModel& md, int cfg, size_t c, StreamPlan* out) {
         if (p.smem <= ST_SMEM_MAX || tr == 1) break;
         tr = (tr + 1) / 2;  // wide entries (FP64): shorter strips
     }
-    p.threads = 32 + ((p.RG * plane + 31) / 32) * 32;  // a producer warp and the consumer warps
+    p.threads = 32 + ((p.RG * plane + 31) / 32) * 32;  // a producer warp, then the consumer warps
     if (p.smem > ST_SMEM_MAX) return false;
     *out = p;
     return true;
@@ -578,7 +558,7 @@ cudaError_t vbk_stream_matvec(const DevModel& md, const StreamPlan& p, const int
                               const double2* b, double2* part, int red, bool fp32, cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
     const size_t c = fp32 ? 8 : 16;
-    // the copies need 16-byte aligned sources: vector starts and the system strides
+    // bulk copies need 16-byte aligned sources: vector starts and the system strides
     if (((uintptr_t)x & 15) || ((uintptr_t)diag & 15) || ((xs * (long long)c) & 15)) return cudaErrorMisalignedAddress;
     // the opt-in is made outside any stream capture by vbk_stream_prepare (model preparation)
     const bool plain = b == nullptr && red == 0;
