@@ -172,11 +172,16 @@ typedef struct {
     int inner_max_iter; /* VBK_MIXED COCG: iterations of one FP32 inner solve before it ends
                           and the refinement residual restarts it (complex-FP32 COCG can stagnate
                           short of inner_tol on hard systems); 0 = no cap                    */
+    int matvec_variant; /* -1: the autotuned (or default) kernel variant of the batched matvec on
+                          the grid-wide paths; 0 .. VBK_MATVEC_NVARIANTS - 1: that variant (see
+                          vbk_matvec) for the Krylov operator and the FP64 residual, wherever it
+                          is valid for their precision; VBK_ERR_INVALID_ARG if it is valid for
+                          neither.  Not used by the one-block-per-system paths (resident 1..3)  */
 } vbk_opts;
 
 /* Fills `o` with defaults: GMRES, VBK_MIXED, Jacobi, restart 64, max_iter 20000,
  * max_refine 40, tol 1e-8, inner_tol 1e-5, check_every 8, timing 0, autotune 1, resident 1,
- * inner_max_iter 2000. */
+ * inner_max_iter 2000, matvec_variant -1. */
 void vbk_default_opts(vbk_opts* o);
 
 typedef struct {

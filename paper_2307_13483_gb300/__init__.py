@@ -72,6 +72,7 @@ class vbk_opts(C.Structure):
         ("autotune", C.c_int),
         ("resident", C.c_int),
         ("inner_max_iter", C.c_int),
+        ("matvec_variant", C.c_int),
     ]
 
 

@@ -1335,6 +1335,7 @@ void vbk_default_opts(vbk_opts* o) {
     o->autotune = 1;
     o->resident = 1;
     o->inner_max_iter = 2000;
+    o->matvec_variant = -1;
 }
 
 int vbk_build_model(const vbk_model_desc* desc, vbk_model** out) {
@@ -1406,6 +1407,8 @@ static int check_opts(const vbk_opts* o) {
     if (o->precond_span < -1) return invalid("precond_span must be -1 or a span mask");
     if (o->inner_max_iter < 0) return invalid("inner_max_iter must be >= 0");
     if (o->resident < 0 || o->resident > 3) return invalid("resident must be 0, 1, 2 or 3");
+    if (o->matvec_variant < -1 || o->matvec_variant >= VBK_MATVEC_NVARIANTS)
+        return invalid("matvec_variant must be -1 or a variant index");
     return VBK_OK;
 }
 

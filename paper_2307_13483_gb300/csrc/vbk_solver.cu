@@ -3664,7 +3664,7 @@ inline int block_partials(const DevPlanBuf& pb) {
 //   16..19 persistent streaming kernel, tiles of rows of mode 0 brought in by bulk asynchronous
 //          copies through a ring of shared-memory stages (k_matvec_stream, vbk_stream.cu)
 constexpr int MV_NWIN = 16;  // variants 0..15 launched from this file
-constexpr int MV_NVAR = 20;
+constexpr int MV_NVAR = VBK_MATVEC_NVARIANTS;
 inline int mv_ept(int v) {
     static const int e[MV_NWIN] = {4, 4, 2, 2, 4, 4, 2, 1, 1, 1, 1, 1, 4, 2, 2, 4};
     return v < MV_NWIN ? e[v] : 1;
@@ -4001,7 +4001,32 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
             return rc;
         }
     }
-    const bool tune = o.autotune != 0 && !sand;
+    // a matvec variant the caller fixed for this solve: used for both operators (the Krylov
+    // operator and the FP64 residual) where it is valid for their precision, in place of the
+    // tuned choice; the model's tuned choices come back when the solve returns
+    struct MvRestore {
+        vbk_model* m;
+        int v[2];
+        bool on;
+        ~MvRestore() {
+            if (on) {
+                m->mv_variant[0] = v[0];
+                m->mv_variant[1] = v[1];
+            }
+        }
+    } mv_restore{mdl, {mdl->mv_variant[0], mdl->mv_variant[1]}, o.matvec_variant >= 0};
+    if (o.matvec_variant >= 0) {
+        const int fv = o.matvec_variant;
+        const bool ok_k = fv < MV_NVAR && mv_valid(md, fv, sizeof(cx<R>)), ok_64 = fv < MV_NVAR && mv_valid(md, fv, 16);
+        if (!ok_k && !ok_64) {
+            if (pbuf.mem) cudaFreeAsync(pbuf.mem, st);
+            vbk_set_error("matvec variant not available for this model");
+            return VBK_ERR_INVALID_ARG;
+        }
+        if (ok_k) mdl->mv_variant[sizeof(R) == 4 ? 0 : 1] = fv;
+        if (ok_64) mdl->mv_variant[1] = fv;
+    }
+    const bool tune = o.autotune != 0 && !sand && o.matvec_variant < 0;
     // FP32 COCG with a point preconditioner and a system small enough for shared memory:
     // one CTA per system (k_cocg_resident)
     bool resident = sizeof(R) == 4 && method == VBK_COCG && pspan <= 0 && !sand && resident_ok(md) && o.resident != 0;

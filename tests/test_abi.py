@@ -102,6 +102,7 @@ def test_default_options(lib):
     assert (o.method, o.precision, o.precond_span, o.restart) == (lib.VBK_GMRES, lib.VBK_MIXED, 0, 64)
     assert o.tol == 1e-8 and o.inner_tol == 1e-5 and o.check_every == 8 and o.timing == 0 and o.autotune == 1 and o.resident == 1
     assert o.inner_max_iter == 2000 and o.max_iter == 20000 and o.max_refine == 40
+    assert o.matvec_variant == -1
     o2 = lib.vbk_default_opts(method="cocg", precision="fp64", tol=1e-10)
     assert (o2.method, o2.precision, o2.tol) == (lib.VBK_COCG, lib.VBK_FP64, 1e-10)
 

@@ -239,6 +239,39 @@ def test_solve_parity(vbk, method, precision, span):
     assert rel.max() <= 1e-8, rel.max()
 
 
+@pytest.mark.parametrize("method,precision", [("cocg", "mixed"), ("gmres", "mixed"), ("cocg", "fp64")])
+@pytest.mark.parametrize("variant", list(range(20)))  # VBK_MATVEC_NVARIANTS
+def test_solve_with_every_matvec_variant(vbk, method, precision, variant):
+    """The grid-wide solve (resident = 0) with each matvec variant fixed for the Krylov operator
+    and the FP64 residual: the variants' partial sums (dot products, residual norms: one slot per
+    system and block or strip) and their system lists (converged systems retire) must serve the
+    solver; true residuals by the oracle."""
+    desc = w.ci2d_model(10)
+    # N = 2 * 10 * 80 = 1600: rows of 80 entries, so that the streaming variants' FP64 plans take
+    # shorter strips than their FP32 plans (different partial counts in one mixed solve)
+    desc["modes"][1]["n"] = 80
+    model = vbk.Model(desc)
+    eps = np.array([0.4, 1.3, 2.2, 2.9])
+    vi = [[0, 0], [1, 0]]
+    opts = vbk.vbk_default_opts(method=method, precision=precision, precond_span=0, tol=1e-10, restart=40,
+                                max_iter=20000, max_refine=200, resident=0, matvec_variant=variant)
+    try:
+        psi, stats = vbk.vbk_solve(model, eps, vi, opts)
+    except vbk.VbkError as err:
+        if err.code == 1 and "variant not available" in str(err):
+            pytest.skip("variant does not fit this model")
+        raise
+    psi = psi.cpu().numpy()
+    for e, ei in enumerate(eps):
+        for i, v in enumerate(vi):
+            E = o.total_energy(desc, ei, v)
+            for mu in range(model.n_mu):
+                st = stats[(e * len(vi) + i) * model.n_mu + mu]
+                assert st["status"] == "converged", st
+                res = o.relative_residual(desc, E, psi[e, i, mu], o.phi(desc, E, v, mu))
+                assert res <= 1e-10 * 1.05, (e, i, mu, res, st)
+
+
 def test_cross_sections_and_t_match_oracle_on_oracle_psi(vbk):
     """Readout alone: sigma and T from the oracle's own psi (Eqs. crs, crs2)."""
     desc = w.ci2d_model(8)
