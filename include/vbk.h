@@ -328,6 +328,16 @@ int vbk_kernel_timings(const vbk_model* model, int cap, const char** names, int*
  * The paper has no counterpart: this serves measurement of the operator kernels alone. */
 int vbk_set_op_timing(vbk_model* model, int on);
 
+/* Test hook for the bounded waits of the streaming matvec (variants 16..19; the paper has no
+ * counterpart).  The next launch of such a variant holds the first copies of every thread
+ * block back by `ms` milliseconds (0 .. 10000; later launches are not affected).  With a delay
+ * past the kernels' wait limit (1 s) the computing warps stop waiting instead of waiting
+ * without end: the launch completes, a device flag records it, its output is not valid, and
+ * the call that reads the flag (vbk_solve, or vbk_matvec with vbk_set_op_timing on) returns
+ * VBK_ERR_CUDA with a message.  The CUDA context stays usable.  VBK_ERR_INVALID_ARG for a delay
+ * out of range. */
+int vbk_debug_stream_delay(int ms);
+
 /* Matvec kernel variant the autotuner chose for this model in `precision` (VBK_MIXED: the FP32
  * Krylov operator, VBK_FP64: the FP64 residual), or -1 if it has not run yet. */
 int vbk_matvec_variant(const vbk_model* model, int precision);

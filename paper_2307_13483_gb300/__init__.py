@@ -116,7 +116,7 @@ EXPORTED = [
     "vbk_cross_sections", "vbk_eels", "vbk_solve_adjoint", "vbk_matvec", "vbk_precond_apply",
     "vbk_kernel_timings", "vbk_last_launch_count", "vbk_level_shift", "vbk_status_str",
     "vbk_sys_status_str", "vbk_last_error", "vbk_matvec_noalloc", "vbk_matvec_variant", "vbk_set_op_timing",
-    "vbk_level_shift_df",
+    "vbk_level_shift_df", "vbk_debug_stream_delay",
 ]
 
 
@@ -141,6 +141,7 @@ def _load():
         "vbk_kernel_timings": (C.c_int, [vp, C.c_int, C.POINTER(C.c_char_p), ip, dp]),
         "vbk_last_launch_count": (C.c_longlong, [vp]),
         "vbk_matvec_variant": (C.c_int, [vp, C.c_int]),
+        "vbk_debug_stream_delay": (C.c_int, [C.c_int]),
         "vbk_set_op_timing": (C.c_int, [vp, C.c_int]),
         "vbk_level_shift": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]),
         "vbk_level_shift_df": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp]),
@@ -379,6 +380,11 @@ def vbk_set_op_timing(model: Model, on: bool = True):
     """Per-kernel CUDA-event timings of later vbk_matvec / vbk_precond_apply calls (see
     vbk_kernel_timings); those calls then synchronise their stream."""
     _check(_lib.vbk_set_op_timing(model.handle, 1 if on else 0), "vbk_set_op_timing")
+
+
+def vbk_debug_stream_delay(ms: int) -> None:
+    """Test hook: the next streaming-matvec launch holds its first copies back by `ms` ms."""
+    _check(_lib.vbk_debug_stream_delay(int(ms)), "vbk_debug_stream_delay")
 
 
 def vbk_matvec_variant(model: Model, precision=VBK_MIXED) -> int:

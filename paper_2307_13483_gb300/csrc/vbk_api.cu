@@ -1812,6 +1812,13 @@ int vbk_kernel_timings(const vbk_model* m, int cap, const char** names, int* lau
 
 long long vbk_last_launch_count(const vbk_model* m) { return m ? m->launches : 0; }
 
+int vbk_debug_stream_delay(int ms) {
+    vbk_set_error("");
+    const int rc = vbk_debug_stream_delay_impl(ms);
+    if (rc) vbk_set_error("delay must be in 0 .. 10000 ms");
+    return rc;
+}
+
 int vbk_matvec_variant(const vbk_model* m, int precision) {
     if (!m) return -1;
     return m->mv_variant[precision == VBK_MIXED ? 0 : 1];

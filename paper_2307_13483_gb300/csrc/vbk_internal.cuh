@@ -510,6 +510,7 @@ struct StreamPlan {
     int threads = 0;
     unsigned stage_bytes = 0, win_bytes = 0;  // bytes of one stage; of which the x windows
     size_t smem = 0;                          // dynamic shared memory of a CTA
+    unsigned long long delay_ns = 0;          // test hook: the producers hold their first copies back
 };
 int vbk_stream_nconfig();
 bool vbk_stream_plan(const DevModel& md, int cfg, size_t c, StreamPlan* p);
@@ -518,6 +519,7 @@ cudaError_t vbk_stream_matvec(const DevModel& md, const StreamPlan& p, const int
                               const double2* b, double2* part, int red, bool fp32, cudaStream_t st);
 int vbk_stream_prepare(const DevModel& md, bool fp32);  // shared-memory opt-in (outside stream capture)
 unsigned vbk_stream_fault_take();
+int vbk_debug_stream_delay_impl(int ms);
 
 // Internal solve over an explicit list of systems with dense FP64 right-hand sides.
 struct SolveJob {

@@ -39,7 +39,7 @@ constexpr int ST_NPM = 16;                          // stencil points per state 
 constexpr int ST_MAXT = 640;                        // consumer threads per CTA at most (and one producer warp)
 constexpr int ST_SMALLT = 352;                      // blocks of at most this many threads: two per SM
 constexpr size_t ST_SMEM_MAX = 220 * 1024;          // dynamic shared memory of a CTA at most
-constexpr unsigned long long ST_WAIT_NS = 2000000000ull;  // a stage barrier wait gives up after 2 s
+constexpr unsigned long long ST_WAIT_NS = 1000000000ull;  // a stage barrier wait gives up after 1 s
 
 __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -116,15 +116,16 @@ __device__ __forceinline__ int st_sel(const int (&n)[MAXM], int m) {
 }
 
 // Wait for the phase of parity `par` of the barrier at `bar`; gives up after ST_WAIT_NS, records
-// that in g_vbk_stream_fault and returns (the data are then not valid; nothing hangs).
-__device__ __forceinline__ void st_wait(unsigned bar, unsigned par) {
-    if (mbar_try_wait(bar, par)) return;
+// that in g_vbk_stream_fault and returns false (the data it guards are then not valid).
+__device__ __forceinline__ bool st_wait(unsigned bar, unsigned par) {
+    if (mbar_try_wait(bar, par)) return true;
     const unsigned long long t0 = st_clock_ns();
     while (!mbar_try_wait(bar, par))
         if (st_clock_ns() - t0 > ST_WAIT_NS) {
             atomicOr(&g_vbk_stream_fault, 1u);
-            return;
+            return false;
         }
+    return true;
 }
 // barrier over the consumer warps only (named barrier 1; the producer warp is not part of it)
 __device__ __forceinline__ void st_cons_sync(int ncons) { asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory"); }
@@ -286,7 +287,19 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
                     slot[k] = 1;
                 }
             }
-            if (u > 0) st_wait(ebase + 8u * s, (unsigned)((u - 1) & 1));  // the consumers released the stage
+            if (u > 0) {
+                st_wait(ebase + 8u * s, (unsigned)((u - 1) & 1));  // the consumers released the stage
+                // and its previous copies have landed (always so, unless a consumer gave up waiting
+                // for them): the barrier's next phase then counts only the copies issued below
+                st_wait(fbase + 8u * s, (unsigned)((u - 1) & 1));
+            }
+            if (it == 0 && p.delay_ns && lane == 0) {
+                // test hook (vbk_debug_stream_delay): hold the first copies back; a delay past the
+                // wait limit makes the consumers' first wait run out.  Bounded by the delay.
+                const unsigned long long t0 = st_clock_ns();
+                while (st_clock_ns() - t0 < p.delay_ns) __nanosleep(100000);
+            }
+            __syncwarp();
             const int g0 = si * p.TR, tre = min(p.TR, nb0 - g0);
             const long long wst = (long long)g0 * Rl + p.lo;
             unsigned char* stg = sm + (size_t)s * p.stage_bytes;
@@ -365,15 +378,16 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
         const int t = blockIdx.x + it * G;
         if (t >= ntile) break;
         const int s = it % p.nst;
-        st_wait(fbase + 8u * s, (unsigned)((it / p.nst) & 1));
+        // a wait that ran out leaves the stage's record and data unset: no system is written
+        const bool landed = st_wait(fbase + 8u * s, (unsigned)((it / p.nst) & 1));
         int sy[S], slot[S], se[S];
 #pragma unroll
         for (int k = 0; k < S; ++k) {
-            sy[k] = info[s][k];
-            slot[k] = info[s][S + k];
-            se[k] = info[s][2 * S + k];
+            sy[k] = landed ? info[s][k] : -1;
+            slot[k] = landed ? info[s][S + k] : -1;
+            se[k] = landed ? info[s][2 * S + k] : -1;
         }
-        const int si = info[s][3 * S];
+        const int si = landed ? info[s][3 * S] : 0;
         const int g0 = si * p.TR, tre = min(p.TR, nb0 - g0);
         const unsigned char* stg = sm + (size_t)s * p.stage_bytes;
         C loc[S];
@@ -555,10 +569,22 @@ bool vbk_stream_plan(const DevModel& md, int cfg, size_t c, StreamPlan* out) {
     return true;
 }
 
-cudaError_t vbk_stream_matvec(const DevModel& md, const StreamPlan& p, const int* sys_e, const int* list, const int* act,
+// test hook: the next launch's producers hold their first copies back by this many milliseconds
+static int g_stream_delay_ms = 0;
+
+int vbk_debug_stream_delay_impl(int ms) {
+    if (ms < 0 || ms > 10000) return VBK_ERR_INVALID_ARG;
+    g_stream_delay_ms = ms;
+    return VBK_OK;
+}
+
+cudaError_t vbk_stream_matvec(const DevModel& md, const StreamPlan& p_in, const int* sys_e, const int* list, const int* act,
                               int nlist, const void* diag, const void* x, long long xs, void* y, long long ys,
                               const double2* b, double2* part, int red, bool fp32, cudaStream_t st) {
     if (nlist <= 0) return cudaSuccess;
+    StreamPlan p = p_in;
+    p.delay_ns = (unsigned long long)g_stream_delay_ms * 1000000ull;
+    g_stream_delay_ms = 0;  // one launch only
     const size_t c = fp32 ? 8 : 16;
     // bulk copies need 16-byte aligned sources: vector starts and the system strides
     if (((uintptr_t)x & 15) || ((uintptr_t)diag & 15) || ((xs * (long long)c) & 15)) return cudaErrorMisalignedAddress;
