@@ -403,13 +403,11 @@ __global__ void __launch_bounds__(MAXT, MINB) k_matvec_stream(DevModel md, Strea
                 const long long gi = (long long)d * Nnu + (long long)g0 * Rl + el;
                 C xi[S], acc[S];
                 st_load_sys<R, S>(wself, sysb, xi);
-                // the diagonal entry of each staged energy once per row (at most ndg of them)
-                const C dga = *reinterpret_cast<const C*>(dgs + (size_t)el * sizeof(C));
-                const C dgb = p.ndg > 1 ? *reinterpret_cast<const C*>(dgs + dbytes + (size_t)el * sizeof(C)) : dga;
 #pragma unroll
                 for (int k = 0; k < S; ++k) {
-                    C dg = slot[k] == 0 ? dga : dgb;
-                    if (slot[k] < 0) dg = se[k] >= 0 ? diag[(long long)se[k] * N + gi] : mkc<R>(0, 0);
+                    C dg;
+                    if (slot[k] >= 0) dg = *reinterpret_cast<const C*>(dgs + (size_t)slot[k] * dbytes + (size_t)el * sizeof(C));
+                    else dg = se[k] >= 0 ? diag[(long long)se[k] * N + gi] : mkc<R>(0, 0);
                     acc[k] = cmul<R>(dg, xi[k]);
                 }
                 // point q: coefficient c_q = (mode-0 factor of the row) (in-row factor of the
