@@ -3206,16 +3206,42 @@ __global__ void __launch_bounds__(TPB) k_vdots(int N, int m, Sel sel, const cx<R
 }
 
 // h[s][k] = sum over blocks of part[s][blk][k]
-__global__ void k_hreduce(int nsys, int m, const int* __restrict__ act, int j, const double2* __restrict__ part, int nb,
-                          double2* __restrict__ h) {
-    const int s = blockIdx.x;
+// h[s][k] = sum over the nb per-block partials of dot k (k = 0 .. j) of system s.  Grid:
+// (dot groups of HR_K, systems); thread (x, y) sums the partials b = y, y + HR_G, .. of dot
+// k0 + x (consecutive dots: coalesced rows of partials), two accumulators in flight, then the
+// HR_G sums of a dot are added in shared memory.
+constexpr int HR_K = 32, HR_G = 8;
+__global__ void __launch_bounds__(HR_K * HR_G) k_hreduce(int nsys, int m, const int* __restrict__ act, int j,
+                                                       const double2* __restrict__ part, int nb, double2* __restrict__ h) {
+    __shared__ double2 sh[HR_G][HR_K];
+    const int s = blockIdx.y;
     if (s >= nsys || !act[s]) return;
-    for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-        double2 t = make_double2(0.0, 0.0);
-        for (int b = 0; b < nb; ++b) {
-            const double2 v = part[((long long)s * nb + b) * (m + 1) + k];
-            t.x += v.x;
-            t.y += v.y;
+    const int k = blockIdx.x * HR_K + threadIdx.x;
+    double2 t0 = make_double2(0.0, 0.0), t1 = t0;
+    if (k <= j) {
+        const double2* pk = part + (long long)s * nb * (m + 1) + k;
+        int b = threadIdx.y;
+        for (; b + HR_G < nb; b += 2 * HR_G) {
+            const double2 v0 = pk[(long long)b * (m + 1)], v1 = pk[(long long)(b + HR_G) * (m + 1)];
+            t0.x += v0.x;
+            t0.y += v0.y;
+            t1.x += v1.x;
+            t1.y += v1.y;
+        }
+        if (b < nb) {
+            const double2 v0 = pk[(long long)b * (m + 1)];
+            t0.x += v0.x;
+            t0.y += v0.y;
+        }
+    }
+    sh[threadIdx.y][threadIdx.x] = make_double2(t0.x + t1.x, t0.y + t1.y);
+    __syncthreads();
+    if (threadIdx.y == 0 && k <= j) {
+        double2 t = sh[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < HR_G; ++q) {
+            t.x += sh[q][threadIdx.x].x;
+            t.y += sh[q][threadIdx.x].y;
         }
         h[(long long)s * (m + 1) + k] = t;
     }
@@ -3292,39 +3318,57 @@ __global__ void __launch_bounds__(TPB) k_vupdate(int N, int m, Sel sel, const cx
 }
 
 // Column j of the Hessenberg matrix, Givens rotations and the residual estimate (FP64).
-__global__ void k_givens(int nsys, int m, SysState* __restrict__ st, int* __restrict__ act,
+// Givens QR step of every active system, one warp per system (GV_W systems per block): the
+// lanes sum the norm partials and stage the new Hessenberg column h1 + h2 and the j earlier
+// rotations in shared memory; lane 0 then applies the rotations with the running entry in
+// registers (no global load inside the dependent chain) and forms the new rotation.
+constexpr int GV_W = 4;
+constexpr int GV_MAXM = 256;  // the restart length is at most 256
+__global__ void __launch_bounds__(32 * GV_W) k_givens(int nsys, int m, SysState* __restrict__ st, int* __restrict__ act,
                          const double2* __restrict__ h1, const double2* __restrict__ h2,
                          const double2* __restrict__ part_n, int nb, double2* __restrict__ H, double* __restrict__ cs,
                          double2* __restrict__ sn, double2* __restrict__ g, double* __restrict__ inv_h, int max_iter,
                          int* __restrict__ count, int* __restrict__ ilist) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * GV_W + (threadIdx.x >> 5);
     if (s >= nsys || !act[s]) return;
     SysState& S = st[s];
     const int j = S.j;
     double rr = 0.0;
-    for (int k = 0; k < nb; ++k) rr += part_n[(long long)s * nb + k].x;
-    const double hn = sqrt(rr);
-    double2* Hc = H + ((long long)s * m + j) * (m + 1);  // column j
-    for (int k = 0; k <= j; ++k) {
-        const double2 a = h1[(long long)s * (m + 1) + k], b = h2[(long long)s * (m + 1) + k];
-        Hc[k] = make_double2(a.x + b.x, a.y + b.y);
-    }
-    Hc[j + 1] = make_double2(hn, 0.0);
-    // apply previous rotations
+    __shared__ double scs[GV_W][GV_MAXM];
+    __shared__ double2 ssn[GV_W][GV_MAXM], scol[GV_W][GV_MAXM + 1];
+    const int wv = threadIdx.x >> 5;
+    for (int k = lane; k < nb; k += 32) rr += part_n[(long long)s * nb + k].x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
     double* csv = cs + (long long)s * m;
     double2* snv = sn + (long long)s * m;
+    const double2* h1s = h1 + (long long)s * (m + 1);
+    const double2* h2s = h2 + (long long)s * (m + 1);
+    for (int k = lane; k < j; k += 32) {
+        scs[wv][k] = csv[k];
+        ssn[wv][k] = snv[k];
+    }
+    for (int k = lane; k <= j; k += 32) scol[wv][k] = make_double2(h1s[k].x + h2s[k].x, h1s[k].y + h2s[k].y);
+    __syncwarp();
+    if (lane != 0) return;
+    const double hn = sqrt(rr);
+    double2* Hc = H + ((long long)s * m + j) * (m + 1);  // column j
+    // apply previous rotations to (h1 + h2)[0 .. j], hn; `cur` is the entry k of the column as
+    // rotated by rotations 0 .. k-1
     double2* gv = g + (long long)s * (m + 1);
+    double2 cur = scol[wv][0];
     for (int k = 0; k < j; ++k) {
-        const double c = csv[k];
-        const double2 sk = snv[k];
-        const double2 a = Hc[k], b = Hc[k + 1];
+        const double c = scs[wv][k];
+        const double2 sk = ssn[wv][k];
+        const double2 a = cur, b = scol[wv][k + 1];
         const double2 t1 = cmul<double>(sk, b);
         const double2 t2 = cconjmul<double>(sk, a);  // conj(s) a
         Hc[k] = make_double2(c * a.x + t1.x, c * a.y + t1.y);
-        Hc[k + 1] = make_double2(c * b.x - t2.x, c * b.y - t2.y);
+        cur = make_double2(c * b.x - t2.x, c * b.y - t2.y);
     }
     // new rotation zeroing H[j+1][j]
-    const double2 a = Hc[j], b = Hc[j + 1];
+    const double2 a = cur, b = make_double2(hn, 0.0);
     const double aa = sqrt(cabs2<double>(a)), bb = sqrt(cabs2<double>(b));
     double c;
     double2 sg;
@@ -4617,17 +4661,18 @@ int Solver<R, M>::run(vbk_model* mdl, const SolveJob& job, const vbk_opts& o, vb
                     }
                     rn.go("gmres_dots", k_vdots<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const cx<R>*)w, partA);
-                    rn.go("gmres_hreduce", k_hreduce, dim3(nsys), dim3(64), nsys, mres, (const int*)inner, j,
-                          (const double2*)partA, nb_v, h1);
+                    rn.go("gmres_hreduce", k_hreduce, dim3(cdiv_u(j + 1, HR_K), nsys), dim3(HR_K, HR_G), nsys, mres,
+                          (const int*)inner, j, (const double2*)partA, nb_v, h1);
                     rn.go("gmres_update_dots", k_vupdate<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const double2*)h1, w, 0, partA);
-                    rn.go("gmres_hreduce", k_hreduce, dim3(nsys), dim3(64), nsys, mres, (const int*)inner, j,
-                          (const double2*)partA, nb_v, h2);
+                    rn.go("gmres_hreduce", k_hreduce, dim3(cdiv_u(j + 1, HR_K), nsys), dim3(HR_K, HR_G), nsys, mres,
+                          (const int*)inner, j, (const double2*)partA, nb_v, h2);
                     rn.go("gmres_update_norm", k_vupdate<R>, dim3(nb_v, n_in), dim3(TPB), N, mres, sc, (const cx<R>*)V, j,
                           (const double2*)h2, w, 1, partB);
                     cudaMemsetAsync(cnt, 0, sizeof(int), st);
                     cudaMemsetAsync(ilist, 0xff, nsys * sizeof(int), st);
-                    rn.go("gmres_givens", k_givens, dim3(gs), dim3(128), nsys, mres, sst, inner, (const double2*)h1,
+                    rn.go("gmres_givens", k_givens, dim3(cdiv_u(nsys, GV_W)), dim3(32 * GV_W), nsys, mres, sst, inner,
+                          (const double2*)h1,
                           (const double2*)h2, (const double2*)partB, nb_v, H, cs, sn, g, invh, o.max_iter, cnt, ilist);
                     if (j + 1 < mres)
                         rn.go("gmres_scale", k_vscale<R>, dim3(nb_e, n_in), dim3(TPB), N, mres, sc, (const double*)invh,
