@@ -111,3 +111,23 @@ def test_bench_level_helpers_match_the_oracle():
             E = eps + bench.level_energy(desc, vi)
             assert abs(E - o.total_energy(desc, eps, vi)) < 1e-12
             assert bench.open_final_levels(desc, E) == [list(map(int, v)) for v in o.open_levels(desc, E)]
+
+
+def test_bench_stencil_point_count_matches_the_oracle_operator():
+    """The FP64 roofline of the bench counts 4 flops per stencil point; its point count equals the
+    off-diagonal nonzeros of an interior row of the oracle's A (CI2D terms have distinct offsets)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import workloads
+    from oracle import vibronic as o
+
+    desc = workloads.ci2d_model(12)
+    A = o.a_matrix(desc, 3.0).tocsr()
+    n_g, n_u = (m["n"] for m in desc["modes"])
+    counts = []
+    for d in range(desc["n_states"]):
+        row = d * n_g * n_u + (n_g // 2) * n_u + n_u // 2  # an interior element of state d
+        counts.append(A.indptr[row + 1] - A.indptr[row] - 1)
+    assert max(counts) == bench.stencil_points(desc) == 8
